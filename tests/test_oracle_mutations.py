@@ -1,0 +1,129 @@
+"""Planted mistakes in the oracle must be caught by its pins.
+
+Each case swaps one oracle function for a subtly wrong copy (a dropped
+term, a wrong sign, a transposed operand, a wrong index order) and runs the
+pins that should notice.  The mistake lives only in this CPU process.
+"""
+
+import numpy as np
+import pytest
+import scipy.linalg as la
+
+import oracle.ams_oracle as O
+import tests.test_oracle_pins as P
+
+
+def _expect_some_pin_fails(pins):
+    failed = []
+    for pin in pins:
+        try:
+            pin()
+        except (AssertionError, ValueError, la.LinAlgError, np.linalg.LinAlgError):
+            failed.append(pin.__name__)
+    assert failed, "no pin caught the planted mistake"
+
+
+def _patch(monkeypatch, name, fn):
+    monkeypatch.setattr(O, name, fn)
+    if hasattr(P, name):
+        monkeypatch.setattr(P, name, fn)
+
+
+def test_mutation_hat_diagonal_kept(monkeypatch):
+    """Forgetting to replace the diagonal (\\hat A_i = A_i)."""
+    orig = O.local_matrices
+
+    def bad(A, dofs):
+        Ai, Ahat, s = orig(A, dofs)
+        return Ai, Ai.copy(), np.diag(Ai).copy()
+
+    _patch(monkeypatch, "local_matrices", bad)
+    _expect_some_pin_fails([P.test_first_mode_is_constant,
+                            lambda: P.test_path_subdomain_closed_form(9)])
+
+
+def test_mutation_weight_from_a_not_ahat(monkeypatch):
+    """S_i taken from diag(A_i) instead of diag(\\hat A_i)."""
+    orig = O.local_matrices
+
+    def bad(A, dofs):
+        Ai, Ahat, s = orig(A, dofs)
+        return Ai, Ahat, np.diag(Ai).copy()
+
+    _patch(monkeypatch, "local_matrices", bad)
+    _expect_some_pin_fails([lambda: P.test_path_subdomain_closed_form(9),
+                            P.test_first_mode_is_constant])
+
+
+def test_mutation_largest_instead_of_smallest_modes(monkeypatch):
+    orig = O.local_eigenpairs
+
+    def bad(Ahat, s, m, tie_rtol=1e-8, all_pairs=False):
+        lam, V = la.eigh(Ahat, np.diag(s))
+        mi = min(m, Ahat.shape[0])
+        return lam[::-1], V[:, ::-1][:, :mi].copy(), mi
+
+    _patch(monkeypatch, "local_eigenpairs", bad)
+    _expect_some_pin_fails([P.test_first_mode_is_constant,
+                            P.test_theorem2_local_approximation_bound,
+                            P.test_iterations_do_not_grow_with_more_modes])
+
+
+def test_mutation_descending_order_in_subdomain(monkeypatch):
+    orig = O.index_maps
+
+    def bad(part, nparts):
+        perm, iperm, sub_ptr = orig(part, nparts)
+        perm = perm.copy()
+        for i in range(nparts):
+            perm[sub_ptr[i]:sub_ptr[i + 1]] = perm[sub_ptr[i]:sub_ptr[i + 1]][::-1]
+        iperm = np.empty_like(perm)
+        iperm[perm] = np.arange(len(perm))
+        return perm, iperm, sub_ptr
+
+    _patch(monkeypatch, "index_maps", bad)
+    _expect_some_pin_fails([P.test_index_maps_brute_force])
+
+
+def test_mutation_coarse_term_dropped_in_apply(monkeypatch):
+    monkeypatch.setattr(O.OracleAMS, "apply", lambda self, r: self.local_part(r))
+    _expect_some_pin_fails([P.test_full_coarse_space_reproduces_inverse,
+                            P.test_iterations_do_not_grow_with_more_modes])
+
+
+def test_mutation_coarse_uses_transposed_restriction(monkeypatch):
+    def bad(self, r):
+        if self.Nc == 0:
+            return np.zeros_like(r)
+        rc = (self.R0T.T @ r)[::-1]
+        ec = la.cho_solve(self.A0_chol, rc)
+        return self.R0T @ ec
+
+    monkeypatch.setattr(O.OracleAMS, "coarse_part", bad)
+    _expect_some_pin_fails([P.test_full_coarse_space_reproduces_inverse,
+                            P.test_preconditioner_symmetric_positive_definite])
+
+
+def test_mutation_wrong_beta(monkeypatch):
+    orig = O.pcg
+
+    def bad(A, f, Minv, rtol=1e-8, maxit=10000, flexible=False):
+        def Mbad(r):
+            return Minv(r)
+        res = orig(A, f, Mbad, rtol, maxit, flexible)
+        res.betas = [b * 1.01 for b in res.betas]
+        return res
+
+    _patch(monkeypatch, "pcg", bad)
+    _expect_some_pin_fails([P.test_lanczos_ritz_values_match_dense_spectrum])
+
+
+def test_mutation_adjoint_sign(monkeypatch):
+    orig = O.adjoint_gradient
+
+    def bad(A, u, g, Minv, rtol=1e-8, maxit=10000):
+        lam, dvals, res = orig(A, u, g, Minv, rtol, maxit)
+        return lam, -dvals, res
+
+    _patch(monkeypatch, "adjoint_gradient", bad)
+    _expect_some_pin_fails([P.test_adjoint_matches_dense_and_closed_form_and_fd])
