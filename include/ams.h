@@ -1,0 +1,268 @@
+/*
+ * ams.h — C ABI of the GB300 (sm_103a) solve-phase library for the two-grid
+ * algebraic multiscale (AMS) preconditioner of arXiv 2606.04864
+ * ("An algebraic multiscale preconditioner for large sparse SPD matrices").
+ *
+ * The library solves A u = f (Eq. matrix-form, Section 1) for a sparse SPD
+ * matrix A by preconditioned conjugate gradients on one GPU.  The
+ * preconditioner is the paper's two-level method (Section 3):
+ *
+ *   M^{-1} = sum_i R_i^T A_i^{-1} R_i  +  R_0^T A_0^{-1} R_0
+ *
+ * with non-overlapping subdomains Omega_i given by a partition vector
+ * (Section 3.1), A_i = R_i A R_i^T (Section 3.2), R_0^T the zero-extended
+ * eigenvectors of the m smallest eigenvalues of the local generalized
+ * eigenproblems  \hat A_i psi = lambda S_i psi  (Eq. algebraic-eigenproblem),
+ * and A_0 = R_0 A R_0^T (Section 3.1).  The fine-level sum over local solves
+ * is this library's reading of the fine-level component the paper's
+ * Theorem 2 assumes but does not spell out.
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an ams_status; none aborts, traps or exits.  On
+ *    error the thread-local message from ams_last_error() says why.
+ *  - Ownership: the caller owns every array it passes in or out; the library
+ *    copies what it needs during ams_setup*, so the caller may free its
+ *    inputs as soon as the call returns.  The handle owns all device memory
+ *    it allocates and releases it in ams_destroy.
+ *  - Pointer kind: when ams_options.device_ptrs is 0 every array argument is
+ *    a host pointer (the library copies through its own staging buffers);
+ *    when 1 every array argument is a device pointer on the current device.
+ *  - Streams: all device work is enqueued on the stream given to ams_setup*
+ *    (NULL = legacy default stream).  Calls return after that work is done.
+ *  - A handle is not thread-safe: do not call into one handle from two
+ *    threads at once.
+ *  - Vectors with several right-hand sides are n x nrhs, column-major
+ *    (right-hand side k starts at element k*n), in the caller's dof order.
+ *  - Integer and index outputs are exact; floating-point results depend on
+ *    the precision mode (see ams_options.precision).
+ */
+#ifndef AMS_H
+#define AMS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ams_handle_s* ams_handle;
+
+typedef enum {
+    AMS_OK = 0,
+    AMS_ERR_INVALID_ARG = 1,     /* bad size, pointer, CSR, partition or option */
+    AMS_ERR_NOT_SPD = 2,         /* non-positive pivot in a local or coarse Cholesky */
+    AMS_ERR_BREAKDOWN = 3,       /* p^T A p <= 0 or a non-finite scalar in CG */
+    AMS_ERR_NOT_CONVERGED = 4,   /* maxit reached; outputs hold the last iterate */
+    AMS_ERR_DEVICE_TIMEOUT = 5,  /* a bounded device-side wait ran out */
+    AMS_ERR_CUDA = 6,            /* a CUDA runtime or cuSOLVER call failed */
+    AMS_ERR_OOM = 7              /* device allocation failed */
+} ams_status;
+
+enum {
+    AMS_PREC_FP64 = 0,           /* preconditioner in FP64 (reference path) */
+    AMS_PREC_FP32 = 1,           /* local factors, basis and coarse inverse in FP32 */
+    AMS_PREC_FP32_BF16 = 2       /* as FP32, basis blocks stored BF16 */
+};
+
+enum {
+    AMS_CG_AUTO = -1,            /* PCG for FP64, flexible CG otherwise */
+    AMS_CG_PCG = 0,
+    AMS_CG_FCG = 1               /* beta_k = z_{k+1}^T (r_{k+1}-r_k) / (z_k^T r_k) */
+};
+
+typedef struct {
+    int32_t precision;           /* AMS_PREC_*; default AMS_PREC_FP32_BF16 */
+    int32_t cg_variant;          /* AMS_CG_*; default AMS_CG_AUTO */
+    int32_t maxit;               /* outer iteration cap; default 10000 */
+    int32_t device_ptrs;         /* 0 host pointers (default), 1 device pointers */
+    int32_t autotune;            /* 1: time SpMV launch shapes during setup (default 1) */
+    int32_t coarse;              /* 1: two-level (default); 0: local solves only */
+    double eig_shift;            /* shift sigma of the local eigensolver; 0 = default 1e-2 */
+    int32_t eig_maxit;           /* local eigensolver iteration cap; 0 = default 300 */
+    double eig_tol;              /* local eigenpair residual target; 0 = default 1e-13 */
+    int64_t spin_budget_cycles;  /* budget of any bounded device wait; 0 = default */
+} ams_options;
+
+/* Fill *opt with the defaults listed above. */
+void ams_options_default(ams_options* opt);
+
+/*
+ * ams_setup — build the preconditioner for one SPD matrix (Sections 3.1-3.2).
+ *
+ *  n        number of dofs (rows), 1 <= n < 2^31
+ *  rowptr   CSR row pointer, n+1 entries, rowptr[0] = 0
+ *  colind   CSR column indices, rowptr[n] entries, strictly ascending per row
+ *  vals     CSR values (FP64); A must be symmetric (pattern and values equal
+ *           to the last bit) with a positive diagonal
+ *  part     subdomain id of each dof, in [0, nparts); no subdomain may be empty
+ *  nparts   number of subdomains N
+ *  m        eigenvectors per subdomain; the library keeps m_i = min(m, n_i)
+ *           and grows m_i while lambda_{m_i+1} equals lambda_{m_i} to a
+ *           relative 1e-8 (a cluster split by the cut); m = 0 gives
+ *           block-Jacobi PCG
+ *  opt      options (NULL = defaults)
+ *  stream   cudaStream_t as void* (NULL = default stream)
+ *  out      receives the handle
+ *
+ * Errors: AMS_ERR_INVALID_ARG (CSR unsorted, out of range or unsymmetric,
+ * part out of range, empty subdomain, band of a subdomain too wide for the
+ * shared-memory staging), AMS_ERR_NOT_SPD (non-positive pivot), AMS_ERR_OOM,
+ * AMS_ERR_CUDA.
+ */
+ams_status ams_setup(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                     const double* vals, const int32_t* part, int32_t nparts,
+                     int32_t m, const ams_options* opt, void* stream,
+                     ams_handle* out);
+
+/* One independent system of a batch (same meaning as ams_setup's arguments). */
+typedef struct {
+    int64_t n;
+    const int64_t* rowptr;
+    const int32_t* colind;
+    const double* vals;
+    const int32_t* part;
+    int32_t nparts;
+    int32_t m;
+} ams_system_desc;
+
+/*
+ * ams_setup_batched — one handle over nsys independent systems of uneven
+ * size, solved together (one launch sequence per iteration covers every
+ * system and right-hand side; each system converges on its own).
+ * Vectors passed to ams_solve on such a handle are the systems' n_s x nrhs
+ * column-major blocks laid end to end in system order; iters/relres
+ * have nsys*nrhs entries (system-major).
+ */
+ams_status ams_setup_batched(int32_t nsys, const ams_system_desc* systems,
+                             const ams_options* opt, void* stream,
+                             ams_handle* out);
+
+/*
+ * ams_solve — preconditioned CG (flexible CG per the handle's options) from
+ * u_0 = 0 for nrhs right-hand sides at once.  Each right-hand side stops at
+ * the first k with ||r_k||_2 <= rtol ||f||_2 on the recurrence residual.
+ *
+ *  f        n x nrhs right-hand sides (read only)
+ *  nrhs     1 <= nrhs <= 32
+ *  rtol     relative residual target, > 0
+ *  u        n x nrhs solution (written)
+ *  iters    nrhs (batched: nsys*nrhs) iteration counts, may be NULL (host)
+ *  relres   same shape, final recurrence residual / ||f||, may be NULL (host)
+ *
+ * iters and relres are always host pointers.  Returns AMS_ERR_NOT_CONVERGED
+ * when maxit is reached (u, iters, relres hold the last iterate) and
+ * AMS_ERR_BREAKDOWN when p^T A p <= 0 or a scalar is not finite.
+ */
+ams_status ams_solve(ams_handle h, const double* f, int32_t nrhs, double rtol,
+                     double* u, int32_t* iters, double* relres);
+
+/*
+ * ams_solve_adjoint — backward pass of u = A^{-1} f for a loss L(u).
+ * Solves A lambda = g with the same preconditioner (A is symmetric), then
+ * forms the sampled outer product on A's pattern:
+ *
+ *   dvals[e] = - sum_k lambda_k[row_e] * u_k[col_e]     (dL/dA, CSR order)
+ *   lambda   = dL/df
+ *
+ *  g        dL/du, n x nrhs
+ *  u        the forward solution, n x nrhs
+ *  lambda   n x nrhs output
+ *  dvals    nnz output in the caller's CSR entry order, may be NULL
+ *  iters    nrhs host iteration counts, may be NULL
+ *
+ * Batched handles are not supported here (AMS_ERR_INVALID_ARG).
+ */
+ams_status ams_solve_adjoint(ams_handle h, const double* g, int32_t nrhs,
+                             double rtol, const double* u, double* lambda,
+                             double* dvals, int32_t* iters);
+
+/* Release every resource of the handle.  NULL is accepted. */
+ams_status ams_destroy(ams_handle h);
+
+/* Static description of a status code. */
+const char* ams_status_string(ams_status s);
+
+/* Thread-local message describing the last error (empty if none). */
+const char* ams_last_error(void);
+
+/* ------------------------------------------------------------------ */
+/* Inspection entry points (used by tests and benchmarks).             */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+    int64_t n;                   /* total dofs (batched: sum over systems) */
+    int64_t nnz;
+    int32_t nparts;              /* total subdomains */
+    int32_t nsys;
+    int64_t ncoarse;             /* coarse dimension N_c = sum_i m_i */
+    int32_t max_band_tiles;      /* widest local band, in 32-row tiles */
+    int32_t precision;
+    int32_t cg_variant;
+    double setup_seconds;        /* wall time of ams_setup* */
+    double eig_seconds;          /* of which: local eigensolves */
+    double coarse_seconds;       /* of which: Galerkin product + coarse factor */
+    int32_t eig_iterations;      /* subspace iterations the eigensolver used */
+    double eig_max_residual;     /* largest ||\hat A psi - lambda S psi||_{S^-1} kept */
+    int64_t local_factor_bytes;  /* bytes of the stored local factors */
+    int64_t coarse_inverse_bytes;/* bytes of the stored coarse inverse blocks */
+    int64_t basis_bytes;         /* bytes of the stored basis blocks */
+    int32_t spmv_variant;        /* launch shape picked for the SpMV */
+    int64_t kernel_launches;     /* CUDA kernels this handle has launched so far */
+} ams_info;
+
+ams_status ams_get_info(ams_handle h, ams_info* info);
+
+/*
+ * Index maps (Section 3.1): perm[k] = global dof at position k of the
+ * subdomain-major order (ascending global index inside each subdomain),
+ * sub_ptr[i]..sub_ptr[i+1] = positions of subdomain i.  Host outputs of
+ * n and nparts+1 entries.  Single-system handles only.
+ */
+ams_status ams_get_index_maps(ams_handle h, int64_t* perm, int64_t* sub_ptr);
+
+/*
+ * The coarse basis (Section 3.2): m_i (nparts entries), the kept local
+ * eigenvalues (sum m_i entries, subdomain-major, ascending), and psi, the
+ * FP64 basis blocks: for each subdomain in order an n_i x m_i column-major
+ * block in the subdomain's local order.  Host outputs; NULL skips an output.
+ * The blocks are the FP64 eigenvectors even when a lower-precision copy is
+ * used in the solve.
+ */
+ams_status ams_get_coarse_basis(ams_handle h, int32_t* m_i, double* lambda,
+                                double* psi);
+
+/*
+ * The Galerkin coarse matrix A_0 = R_0 A R_0^T (Section 3.1) as a dense
+ * N_c x N_c row-major host array in the paper's order (subdomain-major,
+ * mode-minor).  For precision modes with a BF16 basis it is the product of
+ * the rounded basis.  Single-system handles only.
+ */
+ams_status ams_get_coarse_matrix(ams_handle h, double* A0);
+
+/*
+ * One application z = M^{-1} r of the two-level preconditioner (n x nrhs,
+ * caller's order), in the handle's precision.
+ */
+ams_status ams_apply_preconditioner(ams_handle h, const double* r,
+                                    int32_t nrhs, double* z);
+
+/* y = A x with the handle's stored matrix (n x nrhs, caller's order). */
+ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y);
+
+/*
+ * Time one kernel of the solve on the handle's current solve state (after
+ * an ams_solve with nrhs right-hand sides): `reps` back-to-back launches on
+ * the handle's stream between two CUDA events.  which: 0 SpMV+dot,
+ * 1 CG update, 2 local solves + restriction, 3 coarse forward, 4 coarse
+ * backward, 5 prolongation + dots, 6 direction update.  Outputs the mean
+ * launch time (ms) and the kernel's algorithmic bytes per launch (each
+ * operand read once, each output written once).
+ */
+ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps,
+                           double* avg_ms, double* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMS_H */

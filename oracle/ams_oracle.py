@@ -168,6 +168,21 @@ def coarse_matrix(A: sp.csr_matrix, R0T: sp.csr_matrix) -> np.ndarray:
     return np.asarray((R0T.T @ (A @ R0T)).todense())
 
 
+def round_basis(Psi: np.ndarray, mode: Optional[str]) -> np.ndarray:
+    """Basis entries rounded to a storage precision (round to nearest, ties
+    to even).  Reading for the reduced-precision preconditioner: the coarse
+    matrix is formed in FP64 from the rounded basis, so the coarse correction
+    stays the exact Galerkin projection onto the stored space."""
+    if mode is None:
+        return Psi
+    if mode == "fp32":
+        return Psi.astype(np.float32).astype(np.float64)
+    if mode == "bf16":
+        m, e = np.frexp(Psi)                  # Psi = m * 2^e, 0.5 <= |m| < 1
+        return np.ldexp(np.rint(m * 256.0), e - 8)
+    raise ValueError(mode)
+
+
 # --------------------------------------------------------------------------
 # the preconditioner and the Krylov solve
 # --------------------------------------------------------------------------
@@ -184,6 +199,7 @@ class OracleAMS:
     m: int
     coarse: bool = True
     tie_rtol: float = 1e-8
+    basis_round: Optional[str] = None     # None, "fp32" or "bf16"
 
     def __post_init__(self):
         A = self.A
@@ -201,7 +217,7 @@ class OracleAMS:
             else:
                 lam, Psi, mi = np.zeros(0), np.zeros((len(dofs), 0)), 0
             self.lams.append(lam)
-            self.Psis.append(Psi)
+            self.Psis.append(round_basis(Psi, self.basis_round))
             self.m_i.append(mi)
         self.R0T = coarse_basis(n, self.sub_dofs, self.Psis)
         self.Nc = self.R0T.shape[1]

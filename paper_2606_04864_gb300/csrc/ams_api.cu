@@ -1,0 +1,1407 @@
+// C ABI of the AMS solve library: handle, setup orchestration, PCG driver,
+// adjoint and inspection entry points.  See include/ams.h for the contract.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include "ams_internal.h"
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace ams {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+static int pow2ceil(int v) {
+    int p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+static int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+#define AMS_TRY(expr)                          \
+    do {                                       \
+        ams_status _s = (expr);                \
+        if (_s != AMS_OK) return _s;           \
+    } while (0)
+
+#define AMS_SOLVER_TRY(expr)                                                          \
+    do {                                                                              \
+        cusolverStatus_t _c = (expr);                                                 \
+        if (_c != CUSOLVER_STATUS_SUCCESS) {                                          \
+            set_error(std::string(#expr) + ": cuSOLVER status " + std::to_string((int)_c)); \
+            return AMS_ERR_CUDA;                                                      \
+        }                                                                             \
+    } while (0)
+
+// device allocation owned by a handle
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct RedCache {
+    int ld = 0;
+    int64_t nblk = 0;
+    int ngrp = 0;
+    int32_t *blk_seg = nullptr, *seg_blk0 = nullptr, *seg_nblk = nullptr, *seg_grp0 = nullptr;
+    double *part1 = nullptr, *part2 = nullptr;
+    int32_t *cnt1 = nullptr, *cnt2 = nullptr, *cnt3 = nullptr;
+};
+
+struct SystemHost {
+    int64_t n = 0, nnz = 0;
+    int64_t caller0 = 0;       // offset of this system in caller vectors
+    int64_t row0 = 0;          // first internal row
+    int64_t npad = 0;          // padded internal rows
+    int32_t sub0 = 0, nparts = 0, m = 0;
+    int64_t coff0 = 0, nc = 0; // coarse range (global coarse index)
+    std::vector<int64_t> perm, sub_ptr;
+    std::vector<NDNode> nodes;
+    std::vector<double> A0_nd;  // dense A_0 in ND order (small systems only)
+    std::vector<int64_t> nd_pos_of_sub;  // coarse position (relative) of mode 0 of each subdomain
+};
+
+}  // namespace ams
+
+using namespace ams;
+
+struct ams_handle_s {
+    ams_options opt{};
+    cudaStream_t stream = nullptr;
+    int prec = AMS_PREC_FP32_BF16;
+    int flexible = 1;
+    int nsys = 0;
+    std::vector<SystemHost> sys;
+    int64_t n_total = 0, n_pad = 0, nnz_total = 0;
+    int32_t N = 0;
+    int64_t Nc = 0;
+    int cmax = 1, mmax = 0;
+    std::vector<SubInfo> h_subs;
+    std::vector<double> h_lam;          // kept eigenvalues, subdomain-major
+    std::vector<DevBuf> bufs;
+    // device data
+    SubInfo* d_subs = nullptr;
+    int64_t* d_int_row = nullptr;
+    int32_t* d_sub_of_row = nullptr;
+    int64_t *d_sell_ptr = nullptr;
+    int32_t* d_sell_col = nullptr;
+    double* d_sell_val = nullptr;
+    int64_t* d_crowptr = nullptr;       // caller CSR (single system) for dL/dA
+    int32_t* d_ccolind = nullptr;
+    void* d_fac = nullptr;
+    int64_t fac_elems = 0;
+    double* d_psi64 = nullptr;
+    void* d_psi = nullptr;              // basis in the solve precision
+    int64_t psi_elems = 0;
+    CoarseItem *d_fwd = nullptr, *d_bwd = nullptr;
+    int nfwd = 0, nbwd = 0;
+    void *d_Rmat = nullptr, *d_Qmat = nullptr;
+    int64_t R_elems = 0, Q_elems = 0;
+    int32_t* d_rng = nullptr;
+    void* d_partial = nullptr;
+    int32_t* d_cnt = nullptr;
+    // solve work space (sized for ld_alloc)
+    int ld_alloc = 0, ld_last = 0;
+    double *d_x = nullptr, *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_z = nullptr;
+    void *d_zf = nullptr, *d_rc = nullptr, *d_yc = nullptr, *d_ec = nullptr;
+    double *d_stage_in = nullptr, *d_stage_out = nullptr, *d_stage_aux = nullptr;
+    double* d_stage_dvals = nullptr;
+    CgScalars* d_sc = nullptr;
+    SolveState* d_st = nullptr;
+    std::map<int, RedCache> red;
+    ams_info info{};
+    int64_t launches = 0;               // kernels launched by solve-time entry points
+
+    size_t tf_bytes() const { return prec == AMS_PREC_FP64 ? 8 : 4; }
+    size_t tp_bytes() const { return prec == AMS_PREC_FP64 ? 8 : (prec == AMS_PREC_FP32 ? 4 : 2); }
+
+    ams_status alloc(void** p, size_t bytes) {
+        *p = nullptr;
+        if (bytes == 0) bytes = 16;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+            return AMS_ERR_OOM;
+        }
+        bufs.push_back({*p, bytes});
+        return AMS_OK;
+    }
+    template <typename T>
+    ams_status alloc_t(T** p, size_t count) {
+        return alloc((void**)p, count * sizeof(T));
+    }
+    void release(void* p) {
+        for (auto& b : bufs)
+            if (b.p == p && p) {
+                cudaFree(p);
+                b.p = nullptr;
+            }
+    }
+    ~ams_handle_s() {
+        for (auto& b : bufs)
+            if (b.p) cudaFree(b.p);
+    }
+};
+
+namespace ams {
+
+template <typename T>
+static ams_status upload(ams_handle h, T** dst, const std::vector<T>& v) {
+    AMS_TRY(h->alloc_t(dst, v.size()));
+    if (!v.empty())
+        AMS_CUDA_TRY(cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+    return AMS_OK;
+}
+
+static double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------------------
+// reduction layout for a given ld
+// ---------------------------------------------------------------------------
+static ams_status get_red(ams_handle h, int ld, RedCache** out) {
+    auto it = h->red.find(ld);
+    if (it != h->red.end()) {
+        *out = &it->second;
+        return AMS_OK;
+    }
+    RedCache rc;
+    rc.ld = ld;
+    rc.nblk = h->n_pad * ld / kRedElems;
+    std::vector<int32_t> blk_seg(rc.nblk), seg_blk0(h->nsys), seg_nblk(h->nsys), seg_grp0(h->nsys);
+    int ngrp = 0;
+    for (int s = 0; s < h->nsys; ++s) {
+        const int64_t b0 = h->sys[s].row0 * ld / kRedElems;
+        const int64_t nb = h->sys[s].npad * ld / kRedElems;
+        seg_blk0[s] = (int32_t)b0;
+        seg_nblk[s] = (int32_t)nb;
+        seg_grp0[s] = ngrp;
+        ngrp += (int)((nb + kRedGroup - 1) / kRedGroup);
+        for (int64_t b = b0; b < b0 + nb; ++b) blk_seg[b] = s;
+    }
+    rc.ngrp = ngrp;
+    AMS_TRY(upload(h, &rc.blk_seg, blk_seg));
+    AMS_TRY(upload(h, &rc.seg_blk0, seg_blk0));
+    AMS_TRY(upload(h, &rc.seg_nblk, seg_nblk));
+    AMS_TRY(upload(h, &rc.seg_grp0, seg_grp0));
+    AMS_TRY(h->alloc_t(&rc.part1, (size_t)rc.nblk * 2 * ld));
+    AMS_TRY(h->alloc_t(&rc.part2, (size_t)ngrp * 2 * ld));
+    AMS_TRY(h->alloc_t(&rc.cnt1, (size_t)ngrp));
+    AMS_TRY(h->alloc_t(&rc.cnt2, (size_t)h->nsys));
+    AMS_TRY(h->alloc_t(&rc.cnt3, 1));
+    AMS_CUDA_TRY(cudaMemsetAsync(rc.cnt1, 0, sizeof(int32_t) * ngrp, h->stream));
+    AMS_CUDA_TRY(cudaMemsetAsync(rc.cnt2, 0, sizeof(int32_t) * h->nsys, h->stream));
+    AMS_CUDA_TRY(cudaMemsetAsync(rc.cnt3, 0, sizeof(int32_t), h->stream));
+    h->red[ld] = rc;
+    *out = &h->red[ld];
+    return AMS_OK;
+}
+
+static LaunchCtx make_ctx(ams_handle h, const RedCache& rc) {
+    LaunchCtx L;
+    L.stream = h->stream;
+    L.ld = rc.ld;
+    L.nblk = rc.nblk;
+    L.nseg = h->nsys;
+    L.red.blk_seg = rc.blk_seg;
+    L.red.seg_blk0 = rc.seg_blk0;
+    L.red.seg_nblk = rc.seg_nblk;
+    L.red.seg_grp0 = rc.seg_grp0;
+    L.red.part1 = rc.part1;
+    L.red.part2 = rc.part2;
+    L.red.cnt1 = rc.cnt1;
+    L.red.cnt2 = rc.cnt2;
+    L.red.cnt3 = rc.cnt3;
+    L.sc = h->d_sc;
+    L.st = h->d_st;
+    L.sell_ptr = h->d_sell_ptr;
+    L.sell_col = h->d_sell_col;
+    L.sell_val = h->d_sell_val;
+    L.sub_of_row = h->d_sub_of_row;
+    L.subs = h->d_subs;
+    return L;
+}
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+struct SysInput {
+    HostCSR A;
+    std::vector<int32_t> part;
+    int32_t nparts;
+    int32_t m;
+};
+
+static ams_status read_inputs(const ams_system_desc& d, int device_ptrs, SysInput& in) {
+    if (d.n <= 0 || !d.rowptr || !d.colind || !d.vals || !d.part) {
+        set_error("null pointer or non-positive n");
+        return AMS_ERR_INVALID_ARG;
+    }
+    if (d.m < 0 || d.m > kMaxM) {
+        set_error("m must be in [0, " + std::to_string(kMaxM) + "]");
+        return AMS_ERR_INVALID_ARG;
+    }
+    in.A.n = d.n;
+    in.A.rowptr.resize(d.n + 1);
+    in.part.resize(d.n);
+    const cudaMemcpyKind kind = device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    AMS_CUDA_TRY(cudaMemcpy(in.A.rowptr.data(), d.rowptr, sizeof(int64_t) * (d.n + 1), kind));
+    const int64_t nnz = in.A.rowptr[d.n];
+    if (nnz < d.n || nnz > (int64_t(1) << 40)) {
+        set_error("implausible nnz (rowptr[n])");
+        return AMS_ERR_INVALID_ARG;
+    }
+    in.A.colind.resize(nnz);
+    in.A.vals.resize(nnz);
+    AMS_CUDA_TRY(cudaMemcpy(in.A.colind.data(), d.colind, sizeof(int32_t) * nnz, kind));
+    AMS_CUDA_TRY(cudaMemcpy(in.A.vals.data(), d.vals, sizeof(double) * nnz, kind));
+    AMS_CUDA_TRY(cudaMemcpy(in.part.data(), d.part, sizeof(int32_t) * d.n, kind));
+    in.nparts = d.nparts;
+    in.m = d.m;
+    return validate_system(in.A, in.part.data(), d.nparts);
+}
+
+static ams_status build_local_factors(ams_handle h, const int64_t* d_rowptr, const int32_t* d_colind,
+                                      const double* d_vals, double* d_S, double* d_ahat, double sigma,
+                                      int eig_mode, void** out_fac, int64_t* out_elems, int out_fp64) {
+    // band buffer
+    std::vector<int64_t> band_off(h->N), fac_off(h->N);
+    int64_t band_tot = 0, fac_tot = 0;
+    std::vector<int2> work;
+    for (int s = 0; s < h->N; ++s) {
+        const SubInfo& S = h->h_subs[s];
+        band_off[s] = band_tot;
+        band_tot += (int64_t)32 * S.nb * (32 * S.c + 1);
+        fac_off[s] = fac_tot;
+        fac_tot += (int64_t)S.nb * blockrow_elems(S.c);
+        for (int K = 0; K < S.nb; ++K) work.push_back(make_int2(s, K));
+    }
+    double* d_band = nullptr;
+    int64_t *d_band_off = nullptr, *d_fac_off = nullptr;
+    int2* d_work = nullptr;
+    int32_t* d_status = nullptr;
+    AMS_TRY(h->alloc_t(&d_band, (size_t)band_tot));
+    AMS_TRY(upload(h, &d_band_off, band_off));
+    AMS_TRY(upload(h, &d_fac_off, fac_off));
+    AMS_TRY(upload(h, &d_work, work));
+    AMS_TRY(h->alloc_t(&d_status, 1));
+    AMS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), h->stream));
+    BandArgs ba{h->stream, h->N, h->d_subs, d_band_off, d_rowptr, d_colind, d_vals};
+    launch_band_assemble(ba, d_band, eig_mode, sigma, d_S, d_ahat);
+    launch_band_cholesky(ba, d_band, d_status);
+    void* fac = nullptr;
+    AMS_TRY(h->alloc(&fac, (size_t)fac_tot * (out_fp64 ? 8 : 4)));
+    launch_band_pack_work(h->stream, (int)work.size(), h->d_subs, d_band_off, d_work, d_band, d_fac_off,
+                          out_fp64 ? (double*)fac : nullptr, out_fp64 ? nullptr : (float*)fac);
+    AMS_CUDA_TRY(cudaGetLastError());
+    int32_t status = 0;
+    AMS_CUDA_TRY(cudaMemcpyAsync(&status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->release(d_band);
+    if (status != 0) {
+        set_error(eig_mode ? "non-positive pivot in the shifted local eigen-operator"
+                           : "non-positive pivot in a local Cholesky factor (A_i not SPD)");
+        return AMS_ERR_NOT_SPD;
+    }
+    // record offsets (only for the solve factor)
+    if (!eig_mode)
+        for (int s = 0; s < h->N; ++s) h->h_subs[s].fac_off = fac_off[s];
+    *out_fac = fac;
+    *out_elems = fac_tot;
+    return AMS_OK;
+}
+
+static ams_status setup_eigen(ams_handle h, const int64_t* d_rowptr, const int32_t* d_colind,
+                              const double* d_vals) {
+    const double t0 = now_s();
+    int mreq = 0;
+    for (auto& s : h->sys) mreq = std::max(mreq, s.m);
+    const int P = std::min(32, pow2ceil(2 * mreq + 4));
+    for (int s = 0; s < h->N; ++s) h->h_subs[s].p = std::min(h->h_subs[s].n, P);
+    AMS_CUDA_TRY(cudaMemcpyAsync(h->d_subs, h->h_subs.data(), sizeof(SubInfo) * h->N, cudaMemcpyHostToDevice,
+                                 h->stream));
+    const double sigma = h->opt.eig_shift > 0 ? h->opt.eig_shift : 1e-2;
+    double *d_S = nullptr, *d_ahat = nullptr;
+    AMS_TRY(h->alloc_t(&d_S, (size_t)h->n_pad));
+    AMS_TRY(h->alloc_t(&d_ahat, (size_t)h->n_pad));
+    AMS_CUDA_TRY(cudaMemsetAsync(d_S, 0, sizeof(double) * h->n_pad, h->stream));
+    AMS_CUDA_TRY(cudaMemsetAsync(d_ahat, 0, sizeof(double) * h->n_pad, h->stream));
+    void* d_efac = nullptr;
+    int64_t efac_elems = 0;
+    // factor of \hat A_i + sigma S_i in the solve layout (FP64); the solve
+    // factor offsets are reused because the band structure is identical
+    std::vector<SubInfo> saved = h->h_subs;
+    AMS_TRY(build_local_factors(h, d_rowptr, d_colind, d_vals, d_S, d_ahat, sigma, 1, &d_efac, &efac_elems, 1));
+    double *d_X = nullptr, *d_Y = nullptr, *d_AY = nullptr, *d_T = nullptr, *d_theta = nullptr,
+           *d_res = nullptr;
+    int32_t* d_status = nullptr;
+    AMS_TRY(h->alloc_t(&d_X, (size_t)h->n_pad * P));
+    AMS_TRY(h->alloc_t(&d_Y, (size_t)h->n_pad * P));
+    AMS_TRY(h->alloc_t(&d_AY, (size_t)h->n_pad * P));
+    AMS_TRY(h->alloc_t(&d_T, (size_t)h->N * P * P));
+    AMS_TRY(h->alloc_t(&d_theta, (size_t)h->N * P));
+    AMS_TRY(h->alloc_t(&d_res, (size_t)h->N));
+    AMS_TRY(h->alloc_t(&d_status, 1));
+    AMS_CUDA_TRY(cudaMemsetAsync(d_X, 0, sizeof(double) * h->n_pad * P, h->stream));
+    AMS_CUDA_TRY(cudaMemsetAsync(d_Y, 0, sizeof(double) * h->n_pad * P, h->stream));
+    AMS_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), h->stream));
+    launch_eig_init(h->stream, h->N, h->d_subs, P, d_X);
+    // the eigen factor was packed with the offsets computed in build_local_factors
+    // (same structure as the solve factor): set them on the device copy
+    std::vector<SubInfo> esubs = h->h_subs;
+    {
+        int64_t off = 0;
+        for (int s = 0; s < h->N; ++s) {
+            esubs[s].fac_off = off;
+            off += (int64_t)esubs[s].nb * blockrow_elems(esubs[s].c);
+            esubs[s].m = 0;
+        }
+    }
+    SubInfo* d_esubs = nullptr;
+    AMS_TRY(upload(h, &d_esubs, esubs));
+    LocalSolveArgs la{h->stream, h->N, d_esubs, d_X, d_S, P, h->cmax, 0, nullptr};
+    const int maxit = h->opt.eig_maxit > 0 ? h->opt.eig_maxit : 300;
+    const double tol = h->opt.eig_tol > 0 ? h->opt.eig_tol : 1e-13;
+    std::vector<double> res(h->N);
+    int it = 0;
+    double worst = 0.0;
+    const int ncheck = std::min(P, mreq + 1);
+    for (it = 1; it <= maxit; ++it) {
+        AMS_CUDA_TRY(launch_local_solve(la, AMS_PREC_FP64, d_efac, nullptr, d_Y, nullptr));
+        launch_eig_rr(h->stream, h->N, d_esubs, P, d_rowptr, d_colind, d_vals, d_S, d_ahat, d_Y, d_AY, d_T,
+                      d_theta, d_status);
+        launch_eig_update(h->stream, h->n_pad, P, h->d_sub_of_row, d_esubs, d_Y, d_T, d_X);
+        AMS_CUDA_TRY(cudaGetLastError());
+        if (it % 4 == 0 || it == maxit) {
+            launch_eig_resid(h->stream, h->N, d_esubs, P, d_rowptr, d_colind, d_vals, d_S, d_ahat, d_X, d_theta,
+                             ncheck, d_res);
+            AMS_CUDA_TRY(cudaMemcpyAsync(res.data(), d_res, sizeof(double) * h->N, cudaMemcpyDeviceToHost,
+                                         h->stream));
+            AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+            worst = *std::max_element(res.begin(), res.end());
+            if (worst <= tol) break;
+        }
+    }
+    // final exact S-orthonormalisation: Rayleigh-Ritz on span(X) itself
+    launch_eig_rr(h->stream, h->N, d_esubs, P, d_rowptr, d_colind, d_vals, d_S, d_ahat, d_X, d_AY, d_T,
+                  d_theta, d_status);
+    launch_eig_update(h->stream, h->n_pad, P, h->d_sub_of_row, d_esubs, d_X, d_T, d_Y);
+    std::swap(d_X, d_Y);
+    launch_eig_resid(h->stream, h->N, d_esubs, P, d_rowptr, d_colind, d_vals, d_S, d_ahat, d_X, d_theta,
+                     ncheck, d_res);
+    std::vector<double> theta((size_t)h->N * P);
+    int32_t status = 0;
+    AMS_CUDA_TRY(cudaMemcpyAsync(theta.data(), d_theta, sizeof(double) * theta.size(), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    AMS_CUDA_TRY(cudaMemcpyAsync(res.data(), d_res, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
+    AMS_CUDA_TRY(cudaMemcpyAsync(&status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (status != 0) {
+        set_error("local eigensolver: Gram matrix lost positive definiteness");
+        return AMS_ERR_CUDA;
+    }
+    h->info.eig_iterations = std::min(it, maxit);
+    h->info.eig_max_residual = *std::max_element(res.begin(), res.end());
+    // kept modes per subdomain: m_i = min(m, n_i), grown across a cut cluster
+    int64_t psi_tot = 0;
+    h->h_lam.clear();
+    h->mmax = 0;
+    for (int s = 0; s < h->N; ++s) {
+        SubInfo& S = h->h_subs[s];
+        const int mreq_s = h->sys[S.seg].m;
+        int mi = std::min(mreq_s, S.n);
+        const double* th = &theta[(size_t)s * P];
+        while (mi > 0 && mi < S.p && mi < kMaxM &&
+               std::fabs(th[mi] - th[mi - 1]) <= 1e-8 * std::max(std::fabs(th[mi]), 1e-300))
+            ++mi;
+        S.m = mi;
+        S.psi_off = psi_tot;
+        psi_tot += (int64_t)S.n * mi;
+        for (int k = 0; k < mi; ++k) h->h_lam.push_back(th[k]);
+        h->mmax = std::max(h->mmax, mi);
+    }
+    h->psi_elems = psi_tot;
+    AMS_CUDA_TRY(cudaMemcpyAsync(h->d_subs, h->h_subs.data(), sizeof(SubInfo) * h->N, cudaMemcpyHostToDevice,
+                                 h->stream));
+    AMS_TRY(h->alloc_t(&h->d_psi64, (size_t)psi_tot));
+    launch_eig_finalize(h->stream, h->N, h->d_subs, P, d_X, d_S, h->d_psi64);
+    AMS_CUDA_TRY(cudaGetLastError());
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    for (void* p : {(void*)d_S, (void*)d_ahat, d_efac, (void*)d_X, (void*)d_Y, (void*)d_AY, (void*)d_T,
+                    (void*)d_theta, (void*)d_res})
+        h->release(p);
+    (void)saved;
+    h->info.eig_seconds = now_s() - t0;
+    return AMS_OK;
+}
+
+static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs, const int64_t* d_rowptr,
+                               const int32_t* d_colind, const double* d_vals, const double* d_psi_used) {
+    const double t0 = now_s();
+    // coarse layout per system: ND order of the subdomain graph
+    int64_t coff = 0;
+    for (int s = 0; s < h->nsys; ++s) {
+        SystemHost& S = h->sys[s];
+        const SysInput& in = inputs[s];
+        const int32_t N = S.nparts;
+        std::vector<std::vector<int32_t>> nb(N);
+        for (int64_t i = 0; i < S.n; ++i)
+            for (int64_t e = in.A.rowptr[i]; e < in.A.rowptr[i + 1]; ++e) {
+                const int32_t a = in.part[i], b = in.part[in.A.colind[e]];
+                if (a != b) nb[a].push_back(b);
+            }
+        std::vector<int64_t> adj_ptr(N + 1, 0);
+        std::vector<int32_t> adj;
+        for (int32_t a = 0; a < N; ++a) {
+            std::sort(nb[a].begin(), nb[a].end());
+            nb[a].erase(std::unique(nb[a].begin(), nb[a].end()), nb[a].end());
+            adj.insert(adj.end(), nb[a].begin(), nb[a].end());
+            adj_ptr[a + 1] = adj.size();
+        }
+        std::vector<int32_t> w(N);
+        for (int32_t a = 0; a < N; ++a) w[a] = h->h_subs[S.sub0 + a].m;
+        nested_dissection(N, adj_ptr, adj, w, 96, S.nodes);
+        S.coff0 = coff;
+        S.nd_pos_of_sub.assign(N, 0);
+        int64_t nc = 0;
+        for (auto& nd : S.nodes) {
+            int64_t pos = nd.a;
+            for (int32_t a : nd.subs) {
+                S.nd_pos_of_sub[a] = pos;
+                h->h_subs[S.sub0 + a].coff = coff + pos;
+                pos += w[a];
+            }
+            nc = std::max(nc, nd.a + nd.k);
+        }
+        S.nc = nc;
+        coff += nc;
+    }
+    h->Nc = coff;
+    AMS_CUDA_TRY(cudaMemcpyAsync(h->d_subs, h->h_subs.data(), sizeof(SubInfo) * h->N, cudaMemcpyHostToDevice,
+                                 h->stream));
+    // neighbour lists (incl. self) for the Galerkin product
+    std::vector<int64_t> nbr_ptr(h->N + 1, 0);
+    std::vector<int32_t> nbr;
+    int max_nbr = 1;
+    for (int s = 0; s < h->nsys; ++s) {
+        const SystemHost& S = h->sys[s];
+        const SysInput& in = inputs[s];
+        std::vector<std::vector<int32_t>> nb(S.nparts);
+        for (int64_t i = 0; i < S.n; ++i)
+            for (int64_t e = in.A.rowptr[i]; e < in.A.rowptr[i + 1]; ++e)
+                nb[in.part[i]].push_back(S.sub0 + in.part[in.A.colind[e]]);
+        for (int32_t a = 0; a < S.nparts; ++a) {
+            auto& v = nb[a];
+            std::sort(v.begin(), v.end());
+            v.erase(std::unique(v.begin(), v.end()), v.end());
+            nbr.insert(nbr.end(), v.begin(), v.end());
+            nbr_ptr[S.sub0 + a + 1] = nbr.size();
+            max_nbr = std::max(max_nbr, (int)v.size());
+        }
+    }
+    if (max_nbr > 256) {
+        set_error("a subdomain has more than 256 neighbouring subdomains");
+        return AMS_ERR_INVALID_ARG;
+    }
+    int64_t* d_nbr_ptr = nullptr;
+    int32_t* d_nbr = nullptr;
+    AMS_TRY(upload(h, &d_nbr_ptr, nbr_ptr));
+    AMS_TRY(upload(h, &d_nbr, nbr));
+    const int mm = std::max(1, h->mmax);
+
+    cusolverDnHandle_t sol = nullptr;
+    AMS_SOLVER_TRY(cusolverDnCreate(&sol));
+    std::unique_ptr<cusolverDnContext, decltype(&cusolverDnDestroy)> sol_guard(sol, cusolverDnDestroy);
+    AMS_SOLVER_TRY(cusolverDnSetStream(sol, h->stream));
+    cusolverDnParams_t params = nullptr;
+    AMS_SOLVER_TRY(cusolverDnCreateParams(&params));
+    std::unique_ptr<cusolverDnParams, decltype(&cusolverDnDestroyParams)> par_guard(params,
+                                                                                    cusolverDnDestroyParams);
+
+    // node matrices and GEMM items (all systems)
+    struct NodeMat { int64_t off; int64_t K; };
+    std::vector<CoarseItem> fwd, bwd;
+    std::vector<int32_t> rng;
+    std::vector<int64_t> desc;   // extraction chunks, 8 per chunk
+    int64_t Roff = 0, Qoff = 0;
+    int32_t tile_id = 0, slot = 0;
+    const int KCHUNK = 2048;
+    const int64_t ECHUNK = 65536;
+    // build all layouts first (host), then run factorisation + extraction per system
+    struct SysChunks { int64_t d0, d1; };
+    std::vector<SysChunks> sys_chunks(h->nsys);
+    auto add_items = [&](std::vector<CoarseItem>& items, int64_t moff, int64_t K, int64_t rows, int64_t out0,
+                         int32_t rng_off, int32_t nrng) {
+        for (int64_t r0 = 0; r0 < rows; r0 += 32) {
+            const int nr = (int)std::min<int64_t>(32, rows - r0);
+            const int nch = (int)std::max<int64_t>(1, (K + KCHUNK - 1) / KCHUNK);
+            for (int ch = 0; ch < nch; ++ch) {
+                CoarseItem it{};
+                it.moff = moff;
+                it.K = (int32_t)K;
+                it.nrows = nr;
+                it.row_in_node = (int32_t)r0;
+                it.out0 = (int32_t)(out0 + r0);
+                it.k0 = ch * KCHUNK;
+                it.k1 = (int32_t)std::min<int64_t>(K, (int64_t)(ch + 1) * KCHUNK);
+                it.rng_off = rng_off;
+                it.nrng = nrng;
+                it.tile_id = tile_id;
+                it.nchunks = nch;
+                it.chunk = ch;
+                it.slot0 = slot;
+                items.push_back(it);
+            }
+            if (nch > 1) slot += nch;
+            ++tile_id;
+        }
+    };
+    for (int s = 0; s < h->nsys; ++s) {
+        SystemHost& S = h->sys[s];
+        sys_chunks[s].d0 = (int64_t)desc.size() / 8;
+        for (size_t ni = 0; ni < S.nodes.size(); ++ni) {
+            const NDNode& nd = S.nodes[ni];
+            if (nd.k == 0) continue;
+            // forward block: rows of the node x its subtree
+            const int64_t a = S.coff0 + nd.a, cst = S.coff0 + nd.cstart;
+            const int64_t Kf = nd.a + nd.k - nd.cstart;
+            const int32_t roff = (int32_t)(rng.size() / 2);
+            rng.push_back((int32_t)cst);
+            rng.push_back((int32_t)Kf);
+            add_items(fwd, Roff, Kf, nd.k, a, roff, 1);
+            for (int64_t e0 = 0; e0 < nd.k * Kf; e0 += ECHUNK) {
+                desc.insert(desc.end(), {Roff, Kf, 0, nd.a, nd.cstart, (int64_t)roff, e0,
+                                         std::min(nd.k * Kf, e0 + ECHUNK)});
+            }
+            Roff += nd.k * Kf;
+            // backward block: rows of the node x (own rows, then ancestors' rows)
+            const int32_t boff = (int32_t)(rng.size() / 2);
+            int64_t Kb = 0;
+            int32_t nrng = 0;
+            for (int32_t q = (int32_t)ni; q >= 0; q = S.nodes[q].parent) {
+                if (S.nodes[q].k == 0) continue;
+                rng.push_back((int32_t)(S.coff0 + S.nodes[q].a));
+                rng.push_back((int32_t)S.nodes[q].k);
+                Kb += S.nodes[q].k;
+                ++nrng;
+            }
+            add_items(bwd, Qoff, Kb, nd.k, a, boff, nrng);
+            for (int64_t e0 = 0; e0 < nd.k * Kb; e0 += ECHUNK) {
+                desc.insert(desc.end(), {Qoff, Kb, 1, nd.a, nd.cstart,
+                                         (int64_t)boff | ((int64_t)nrng << 32), e0,
+                                         std::min(nd.k * Kb, e0 + ECHUNK)});
+            }
+            Qoff += nd.k * Kb;
+        }
+        sys_chunks[s].d1 = (int64_t)desc.size() / 8;
+    }
+    // the extraction ranges index the dense per-system matrix: make them
+    // system-relative (subtract coff0) for the backward gather list copy
+    std::vector<int32_t> rng_rel = rng;
+    {
+        // forward/backward ranges hold global coarse rows; extraction needs
+        // rows relative to the system: build a relative copy per system
+        for (int s = 0; s < h->nsys; ++s) {
+            (void)s;
+        }
+    }
+    h->R_elems = Roff;
+    h->Q_elems = Qoff;
+    h->nfwd = (int)fwd.size();
+    h->nbwd = (int)bwd.size();
+    const size_t tfb = h->tf_bytes();
+    AMS_TRY(h->alloc(&h->d_Rmat, (size_t)Roff * tfb));
+    AMS_TRY(h->alloc(&h->d_Qmat, (size_t)Qoff * tfb));
+    AMS_TRY(upload(h, &h->d_fwd, fwd));
+    AMS_TRY(upload(h, &h->d_bwd, bwd));
+    AMS_TRY(upload(h, &h->d_rng, rng));
+    AMS_TRY(h->alloc(&h->d_partial, (size_t)std::max<int32_t>(slot, 1) * 32 * kMaxLd * tfb));
+    AMS_TRY(h->alloc_t(&h->d_cnt, (size_t)std::max<int32_t>(tile_id, 1)));
+    AMS_CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(int32_t) * std::max<int32_t>(tile_id, 1), h->stream));
+
+    // per system: dense A_0 (ND order), Cholesky, triangular inverse, extraction
+    for (int s = 0; s < h->nsys; ++s) {
+        SystemHost& S = h->sys[s];
+        const int64_t nc = S.nc;
+        if (nc == 0) continue;
+        double* d_A = nullptr;
+        AMS_TRY(h->alloc_t(&d_A, (size_t)nc * nc));
+        AMS_CUDA_TRY(cudaMemsetAsync(d_A, 0, sizeof(double) * nc * nc, h->stream));
+        launch_galerkin(h->stream, S.nparts, h->d_subs, d_rowptr, d_colind, d_vals, h->d_sub_of_row, d_psi_used,
+                        d_nbr_ptr, d_nbr, max_nbr, mm, d_A, nc, S.coff0, S.sub0);
+        AMS_CUDA_TRY(cudaGetLastError());
+        if (nc <= 4096) {
+            S.A0_nd.resize((size_t)nc * nc);
+            AMS_CUDA_TRY(cudaMemcpyAsync(S.A0_nd.data(), d_A, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost,
+                                         h->stream));
+        }
+        size_t wdev = 0, whost = 0, wdev2 = 0, whost2 = 0;
+        AMS_SOLVER_TRY(cusolverDnXpotrf_bufferSize(sol, params, CUBLAS_FILL_MODE_LOWER, nc, CUDA_R_64F, d_A, nc,
+                                                   CUDA_R_64F, &wdev, &whost));
+        AMS_SOLVER_TRY(cusolverDnXtrtri_bufferSize(sol, CUBLAS_FILL_MODE_LOWER, CUBLAS_DIAG_NON_UNIT, nc,
+                                                   CUDA_R_64F, d_A, nc, &wdev2, &whost2));
+        void* d_work = nullptr;
+        int* d_info = nullptr;
+        AMS_TRY(h->alloc(&d_work, std::max(wdev, wdev2)));
+        AMS_TRY(h->alloc((void**)&d_info, sizeof(int)));
+        std::vector<char> hwork(std::max<size_t>(1, std::max(whost, whost2)));
+        AMS_SOLVER_TRY(cusolverDnXpotrf(sol, params, CUBLAS_FILL_MODE_LOWER, nc, CUDA_R_64F, d_A, nc, CUDA_R_64F,
+                                        d_work, wdev, hwork.data(), whost, d_info));
+        int info = 0;
+        AMS_CUDA_TRY(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        if (info != 0) {
+            set_error("coarse matrix A_0 is not SPD (Cholesky pivot " + std::to_string(info) + ")");
+            return AMS_ERR_NOT_SPD;
+        }
+        AMS_SOLVER_TRY(cusolverDnXtrtri(sol, CUBLAS_FILL_MODE_LOWER, CUBLAS_DIAG_NON_UNIT, nc, CUDA_R_64F, d_A, nc,
+                                        d_work, wdev2, hwork.data(), whost2, d_info));
+        AMS_CUDA_TRY(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        if (info != 0) {
+            set_error("coarse triangular inverse failed");
+            return AMS_ERR_NOT_SPD;
+        }
+        // system-relative gather ranges for the extraction
+        std::vector<int32_t> rel = rng;
+        for (size_t q = 0; q < rel.size(); q += 2) rel[q] -= (int32_t)S.coff0;
+        int32_t* d_rel = nullptr;
+        AMS_TRY(upload(h, &d_rel, rel));
+        const int64_t nch = sys_chunks[s].d1 - sys_chunks[s].d0;
+        std::vector<int64_t> dsub(desc.begin() + 8 * sys_chunks[s].d0, desc.begin() + 8 * sys_chunks[s].d1);
+        int64_t* d_desc = nullptr;
+        AMS_TRY(upload(h, &d_desc, dsub));
+        // forward chunks write R, backward chunks write Q: two passes with the
+        // kind filter done by splitting the descriptor list
+        std::vector<int64_t> df, db;
+        for (int64_t c = 0; c < nch; ++c) (dsub[8 * c + 2] == 0 ? df : db).insert((dsub[8 * c + 2] == 0 ? df : db).end(),
+                                                                                   dsub.begin() + 8 * c, dsub.begin() + 8 * c + 8);
+        int64_t *d_df = nullptr, *d_db = nullptr;
+        AMS_TRY(upload(h, &d_df, df));
+        AMS_TRY(upload(h, &d_db, db));
+        const bool f64 = h->prec == AMS_PREC_FP64;
+        launch_extract_chunks(h->stream, (int)(df.size() / 8), d_df, d_rel, d_A, nc,
+                              f64 ? (double*)h->d_Rmat : nullptr, f64 ? nullptr : (float*)h->d_Rmat);
+        launch_extract_chunks(h->stream, (int)(db.size() / 8), d_db, d_rel, d_A, nc,
+                              f64 ? (double*)h->d_Qmat : nullptr, f64 ? nullptr : (float*)h->d_Qmat);
+        AMS_CUDA_TRY(cudaGetLastError());
+        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        for (void* p : {(void*)d_A, d_work, (void*)d_info, (void*)d_rel, (void*)d_desc, (void*)d_df, (void*)d_db})
+            h->release(p);
+    }
+    h->release(d_nbr_ptr);
+    h->release(d_nbr);
+    h->info.coarse_seconds = now_s() - t0;
+    return AMS_OK;
+}
+
+static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const ams_options* opt,
+                             void* stream, ams_handle* out) {
+    const double t0 = now_s();
+    if (!out || nsys <= 0 || !systems) {
+        set_error("invalid arguments to setup");
+        return AMS_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    std::unique_ptr<ams_handle_s> h(new ams_handle_s());
+    if (opt) h->opt = *opt;
+    else ams_options_default(&h->opt);
+    if (h->opt.precision < 0 || h->opt.precision > 2) {
+        set_error("unknown precision mode");
+        return AMS_ERR_INVALID_ARG;
+    }
+    if (h->opt.maxit <= 0) h->opt.maxit = 10000;
+    h->prec = h->opt.precision;
+    h->flexible = h->opt.cg_variant == AMS_CG_AUTO ? (h->prec != AMS_PREC_FP64) : (h->opt.cg_variant == AMS_CG_FCG);
+    h->stream = (cudaStream_t)stream;
+    h->nsys = nsys;
+    std::vector<SysInput> inputs(nsys);
+    for (int s = 0; s < nsys; ++s) AMS_TRY(read_inputs(systems[s], h->opt.device_ptrs, inputs[s]));
+    // layout
+    h->sys.resize(nsys);
+    int64_t caller = 0, row = 0;
+    int32_t sub = 0;
+    for (int s = 0; s < nsys; ++s) {
+        SystemHost& S = h->sys[s];
+        S.n = inputs[s].A.n;
+        S.nnz = inputs[s].A.rowptr[S.n];
+        S.caller0 = caller;
+        S.row0 = row;
+        S.npad = round_up(S.n, kRowAlign);
+        S.sub0 = sub;
+        S.nparts = inputs[s].nparts;
+        S.m = h->opt.coarse ? inputs[s].m : 0;
+        std::vector<int64_t> iperm;
+        build_index_maps(S.n, inputs[s].part.data(), S.nparts, S.perm, iperm, S.sub_ptr);
+        caller += S.n;
+        row += S.npad;
+        sub += S.nparts;
+        h->nnz_total += S.nnz;
+    }
+    h->n_total = caller;
+    h->n_pad = row;
+    h->N = sub;
+    if (h->n_pad > (int64_t(1) << 31) - 1) {
+        set_error("total padded size exceeds 2^31 rows");
+        return AMS_ERR_INVALID_ARG;
+    }
+    // index maps, internal CSR, subdomain descriptors
+    std::vector<int64_t> int_row(h->n_total), irp(h->n_pad + 1, 0);
+    std::vector<int32_t> sub_of_row(h->n_pad, -1), icol;
+    std::vector<double> ival;
+    icol.reserve(h->nnz_total);
+    ival.reserve(h->nnz_total);
+    h->h_subs.resize(h->N);
+    std::vector<std::pair<int32_t, double>> rowbuf;
+    int64_t rp = 0;
+    for (int s = 0; s < nsys; ++s) {
+        SystemHost& S = h->sys[s];
+        const HostCSR& A = inputs[s].A;
+        std::vector<int64_t> iperm(S.n);
+        for (int64_t k = 0; k < S.n; ++k) iperm[S.perm[k]] = k;
+        for (int64_t g = 0; g < S.n; ++g) int_row[S.caller0 + g] = S.row0 + iperm[g];
+        for (int32_t a = 0; a < S.nparts; ++a) {
+            SubInfo& I = h->h_subs[S.sub0 + a];
+            I = SubInfo{};
+            I.row0 = S.row0 + S.sub_ptr[a];
+            I.n = (int32_t)(S.sub_ptr[a + 1] - S.sub_ptr[a]);
+            I.nb = (I.n + 31) / 32;
+            I.seg = s;
+            I.m = 0;
+            int64_t bw = 0;
+            for (int64_t k = S.sub_ptr[a]; k < S.sub_ptr[a + 1]; ++k) {
+                sub_of_row[S.row0 + k] = S.sub0 + a;
+                const int64_t g = S.perm[k];
+                for (int64_t e = A.rowptr[g]; e < A.rowptr[g + 1]; ++e) {
+                    const int64_t kk = iperm[A.colind[e]];
+                    if (kk >= S.sub_ptr[a] && kk < k) bw = std::max(bw, k - kk);
+                }
+            }
+            I.c = (int32_t)std::max<int64_t>(1, (bw + 31) / 32);
+            h->cmax = std::max(h->cmax, I.c);
+        }
+        for (int64_t k = 0; k < S.npad; ++k) {
+            irp[S.row0 + k] = rp;
+            if (k < S.n) {
+                const int64_t g = S.perm[k];
+                rowbuf.clear();
+                for (int64_t e = A.rowptr[g]; e < A.rowptr[g + 1]; ++e)
+                    rowbuf.push_back({(int32_t)(S.row0 + iperm[A.colind[e]]), A.vals[e]});
+                std::sort(rowbuf.begin(), rowbuf.end(),
+                          [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+                              return x.first < y.first;
+                          });
+                for (auto& pr : rowbuf) {
+                    icol.push_back(pr.first);
+                    ival.push_back(pr.second);
+                }
+                rp += (int64_t)rowbuf.size();
+            }
+        }
+    }
+    irp[h->n_pad] = rp;
+    // shared-memory staging limits of the local solve
+    {
+        const size_t lim = 227 * 1024;
+        const size_t need_solve = local_solve_smem(h->cmax, kMaxLd, h->tf_bytes());
+        const size_t need_eig = local_solve_smem(h->cmax, 32, 8);
+        if (need_solve > lim || (h->opt.coarse && need_eig > lim)) {
+            set_error("a subdomain's band (" + std::to_string(32 * h->cmax) +
+                      ") is too wide for shared-memory staging; renumber the subdomain or use smaller subdomains");
+            return AMS_ERR_INVALID_ARG;
+        }
+    }
+    // SELL-32 layout of the internal matrix
+    const int64_t nslices = h->n_pad / 32;
+    std::vector<int64_t> sell_ptr(nslices + 1, 0);
+    for (int64_t sl = 0; sl < nslices; ++sl) {
+        int64_t w = 0;
+        for (int l = 0; l < 32; ++l) w = std::max(w, irp[sl * 32 + l + 1] - irp[sl * 32 + l]);
+        sell_ptr[sl + 1] = sell_ptr[sl] + 32 * w;
+    }
+    std::vector<int32_t> sell_col(sell_ptr[nslices]);
+    std::vector<double> sell_val(sell_ptr[nslices], 0.0);
+    for (int64_t sl = 0; sl < nslices; ++sl) {
+        const int64_t w = (sell_ptr[sl + 1] - sell_ptr[sl]) / 32;
+        for (int l = 0; l < 32; ++l) {
+            const int64_t r = sl * 32 + l;
+            const int64_t len = irp[r + 1] - irp[r];
+            for (int64_t j = 0; j < w; ++j) {
+                const int64_t o = sell_ptr[sl] + 32 * j + l;
+                if (j < len) {
+                    sell_col[o] = icol[irp[r] + j];
+                    sell_val[o] = ival[irp[r] + j];
+                } else {
+                    sell_col[o] = (int32_t)r;
+                    sell_val[o] = 0.0;
+                }
+            }
+        }
+    }
+    ams_handle H = h.get();
+    AMS_TRY(upload(H, &h->d_int_row, int_row));
+    AMS_TRY(upload(H, &h->d_sub_of_row, sub_of_row));
+    AMS_TRY(upload(H, &h->d_sell_ptr, sell_ptr));
+    AMS_TRY(upload(H, &h->d_sell_col, sell_col));
+    AMS_TRY(upload(H, &h->d_sell_val, sell_val));
+    int64_t* d_irp = nullptr;
+    int32_t* d_icol = nullptr;
+    double* d_ival = nullptr;
+    AMS_TRY(upload(H, &d_irp, irp));
+    AMS_TRY(upload(H, &d_icol, icol));
+    AMS_TRY(upload(H, &d_ival, ival));
+    if (nsys == 1) {
+        AMS_TRY(upload(H, &h->d_crowptr, inputs[0].A.rowptr));
+        AMS_TRY(upload(H, &h->d_ccolind, inputs[0].A.colind));
+    }
+    AMS_TRY(h->alloc_t(&h->d_subs, (size_t)h->N));
+    AMS_CUDA_TRY(cudaMemcpyAsync(h->d_subs, h->h_subs.data(), sizeof(SubInfo) * h->N, cudaMemcpyHostToDevice,
+                                 h->stream));
+    // local factors of A_i
+    AMS_TRY(build_local_factors(H, d_irp, d_icol, d_ival, nullptr, nullptr, 0.0, 0, &h->d_fac, &h->fac_elems,
+                                h->prec == AMS_PREC_FP64));
+    AMS_CUDA_TRY(cudaMemcpyAsync(h->d_subs, h->h_subs.data(), sizeof(SubInfo) * h->N, cudaMemcpyHostToDevice,
+                                 h->stream));
+    // coarse space
+    bool any_m = false;
+    for (auto& S : h->sys) any_m = any_m || S.m > 0;
+    if (any_m) {
+        AMS_TRY(setup_eigen(H, d_irp, d_icol, d_ival));
+        double* d_psi_used = nullptr;
+        AMS_TRY(h->alloc_t(&d_psi_used, (size_t)h->psi_elems));
+        AMS_TRY(h->alloc(&h->d_psi, (size_t)h->psi_elems * h->tp_bytes()));
+        launch_psi_round(h->stream, h->psi_elems, h->d_psi64, h->prec, d_psi_used,
+                         h->prec == AMS_PREC_FP32 ? (float*)h->d_psi : nullptr,
+                         h->prec == AMS_PREC_FP32_BF16 ? (__nv_bfloat16*)h->d_psi : nullptr);
+        if (h->prec == AMS_PREC_FP64)
+            AMS_CUDA_TRY(cudaMemcpyAsync(h->d_psi, h->d_psi64, sizeof(double) * h->psi_elems,
+                                         cudaMemcpyDeviceToDevice, h->stream));
+        AMS_CUDA_TRY(cudaGetLastError());
+        if (h->mmax > 0) AMS_TRY(setup_coarse(H, inputs, d_irp, d_icol, d_ival, d_psi_used));
+        h->release(d_psi_used);
+    }
+    for (void* p : {(void*)d_irp, (void*)d_icol, (void*)d_ival}) h->release(p);
+    AMS_TRY(h->alloc_t(&h->d_st, 1));
+    AMS_CUDA_TRY(cudaMemsetAsync(h->d_st, 0, sizeof(SolveState), h->stream));
+    AMS_TRY(h->alloc_t(&h->d_sc, (size_t)h->nsys * kMaxLd));
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    // info
+    ams_info& I = h->info;
+    I.n = h->n_total;
+    I.nnz = h->nnz_total;
+    I.nparts = h->N;
+    I.nsys = h->nsys;
+    I.ncoarse = h->Nc;
+    I.max_band_tiles = h->cmax;
+    I.precision = h->prec;
+    I.cg_variant = h->flexible ? AMS_CG_FCG : AMS_CG_PCG;
+    I.local_factor_bytes = h->fac_elems * (int64_t)h->tf_bytes();
+    I.coarse_inverse_bytes = (h->R_elems + h->Q_elems) * (int64_t)h->tf_bytes();
+    I.basis_bytes = h->psi_elems * (int64_t)h->tp_bytes();
+    I.spmv_variant = 0;
+    I.setup_seconds = now_s() - t0;
+    *out = h.release();
+    return AMS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+static ams_status ensure_work(ams_handle h, int ld) {
+    if (ld > h->ld_alloc) {
+        for (void* p : {(void*)h->d_x, (void*)h->d_r, (void*)h->d_p, (void*)h->d_q, (void*)h->d_z, h->d_zf, h->d_rc,
+                        h->d_yc, h->d_ec, (void*)h->d_stage_in, (void*)h->d_stage_out, (void*)h->d_stage_aux})
+            h->release(p);
+        const size_t nv = (size_t)h->n_pad * ld;
+        const size_t nc = (size_t)std::max<int64_t>(h->Nc, 1) * ld;
+        AMS_TRY(h->alloc_t(&h->d_x, nv));
+        AMS_TRY(h->alloc_t(&h->d_r, nv));
+        AMS_TRY(h->alloc_t(&h->d_p, nv));
+        AMS_TRY(h->alloc_t(&h->d_q, nv));
+        AMS_TRY(h->alloc_t(&h->d_z, nv));
+        AMS_TRY(h->alloc(&h->d_zf, nv * h->tf_bytes()));
+        AMS_TRY(h->alloc(&h->d_rc, nc * h->tf_bytes()));
+        AMS_TRY(h->alloc(&h->d_yc, nc * h->tf_bytes()));
+        AMS_TRY(h->alloc(&h->d_ec, nc * h->tf_bytes()));
+        AMS_TRY(h->alloc_t(&h->d_stage_in, (size_t)h->n_total * ld));
+        AMS_TRY(h->alloc_t(&h->d_stage_out, (size_t)h->n_total * ld));
+        AMS_TRY(h->alloc_t(&h->d_stage_aux, (size_t)h->n_total * ld));
+        h->ld_alloc = ld;
+        h->ld_last = 0;
+    }
+    if (ld != h->ld_last) {
+        const size_t nv = (size_t)h->n_pad * ld;
+        for (double* p : {h->d_x, h->d_r, h->d_p, h->d_q, h->d_z})
+            AMS_CUDA_TRY(cudaMemsetAsync(p, 0, nv * sizeof(double), h->stream));
+        AMS_CUDA_TRY(cudaMemsetAsync(h->d_zf, 0, nv * h->tf_bytes(), h->stream));
+        h->ld_last = ld;
+    }
+    return AMS_OK;
+}
+
+// z = M^{-1} r (internal layout); with_dot/first control the fused dots
+static ams_status apply_precond(ams_handle h, const LaunchCtx& L, const double* r, double* z, int first,
+                                int with_dot) {
+    LocalSolveArgs la{h->stream, h->N, h->d_subs, r, nullptr, L.ld, h->cmax, std::max(1, h->mmax),
+                      with_dot ? h->d_st : nullptr};
+    const bool coarse = h->Nc > 0;
+    AMS_CUDA_TRY(launch_local_solve(la, h->prec, h->d_fac, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
+    h->launches += coarse ? 4 : 2;
+    if (coarse) {
+        CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_partial, h->d_cnt,
+                        with_dot ? h->d_st : nullptr};
+        launch_coarse_gemm(cf, h->prec, L.ld, h->d_rc, h->d_yc);
+        CoarseLaunch cb{h->stream, h->nbwd, h->d_bwd, h->d_Qmat, h->d_rng, h->d_partial, h->d_cnt,
+                        with_dot ? h->d_st : nullptr};
+        launch_coarse_gemm(cb, h->prec, L.ld, h->d_yc, h->d_ec);
+    }
+    LaunchCtx L2 = L;
+    if (!with_dot) L2.st = nullptr;
+    launch_prolong_dot(L2, h->prec, h->d_psi, coarse ? h->d_ec : nullptr, h->d_zf, r, h->d_q, z, h->flexible,
+                       first, with_dot);
+    AMS_CUDA_TRY(cudaGetLastError());
+    return AMS_OK;
+}
+
+static ams_status launch_iteration(ams_handle h, const LaunchCtx& L, double rtol2) {
+    h->launches += 3;
+    launch_spmv_dot(L, h->d_p, h->d_q, 1);
+    launch_cg_update(L, h->d_x, h->d_r, h->d_p, h->d_q, rtol2, h->opt.maxit);
+    AMS_TRY(apply_precond(h, L, h->d_r, h->d_z, 0, 1));
+    launch_dir_update(L, h->d_p, h->d_z);
+    return AMS_OK;
+}
+
+// Stage caller vectors (host or device) into device memory in caller order.
+static ams_status stage_in(ams_handle h, const double* src, int nrhs, double* dst, const double** dev) {
+    if (h->opt.device_ptrs) {
+        *dev = src;
+        return AMS_OK;
+    }
+    AMS_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(double) * h->n_total * nrhs, cudaMemcpyHostToDevice, h->stream));
+    *dev = dst;
+    return AMS_OK;
+}
+
+static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, double* u_dev, int32_t* iters,
+                      double* relres) {
+    const int ld = pow2ceil(nrhs);
+    AMS_TRY(ensure_work(h, ld));
+    RedCache* rc = nullptr;
+    AMS_TRY(get_red(h, ld, &rc));
+    LaunchCtx L = make_ctx(h, *rc);
+    // caller order -> internal rows (each system's block is contiguous in f)
+    for (int s = 0; s < h->nsys; ++s) {
+        const SystemHost& S = h->sys[s];
+        (void)S;
+    }
+    if (h->nsys == 1) {
+        launch_permute_in(h->stream, f_dev, h->n_total, nrhs, ld, h->d_int_row, h->d_r, h->d_x);
+    } else {
+        for (int s = 0; s < h->nsys; ++s) {
+            const SystemHost& S = h->sys[s];
+            launch_permute_in(h->stream, f_dev + S.caller0 * nrhs, S.n, nrhs, ld, h->d_int_row + S.caller0, h->d_r,
+                              h->d_x);
+        }
+    }
+    AMS_CUDA_TRY(cudaMemsetAsync(h->d_p, 0, sizeof(double) * h->n_pad * ld, h->stream));
+    h->launches += 2 * h->nsys + 2;     // permutes in/out, norms, first direction
+    launch_init_norms(L, h->d_r, nrhs);
+    AMS_TRY(apply_precond(h, L, h->d_r, h->d_z, 1, 1));
+    launch_dir_update(L, h->d_p, h->d_z);
+    AMS_CUDA_TRY(cudaGetLastError());
+    const double rtol2 = rtol * rtol;
+    SolveState st{};
+    int chunk = 4;
+    while (true) {
+        for (int k = 0; k < chunk; ++k) AMS_TRY(launch_iteration(h, L, rtol2));
+        AMS_CUDA_TRY(cudaMemcpyAsync(&st, h->d_st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
+        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        if (st.done) break;
+        chunk = std::min(chunk * 2, 32);
+    }
+    // outputs
+    if (h->nsys == 1) {
+        launch_permute_out(h->stream, h->d_x, h->n_total, nrhs, ld, h->d_int_row, u_dev);
+    } else {
+        for (int s = 0; s < h->nsys; ++s) {
+            const SystemHost& S = h->sys[s];
+            launch_permute_out(h->stream, h->d_x, S.n, nrhs, ld, h->d_int_row + S.caller0, u_dev + S.caller0 * nrhs);
+        }
+    }
+    std::vector<CgScalars> sc((size_t)h->nsys * ld);
+    AMS_CUDA_TRY(cudaMemcpyAsync(sc.data(), h->d_sc, sizeof(CgScalars) * sc.size(), cudaMemcpyDeviceToHost,
+                                 h->stream));
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    bool any_active = false;
+    for (int s = 0; s < h->nsys; ++s)
+        for (int k = 0; k < nrhs; ++k) {
+            const CgScalars& c = sc[(size_t)s * ld + k];
+            if (iters) iters[s * nrhs + k] = c.iters;
+            if (relres) relres[s * nrhs + k] = c.fnorm2 > 0 ? std::sqrt(c.rr / c.fnorm2) : 0.0;
+            any_active = any_active || c.active;
+        }
+    if (st.status == AMS_ERR_BREAKDOWN) {
+        set_error("CG breakdown (p^T A p <= 0 or non-finite scalar)");
+        return AMS_ERR_BREAKDOWN;
+    }
+    if (any_active) {
+        set_error("maximum iteration count reached");
+        return AMS_ERR_NOT_CONVERGED;
+    }
+    return AMS_OK;
+}
+
+}  // namespace ams
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void ams_options_default(ams_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = AMS_PREC_FP32_BF16;
+    opt->cg_variant = AMS_CG_AUTO;
+    opt->maxit = 10000;
+    opt->device_ptrs = 0;
+    opt->autotune = 1;
+    opt->coarse = 1;
+    opt->eig_shift = 0.0;
+    opt->eig_maxit = 0;
+    opt->eig_tol = 0.0;
+    opt->spin_budget_cycles = 0;
+}
+
+const char* ams_status_string(ams_status s) {
+    switch (s) {
+        case AMS_OK: return "AMS_OK";
+        case AMS_ERR_INVALID_ARG: return "AMS_ERR_INVALID_ARG";
+        case AMS_ERR_NOT_SPD: return "AMS_ERR_NOT_SPD";
+        case AMS_ERR_BREAKDOWN: return "AMS_ERR_BREAKDOWN";
+        case AMS_ERR_NOT_CONVERGED: return "AMS_ERR_NOT_CONVERGED";
+        case AMS_ERR_DEVICE_TIMEOUT: return "AMS_ERR_DEVICE_TIMEOUT";
+        case AMS_ERR_CUDA: return "AMS_ERR_CUDA";
+        case AMS_ERR_OOM: return "AMS_ERR_OOM";
+    }
+    return "AMS_ERR_UNKNOWN";
+}
+
+const char* ams_last_error(void) { return g_last_error.c_str(); }
+
+ams_status ams_setup(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                     const int32_t* part, int32_t nparts, int32_t m, const ams_options* opt, void* stream,
+                     ams_handle* out) {
+    g_last_error.clear();
+    ams_system_desc d{n, rowptr, colind, vals, part, nparts, m};
+    return setup_impl(1, &d, opt, stream, out);
+}
+
+ams_status ams_setup_batched(int32_t nsys, const ams_system_desc* systems, const ams_options* opt, void* stream,
+                             ams_handle* out) {
+    g_last_error.clear();
+    return setup_impl(nsys, systems, opt, stream, out);
+}
+
+ams_status ams_destroy(ams_handle h) {
+    if (h) {
+        cudaStreamSynchronize(h->stream);
+        delete h;
+    }
+    return AMS_OK;
+}
+
+static ams_status check_solve_args(ams_handle h, const void* a, const void* b, int32_t nrhs, double rtol) {
+    if (!h || !a || !b) {
+        set_error("null handle or vector");
+        return AMS_ERR_INVALID_ARG;
+    }
+    if (nrhs < 1 || nrhs > kMaxLd) {
+        set_error("nrhs must be in [1, 32]");
+        return AMS_ERR_INVALID_ARG;
+    }
+    if (!(rtol > 0.0) || !std::isfinite(rtol)) {
+        set_error("rtol must be positive and finite");
+        return AMS_ERR_INVALID_ARG;
+    }
+    return AMS_OK;
+}
+
+ams_status ams_solve(ams_handle h, const double* f, int32_t nrhs, double rtol, double* u, int32_t* iters,
+                     double* relres) {
+    g_last_error.clear();
+    AMS_TRY(check_solve_args(h, f, u, nrhs, rtol));
+    AMS_TRY(ensure_work(h, pow2ceil(nrhs)));
+    const double* f_dev = nullptr;
+    AMS_TRY(stage_in(h, f, nrhs, h->d_stage_in, &f_dev));
+    double* u_dev = h->opt.device_ptrs ? u : h->d_stage_out;
+    ams_status st = pcg(h, f_dev, nrhs, rtol, u_dev, iters, relres);
+    if (st != AMS_OK && st != AMS_ERR_NOT_CONVERGED && st != AMS_ERR_BREAKDOWN) return st;
+    if (!h->opt.device_ptrs) {
+        AMS_CUDA_TRY(cudaMemcpyAsync(u, u_dev, sizeof(double) * h->n_total * nrhs, cudaMemcpyDeviceToHost,
+                                     h->stream));
+        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    return st;
+}
+
+ams_status ams_solve_adjoint(ams_handle h, const double* g, int32_t nrhs, double rtol, const double* u,
+                             double* lambda, double* dvals, int32_t* iters) {
+    g_last_error.clear();
+    AMS_TRY(check_solve_args(h, g, lambda, nrhs, rtol));
+    if (h->nsys != 1) {
+        set_error("adjoint solves need a single-system handle");
+        return AMS_ERR_INVALID_ARG;
+    }
+    if (!u && dvals) {
+        set_error("u is required to form dL/dA");
+        return AMS_ERR_INVALID_ARG;
+    }
+    AMS_TRY(ensure_work(h, pow2ceil(nrhs)));
+    const double* g_dev = nullptr;
+    AMS_TRY(stage_in(h, g, nrhs, h->d_stage_in, &g_dev));
+    double* lam_dev = h->opt.device_ptrs ? lambda : h->d_stage_out;
+    std::vector<double> rel(nrhs);
+    ams_status st = pcg(h, g_dev, nrhs, rtol, lam_dev, iters, rel.data());
+    if (st != AMS_OK && st != AMS_ERR_NOT_CONVERGED) return st;
+    if (dvals) {
+        const double* u_dev = nullptr;
+        AMS_TRY(stage_in(h, u, nrhs, h->d_stage_aux, &u_dev));
+        double* dv_dev = dvals;
+        if (!h->opt.device_ptrs) {
+            if (!h->d_stage_dvals) AMS_TRY(h->alloc_t(&h->d_stage_dvals, (size_t)h->nnz_total));
+            dv_dev = h->d_stage_dvals;
+        }
+        launch_sddmm(h->stream, h->d_crowptr, h->d_ccolind, h->n_total, nrhs, lam_dev, u_dev, dv_dev);
+        h->launches += 1;
+        AMS_CUDA_TRY(cudaGetLastError());
+        if (!h->opt.device_ptrs)
+            AMS_CUDA_TRY(cudaMemcpyAsync(dvals, dv_dev, sizeof(double) * h->nnz_total, cudaMemcpyDeviceToHost,
+                                         h->stream));
+    }
+    if (!h->opt.device_ptrs)
+        AMS_CUDA_TRY(cudaMemcpyAsync(lambda, lam_dev, sizeof(double) * h->n_total * nrhs, cudaMemcpyDeviceToHost,
+                                     h->stream));
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return st;
+}
+
+ams_status ams_get_info(ams_handle h, ams_info* info) {
+    if (!h || !info) {
+        set_error("null argument");
+        return AMS_ERR_INVALID_ARG;
+    }
+    *info = h->info;
+    info->kernel_launches = h->launches;
+    return AMS_OK;
+}
+
+ams_status ams_get_index_maps(ams_handle h, int64_t* perm, int64_t* sub_ptr) {
+    if (!h || h->nsys != 1) {
+        set_error("single-system handle required");
+        return AMS_ERR_INVALID_ARG;
+    }
+    const SystemHost& S = h->sys[0];
+    if (perm) std::memcpy(perm, S.perm.data(), sizeof(int64_t) * S.n);
+    if (sub_ptr) std::memcpy(sub_ptr, S.sub_ptr.data(), sizeof(int64_t) * (S.nparts + 1));
+    return AMS_OK;
+}
+
+ams_status ams_get_coarse_basis(ams_handle h, int32_t* m_i, double* lambda, double* psi) {
+    if (!h) {
+        set_error("null handle");
+        return AMS_ERR_INVALID_ARG;
+    }
+    if (m_i)
+        for (int s = 0; s < h->N; ++s) m_i[s] = h->h_subs[s].m;
+    if (lambda && !h->h_lam.empty()) std::memcpy(lambda, h->h_lam.data(), sizeof(double) * h->h_lam.size());
+    if (psi && h->psi_elems > 0) {
+        std::vector<double> tmp(h->psi_elems);
+        AMS_CUDA_TRY(cudaMemcpy(tmp.data(), h->d_psi64, sizeof(double) * h->psi_elems, cudaMemcpyDeviceToHost));
+        int64_t o = 0;
+        for (int s = 0; s < h->N; ++s) {
+            const SubInfo& S = h->h_subs[s];
+            for (int k = 0; k < S.m; ++k)
+                for (int i = 0; i < S.n; ++i) psi[o + (int64_t)k * S.n + i] = tmp[S.psi_off + (int64_t)i * S.m + k];
+            o += (int64_t)S.n * S.m;
+        }
+    }
+    return AMS_OK;
+}
+
+ams_status ams_get_coarse_matrix(ams_handle h, double* A0) {
+    if (!h || h->nsys != 1 || !A0) {
+        set_error("single-system handle and output required");
+        return AMS_ERR_INVALID_ARG;
+    }
+    const SystemHost& S = h->sys[0];
+    if (S.nc > 0 && S.A0_nd.empty()) {
+        set_error("coarse matrix not retained (N_c > 4096)");
+        return AMS_ERR_INVALID_ARG;
+    }
+    // paper order: subdomain-major, mode-minor
+    std::vector<int64_t> paper_of_nd(S.nc);
+    int64_t pos = 0;
+    for (int32_t a = 0; a < S.nparts; ++a) {
+        const int m = h->h_subs[S.sub0 + a].m;
+        for (int k = 0; k < m; ++k) paper_of_nd[S.nd_pos_of_sub[a] + k] = pos + k;
+        pos += m;
+    }
+    for (int64_t i = 0; i < S.nc; ++i)
+        for (int64_t j = 0; j < S.nc; ++j) A0[paper_of_nd[i] * S.nc + paper_of_nd[j]] = S.A0_nd[i * S.nc + j];
+    return AMS_OK;
+}
+
+ams_status ams_apply_preconditioner(ams_handle h, const double* r, int32_t nrhs, double* z) {
+    g_last_error.clear();
+    AMS_TRY(check_solve_args(h, r, z, nrhs, 1.0));
+    if (h->nsys != 1) {
+        set_error("single-system handle required");
+        return AMS_ERR_INVALID_ARG;
+    }
+    const int ld = pow2ceil(nrhs);
+    AMS_TRY(ensure_work(h, ld));
+    RedCache* rc = nullptr;
+    AMS_TRY(get_red(h, ld, &rc));
+    LaunchCtx L = make_ctx(h, *rc);
+    const double* r_dev = nullptr;
+    AMS_TRY(stage_in(h, r, nrhs, h->d_stage_in, &r_dev));
+    launch_permute_in(h->stream, r_dev, h->n_total, nrhs, ld, h->d_int_row, h->d_r, nullptr);
+    h->launches += 2;
+    AMS_TRY(apply_precond(h, L, h->d_r, h->d_z, 1, 0));
+    double* z_dev = h->opt.device_ptrs ? z : h->d_stage_out;
+    launch_permute_out(h->stream, h->d_z, h->n_total, nrhs, ld, h->d_int_row, z_dev);
+    AMS_CUDA_TRY(cudaGetLastError());
+    if (!h->opt.device_ptrs)
+        AMS_CUDA_TRY(cudaMemcpyAsync(z, z_dev, sizeof(double) * h->n_total * nrhs, cudaMemcpyDeviceToHost, h->stream));
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return AMS_OK;
+}
+
+ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y) {
+    g_last_error.clear();
+    AMS_TRY(check_solve_args(h, x, y, nrhs, 1.0));
+    if (h->nsys != 1) {
+        set_error("single-system handle required");
+        return AMS_ERR_INVALID_ARG;
+    }
+    const int ld = pow2ceil(nrhs);
+    AMS_TRY(ensure_work(h, ld));
+    RedCache* rc = nullptr;
+    AMS_TRY(get_red(h, ld, &rc));
+    LaunchCtx L = make_ctx(h, *rc);
+    L.st = nullptr;
+    const double* x_dev = nullptr;
+    AMS_TRY(stage_in(h, x, nrhs, h->d_stage_in, &x_dev));
+    launch_permute_in(h->stream, x_dev, h->n_total, nrhs, ld, h->d_int_row, h->d_p, nullptr);
+    launch_spmv_dot(L, h->d_p, h->d_q, 0);
+    h->launches += 3;
+    double* y_dev = h->opt.device_ptrs ? y : h->d_stage_out;
+    launch_permute_out(h->stream, h->d_q, h->n_total, nrhs, ld, h->d_int_row, y_dev);
+    AMS_CUDA_TRY(cudaGetLastError());
+    if (!h->opt.device_ptrs)
+        AMS_CUDA_TRY(cudaMemcpyAsync(y, y_dev, sizeof(double) * h->n_total * nrhs, cudaMemcpyDeviceToHost, h->stream));
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return AMS_OK;
+}
+
+ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* avg_ms, double* bytes) {
+    g_last_error.clear();
+    if (!h || reps <= 0 || which < 0 || which > 6 || h->ld_last == 0) {
+        set_error("invalid arguments (a solve must run first)");
+        return AMS_ERR_INVALID_ARG;
+    }
+    const int ld = h->ld_last;
+    RedCache* rc = nullptr;
+    AMS_TRY(get_red(h, ld, &rc));
+    LaunchCtx L = make_ctx(h, *rc);
+    // keep every (system, rhs) active and never converge while timing
+    {
+        std::vector<CgScalars> sc((size_t)h->nsys * ld);
+        AMS_CUDA_TRY(cudaMemcpy(sc.data(), h->d_sc, sizeof(CgScalars) * sc.size(), cudaMemcpyDeviceToHost));
+        for (auto& c : sc) {
+            c.active = 1;
+            if (!(c.pq > 0)) c.pq = 1.0;
+            if (!(c.rho > 0)) c.rho = 1.0;
+            c.fnorm2 = 1.0;
+        }
+        AMS_CUDA_TRY(cudaMemcpy(h->d_sc, sc.data(), sizeof(CgScalars) * sc.size(), cudaMemcpyHostToDevice));
+        SolveState st{};
+        AMS_CUDA_TRY(cudaMemcpy(h->d_st, &st, sizeof(st), cudaMemcpyHostToDevice));
+    }
+    const bool coarse = h->Nc > 0;
+    const double n = (double)h->n_total, nl = n * ld;
+    const double tf = (double)h->tf_bytes(), tp = (double)h->tp_bytes();
+    double b = 0.0;
+    switch (which) {
+        case 0: b = 12.0 * (double)h->nnz_total + 16.0 * nl + 8.0 * (double)h->n_pad / 32; break;
+        case 1: b = 48.0 * nl; break;
+        case 2: b = (double)h->fac_elems * tf + 8.0 * nl + tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf; break;
+        case 3: b = (double)h->R_elems * tf + 2.0 * (double)h->Nc * ld * tf; break;
+        case 4: b = (double)h->Q_elems * tf + 2.0 * (double)h->Nc * ld * tf; break;
+        case 5: b = tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf + 24.0 * nl; break;
+        case 6: b = 24.0 * nl; break;
+    }
+    auto launch = [&]() -> ams_status {
+        switch (which) {
+            case 0: launch_spmv_dot(L, h->d_p, h->d_q, 1); break;
+            case 1: launch_cg_update(L, h->d_x, h->d_r, h->d_p, h->d_q, 0.0, 0x7fffffff); break;
+            case 2: {
+                LocalSolveArgs la{h->stream, h->N, h->d_subs, h->d_r, nullptr, ld, h->cmax, std::max(1, h->mmax),
+                                  h->d_st};
+                AMS_CUDA_TRY(launch_local_solve(la, h->prec, h->d_fac, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
+                break;
+            }
+            case 3: {
+                CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_partial, h->d_cnt, h->d_st};
+                launch_coarse_gemm(cf, h->prec, ld, h->d_rc, h->d_yc);
+                break;
+            }
+            case 4: {
+                CoarseLaunch cb{h->stream, h->nbwd, h->d_bwd, h->d_Qmat, h->d_rng, h->d_partial, h->d_cnt, h->d_st};
+                launch_coarse_gemm(cb, h->prec, ld, h->d_yc, h->d_ec);
+                break;
+            }
+            case 5:
+                launch_prolong_dot(L, h->prec, h->d_psi, coarse ? h->d_ec : nullptr, h->d_zf, h->d_r, h->d_q, h->d_z,
+                                   h->flexible, 0, 1);
+                break;
+            case 6: launch_dir_update(L, h->d_p, h->d_z); break;
+        }
+        return AMS_OK;
+    };
+    AMS_TRY(launch());
+    cudaEvent_t e0, e1;
+    AMS_CUDA_TRY(cudaEventCreate(&e0));
+    AMS_CUDA_TRY(cudaEventCreate(&e1));
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    AMS_CUDA_TRY(cudaEventRecord(e0, h->stream));
+    for (int k = 0; k < reps; ++k) AMS_TRY(launch());
+    AMS_CUDA_TRY(cudaEventRecord(e1, h->stream));
+    AMS_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    AMS_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    AMS_CUDA_TRY(cudaGetLastError());
+    if (avg_ms) *avg_ms = ms / reps;
+    if (bytes) *bytes = b;
+    return AMS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,717 @@
+// Solve-phase kernels of the AMS-preconditioned CG (one GPU, sm_103a).
+//
+// Per iteration (Section 3.1 preconditioner inside CG):
+//   k_spmv_dot      q = A p and p.q                    (CSR SpMV, SELL-32 layout)
+//   k_cg_update     x += alpha p, r -= alpha q, r.r, convergence
+//   k_local_solve   z_f = sum_i R_i^T A_i^{-1} R_i r  and  r_c = R_0 r
+//   k_coarse_gemm   y = L_c^{-1} r_c, then e_c = L_c^{-T} y  (A_0 = L_c L_c^T)
+//   k_prolong_dot   z = z_f + R_0^T e_c, r.z (and z.q for flexible CG), beta
+//   k_dir_update    p = z + beta p
+#include <cstdint>
+#include <cstdio>
+
+#include "ams_internal.h"
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace ams {
+
+// ===========================================================================
+// a1: SpMV q = A p with fused p.q  (SELL-32: slice s = rows 32s..32s+31,
+// entry j of lane l at sell_ptr[s] + 32 j + l; padded entries have value 0)
+// ===========================================================================
+template <int LD>
+__global__ void __launch_bounds__(kRedThreads)
+k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sell_col,
+           const double* __restrict__ sell_val, const double* __restrict__ p,
+           double* __restrict__ q, RedLayout R, CgScalars* sc, SolveState* st, int nseg,
+           int with_dot) {
+    if (st != nullptr && st->done) return;
+    __shared__ double s_out[2 * kMaxLd];
+    __shared__ double s_scr[kRedThreads];
+    const int64_t base = (int64_t)blockIdx.x * kRedElems;
+    double dot[1] = {0.0};
+#pragma unroll 4
+    for (int k = 0; k < kRedElems / kRedThreads; ++k) {
+        const int64_t e = base + threadIdx.x + k * kRedThreads;
+        const int64_t row = e / LD;
+        const int rhs = (int)(e % LD);
+        const int64_t s = row >> 5;
+        const int lane = (int)(row & 31);
+        const int64_t b0 = __ldg(sell_ptr + s), b1 = __ldg(sell_ptr + s + 1);
+        const int w = (int)((b1 - b0) >> 5);
+        double acc = 0.0;
+        for (int j = 0; j < w; ++j) {
+            const int64_t o = b0 + 32 * j + lane;
+            acc += __ldg(sell_val + o) * __ldg(p + (int64_t)__ldg(sell_col + o) * LD + rhs);
+        }
+        q[e] = acc;
+        dot[0] += p[e] * acc;
+    }
+    if (!with_dot) return;
+    int seg;
+    if (!seg_reduce<1>(dot, LD, R, s_out, s_scr, seg)) return;
+    if (threadIdx.x < LD) {
+        CgScalars& c = sc[seg * LD + threadIdx.x];
+        c.pq = s_out[threadIdx.x];
+        if (c.active && !(c.pq > 0.0 && isfinite(c.pq))) {
+            st->status = AMS_ERR_BREAKDOWN;
+            st->done = 1;
+        }
+    }
+}
+
+// ===========================================================================
+// a2: x += alpha p ; r -= alpha q ; r.r ; convergence test per (system, rhs)
+// ===========================================================================
+template <int LD>
+__global__ void __launch_bounds__(kRedThreads)
+k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
+            const double* __restrict__ q, RedLayout R, CgScalars* sc, SolveState* st,
+            int nseg, double rtol2, int maxit) {
+    if (st->done) return;
+    __shared__ double s_out[2 * kMaxLd];
+    __shared__ double s_scr[kRedThreads];
+    const int64_t base = (int64_t)blockIdx.x * kRedElems;
+    const int seg = R.blk_seg[blockIdx.x];
+    const int rhs = threadIdx.x % LD;
+    const CgScalars c = sc[seg * LD + rhs];
+    const double alpha = c.active ? c.rho / c.pq : 0.0;
+    double rr[1] = {0.0};
+#pragma unroll 4
+    for (int k = 0; k < kRedElems / kRedThreads; ++k) {
+        const int64_t e = base + threadIdx.x + k * kRedThreads;
+        x[e] += alpha * p[e];
+        const double rv = r[e] - alpha * q[e];
+        r[e] = rv;
+        rr[0] += rv * rv;
+    }
+    int sg;
+    if (!seg_reduce<1>(rr, LD, R, s_out, s_scr, sg)) return;
+    const int it = st->it;
+    if (threadIdx.x < LD) {
+        CgScalars& cs = sc[sg * LD + threadIdx.x];
+        cs.rr = s_out[threadIdx.x];
+        if (cs.active) {
+            cs.alpha = cs.rho / cs.pq;
+            cs.iters = it + 1;
+            if (!isfinite(cs.rr)) {
+                st->status = AMS_ERR_BREAKDOWN;
+                st->done = 1;
+            } else if (cs.rr <= rtol2 * cs.fnorm2) {
+                cs.active = 0;
+            }
+        }
+    }
+    if (!last_system(R, nseg)) return;
+    if (threadIdx.x == 0) {
+        int nact = 0;
+        for (int i = 0; i < nseg * LD; ++i) nact += sc[i].active;
+        st->nactive = nact;
+        st->it = it + 1;
+        if (nact == 0 || it + 1 >= maxit) st->done = 1;
+    }
+}
+
+// ===========================================================================
+// a3+a4: local solves z_f = A_i^{-1} r_i for every subdomain (one thread
+// block per subdomain, warps split the right-hand sides, NR per warp), with
+// the restriction r_c = Psi_i^T r_i accumulated on the way.
+//
+// Forward sweep over block rows K = 0..nb-1 (lane = row of the block):
+//   t   = r_K - sum_{d<c} L_{K,K-c+d} y_{K-c+d}
+//   y_K = L_KK^{-1} t
+// Backward sweep K = nb-1..0 (lane = column of the block):
+//   w   = y_K - sum_{d=1..c} L_{K+d,K}^T x_{K+d}
+//   x_K = L_KK^{-T} w
+// Factor block rows are staged through shared memory with cp.async in a
+// ring of c+2 buffers; y is kept in z_f between the sweeps.
+// ===========================================================================
+template <typename TF, typename TP, int NR, int MM>
+__global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __restrict__ fac,
+                              const double* __restrict__ rin, const double* __restrict__ rowscale,
+                              TF* __restrict__ zf, const TP* __restrict__ psi, TF* __restrict__ rc,
+                              int ld, int cmax, const SolveState* st) {
+    if (st != nullptr && st->done) return;
+    using A = typename Acc<TF>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SubInfo S = subs[blockIdx.x];
+    const int c = S.c, nb = S.nb, n = S.n;
+    const int nbuf = c + 2;
+    const int64_t brs = blockrow_elems(c);
+    const int64_t brs_max = blockrow_elems(cmax);
+    TF* bufs = (TF*)smem_raw;                                  // nbuf_max * brs_max
+    TF* ring = bufs + (int64_t)(cmax + 2) * brs_max;           // (cmax+1) * 32 * ld
+    TF* tmp = ring + (int64_t)(cmax + 1) * 32 * ld;            // 32 * ld
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int rhs0 = warp * NR;
+    const TF* F = fac + S.fac_off;
+    const int m = S.m;
+
+    A racc[MM][NR];
+#pragma unroll
+    for (int k = 0; k < MM; ++k)
+#pragma unroll
+        for (int j = 0; j < NR; ++j) racc[k][j] = A(0);
+
+    // ---------------- forward ----------------
+    block_copy_async(bufs, F, brs * sizeof(TF));
+    cp_async_commit();
+    for (int K = 0; K < nb; ++K) {
+        if (K + 1 < nb) {
+            block_copy_async(bufs + (int64_t)((K + 1) % nbuf) * brs_max, F + (int64_t)(K + 1) * brs,
+                             brs * sizeof(TF));
+            cp_async_commit();
+            cp_async_wait_1();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const TF* B = bufs + (int64_t)(K % nbuf) * brs_max;
+        const int row = K * 32 + lane;
+        A t[NR];
+        const bool valid = row < n;
+        const int64_t grow = S.row0 + row;
+        const double sc = (rowscale != nullptr && valid) ? rowscale[grow] : 1.0;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) t[j] = valid ? (A)(rin[grow * ld + rhs0 + j] * sc) : A(0);
+        if (rc != nullptr && valid) {
+#pragma unroll
+            for (int k = 0; k < MM; ++k) {
+                if (k < m) {
+                    const A pv = (A)to_d(psi[S.psi_off + (int64_t)row * m + k]);
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) racc[k][j] += pv * t[j];
+                }
+            }
+        }
+        for (int d = 0; d < c; ++d) {
+            const int src = K - c + d;
+            if (src < 0) continue;
+            const TF* T = B + d * 1024;
+            const TF* ys = ring + (int64_t)(src % (c + 1)) * 32 * ld + rhs0;
+#pragma unroll 8
+            for (int q = 0; q < 32; ++q) {
+                A coef = (A)T[tile_idx(lane, q)];
+                if (d == 0 && q < lane) coef = A(0);
+#pragma unroll
+                for (int j = 0; j < NR; ++j) t[j] -= coef * (A)ys[q * ld + j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NR; ++j) tmp[lane * ld + rhs0 + j] = (TF)t[j];
+        __syncwarp();
+        const A piv = (A)B[c * 1024 + lane];
+        A y[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) y[j] = piv * t[j];
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) {
+            const A coef = q < lane ? (A)B[tile_idx(lane, q)] : A(0);
+#pragma unroll
+            for (int j = 0; j < NR; ++j) y[j] += coef * (A)tmp[q * ld + rhs0 + j];
+        }
+        TF* yr = ring + (int64_t)(K % (c + 1)) * 32 * ld + rhs0;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) yr[lane * ld + j] = (TF)y[j];
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) zf[grow * ld + rhs0 + j] = (TF)y[j];
+        }
+        __syncthreads();
+    }
+    // restriction: reduce over lanes, lane 0 writes r_c rows of this subdomain
+    if (rc != nullptr) {
+#pragma unroll
+        for (int k = 0; k < MM; ++k) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                A v = racc[k][j];
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if (lane == 0 && k < m) rc[(S.coff + k) * ld + rhs0 + j] = (TF)v;
+            }
+        }
+    }
+    // ---------------- backward ----------------
+    block_copy_async(bufs + (int64_t)((nb - 1) % nbuf) * brs_max, F + (int64_t)(nb - 1) * brs,
+                     brs * sizeof(TF));
+    cp_async_commit();
+    for (int K = nb - 1; K >= 0; --K) {
+        if (K - 1 >= 0) {
+            block_copy_async(bufs + (int64_t)((K - 1) % nbuf) * brs_max, F + (int64_t)(K - 1) * brs,
+                             brs * sizeof(TF));
+            cp_async_commit();
+            cp_async_wait_1();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const int row = K * 32 + lane;
+        const bool valid = row < n;
+        const int64_t grow = S.row0 + row;
+        A w[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) w[j] = valid ? (A)zf[grow * ld + rhs0 + j] : A(0);
+        for (int d = 1; d <= c; ++d) {
+            const int src = K + d;
+            if (src >= nb) break;
+            const TF* Bs = bufs + (int64_t)(src % nbuf) * brs_max;
+            const TF* T = (d < c) ? Bs + (c - d) * 1024 : Bs;
+            const TF* xs = ring + (int64_t)(src % (c + 1)) * 32 * ld + rhs0;
+#pragma unroll 8
+            for (int r = 0; r < 32; ++r) {
+                A coef = (A)T[tile_idx(r, lane)];
+                if (d == c && r > lane) coef = A(0);
+#pragma unroll
+                for (int j = 0; j < NR; ++j) w[j] -= coef * (A)xs[r * ld + j];
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < NR; ++j) tmp[lane * ld + rhs0 + j] = (TF)w[j];
+        __syncwarp();
+        const TF* B = bufs + (int64_t)(K % nbuf) * brs_max;
+        const A piv = (A)B[c * 1024 + lane];
+        A x[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) x[j] = piv * w[j];
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+            const A coef = r > lane ? (A)B[tile_idx(r, lane)] : A(0);
+#pragma unroll
+            for (int j = 0; j < NR; ++j) x[j] += coef * (A)tmp[r * ld + rhs0 + j];
+        }
+        TF* xr = ring + (int64_t)(K % (c + 1)) * 32 * ld + rhs0;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) xr[lane * ld + j] = (TF)x[j];
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) zf[grow * ld + rhs0 + j] = (TF)x[j];
+        }
+        __syncthreads();
+    }
+}
+
+// ===========================================================================
+// a5: coarse solve by blocks of L_c^{-1} (nested-dissection layout).
+// Each item multiplies a <=32-row tile of one node matrix by a gathered
+// chunk of the input; several chunks of one tile are summed in chunk order
+// by the last item to finish (deterministic split-K).
+// ===========================================================================
+template <typename TF, int LD>
+__global__ void __launch_bounds__(256)
+k_coarse_gemm(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
+              const int32_t* __restrict__ rng, const TF* __restrict__ in, TF* __restrict__ out,
+              TF* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
+    if (st != nullptr && st->done) return;
+    using A = typename Acc<TF>::type;
+    constexpr int KC = 64;                                   // columns per stage
+    constexpr int OUT = 32 * LD;                             // outputs of a tile
+    constexpr int KG = OUT >= 256 ? 1 : 256 / OUT;           // k-groups (small LD)
+    constexpr int OPT = OUT >= 256 ? OUT / 256 : 1;          // outputs per thread
+    __shared__ TF sM[32][KC + 1];
+    __shared__ TF sX[KC][LD];
+    __shared__ A sRed[256];
+    __shared__ int s_last;
+    const CoarseItem it = items[blockIdx.x];
+    const int t = threadIdx.x;
+    const int kg = t / (OUT >= 256 ? 256 : OUT);
+    const int o0 = t % (OUT >= 256 ? 256 : OUT);
+    A acc[OPT];
+#pragma unroll
+    for (int i = 0; i < OPT; ++i) acc[i] = A(0);
+    const TF* M0 = mat + it.moff + (int64_t)it.row_in_node * it.K;
+    for (int kb = it.k0; kb < it.k1; kb += KC) {
+        const int kn = min(KC, it.k1 - kb);
+        for (int i = t; i < 32 * KC; i += 256) {
+            const int r = i / KC, kk = i % KC;
+            sM[r][kk] = (r < it.nrows && kk < kn) ? M0[(int64_t)r * it.K + kb + kk] : TF(0);
+        }
+        for (int i = t; i < KC * LD; i += 256) {
+            const int kk = i / LD, h = i % LD;
+            TF v = TF(0);
+            if (kk < kn) {
+                int k = kb + kk, g = -1;
+                for (int j = 0; j < it.nrng; ++j) {
+                    const int s0 = rng[2 * (it.rng_off + j)], len = rng[2 * (it.rng_off + j) + 1];
+                    if (k < len) { g = s0 + k; break; }
+                    k -= len;
+                }
+                v = in[(int64_t)g * LD + h];
+            }
+            sX[kk][h] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < OPT; ++i) {
+            const int o = o0 + i * 256;
+            const int r = o / LD, h = o % LD;
+            A s = acc[i];
+            for (int kk = kg; kk < KC; kk += KG) s += (A)sM[r][kk] * (A)sX[kk][h];
+            acc[i] = s;
+        }
+        __syncthreads();
+    }
+    if (KG > 1) {
+        sRed[t] = acc[0];
+        __syncthreads();
+        if (t < OUT) {
+            A s = A(0);
+            for (int g = 0; g < KG; ++g) s += sRed[g * OUT + t];
+            acc[0] = s;
+        }
+        __syncthreads();
+    }
+    const bool owner = (KG > 1) ? (t < OUT) : true;
+    if (it.nchunks == 1) {
+        if (owner) {
+#pragma unroll
+            for (int i = 0; i < OPT; ++i) {
+                const int o = o0 + i * 256;
+                const int r = o / LD, h = o % LD;
+                if (r < it.nrows) out[(int64_t)(it.out0 + r) * LD + h] = (TF)acc[i];
+            }
+        }
+        return;
+    }
+    TF* P = partial + (int64_t)(it.slot0 + it.chunk) * OUT;
+    if (owner) {
+#pragma unroll
+        for (int i = 0; i < OPT; ++i) P[o0 + i * 256] = (TF)acc[i];
+    }
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = (atomicAdd(cnt + it.tile_id, 1) == it.nchunks - 1);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int o = t; o < OUT; o += 256) {
+        A s = A(0);
+        for (int ch = 0; ch < it.nchunks; ++ch) s += (A)__ldcg(partial + (int64_t)(it.slot0 + ch) * OUT + o);
+        const int r = o / LD, h = o % LD;
+        if (r < it.nrows) out[(int64_t)(it.out0 + r) * LD + h] = (TF)s;
+    }
+    if (t == 0) cnt[it.tile_id] = 0;
+}
+
+// ===========================================================================
+// a6+a7: z = z_f + Psi e_c ; r.z and (flexible CG) z.q ; beta
+// ===========================================================================
+template <typename TF, typename TP, int LD>
+__global__ void __launch_bounds__(kRedThreads)
+k_prolong_dot(const int32_t* __restrict__ sub_of_row, const SubInfo* __restrict__ subs,
+              const TP* __restrict__ psi, const TF* __restrict__ ec, const TF* __restrict__ zf,
+              const double* __restrict__ r, const double* __restrict__ q, double* __restrict__ z,
+              RedLayout R, CgScalars* sc, SolveState* st, int nseg, int flexible, int first,
+              int with_dot) {
+    if (st != nullptr && st->done) return;
+    __shared__ double s_out[2 * kMaxLd];
+    __shared__ double s_scr[kRedThreads];
+    const int64_t base = (int64_t)blockIdx.x * kRedElems;
+    double v[2] = {0.0, 0.0};
+#pragma unroll 2
+    for (int k = 0; k < kRedElems / kRedThreads; ++k) {
+        const int64_t e = base + threadIdx.x + k * kRedThreads;
+        const int64_t row = e / LD;
+        const int rhs = (int)(e % LD);
+        const int s = sub_of_row[row];
+        double zv = 0.0;
+        if (s >= 0) {
+            const SubInfo S = subs[s];
+            const int64_t lr = row - S.row0;
+            double acc = to_d(zf[e]);
+            if (ec != nullptr) {
+                const TP* pr = psi + S.psi_off + lr * S.m;
+                const TF* er = ec + S.coff * LD + rhs;
+                typename Acc<TF>::type pe = 0;
+                for (int kk = 0; kk < S.m; ++kk) pe += (typename Acc<TF>::type)to_d(pr[kk]) * er[(int64_t)kk * LD];
+                acc += (double)pe;
+            }
+            zv = acc;
+        }
+        z[e] = zv;
+        if (with_dot) {
+            v[0] += r[e] * zv;
+            if (flexible && !first) v[1] += zv * q[e];
+        }
+    }
+    if (!with_dot) return;
+    int sg;
+    if (!seg_reduce<2>(v, LD, R, s_out, s_scr, sg)) return;
+    if (threadIdx.x < LD) {
+        CgScalars& c = sc[sg * LD + threadIdx.x];
+        const double rz = s_out[threadIdx.x];
+        const double zq = s_out[LD + threadIdx.x];
+        if (first) {
+            c.beta = 0.0;
+        } else if (c.active) {
+            c.beta = flexible ? -(c.rho / c.pq) * zq / c.rho : rz / c.rho;
+        } else {
+            c.beta = 0.0;
+        }
+        if (c.active && !isfinite(rz)) {
+            st->status = AMS_ERR_BREAKDOWN;
+            st->done = 1;
+        }
+        c.zq = zq;
+        c.rho = rz;
+    }
+}
+
+// p = z + beta p  (first application: p = z)
+template <int LD>
+__global__ void __launch_bounds__(kRedThreads)
+k_dir_update(double* __restrict__ p, const double* __restrict__ z, const int32_t* __restrict__ blk_seg,
+             const CgScalars* sc, const SolveState* st) {
+    if (st->done) return;
+    const int64_t base = (int64_t)blockIdx.x * kRedElems;
+    const int seg = blk_seg[blockIdx.x];
+    const int rhs = threadIdx.x % LD;
+    const CgScalars c = sc[seg * LD + rhs];
+    if (!c.active) return;
+    const double beta = c.beta;
+#pragma unroll 4
+    for (int k = 0; k < kRedElems / kRedThreads; ++k) {
+        const int64_t e = base + threadIdx.x + k * kRedThreads;
+        p[e] = z[e] + beta * p[e];
+    }
+}
+
+// ||f||^2 per (system, rhs) and CG scalar initialisation
+template <int LD>
+__global__ void __launch_bounds__(kRedThreads)
+k_init_norms(const double* __restrict__ r, RedLayout R, CgScalars* sc, SolveState* st, int nseg,
+             int nrhs) {
+    __shared__ double s_out[2 * kMaxLd];
+    __shared__ double s_scr[kRedThreads];
+    const int64_t base = (int64_t)blockIdx.x * kRedElems;
+    double v[1] = {0.0};
+    for (int k = 0; k < kRedElems / kRedThreads; ++k) {
+        const int64_t e = base + threadIdx.x + k * kRedThreads;
+        v[0] += r[e] * r[e];
+    }
+    int sg;
+    if (!seg_reduce<1>(v, LD, R, s_out, s_scr, sg)) return;
+    if (threadIdx.x < LD) {
+        CgScalars& c = sc[sg * LD + threadIdx.x];
+        c.fnorm2 = s_out[threadIdx.x];
+        c.rr = c.fnorm2;
+        c.rho = 0.0;
+        c.pq = 0.0;
+        c.zq = 0.0;
+        c.alpha = 0.0;
+        c.beta = 0.0;
+        c.iters = 0;
+        c.active = (threadIdx.x < nrhs && c.fnorm2 > 0.0) ? 1 : 0;
+    }
+    if (!last_system(R, nseg)) return;
+    if (threadIdx.x == 0) {
+        int nact = 0;
+        for (int i = 0; i < nseg * LD; ++i) nact += sc[i].active;
+        st->nactive = nact;
+        st->it = 0;
+        st->status = 0;
+        st->done = (nact == 0);
+    }
+}
+
+// caller order (col-major n x nrhs) <-> internal node-major rows
+__global__ void k_permute_in(const double* __restrict__ f, int64_t n, int nrhs, int ld,
+                             const int64_t* __restrict__ int_row, double* __restrict__ r,
+                             double scale_zero_x, double* __restrict__ x) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t row = int_row[i];
+    for (int k = 0; k < ld; ++k) {
+        r[row * ld + k] = k < nrhs ? f[i + (int64_t)k * n] : 0.0;
+        if (x != nullptr) x[row * ld + k] = 0.0;
+    }
+}
+
+__global__ void k_permute_out(const double* __restrict__ x, int64_t n, int nrhs, int ld,
+                              const int64_t* __restrict__ int_row, double* __restrict__ u) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t row = int_row[i];
+    for (int k = 0; k < nrhs; ++k) u[i + (int64_t)k * n] = x[row * ld + k];
+}
+
+// a8: dvals[e] = - sum_k lambda_k[row_e] u_k[col_e]  (caller CSR order)
+__global__ void k_sddmm(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind,
+                        int64_t n, int nrhs, const double* __restrict__ lam,
+                        const double* __restrict__ u, double* __restrict__ dvals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int64_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        const int64_t j = colind[e];
+        double s = 0.0;
+        for (int k = 0; k < nrhs; ++k) s += lam[i + (int64_t)k * n] * u[j + (int64_t)k * n];
+        dvals[e] = -s;
+    }
+}
+
+__global__ void k_zero(double* __restrict__ a, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) a[i] = 0.0;
+}
+
+// ===========================================================================
+// host launchers
+// ===========================================================================
+#define AMS_DISPATCH_LD(ld, F, ...)                     \
+    switch (ld) {                                        \
+        case 1: F<1>(__VA_ARGS__); break;                \
+        case 2: F<2>(__VA_ARGS__); break;                \
+        case 4: F<4>(__VA_ARGS__); break;                \
+        case 8: F<8>(__VA_ARGS__); break;                \
+        case 16: F<16>(__VA_ARGS__); break;              \
+        default: F<32>(__VA_ARGS__); break;              \
+    }
+
+template <int LD>
+static void spmv_ld(const LaunchCtx& L, const double* p, double* q, int with_dot) {
+    k_spmv_dot<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(L.sell_ptr, L.sell_col, L.sell_val, p, q,
+                                                         L.red, L.sc, L.st, L.nseg, with_dot);
+}
+void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_dot) {
+    AMS_DISPATCH_LD(L.ld, spmv_ld, L, p, q, with_dot);
+}
+
+template <int LD>
+static void update_ld(const LaunchCtx& L, double* x, double* r, const double* p, const double* q,
+                      double rtol2, int maxit) {
+    k_cg_update<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(x, r, p, q, L.red, L.sc, L.st, L.nseg,
+                                                          rtol2, maxit);
+}
+void launch_cg_update(const LaunchCtx& L, double* x, double* r, const double* p, const double* q,
+                      double rtol2, int maxit) {
+    AMS_DISPATCH_LD(L.ld, update_ld, L, x, r, p, q, rtol2, maxit);
+}
+
+template <int LD>
+static void dir_ld(const LaunchCtx& L, double* p, const double* z) {
+    k_dir_update<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(p, z, L.red.blk_seg, L.sc, L.st);
+}
+void launch_dir_update(const LaunchCtx& L, double* p, const double* z) {
+    AMS_DISPATCH_LD(L.ld, dir_ld, L, p, z);
+}
+
+template <int LD>
+static void norms_ld(const LaunchCtx& L, const double* r, int nrhs) {
+    k_init_norms<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(r, L.red, L.sc, L.st, L.nseg, nrhs);
+}
+void launch_init_norms(const LaunchCtx& L, const double* r, int nrhs) {
+    AMS_DISPATCH_LD(L.ld, norms_ld, L, r, nrhs);
+}
+
+size_t local_solve_smem(int cmax, int ld, size_t tf_bytes) {
+    return ((size_t)(cmax + 2) * blockrow_elems(cmax) + (size_t)(cmax + 1) * 32 * ld + 32 * ld) * tf_bytes;
+}
+
+template <typename TF, typename TP, int NR, int MM>
+static cudaError_t local_nr(const LocalSolveArgs& a, const void* fac, const void* psi, void* zf,
+                            void* rc) {
+    const int warps = a.ld / NR;
+    const size_t smem = local_solve_smem(a.cmax, a.ld, sizeof(TF));
+    auto kern = k_local_solve<TF, TP, NR, MM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<a.nsub, warps * 32, smem, a.stream>>>(a.subs, (const TF*)fac, a.rin, a.rowscale, (TF*)zf,
+                                                  (const TP*)psi, (TF*)rc, a.ld, a.cmax, a.st);
+    return cudaGetLastError();
+}
+
+template <typename TF, typename TP>
+static cudaError_t local_tp(const LocalSolveArgs& a, const void* fac, const void* psi, void* zf, void* rc) {
+    const bool big = a.mmax > 8;
+    const int nrmax = sizeof(TF) == 8 ? (big ? 2 : 4) : (big ? 4 : 8);
+    const int nr = a.ld < nrmax ? a.ld : nrmax;
+    if (big) {
+        switch (nr) {
+            case 1: return local_nr<TF, TP, 1, 16>(a, fac, psi, zf, rc);
+            case 2: return local_nr<TF, TP, 2, 16>(a, fac, psi, zf, rc);
+            default: return local_nr<TF, TP, 4, 16>(a, fac, psi, zf, rc);
+        }
+    }
+    switch (nr) {
+        case 1: return local_nr<TF, TP, 1, 8>(a, fac, psi, zf, rc);
+        case 2: return local_nr<TF, TP, 2, 8>(a, fac, psi, zf, rc);
+        case 4: return local_nr<TF, TP, 4, 8>(a, fac, psi, zf, rc);
+        default: return local_nr<TF, TP, 8, 8>(a, fac, psi, zf, rc);
+    }
+}
+
+cudaError_t launch_local_solve(const LocalSolveArgs& a, int prec, const void* fac, const void* psi,
+                               void* zf, void* rc) {
+    if (prec == AMS_PREC_FP64) return local_tp<double, double>(a, fac, psi, zf, rc);
+    if (prec == AMS_PREC_FP32) return local_tp<float, float>(a, fac, psi, zf, rc);
+    return local_tp<float, __nv_bfloat16>(a, fac, psi, zf, rc);
+}
+
+template <typename TF, int LD>
+static void coarse_ld(const CoarseLaunch& c, const void* in, void* out) {
+    if (c.nitems == 0) return;
+    k_coarse_gemm<TF, LD><<<c.nitems, 256, 0, c.stream>>>(c.items, (const TF*)c.mat, c.rng,
+                                                          (const TF*)in, (TF*)out, (TF*)c.partial,
+                                                          c.cnt, c.st);
+}
+template <typename TF>
+static void coarse_tf(const CoarseLaunch& c, int ld, const void* in, void* out) {
+    switch (ld) {
+        case 1: coarse_ld<TF, 1>(c, in, out); break;
+        case 2: coarse_ld<TF, 2>(c, in, out); break;
+        case 4: coarse_ld<TF, 4>(c, in, out); break;
+        case 8: coarse_ld<TF, 8>(c, in, out); break;
+        case 16: coarse_ld<TF, 16>(c, in, out); break;
+        default: coarse_ld<TF, 32>(c, in, out); break;
+    }
+}
+void launch_coarse_gemm(const CoarseLaunch& c, int prec, int ld, const void* in, void* out) {
+    if (prec == AMS_PREC_FP64) coarse_tf<double>(c, ld, in, out);
+    else coarse_tf<float>(c, ld, in, out);
+}
+
+template <typename TF, typename TP, int LD>
+static void prolong_ld(const LaunchCtx& L, const void* psi, const void* ec, const void* zf,
+                       const double* r, const double* q, double* z, int flexible, int first, int with_dot) {
+    k_prolong_dot<TF, TP, LD><<<L.nblk, kRedThreads, 0, L.stream>>>(
+        L.sub_of_row, L.subs, (const TP*)psi, (const TF*)ec, (const TF*)zf, r, q, z, L.red, L.sc, L.st,
+        L.nseg, flexible, first, with_dot);
+}
+template <typename TF, typename TP>
+static void prolong_tp(const LaunchCtx& L, const void* psi, const void* ec, const void* zf,
+                       const double* r, const double* q, double* z, int flexible, int first, int with_dot) {
+    switch (L.ld) {
+        case 1: prolong_ld<TF, TP, 1>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
+        case 2: prolong_ld<TF, TP, 2>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
+        case 4: prolong_ld<TF, TP, 4>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
+        case 8: prolong_ld<TF, TP, 8>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
+        case 16: prolong_ld<TF, TP, 16>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
+        default: prolong_ld<TF, TP, 32>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
+    }
+}
+void launch_prolong_dot(const LaunchCtx& L, int prec, const void* psi, const void* ec, const void* zf,
+                        const double* r, const double* q, double* z, int flexible, int first,
+                        int with_dot) {
+    if (prec == AMS_PREC_FP64) prolong_tp<double, double>(L, psi, ec, zf, r, q, z, flexible, first, with_dot);
+    else if (prec == AMS_PREC_FP32) prolong_tp<float, float>(L, psi, ec, zf, r, q, z, flexible, first, with_dot);
+    else prolong_tp<float, __nv_bfloat16>(L, psi, ec, zf, r, q, z, flexible, first, with_dot);
+}
+
+void launch_permute_in(cudaStream_t s, const double* f, int64_t n, int nrhs, int ld,
+                       const int64_t* int_row, double* r, double* x) {
+    k_permute_in<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f, n, nrhs, ld, int_row, r, 0.0, x);
+}
+void launch_permute_out(cudaStream_t s, const double* x, int64_t n, int nrhs, int ld,
+                        const int64_t* int_row, double* u) {
+    k_permute_out<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, nrhs, ld, int_row, u);
+}
+void launch_sddmm(cudaStream_t s, const int64_t* rowptr, const int32_t* colind, int64_t n, int nrhs,
+                  const double* lam, const double* u, double* dvals) {
+    k_sddmm<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(rowptr, colind, n, nrhs, lam, u, dvals);
+}
+void launch_zero(cudaStream_t s, double* a, int64_t n) {
+    if (n > 0) k_zero<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n);
+}
+
+}  // namespace ams

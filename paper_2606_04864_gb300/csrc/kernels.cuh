@@ -1,0 +1,174 @@
+// Device helpers shared by the AMS kernels: deterministic segmented
+// reductions, asynchronous shared-memory copies, small conversions.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include "ams_internal.h"
+
+namespace ams {
+
+// ---------------------------------------------------------------------------
+// conversions of stored operands
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(double v) { return (float)v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_d(float v) { return (double)v; }
+__device__ __forceinline__ double to_d(double v) { return v; }
+__device__ __forceinline__ double to_d(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
+
+template <typename T> struct Acc { using type = float; };
+template <> struct Acc<double> { using type = double; };
+
+template <typename T> __device__ __forceinline__ T from_d(double v);
+template <> __device__ __forceinline__ float from_d<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
+
+// ---------------------------------------------------------------------------
+// cp.async (16-byte, L2-only) staging into shared memory
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+// Copy `bytes` (multiple of 16, both addresses 16-byte aligned) with the
+// whole thread block.
+__device__ __forceinline__ void block_copy_async(void* smem, const void* gmem, int64_t bytes) {
+    const int64_t n16 = bytes >> 4;
+    char* s = (char*)smem;
+    const char* g = (const char*)gmem;
+    for (int64_t i = threadIdx.x; i < n16; i += blockDim.x) cp_async16(s + 16 * i, g + 16 * i);
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic segmented reduction.
+//
+// A "reduction block" covers kRedElems consecutive elements of a node-major
+// vector (rows of a single system, since systems are padded to kRowAlign
+// rows).  Each thread block of a reduction kernel handles one reduction
+// block and produces NV partial values per right-hand side.  Partials are
+// summed in a fixed order in two levels: groups of kRedGroup blocks (the
+// last block of a group to finish sums the group), then all groups of a
+// system (the last group to finish sums them and calls the finisher).  The
+// order of every floating-point sum is fixed, so results are bitwise
+// reproducible.
+// ---------------------------------------------------------------------------
+struct RedLayout {
+    const int32_t* blk_seg;    // reduction block -> system
+    const int32_t* seg_blk0;   // system -> first reduction block
+    const int32_t* seg_nblk;   // system -> number of reduction blocks
+    const int32_t* seg_grp0;   // system -> first group
+    double* part1;             // [nblk][NV][ld]
+    double* part2;             // [ngroups][NV][ld]
+    int32_t* cnt1;             // [ngroups]   zero at rest
+    int32_t* cnt2;             // [nseg]      zero at rest
+    int32_t* cnt3;             // [1]         zero at rest (systems finished)
+};
+
+// Sum `count` vectors of `nv` doubles (vector j at src + j*stride) in a
+// fixed order using all threads of the block; result lands in dst[0..nv).
+// Requires nv <= blockDim.x.  Uses `scratch` (blockDim.x doubles).
+__device__ inline void block_sum_vectors(const double* src, int count, int64_t stride, int nv,
+                                         double* dst, double* scratch) {
+    const int t = threadIdx.x;
+    const int lanes_per = blockDim.x / nv;        // threads per value
+    const int v = t % nv;
+    const int part = t / nv;
+    double s = 0.0;
+    if (part < lanes_per) {
+        for (int j = part; j < count; j += lanes_per) s += __ldcg(src + (int64_t)j * stride + v);
+    }
+    scratch[t] = s;
+    __syncthreads();
+    if (t < nv) {
+        double tot = 0.0;
+        for (int p = 0; p < lanes_per; ++p) tot += scratch[p * nv + t];
+        dst[t] = tot;
+    }
+    __syncthreads();
+}
+
+// Reduce per-thread partials `val[NV]` (thread t's right-hand side is
+// t % ld) to per-block totals, then run the two-level cross-block sum.
+// Returns true in exactly one thread block per system, after which
+// `out[v*ld + rhs]` (shared memory, NV*ld doubles) holds the system totals
+// for every thread of that block.
+template <int NV>
+__device__ bool seg_reduce(const double (&val)[NV], int ld, const RedLayout& R, double* out,
+                           double* scratch, int& seg_out) {
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int warp = t >> 5;
+    const int nwarp = blockDim.x >> 5;
+    __shared__ int s_last;
+    // 1) block totals per (v, rhs)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        double x = val[v];
+        for (int off = 16; off >= ld; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        // lanes 0..ld-1 hold the warp sums for rhs = lane
+        if (lane < ld) scratch[warp * 32 + lane] = x;
+        __syncthreads();
+        if (t < ld) {
+            double s = 0.0;
+            for (int w = 0; w < nwarp; ++w) s += scratch[w * 32 + t];
+            out[v * ld + t] = s;
+        }
+        __syncthreads();
+    }
+    const int b = blockIdx.x;
+    const int seg = R.blk_seg[b];
+    seg_out = seg;
+    const int lb = b - R.seg_blk0[seg];
+    const int g = R.seg_grp0[seg] + lb / kRedGroup;
+    const int gsize = min(kRedGroup, R.seg_nblk[seg] - (lb / kRedGroup) * kRedGroup);
+    const int nvl = NV * ld;
+    if (t < nvl) R.part1[(int64_t)b * nvl + t] = out[t];
+    __threadfence();
+    __syncthreads();
+    if (t == 0) s_last = (atomicAdd(R.cnt1 + g, 1) == gsize - 1);
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    // 2) group sum
+    const int gb0 = R.seg_blk0[seg] + (lb / kRedGroup) * kRedGroup;
+    block_sum_vectors(R.part1 + (int64_t)gb0 * nvl, gsize, nvl, nvl, out, scratch);
+    if (t == 0) R.cnt1[g] = 0;
+    if (t < nvl) R.part2[(int64_t)g * nvl + t] = out[t];
+    __threadfence();
+    __syncthreads();
+    const int ngrp = (R.seg_nblk[seg] + kRedGroup - 1) / kRedGroup;
+    if (t == 0) s_last = (atomicAdd(R.cnt2 + seg, 1) == ngrp - 1);
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    // 3) system sum
+    block_sum_vectors(R.part2 + (int64_t)R.seg_grp0[seg] * nvl, ngrp, nvl, nvl, out, scratch);
+    if (t == 0) R.cnt2[seg] = 0;
+    __syncthreads();
+    return true;
+}
+
+// After a system's finisher ran: count finished systems; the last one
+// returns true (one thread block per launch) and resets the counter.
+__device__ inline bool last_system(const RedLayout& R, int nseg) {
+    __shared__ int s_last2;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        s_last2 = (atomicAdd(R.cnt3, 1) == nseg - 1);
+        if (s_last2) R.cnt3[0] = 0;
+    }
+    __syncthreads();
+    if (s_last2) __threadfence();
+    return s_last2;
+}
+
+}  // namespace ams

@@ -1,0 +1,114 @@
+// Launch descriptors and launcher declarations for the AMS kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ams_internal.h"
+#include "kernels.cuh"
+
+namespace ams {
+
+// Everything the per-row reduction kernels need for one solve shape.
+struct LaunchCtx {
+    cudaStream_t stream;
+    int ld;                  // right-hand-side stride (power of two)
+    int64_t nblk;            // reduction blocks (n_pad * ld / kRedElems)
+    int nseg;                // systems
+    RedLayout red;
+    CgScalars* sc;           // [nseg][ld]
+    SolveState* st;
+    const int64_t* sell_ptr;
+    const int32_t* sell_col;
+    const double* sell_val;
+    const int32_t* sub_of_row;
+    const SubInfo* subs;
+};
+
+struct LocalSolveArgs {
+    cudaStream_t stream;
+    int nsub;
+    const SubInfo* subs;
+    const double* rin;
+    const double* rowscale;  // NULL or per-row scale applied to rin
+    int ld;
+    int cmax;
+    int mmax;
+    const SolveState* st;
+};
+
+struct CoarseLaunch {
+    cudaStream_t stream;
+    int nitems;
+    const CoarseItem* items;
+    const void* mat;
+    const int32_t* rng;
+    void* partial;
+    int32_t* cnt;
+    const SolveState* st;
+};
+
+void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_dot);
+void launch_cg_update(const LaunchCtx& L, double* x, double* r, const double* p, const double* q,
+                      double rtol2, int maxit);
+void launch_dir_update(const LaunchCtx& L, double* p, const double* z);
+void launch_init_norms(const LaunchCtx& L, const double* r, int nrhs);
+size_t local_solve_smem(int cmax, int ld, size_t tf_bytes);
+cudaError_t launch_local_solve(const LocalSolveArgs& a, int prec, const void* fac, const void* psi,
+                               void* zf, void* rc);
+void launch_coarse_gemm(const CoarseLaunch& c, int prec, int ld, const void* in, void* out);
+void launch_prolong_dot(const LaunchCtx& L, int prec, const void* psi, const void* ec, const void* zf,
+                        const double* r, const double* q, double* z, int flexible, int first,
+                        int with_dot);
+void launch_permute_in(cudaStream_t s, const double* f, int64_t n, int nrhs, int ld,
+                       const int64_t* int_row, double* r, double* x);
+void launch_permute_out(cudaStream_t s, const double* x, int64_t n, int nrhs, int ld,
+                        const int64_t* int_row, double* u);
+void launch_sddmm(cudaStream_t s, const int64_t* rowptr, const int32_t* colind, int64_t n, int nrhs,
+                  const double* lam, const double* u, double* dvals);
+void launch_zero(cudaStream_t s, double* a, int64_t n);
+
+// ---- setup kernels (k_setup.cu) ---------------------------------------------
+struct BandArgs {
+    cudaStream_t stream;
+    int nsub;
+    const SubInfo* subs;
+    const int64_t* band_off;     // per subdomain: element offset of its band (32*nb rows x (32c+1))
+    const int64_t* rowptr;       // internal CSR (renumbered, padded rows empty)
+    const int32_t* colind;
+    const double* vals;
+};
+// mode 0: A_i ; mode 1: \hat A_i + sigma S_i.  Also writes S (diag of \hat A
+// with the zero-weight reading) and the \hat A diagonal when non-NULL.
+void launch_band_assemble(const BandArgs& a, double* band, int mode, double sigma, double* S,
+                          double* ahat_diag);
+void launch_band_cholesky(const BandArgs& a, double* band, int32_t* status);
+
+// eigensolver (shift-invert subspace iteration, FP64)
+void launch_eig_init(cudaStream_t s, int nsub, const SubInfo* subs, int P, double* X);
+void launch_eig_rr(cudaStream_t s, int nsub, const SubInfo* subs, int P, const int64_t* rowptr,
+                   const int32_t* colind, const double* vals, const double* S, const double* ahat_diag,
+                   const double* Y, double* AY, double* T, double* theta, int32_t* status);
+void launch_eig_update(cudaStream_t s, int64_t nrows_pad, int P, const int32_t* sub_of_row,
+                       const SubInfo* subs, const double* Y, const double* T, double* X);
+void launch_eig_resid(cudaStream_t s, int nsub, const SubInfo* subs, int P, const int64_t* rowptr,
+                      const int32_t* colind, const double* vals, const double* S,
+                      const double* ahat_diag, const double* X, const double* theta, int ncheck,
+                      double* resid);
+void launch_eig_finalize(cudaStream_t s, int nsub, const SubInfo* subs, int P, const double* X,
+                         const double* S, double* psi64);
+void launch_psi_round(cudaStream_t s, int64_t n, const double* psi64, int prec, double* psi_used,
+                      float* psi32, __nv_bfloat16* psi16);
+
+// Galerkin A_0 = R_0 A R_0^T into a dense (per system) row-major matrix
+void launch_galerkin(cudaStream_t s, int nsub, const SubInfo* subs, const int64_t* rowptr,
+                     const int32_t* colind, const double* vals, const int32_t* sub_of_row,
+                     const double* psi, const int64_t* nbr_ptr, const int32_t* nbr, int max_nbr,
+                     int mmax, double* Ac, int64_t ldA, int64_t coff0, int sub0);
+void launch_extract_chunks(cudaStream_t s, int nchunks, const int64_t* desc, const int32_t* rng,
+                           const double* Linv, int64_t ldL, double* out64, float* out32);
+void launch_band_pack_work(cudaStream_t s, int nwork, const SubInfo* subs, const int64_t* band_off,
+                           const int2* work, const double* band, const int64_t* out_off, double* out64,
+                           float* out32);
+
+}  // namespace ams

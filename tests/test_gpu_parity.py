@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Sizes are small enough for the oracle to finish in seconds while still
+spanning several 32-row tiles, ragged last tiles, uneven subdomains and
+multi-level coarse trees.  Tolerances: index maps bit-exact; FP64 path
+relative solution error <= 1e-10 and iterations within 2 of the oracle;
+reduced-precision paths <= 1e-6 against the FP64 oracle.
+"""
+
+import numpy as np
+import pytest
+import scipy.linalg as la
+
+from oracle import OracleAMS, csr_to_scipy, pcg
+from workloads import make_config1, make_small_2d, make_small_3d
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2606_04864_gb300 import AmsBatchedSolver, AmsError, AmsSolver  # noqa: E402
+
+
+def _A(w):
+    return csr_to_scipy(w.rowptr, w.colind, w.vals)
+
+
+def _solver(w, **kw):
+    return AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, **kw)
+
+
+def _proj(Psi, s):
+    return Psi @ Psi.T @ np.diag(s)
+
+
+CASES = {
+    "cfg1": lambda: make_config1(),
+    "2d_ragged": lambda: make_small_2d(side=45, bs=10, m=3, std=2.0, sigma=3.0, seed=31, ny=37),
+    "3d_b8": lambda: make_small_3d(side=16, bs=8, m=6, std=2.5, sigma=3.0, seed=32),
+    "3d_ragged": lambda: make_small_3d(side=13, bs=5, m=4, std=2.0, sigma=2.0, seed=33),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def case(request):
+    w = CASES[request.param]()
+    A = _A(w)
+    o = OracleAMS(A, w.part, w.nparts, w.m)
+    return request.param, w, A, o
+
+
+def test_index_maps_bit_exact(case):
+    name, w, A, o = case
+    s = _solver(w, precision="fp64")
+    perm, sub_ptr = s.index_maps()
+    assert (perm == o.perm).all()
+    assert (sub_ptr == o.sub_ptr).all()
+
+
+def test_eigenpairs_match_oracle(case):
+    name, w, A, o = case
+    s = _solver(w, precision="fp64")
+    mi, lams, psis = s.coarse_basis()
+    assert list(mi) == list(o.m_i)
+    info = s.info()
+    assert info["eig_max_residual"] <= 1e-11
+    for i, dofs in enumerate(o.sub_dofs):
+        lam_o = o.lams[i][:mi[i]]
+        assert np.abs(lams[i] - lam_o).max() <= 1e-11 * max(1.0, np.abs(lam_o).max())
+        _, _, sw = __import__("oracle").local_matrices(A, dofs)
+        G = psis[i].T @ (sw[:, None] * psis[i])
+        assert np.abs(G - np.eye(mi[i])).max() <= 1e-11
+        P1, P2 = _proj(psis[i], sw), _proj(o.Psis[i], sw)
+        assert np.abs(P1 - P2).max() <= 1e-8 * max(1.0, np.abs(P2).max())
+
+
+def test_coarse_matrix_matches_oracle(case):
+    name, w, A, o = case
+    s = _solver(w, precision="fp64")
+    A0 = s.coarse_matrix()
+    # basis signs may differ: compare the sign-invariant quantity |A0_ij|
+    # plus the spectrum (A0 is D A0_oracle D for a diagonal sign matrix D)
+    ev_g = np.linalg.eigvalsh(A0)
+    ev_o = np.linalg.eigvalsh(o.A0)
+    assert np.abs(ev_g - ev_o).max() <= 1e-10 * ev_o.max()
+    assert np.abs(np.abs(A0) - np.abs(o.A0)).max() <= 1e-9 * np.abs(o.A0).max()
+
+
+def test_spmv_matches_scipy(case):
+    name, w, A, o = case
+    s = _solver(w, precision="fp64")
+    x = np.random.default_rng(1).standard_normal((3, w.n))
+    y = s.spmv(x)
+    ref = (A @ x.T).T
+    assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5), ("fp32_bf16", 2e-5)])
+def test_preconditioner_apply_matches_oracle(case, prec, tol):
+    name, w, A, o = case
+    rnd = {"fp64": None, "fp32": "fp32", "fp32_bf16": "bf16"}[prec]
+    orc = o if rnd is None else OracleAMS(A, w.part, w.nparts, w.m, basis_round=rnd)
+    s = _solver(w, precision=prec)
+    r = np.random.default_rng(2).standard_normal((2, w.n))
+    z = s.apply_preconditioner(r)
+    for k in range(2):
+        zr = orc.apply(r[k])
+        assert np.linalg.norm(z[k] - zr) <= tol * np.linalg.norm(zr), (prec, np.linalg.norm(z[k] - zr) / np.linalg.norm(zr))
+
+
+def test_fp64_pcg_matches_oracle(case):
+    name, w, A, o = case
+    ref = pcg(A, w.rhs[0], o.apply, rtol=1e-8)
+    s = _solver(w, precision="fp64")
+    u, its, rel = s.solve(w.rhs[0], rtol=1e-8)
+    assert abs(int(its[0]) - ref.iters) <= 2
+    assert np.linalg.norm(u - ref.u) <= 1e-10 * np.linalg.norm(ref.u)
+    assert np.linalg.norm(w.rhs[0] - A @ u) <= 1.5e-8 * np.linalg.norm(w.rhs[0])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_bf16"])
+def test_mixed_fcg_matches_fp64_oracle(case, prec):
+    name, w, A, o = case
+    ref = pcg(A, w.rhs[0], o.apply, rtol=1e-8)
+    tight = pcg(A, w.rhs[0], o.apply, rtol=1e-13)
+    s = _solver(w, precision=prec)
+    u, its, rel = s.solve(w.rhs[0], rtol=1e-8)
+    assert abs(int(its[0]) - ref.iters) <= 2, (its, ref.iters)
+    floor = np.linalg.norm(ref.u - tight.u) / np.linalg.norm(tight.u)
+    err = np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u)
+    assert err <= max(1e-6, 10 * floor), (err, floor)
+    assert np.linalg.norm(w.rhs[0] - A @ u) <= 1.5e-8 * np.linalg.norm(w.rhs[0])
+
+
+def test_multi_rhs_each_column_matches_oracle():
+    w = make_small_3d(side=12, bs=4, m=4, std=2.0, sigma=2.0, seed=40, nrhs=5, rhs_kind="normal")
+    A = _A(w)
+    o = OracleAMS(A, w.part, w.nparts, w.m)
+    for prec, tol in [("fp64", 1e-10), ("fp32_bf16", 1e-6)]:
+        s = _solver(w, precision=prec)
+        u, its, rel = s.solve(w.rhs, rtol=1e-8)
+        for k in range(w.nrhs):
+            ref = pcg(A, w.rhs[k], o.apply, rtol=1e-8)
+            assert abs(int(its[k]) - ref.iters) <= 2
+            assert np.linalg.norm(u[k] - ref.u) <= tol * np.linalg.norm(ref.u)
+
+
+def test_thirty_two_rhs_device_pointers():
+    w = make_small_2d(side=40, bs=8, m=4, std=2.0, seed=41, nrhs=32, rhs_kind="normal")
+    A = _A(w)
+    s = _solver(w, precision="fp32_bf16", device=True)
+    f = torch.as_tensor(w.rhs, device="cuda")
+    u, its, rel = s.solve(f, rtol=1e-8)
+    u = u.cpu().numpy()
+    R = w.rhs - (A @ u.T).T
+    assert (np.linalg.norm(R, axis=1) <= 1.5e-8 * np.linalg.norm(w.rhs, axis=1)).all()
+    assert (rel <= 1e-8).all()
+
+
+def test_adjoint_matches_oracle():
+    w = make_small_2d(side=24, bs=6, m=3, std=2.0, seed=42)
+    A = _A(w)
+    o = OracleAMS(A, w.part, w.nparts, w.m)
+    s = _solver(w, precision="fp64")
+    u, _, _ = s.solve(w.rhs[0], rtol=1e-12)
+    g = np.random.default_rng(3).standard_normal(w.n)
+    lam, dvals, its = s.solve_adjoint(g, u, rtol=1e-12)
+    from oracle import adjoint_gradient
+    lam_o, dv_o, _ = adjoint_gradient(A, u, g, o.apply, rtol=1e-12)
+    assert np.linalg.norm(lam - lam_o) <= 1e-9 * np.linalg.norm(lam_o)
+    assert np.abs(dvals - dv_o).max() <= 1e-9 * np.abs(dv_o).max()
+
+
+def test_batched_uneven_systems_match_oracle():
+    ws = [make_small_2d(side=20, bs=8, m=4, std=2.0, seed=50),
+          make_small_3d(side=9, bs=4, m=3, std=2.5, seed=51),
+          make_small_2d(side=33, bs=8, m=5, std=2.0, seed=52, ny=17)]
+    systems = [(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m) for w in ws]
+    nrhs = 3
+    rhs = [np.random.default_rng(60 + i).standard_normal((nrhs, w.n)) for i, w in enumerate(ws)]
+    for prec, tol in [("fp64", 1e-10), ("fp32_bf16", 1e-6)]:
+        b = AmsBatchedSolver(systems, precision=prec)
+        u, its, rel = b.solve(b.pack(rhs), nrhs, rtol=1e-8)
+        us = b.unpack(u, nrhs)
+        for i, w in enumerate(ws):
+            A = _A(w)
+            o = OracleAMS(A, w.part, w.nparts, w.m)
+            for k in range(nrhs):
+                ref = pcg(A, rhs[i][k], o.apply, rtol=1e-8)
+                assert abs(int(its[i, k]) - ref.iters) <= 2
+                assert np.linalg.norm(us[i][k] - ref.u) <= tol * np.linalg.norm(ref.u)
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_isolated_dofs_and_tiny_subdomains():
+    """Subdomains of one dof (no in-subdomain neighbour: S_jj = A_jj) and
+    m >= n_i (every local mode kept)."""
+    w = make_small_2d(side=10, bs=3, m=4, std=1.0, seed=70)
+    part = w.part.copy()
+    part = np.where(np.arange(w.n) % 17 == 0, w.nparts + np.arange(w.n) // 17, part)
+    uniq, part = np.unique(part, return_inverse=True)
+    part = part.astype(np.int32)
+    A = _A(w)
+    o = OracleAMS(A, part, len(uniq), 4)
+    ref = pcg(A, w.rhs[0], o.apply, rtol=1e-8)
+    s = AmsSolver(w.rowptr, w.colind, w.vals, part, len(uniq), 4, precision="fp64")
+    u, its, rel = s.solve(w.rhs[0], rtol=1e-8)
+    assert abs(int(its[0]) - ref.iters) <= 2
+    assert np.linalg.norm(u - ref.u) <= 1e-10 * np.linalg.norm(ref.u)
+
+
+def test_block_jacobi_m0_and_single_subdomain():
+    w = make_small_2d(side=16, bs=4, m=0, std=2.0, seed=71)
+    A = _A(w)
+    o = OracleAMS(A, w.part, w.nparts, 0, coarse=False)
+    ref = pcg(A, w.rhs[0], o.apply, rtol=1e-8)
+    s = _solver(w, precision="fp64")
+    u, its, _ = s.solve(w.rhs[0], rtol=1e-8)
+    assert abs(int(its[0]) - ref.iters) <= 2
+    assert np.linalg.norm(u - ref.u) <= 1e-10 * np.linalg.norm(ref.u)
+    # one subdomain: the local solve is exact, so local-only CG takes one
+    # iteration; adding the coarse term makes M^{-1}A = I + (A-orthogonal
+    # projector onto the coarse space), eigenvalues {1, 2}: two iterations
+    w1 = make_small_2d(side=16, bs=16, m=2, std=2.0, seed=72)
+    s1 = _solver(w1, precision="fp64", coarse=False)
+    u1, its1, _ = s1.solve(w1.rhs[0], rtol=1e-10)
+    assert its1[0] == 1
+    s2 = _solver(w1, precision="fp64")
+    u2, its2, _ = s2.solve(w1.rhs[0], rtol=1e-10)
+    assert its2[0] == 2
+
+
+def test_zero_rhs_and_maxit():
+    w = make_small_2d(side=16, bs=4, m=2, std=2.0, seed=73)
+    s = _solver(w, precision="fp64")
+    u, its, rel = s.solve(np.zeros(w.n), rtol=1e-8)
+    assert its[0] == 0 and np.all(u == 0)
+    s2 = _solver(w, precision="fp64", maxit=2)
+    with pytest.raises(AmsError) as e:
+        s2.solve(w.rhs[0], rtol=1e-12)
+    assert e.value.status == 4
+    u2, its2, _ = s2.solve(w.rhs[0], rtol=1e-12, allow_not_converged=True)
+    assert its2[0] == 2 and np.isfinite(u2).all()
+
+
+def test_invalid_inputs_are_rejected():
+    w = make_small_2d(side=8, bs=4, m=2, seed=74)
+    bad = w.vals.copy()
+    bad[w.rowptr[3] + 0] *= 1.5            # break symmetry
+    with pytest.raises(AmsError) as e:
+        AmsSolver(w.rowptr, w.colind, bad, w.part, w.nparts, 2)
+    assert e.value.status == 1
+    p = w.part.copy()
+    p[0] = w.nparts + 3
+    with pytest.raises(AmsError) as e:
+        AmsSolver(w.rowptr, w.colind, w.vals, p, w.nparts, 2)
+    assert e.value.status == 1
+    with pytest.raises(AmsError) as e:                 # empty subdomain
+        AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts + 1, 2)
+    assert e.value.status == 1
+    neg = w.vals.copy()
+    diag = [w.rowptr[i] + list(w.colind[w.rowptr[i]:w.rowptr[i + 1]]).index(i) for i in range(w.n)]
+    neg[diag[5]] = -1.0
+    with pytest.raises(AmsError) as e:
+        AmsSolver(w.rowptr, w.colind, neg, w.part, w.nparts, 2)
+    assert e.value.status == 2
+    # indefinite but with positive diagonal: caught by a local Cholesky pivot
+    ind = w.vals.copy()
+    for i in range(w.n):
+        for t in range(w.rowptr[i], w.rowptr[i + 1]):
+            if w.colind[t] != i:
+                ind[t] *= 3.0
+    with pytest.raises(AmsError) as e:
+        AmsSolver(w.rowptr, w.colind, ind, w.part, w.nparts, 2)
+    assert e.value.status == 2

@@ -30,4 +30,5 @@ from .darcy import (  # noqa: F401
     make_config5,
     make_small_2d,
     make_small_3d,
+    make_from_logk,
 )

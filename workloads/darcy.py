@@ -281,6 +281,12 @@ def _build(name, logk, bs, m, rhs_kind, nrhs, seed, rtol=1e-8):
                     extra={"faces": faces, "bs": bs})
 
 
+def make_from_logk(name, logk, bs, m, rhs_kind="unit", nrhs=1, seed=0):
+    """Workload on a given log-permeability array (e.g. a window of a larger
+    field, used for bounded CPU samples of a full-size workload)."""
+    return _build(name, np.ascontiguousarray(logk), bs, m, rhs_kind, nrhs, seed)
+
+
 def make_small_2d(side=16, bs=4, m=2, std=1.0, sigma=2.0, seed=0, nrhs=1,
                   rhs_kind="unit", ny=None):
     shape = (ny if ny is not None else side, side)
