@@ -176,6 +176,18 @@ ams_status ams_solve_adjoint(ams_handle h, const double* g, int32_t nrhs,
                              double rtol, const double* u, double* lambda,
                              double* dvals, int32_t* iters);
 
+/*
+ * ams_set_matrix_values — replace the values of A (same CSR pattern, caller
+ * order, nnz entries; host or device per the handle's pointer mode) used by
+ * the SpMV of later solves, keeping the preconditioner built at setup.  PCG
+ * stays correct for any SPD matrix with this pattern (the preconditioner is
+ * only an approximation of its inverse); it converges fastest while the new
+ * matrix is close to the one the preconditioner was built from.  The values
+ * are not validated (symmetry and definiteness are the caller's
+ * responsibility).  Single-system handles only.
+ */
+ams_status ams_set_matrix_values(ams_handle h, const double* vals);
+
 /* Release every resource of the handle.  NULL is accepted. */
 ams_status ams_destroy(ams_handle h);
 
@@ -260,6 +272,18 @@ ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y);
  */
 ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps,
                            double* avg_ms, double* bytes);
+
+/*
+ * One solve (same arguments and result as ams_solve, output discarded) with
+ * a CUDA event pair recorded around every kernel on the handle's stream, so
+ * each kernel's device time is measured inside a real solve (cold caches,
+ * real data).  Outputs per kernel (same order as ams_time_kernel): total
+ * milliseconds `ms[7]`, launches `count[7]`, algorithmic bytes per launch
+ * `bytes[7]`.  Host arrays; the solve runs without graph capture.
+ */
+ams_status ams_profile_solve(ams_handle h, const double* f, int32_t nrhs,
+                             double rtol, double* ms, double* bytes,
+                             int64_t* count);
 
 #ifdef __cplusplus
 }

@@ -85,6 +85,7 @@ SIGNATURES = {
     "ams_solve_adjoint": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p]),
     "ams_destroy": (C.c_int, [C.c_void_p]),
+    "ams_set_matrix_values": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ams_status_string": (C.c_char_p, [C.c_int]),
     "ams_last_error": (C.c_char_p, []),
     "ams_get_info": (C.c_int, [C.c_void_p, C.POINTER(ams_info)]),
@@ -95,6 +96,8 @@ SIGNATURES = {
     "ams_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ams_time_kernel": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
                                   C.POINTER(C.c_double)]),
+    "ams_profile_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
+                                    C.c_void_p, C.c_void_p]),
 }
 
 _lock = threading.Lock()

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
 
@@ -63,6 +64,7 @@ struct RedCache {
 struct SystemHost {
     int64_t n = 0, nnz = 0;
     int64_t caller0 = 0;       // offset of this system in caller vectors
+    int64_t caller_nnz0 = 0;   // offset of this system's entries among all systems' entries
     int64_t row0 = 0;          // first internal row
     int64_t npad = 0;          // padded internal rows
     int32_t sub0 = 0, nparts = 0, m = 0;
@@ -77,9 +79,22 @@ struct SystemHost {
 
 using namespace ams;
 
+// per-kernel event timing of one solve (ams_profile_solve)
+struct KernelProfile {
+    double ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    int64_t count[7] = {0, 0, 0, 0, 0, 0, 0};
+    cudaEvent_t ev[32];
+    int nev = 0;
+    int which[16];
+};
+
 struct ams_handle_s {
     ams_options opt{};
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;      // internal non-blocking stream (all device work)
+    cudaStream_t ustream = nullptr;     // caller's stream (ordering only)
+    cudaEvent_t ev_enter = nullptr;
+    std::map<int, cudaGraphExec_t> iter_graph;   // one captured PCG iteration per ld
+    KernelProfile* prof = nullptr;
     int prec = AMS_PREC_FP32_BF16;
     int flexible = 1;
     int nsys = 0;
@@ -100,8 +115,15 @@ struct ams_handle_s {
     double* d_sell_val = nullptr;
     int64_t* d_crowptr = nullptr;       // caller CSR (single system) for dL/dA
     int32_t* d_ccolind = nullptr;
+    int64_t* d_sell_pos = nullptr;      // caller CSR entry -> SELL slot (single system)
     void* d_fac = nullptr;
     int64_t fac_elems = 0;
+    // reduced-precision local factors in the TMA tile layout
+    bool use_tma = false;
+    float *d_tfwd = nullptr, *d_tbwd = nullptr, *d_piv = nullptr;
+    int64_t* d_trow0 = nullptr;
+    int64_t tile_elems = 0;
+    CUtensorMap tmF{}, tmB{};
     double* d_psi64 = nullptr;
     void* d_psi = nullptr;              // basis in the solve precision
     int64_t psi_elems = 0;
@@ -151,8 +173,12 @@ struct ams_handle_s {
             }
     }
     ~ams_handle_s() {
+        if (stream) cudaStreamSynchronize(stream);
+        for (auto& g : iter_graph) cudaGraphExecDestroy(g.second);
         for (auto& b : bufs)
             if (b.p) cudaFree(b.p);
+        if (ev_enter) cudaEventDestroy(ev_enter);
+        if (stream) cudaStreamDestroy(stream);
     }
 };
 
@@ -277,7 +303,8 @@ static ams_status read_inputs(const ams_system_desc& d, int device_ptrs, SysInpu
 
 static ams_status build_local_factors(ams_handle h, const int64_t* d_rowptr, const int32_t* d_colind,
                                       const double* d_vals, double* d_S, double* d_ahat, double sigma,
-                                      int eig_mode, void** out_fac, int64_t* out_elems, int out_fp64) {
+                                      int eig_mode, void** out_fac, int64_t* out_elems, int out_fp64,
+                                      bool tiles = false) {
     // band buffer
     std::vector<int64_t> band_off(h->N), fac_off(h->N);
     int64_t band_tot = 0, fac_tot = 0;
@@ -304,10 +331,37 @@ static ams_status build_local_factors(ams_handle h, const int64_t* d_rowptr, con
     launch_band_assemble(ba, d_band, eig_mode, sigma, d_S, d_ahat);
     launch_band_cholesky(ba, d_band, d_status);
     void* fac = nullptr;
-    AMS_TRY(h->alloc(&fac, (size_t)fac_tot * (out_fp64 ? 8 : 4)));
-    launch_band_pack_work(h->stream, (int)work.size(), h->d_subs, d_band_off, d_work, d_band, d_fac_off,
-                          out_fp64 ? (double*)fac : nullptr, out_fp64 ? nullptr : (float*)fac);
-    AMS_CUDA_TRY(cudaGetLastError());
+    if (tiles) {
+        // forward/backward FP32 tiles (c tiles per block row) + pivots
+        std::vector<int64_t> toff(h->N), trow0(h->N);
+        int64_t ttot = 0;
+        for (int s = 0; s < h->N; ++s) {
+            toff[s] = ttot;
+            trow0[s] = ttot / 32;
+            ttot += (int64_t)h->h_subs[s].nb * h->h_subs[s].c * 1024;
+        }
+        int64_t* d_toff = nullptr;
+        AMS_TRY(upload(h, &d_toff, toff));
+        AMS_TRY(upload(h, &h->d_trow0, trow0));
+        AMS_TRY(h->alloc_t(&h->d_tfwd, (size_t)ttot));
+        AMS_TRY(h->alloc_t(&h->d_tbwd, (size_t)ttot));
+        AMS_TRY(h->alloc_t(&h->d_piv, (size_t)h->n_pad));
+        launch_band_pack_tiles(h->stream, (int)work.size(), h->d_subs, d_band_off, d_work, d_band, d_toff,
+                               h->d_tfwd, h->d_tbwd, h->d_piv);
+        AMS_CUDA_TRY(cudaGetLastError());
+        AMS_CUDA_TRY(make_tile_map(h->d_tfwd, ttot / 32, &h->tmF));
+        AMS_CUDA_TRY(make_tile_map(h->d_tbwd, ttot / 32, &h->tmB));
+        h->tile_elems = ttot;
+        h->use_tma = true;
+        fac_tot = 0;
+        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        h->release(d_toff);
+    } else {
+        AMS_TRY(h->alloc(&fac, (size_t)fac_tot * (out_fp64 ? 8 : 4)));
+        launch_band_pack_work(h->stream, (int)work.size(), h->d_subs, d_band_off, d_work, d_band, d_fac_off,
+                              out_fp64 ? (double*)fac : nullptr, out_fp64 ? nullptr : (float*)fac);
+        AMS_CUDA_TRY(cudaGetLastError());
+    }
     int32_t status = 0;
     AMS_CUDA_TRY(cudaMemcpyAsync(&status, d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
     AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -539,7 +593,7 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
     std::vector<int64_t> desc;   // extraction chunks, 8 per chunk
     int64_t Roff = 0, Qoff = 0;
     int32_t tile_id = 0, slot = 0;
-    const int KCHUNK = 2048;
+    const int KCHUNK = kCoarseChunk;
     const int64_t ECHUNK = 65536;
     // build all layouts first (host), then run factorisation + extraction per system
     struct SysChunks { int64_t d0, d1; };
@@ -727,7 +781,11 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     if (h->opt.maxit <= 0) h->opt.maxit = 10000;
     h->prec = h->opt.precision;
     h->flexible = h->opt.cg_variant == AMS_CG_AUTO ? (h->prec != AMS_PREC_FP64) : (h->opt.cg_variant == AMS_CG_FCG);
-    h->stream = (cudaStream_t)stream;
+    h->ustream = (cudaStream_t)stream;
+    AMS_CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    AMS_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_enter, cudaEventDisableTiming));
+    AMS_CUDA_TRY(cudaEventRecord(h->ev_enter, h->ustream));
+    AMS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_enter, 0));
     h->nsys = nsys;
     std::vector<SysInput> inputs(nsys);
     for (int s = 0; s < nsys; ++s) AMS_TRY(read_inputs(systems[s], h->opt.device_ptrs, inputs[s]));
@@ -740,6 +798,7 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
         S.n = inputs[s].A.n;
         S.nnz = inputs[s].A.rowptr[S.n];
         S.caller0 = caller;
+        S.caller_nnz0 = h->nnz_total;
         S.row0 = row;
         S.npad = round_up(S.n, kRowAlign);
         S.sub0 = sub;
@@ -767,6 +826,9 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     ival.reserve(h->nnz_total);
     h->h_subs.resize(h->N);
     std::vector<std::pair<int32_t, double>> rowbuf;
+    std::vector<std::pair<int32_t, int64_t>> rowsrc;   // (internal col, caller entry)
+    std::vector<int64_t> ientry_src;                    // internal CSR entry -> caller entry
+    ientry_src.reserve(h->nnz_total);
     int64_t rp = 0;
     for (int s = 0; s < nsys; ++s) {
         SystemHost& S = h->sys[s];
@@ -798,18 +860,17 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
             irp[S.row0 + k] = rp;
             if (k < S.n) {
                 const int64_t g = S.perm[k];
-                rowbuf.clear();
+                rowsrc.clear();
                 for (int64_t e = A.rowptr[g]; e < A.rowptr[g + 1]; ++e)
-                    rowbuf.push_back({(int32_t)(S.row0 + iperm[A.colind[e]]), A.vals[e]});
-                std::sort(rowbuf.begin(), rowbuf.end(),
-                          [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
-                              return x.first < y.first;
-                          });
-                for (auto& pr : rowbuf) {
+                    rowsrc.push_back({(int32_t)(S.row0 + iperm[A.colind[e]]), S.caller_nnz0 + e});
+                std::sort(rowsrc.begin(), rowsrc.end());
+                for (auto& pr : rowsrc) {
                     icol.push_back(pr.first);
-                    ival.push_back(pr.second);
+                    const int64_t ce = pr.second - S.caller_nnz0;
+                    ival.push_back(A.vals[ce]);
+                    ientry_src.push_back(pr.second);
                 }
-                rp += (int64_t)rowbuf.size();
+                rp += (int64_t)rowsrc.size();
             }
         }
     }
@@ -817,8 +878,8 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     // shared-memory staging limits of the local solve
     {
         const size_t lim = 227 * 1024;
-        const size_t need_solve = local_solve_smem(h->cmax, kMaxLd, h->tf_bytes());
-        const size_t need_eig = local_solve_smem(h->cmax, 32, 8);
+        const size_t need_solve = local_solve_smem(h->cmax, kMaxLd, h->tf_bytes(), 1);
+        const size_t need_eig = local_solve_smem(h->cmax, 32, 8, 1);
         if (need_solve > lim || (h->opt.coarse && need_eig > lim)) {
             set_error("a subdomain's band (" + std::to_string(32 * h->cmax) +
                       ") is too wide for shared-memory staging; renumber the subdomain or use smaller subdomains");
@@ -835,6 +896,7 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     }
     std::vector<int32_t> sell_col(sell_ptr[nslices]);
     std::vector<double> sell_val(sell_ptr[nslices], 0.0);
+    std::vector<int64_t> sell_pos(h->nnz_total, 0);
     for (int64_t sl = 0; sl < nslices; ++sl) {
         const int64_t w = (sell_ptr[sl + 1] - sell_ptr[sl]) / 32;
         for (int l = 0; l < 32; ++l) {
@@ -845,6 +907,7 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
                 if (j < len) {
                     sell_col[o] = icol[irp[r] + j];
                     sell_val[o] = ival[irp[r] + j];
+                    sell_pos[ientry_src[irp[r] + j]] = o;
                 } else {
                     sell_col[o] = (int32_t)r;
                     sell_val[o] = 0.0;
@@ -867,13 +930,14 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     if (nsys == 1) {
         AMS_TRY(upload(H, &h->d_crowptr, inputs[0].A.rowptr));
         AMS_TRY(upload(H, &h->d_ccolind, inputs[0].A.colind));
+        AMS_TRY(upload(H, &h->d_sell_pos, sell_pos));
     }
     AMS_TRY(h->alloc_t(&h->d_subs, (size_t)h->N));
     AMS_CUDA_TRY(cudaMemcpyAsync(h->d_subs, h->h_subs.data(), sizeof(SubInfo) * h->N, cudaMemcpyHostToDevice,
                                  h->stream));
     // local factors of A_i
     AMS_TRY(build_local_factors(H, d_irp, d_icol, d_ival, nullptr, nullptr, 0.0, 0, &h->d_fac, &h->fac_elems,
-                                h->prec == AMS_PREC_FP64));
+                                h->prec == AMS_PREC_FP64, h->prec != AMS_PREC_FP64));
     AMS_CUDA_TRY(cudaMemcpyAsync(h->d_subs, h->h_subs.data(), sizeof(SubInfo) * h->N, cudaMemcpyHostToDevice,
                                  h->stream));
     // coarse space
@@ -909,7 +973,7 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     I.max_band_tiles = h->cmax;
     I.precision = h->prec;
     I.cg_variant = h->flexible ? AMS_CG_FCG : AMS_CG_PCG;
-    I.local_factor_bytes = h->fac_elems * (int64_t)h->tf_bytes();
+    I.local_factor_bytes = h->use_tma ? 2 * h->tile_elems * 4 + 4 * h->n_pad : h->fac_elems * (int64_t)h->tf_bytes();
     I.coarse_inverse_bytes = (h->R_elems + h->Q_elems) * (int64_t)h->tf_bytes();
     I.basis_bytes = h->psi_elems * (int64_t)h->tp_bytes();
     I.spmv_variant = 0;
@@ -953,36 +1017,118 @@ static ams_status ensure_work(ams_handle h, int ld) {
     return AMS_OK;
 }
 
+// Event bracketing of single kernels while profiling (one solve).
+static void prof_begin(ams_handle h, int which) {
+    KernelProfile* P = h->prof;
+    if (!P) return;
+    cudaEventRecord(P->ev[2 * P->nev], h->stream);
+    P->which[P->nev] = which;
+}
+static void prof_end(ams_handle h) {
+    KernelProfile* P = h->prof;
+    if (!P) return;
+    cudaEventRecord(P->ev[2 * P->nev + 1], h->stream);
+    P->nev++;
+}
+static ams_status prof_flush(ams_handle h) {
+    KernelProfile* P = h->prof;
+    if (!P || P->nev == 0) return AMS_OK;
+    AMS_CUDA_TRY(cudaEventSynchronize(P->ev[2 * P->nev - 1]));
+    for (int i = 0; i < P->nev; ++i) {
+        float ms = 0.f;
+        AMS_CUDA_TRY(cudaEventElapsedTime(&ms, P->ev[2 * i], P->ev[2 * i + 1]));
+        P->ms[P->which[i]] += ms;
+        P->count[P->which[i]] += 1;
+    }
+    P->nev = 0;
+    return AMS_OK;
+}
+
+// Fine-level local solves (+ restriction when the coarse space exists).
+static ams_status launch_local(ams_handle h, int ld, const double* r, bool with_state) {
+    const bool coarse = h->Nc > 0;
+    if (h->use_tma) {
+        LocalTmaArgs a{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, r, ld, h->cmax,
+                       std::max(1, h->mmax), int64_t(1) << 20, with_state ? h->d_st : nullptr};
+        AMS_CUDA_TRY(launch_local_tma(a, h->prec, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
+    } else {
+        LocalSolveArgs la{h->stream, h->N, h->d_subs, r, nullptr, ld, h->cmax, std::max(1, h->mmax),
+                          with_state ? h->d_st : nullptr};
+        AMS_CUDA_TRY(launch_local_solve(la, h->prec, h->d_fac, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
+    }
+    return AMS_OK;
+}
+
 // z = M^{-1} r (internal layout); with_dot/first control the fused dots
 static ams_status apply_precond(ams_handle h, const LaunchCtx& L, const double* r, double* z, int first,
                                 int with_dot) {
-    LocalSolveArgs la{h->stream, h->N, h->d_subs, r, nullptr, L.ld, h->cmax, std::max(1, h->mmax),
-                      with_dot ? h->d_st : nullptr};
     const bool coarse = h->Nc > 0;
-    AMS_CUDA_TRY(launch_local_solve(la, h->prec, h->d_fac, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
+    prof_begin(h, 2);
+    AMS_TRY(launch_local(h, L.ld, r, with_dot != 0));
+    prof_end(h);
     h->launches += coarse ? 4 : 2;
     if (coarse) {
         CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_partial, h->d_cnt,
                         with_dot ? h->d_st : nullptr};
+        prof_begin(h, 3);
         launch_coarse_gemm(cf, h->prec, L.ld, h->d_rc, h->d_yc);
+        prof_end(h);
         CoarseLaunch cb{h->stream, h->nbwd, h->d_bwd, h->d_Qmat, h->d_rng, h->d_partial, h->d_cnt,
                         with_dot ? h->d_st : nullptr};
+        prof_begin(h, 4);
         launch_coarse_gemm(cb, h->prec, L.ld, h->d_yc, h->d_ec);
+        prof_end(h);
     }
     LaunchCtx L2 = L;
     if (!with_dot) L2.st = nullptr;
+    prof_begin(h, 5);
     launch_prolong_dot(L2, h->prec, h->d_psi, coarse ? h->d_ec : nullptr, h->d_zf, r, h->d_q, z, h->flexible,
                        first, with_dot);
+    prof_end(h);
     AMS_CUDA_TRY(cudaGetLastError());
     return AMS_OK;
 }
 
-static ams_status launch_iteration(ams_handle h, const LaunchCtx& L, double rtol2) {
+static int launches_per_iteration(ams_handle h) { return h->Nc > 0 ? 7 : 5; }
+
+static ams_status launch_iteration(ams_handle h, const LaunchCtx& L) {
     h->launches += 3;
+    prof_begin(h, 0);
     launch_spmv_dot(L, h->d_p, h->d_q, 1);
-    launch_cg_update(L, h->d_x, h->d_r, h->d_p, h->d_q, rtol2, h->opt.maxit);
+    prof_end(h);
+    prof_begin(h, 1);
+    launch_cg_update(L, h->d_x, h->d_r, h->d_p, h->d_q);
+    prof_end(h);
     AMS_TRY(apply_precond(h, L, h->d_r, h->d_z, 0, 1));
+    prof_begin(h, 6);
     launch_dir_update(L, h->d_p, h->d_z);
+    prof_end(h);
+    return AMS_OK;
+}
+
+// One PCG iteration captured as a CUDA graph (kernel arguments are fixed
+// device pointers; every scalar lives in device memory).
+static ams_status get_iter_graph(ams_handle h, const LaunchCtx& L, cudaGraphExec_t* out) {
+    auto it = h->iter_graph.find(L.ld);
+    if (it != h->iter_graph.end()) {
+        *out = it->second;
+        return AMS_OK;
+    }
+    // one un-captured iteration first: sets kernel attributes outside capture
+    const int64_t saved = h->launches;
+    cudaGraph_t g = nullptr;
+    AMS_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    ams_status st = launch_iteration(h, L);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->launches = saved;
+    if (st != AMS_OK) return st;
+    AMS_CUDA_TRY(e);
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    AMS_CUDA_TRY(e);
+    h->iter_graph[L.ld] = ex;
+    *out = ex;
     return AMS_OK;
 }
 
@@ -1019,20 +1165,50 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
         }
     }
     AMS_CUDA_TRY(cudaMemsetAsync(h->d_p, 0, sizeof(double) * h->n_pad * ld, h->stream));
+    {
+        SolveState init{};
+        init.maxit = h->opt.maxit;
+        init.rtol2 = rtol * rtol;
+        AMS_CUDA_TRY(cudaMemcpyAsync(h->d_st, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
+    }
     h->launches += 2 * h->nsys + 2;     // permutes in/out, norms, first direction
     launch_init_norms(L, h->d_r, nrhs);
     AMS_TRY(apply_precond(h, L, h->d_r, h->d_z, 1, 1));
     launch_dir_update(L, h->d_p, h->d_z);
     AMS_CUDA_TRY(cudaGetLastError());
-    const double rtol2 = rtol * rtol;
+    AMS_TRY(prof_flush(h));
+    cudaGraphExec_t graph = nullptr;
+    if (!h->prof) AMS_TRY(get_iter_graph(h, L, &graph));
+    // Launch iterations in chunks; between chunks read the device state and
+    // size the next chunk from the observed residual decay.  Iterations
+    // launched after convergence return at once (device-side done flag).
     SolveState st{};
-    int chunk = 4;
+    int chunk = 8;
+    int it_prev = 0;
+    double w_prev = 1.0;
+    const double target = rtol * rtol;
     while (true) {
-        for (int k = 0; k < chunk; ++k) AMS_TRY(launch_iteration(h, L, rtol2));
+        for (int k = 0; k < chunk; ++k) {
+            if (graph) {
+                AMS_CUDA_TRY(cudaGraphLaunch(graph, h->stream));
+                h->launches += launches_per_iteration(h);
+            } else {
+                AMS_TRY(launch_iteration(h, L));
+                AMS_TRY(prof_flush(h));
+            }
+        }
         AMS_CUDA_TRY(cudaMemcpyAsync(&st, h->d_st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
         AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
         if (st.done) break;
-        chunk = std::min(chunk * 2, 32);
+        int next = 2 * chunk;
+        if (st.it > it_prev && st.worst > 0 && w_prev > 0 && st.worst < w_prev) {
+            const double rate = std::log(st.worst / w_prev) / (st.it - it_prev);   // < 0
+            const double need = std::log(target / st.worst) / rate;
+            next = (int)std::ceil(need);
+        }
+        chunk = std::max(1, std::min(next, 64));
+        it_prev = st.it;
+        w_prev = st.worst;
     }
     // outputs
     if (h->nsys == 1) {
@@ -1126,6 +1302,36 @@ ams_status ams_destroy(ams_handle h) {
     return AMS_OK;
 }
 
+// Algorithmic bytes of one launch of kernel `which` (each operand read once,
+// each output written once) at `ld` right-hand sides.
+static double kernel_bytes(ams_handle h, int which, int ld) {
+    const double n = (double)h->n_total, nl = n * ld;
+    const double tf = (double)h->tf_bytes(), tp = (double)h->tp_bytes();
+    switch (which) {
+        case 0: return 12.0 * (double)h->nnz_total + 16.0 * nl + 8.0 * (double)h->n_pad / 32;
+        case 1: return 48.0 * nl;
+        case 2: {
+            // factor read once (the TMA path stores it twice, once per sweep
+            // direction, and reads each copy once: 2x these factor bytes)
+            const double fb = h->use_tma ? (double)h->tile_elems * 4.0 + 4.0 * n : (double)h->fac_elems * tf;
+            return fb + 8.0 * nl + tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf;
+        }
+        case 3: return (double)h->R_elems * tf + 2.0 * (double)h->Nc * ld * tf;
+        case 4: return (double)h->Q_elems * tf + 2.0 * (double)h->Nc * ld * tf;
+        case 5: return tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf + 24.0 * nl;
+        case 6: return 24.0 * nl;
+    }
+    return 0.0;
+}
+
+// Order the handle's internal stream after work already queued on the
+// caller's stream (the caller's inputs may be produced there).
+static ams_status enter(ams_handle h) {
+    AMS_CUDA_TRY(cudaEventRecord(h->ev_enter, h->ustream));
+    AMS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_enter, 0));
+    return AMS_OK;
+}
+
 static ams_status check_solve_args(ams_handle h, const void* a, const void* b, int32_t nrhs, double rtol) {
     if (!h || !a || !b) {
         set_error("null handle or vector");
@@ -1139,7 +1345,7 @@ static ams_status check_solve_args(ams_handle h, const void* a, const void* b, i
         set_error("rtol must be positive and finite");
         return AMS_ERR_INVALID_ARG;
     }
-    return AMS_OK;
+    return enter(h);
 }
 
 ams_status ams_solve(ams_handle h, const double* f, int32_t nrhs, double rtol, double* u, int32_t* iters,
@@ -1199,6 +1405,28 @@ ams_status ams_solve_adjoint(ams_handle h, const double* g, int32_t nrhs, double
                                      h->stream));
     AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
     return st;
+}
+
+ams_status ams_set_matrix_values(ams_handle h, const double* vals) {
+    g_last_error.clear();
+    if (!h || !vals || h->nsys != 1) {
+        set_error("single-system handle and values required");
+        return AMS_ERR_INVALID_ARG;
+    }
+    AMS_TRY(enter(h));
+    const double* dv = vals;
+    double* tmp = nullptr;
+    if (!h->opt.device_ptrs) {
+        AMS_TRY(h->alloc_t(&tmp, (size_t)h->nnz_total));
+        AMS_CUDA_TRY(cudaMemcpyAsync(tmp, vals, sizeof(double) * h->nnz_total, cudaMemcpyHostToDevice, h->stream));
+        dv = tmp;
+    }
+    launch_scatter_vals(h->stream, dv, h->d_sell_pos, h->nnz_total, h->d_sell_val);
+    h->launches += 1;
+    AMS_CUDA_TRY(cudaGetLastError());
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (tmp) h->release(tmp);
+    return AMS_OK;
 }
 
 ams_status ams_get_info(ams_handle h, ams_info* info) {
@@ -1326,6 +1554,7 @@ ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* av
         set_error("invalid arguments (a solve must run first)");
         return AMS_ERR_INVALID_ARG;
     }
+    AMS_TRY(enter(h));
     const int ld = h->ld_last;
     RedCache* rc = nullptr;
     AMS_TRY(get_red(h, ld, &rc));
@@ -1342,31 +1571,17 @@ ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* av
         }
         AMS_CUDA_TRY(cudaMemcpy(h->d_sc, sc.data(), sizeof(CgScalars) * sc.size(), cudaMemcpyHostToDevice));
         SolveState st{};
+        st.maxit = 0x7fffffff;
+        st.rtol2 = 0.0;
         AMS_CUDA_TRY(cudaMemcpy(h->d_st, &st, sizeof(st), cudaMemcpyHostToDevice));
     }
     const bool coarse = h->Nc > 0;
-    const double n = (double)h->n_total, nl = n * ld;
-    const double tf = (double)h->tf_bytes(), tp = (double)h->tp_bytes();
-    double b = 0.0;
-    switch (which) {
-        case 0: b = 12.0 * (double)h->nnz_total + 16.0 * nl + 8.0 * (double)h->n_pad / 32; break;
-        case 1: b = 48.0 * nl; break;
-        case 2: b = (double)h->fac_elems * tf + 8.0 * nl + tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf; break;
-        case 3: b = (double)h->R_elems * tf + 2.0 * (double)h->Nc * ld * tf; break;
-        case 4: b = (double)h->Q_elems * tf + 2.0 * (double)h->Nc * ld * tf; break;
-        case 5: b = tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf + 24.0 * nl; break;
-        case 6: b = 24.0 * nl; break;
-    }
+    const double b = kernel_bytes(h, which, ld);
     auto launch = [&]() -> ams_status {
         switch (which) {
             case 0: launch_spmv_dot(L, h->d_p, h->d_q, 1); break;
-            case 1: launch_cg_update(L, h->d_x, h->d_r, h->d_p, h->d_q, 0.0, 0x7fffffff); break;
-            case 2: {
-                LocalSolveArgs la{h->stream, h->N, h->d_subs, h->d_r, nullptr, ld, h->cmax, std::max(1, h->mmax),
-                                  h->d_st};
-                AMS_CUDA_TRY(launch_local_solve(la, h->prec, h->d_fac, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
-                break;
-            }
+            case 1: launch_cg_update(L, h->d_x, h->d_r, h->d_p, h->d_q); break;
+            case 2: AMS_TRY(launch_local(h, ld, h->d_r, true)); break;
             case 3: {
                 CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_partial, h->d_cnt, h->d_st};
                 launch_coarse_gemm(cf, h->prec, ld, h->d_rc, h->d_yc);
@@ -1402,6 +1617,33 @@ ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* av
     if (avg_ms) *avg_ms = ms / reps;
     if (bytes) *bytes = b;
     return AMS_OK;
+}
+
+ams_status ams_profile_solve(ams_handle h, const double* f, int32_t nrhs, double rtol, double* ms,
+                             double* bytes, int64_t* count) {
+    g_last_error.clear();
+    AMS_TRY(check_solve_args(h, f, f, nrhs, rtol));
+    AMS_TRY(ensure_work(h, pow2ceil(nrhs)));
+    KernelProfile P;
+    for (auto& e : P.ev) AMS_CUDA_TRY(cudaEventCreate(&e));
+    const double* f_dev = nullptr;
+    ams_status st = stage_in(h, f, nrhs, h->d_stage_in, &f_dev);
+    if (st == AMS_OK) {
+        h->prof = &P;
+        std::vector<int32_t> its(h->nsys * nrhs);
+        st = pcg(h, f_dev, nrhs, rtol, h->d_stage_out, its.data(), nullptr);
+        h->prof = nullptr;
+        if (st == AMS_OK) st = prof_flush(h);
+    }
+    for (auto& e : P.ev) cudaEventDestroy(e);
+    if (st != AMS_OK && st != AMS_ERR_NOT_CONVERGED) return st;
+    const int ld = pow2ceil(nrhs);
+    for (int k = 0; k < 7; ++k) {
+        if (ms) ms[k] = P.ms[k];
+        if (count) count[k] = P.count[k];
+        if (bytes) bytes[k] = kernel_bytes(h, k, ld);
+    }
+    return st;
 }
 
 }  // extern "C"

@@ -22,10 +22,12 @@ namespace ams {
 constexpr int kTile = 32;              // rows per block row of a local factor
 constexpr int kRowAlign = 2048;        // row padding of each system
 constexpr int kRedThreads = 256;       // threads of the reduction kernels
-constexpr int kRedElems = 2048;        // elements per reduction block
-constexpr int kRedGroup = 32;          // blocks summed per first-level group
+constexpr int kRedElems = 1024;        // elements per reduction block
+constexpr int kRedGroup = 64;          // blocks summed per first-level group
+constexpr int kRedDirect = 2048;       // at most this many blocks: one-stage sum
 constexpr int kMaxLd = 32;             // right-hand sides per solve call
 constexpr int kMaxM = 16;              // eigenvectors per subdomain (cap)
+constexpr int kCoarseChunk = 1024;     // node-matrix columns per coarse item
 
 // ---- per-subdomain descriptor (device array) ------------------------------
 struct SubInfo {
@@ -87,6 +89,10 @@ struct SolveState {    // device-resident control block
     int32_t done;      // all (system, rhs) converged
     int32_t status;    // ams_status set by device-side checks
     int32_t nactive;
+    int32_t maxit;     // iteration cap of the current solve
+    int32_t pad;
+    double rtol2;      // squared relative residual target
+    double worst;      // max over active (system, rhs) of ||r||^2 / ||f||^2
 };
 
 // ---- error bookkeeping ------------------------------------------------------

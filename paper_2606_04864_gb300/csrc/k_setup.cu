@@ -149,6 +149,58 @@ __global__ void k_band_pack(const SubInfo* __restrict__ subs, const int64_t* __r
     }
 }
 
+// Same factor, TMA tile layout: forward tiles row-major, backward tiles
+// transposed, reciprocal pivots per row (FP32).  One warp per (subdomain,
+// block row); lane = tile column.
+__global__ void k_band_pack_tiles(const SubInfo* __restrict__ subs, const int64_t* __restrict__ band_off,
+                                  const int2* __restrict__ work, const double* __restrict__ band,
+                                  const int64_t* __restrict__ out_off, float* __restrict__ fwd,
+                                  float* __restrict__ bwd, float* __restrict__ piv) {
+    const int2 wk = work[blockIdx.x];
+    const int s = wk.x, K = wk.y;
+    const SubInfo Sb = subs[s];
+    const int c = Sb.c, bw = 32 * c;
+    const double* B = band + band_off[s];
+    const int lane = threadIdx.x;
+    const int64_t r0 = 32LL * K;
+    double x[32];   // column `lane` of L_KK^{-1}
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        double acc = (i == lane) ? 1.0 : 0.0;
+#pragma unroll
+        for (int k = 0; k < i; ++k) acc -= B[bidx(r0 + i, r0 + k, bw)] * x[k];
+        x[i] = (i >= lane) ? acc / B[bidx(r0 + i, r0 + i, bw)] : 0.0;
+    }
+    auto Lval = [&](int64_t row, int64_t col) -> double {
+        return (col >= 0 && col >= row - bw && col <= row) ? B[bidx(row, col, bw)] : 0.0;
+    };
+    const int64_t tbase = out_off[s] + (int64_t)K * c * 1024;
+    // tile 0: M_K (upper part from L_{K,K-c}, strict lower part from L_KK^{-1})
+    const int64_t cb = 32LL * (K - c);
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+        const float v = (float)(lane >= r ? Lval(r0 + r, cb + lane) : x[r]);
+        fwd[tbase + r * 32 + lane] = v;
+        bwd[tbase + lane * 32 + r] = v;
+    }
+    for (int t = 1; t < c; ++t) {
+        const int64_t cbt = 32LL * (K - c + t);
+        for (int r = 0; r < 32; ++r) {
+            const float v = (float)Lval(r0 + r, cbt + lane);
+            fwd[tbase + (int64_t)t * 1024 + r * 32 + lane] = v;
+            bwd[tbase + (int64_t)t * 1024 + lane * 32 + r] = v;
+        }
+    }
+    const int64_t row = r0 + lane;
+    if (row < Sb.n) {
+        double d = 0.0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (i == lane) d = x[i];
+        piv[Sb.row0 + row] = (float)d;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // eigensolver pieces
 // ---------------------------------------------------------------------------
@@ -575,6 +627,11 @@ void launch_band_pack_work(cudaStream_t s, int nwork, const SubInfo* subs, const
                            const int2* work, const double* band, const int64_t* out_off, double* out64,
                            float* out32) {
     k_band_pack<<<nwork, 32, 0, s>>>(subs, band_off, work, band, out_off, out64, out32);
+}
+void launch_band_pack_tiles(cudaStream_t s, int nwork, const SubInfo* subs, const int64_t* band_off,
+                            const int2* work, const double* band, const int64_t* out_off, float* fwd, float* bwd,
+                            float* piv) {
+    k_band_pack_tiles<<<nwork, 32, 0, s>>>(subs, band_off, work, band, out_off, fwd, bwd, piv);
 }
 void launch_eig_init(cudaStream_t s, int nsub, const SubInfo* subs, int P, double* X) {
     k_eig_init<<<nsub, 256, 0, s>>>(subs, P, X);

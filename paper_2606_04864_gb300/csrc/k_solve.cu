@@ -31,7 +31,7 @@ k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
     __shared__ double s_scr[kRedThreads];
     const int64_t base = (int64_t)blockIdx.x * kRedElems;
     double dot[1] = {0.0};
-#pragma unroll 4
+#pragma unroll
     for (int k = 0; k < kRedElems / kRedThreads; ++k) {
         const int64_t e = base + threadIdx.x + k * kRedThreads;
         const int64_t row = e / LD;
@@ -67,9 +67,9 @@ k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
 template <int LD>
 __global__ void __launch_bounds__(kRedThreads)
 k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-            const double* __restrict__ q, RedLayout R, CgScalars* sc, SolveState* st,
-            int nseg, double rtol2, int maxit) {
+            const double* __restrict__ q, RedLayout R, CgScalars* sc, SolveState* st, int nseg) {
     if (st->done) return;
+    const double rtol2 = st->rtol2;
     __shared__ double s_out[2 * kMaxLd];
     __shared__ double s_scr[kRedThreads];
     const int64_t base = (int64_t)blockIdx.x * kRedElems;
@@ -78,7 +78,7 @@ k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* __rest
     const CgScalars c = sc[seg * LD + rhs];
     const double alpha = c.active ? c.rho / c.pq : 0.0;
     double rr[1] = {0.0};
-#pragma unroll 4
+#pragma unroll
     for (int k = 0; k < kRedElems / kRedThreads; ++k) {
         const int64_t e = base + threadIdx.x + k * kRedThreads;
         x[e] += alpha * p[e];
@@ -106,10 +106,15 @@ k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* __rest
     if (!last_system(R, nseg)) return;
     if (threadIdx.x == 0) {
         int nact = 0;
-        for (int i = 0; i < nseg * LD; ++i) nact += sc[i].active;
+        double worst = 0.0;
+        for (int i = 0; i < nseg * LD; ++i) {
+            nact += sc[i].active;
+            if (sc[i].active) worst = fmax(worst, sc[i].rr / sc[i].fnorm2);
+        }
         st->nactive = nact;
+        st->worst = worst;
         st->it = it + 1;
-        if (nact == 0 || it + 1 >= maxit) st->done = 1;
+        if (nact == 0 || it + 1 >= st->maxit) st->done = 1;
     }
 }
 
@@ -125,23 +130,25 @@ k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* __rest
 //   w   = y_K - sum_{d=1..c} L_{K+d,K}^T x_{K+d}
 //   x_K = L_KK^{-T} w
 // Factor block rows are staged through shared memory with cp.async in a
-// ring of c+2 buffers; y is kept in z_f between the sweeps.
+// ring of c+D+1 buffers, D block rows ahead of the sweep (one commit group
+// per block row); y is kept in z_f between the sweeps.
 // ===========================================================================
 template <typename TF, typename TP, int NR, int MM>
 __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __restrict__ fac,
                               const double* __restrict__ rin, const double* __restrict__ rowscale,
                               TF* __restrict__ zf, const TP* __restrict__ psi, TF* __restrict__ rc,
-                              int ld, int cmax, const SolveState* st) {
+                              int ld, int cmax, int depth, const SolveState* st) {
     if (st != nullptr && st->done) return;
     using A = typename Acc<TF>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SubInfo S = subs[blockIdx.x];
     const int c = S.c, nb = S.nb, n = S.n;
-    const int nbuf = c + 2;
+    const int D = depth;                                       // block rows in flight
+    const int nbuf = c + D + 1;
     const int64_t brs = blockrow_elems(c);
     const int64_t brs_max = blockrow_elems(cmax);
-    TF* bufs = (TF*)smem_raw;                                  // nbuf_max * brs_max
-    TF* ring = bufs + (int64_t)(cmax + 2) * brs_max;           // (cmax+1) * 32 * ld
+    TF* bufs = (TF*)smem_raw;                                  // (cmax+D+1) * brs_max
+    TF* ring = bufs + (int64_t)(cmax + D + 1) * brs_max;       // (cmax+1) * 32 * ld
     TF* tmp = ring + (int64_t)(cmax + 1) * 32 * ld;            // 32 * ld
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -155,36 +162,52 @@ __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __rest
 #pragma unroll
         for (int j = 0; j < NR; ++j) racc[k][j] = A(0);
 
-    // ---------------- forward ----------------
-    block_copy_async(bufs, F, brs * sizeof(TF));
-    cp_async_commit();
-    for (int K = 0; K < nb; ++K) {
-        if (K + 1 < nb) {
-            block_copy_async(bufs + (int64_t)((K + 1) % nbuf) * brs_max, F + (int64_t)(K + 1) * brs,
-                             brs * sizeof(TF));
-            cp_async_commit();
-            cp_async_wait_1();
-        } else {
-            cp_async_wait_all();
-        }
-        __syncthreads();
-        const TF* B = bufs + (int64_t)(K % nbuf) * brs_max;
+    // inputs of block row K (r rows and basis rows), prefetched two block
+    // rows ahead into registers so their global-memory latency overlaps the
+    // substitution of the previous rows
+    auto load_fwd = [&](int K, A (&tv)[NR], A (&pv)[MM]) {
         const int row = K * 32 + lane;
-        A t[NR];
-        const bool valid = row < n;
+        const bool valid = K < nb && row < n;
         const int64_t grow = S.row0 + row;
         const double sc = (rowscale != nullptr && valid) ? rowscale[grow] : 1.0;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) t[j] = valid ? (A)(rin[grow * ld + rhs0 + j] * sc) : A(0);
-        if (rc != nullptr && valid) {
+        for (int j = 0; j < NR; ++j) tv[j] = valid ? (A)(rin[grow * ld + rhs0 + j] * sc) : A(0);
 #pragma unroll
-            for (int k = 0; k < MM; ++k) {
-                if (k < m) {
-                    const A pv = (A)to_d(psi[S.psi_off + (int64_t)row * m + k]);
+        for (int k = 0; k < MM; ++k)
+            pv[k] = (rc != nullptr && valid && k < m) ? (A)to_d(psi[S.psi_off + (int64_t)row * m + k]) : A(0);
+    };
+    A tn0[NR], pn0[MM], tn1[NR], pn1[MM];
+    load_fwd(0, tn0, pn0);
+    load_fwd(1, tn1, pn1);
+
+    // ---------------- forward ----------------
+    // one commit group per block row; row K+D is requested at step K
+    for (int j = 0; j < D; ++j) {
+        if (j < nb) block_copy_async(bufs + (int64_t)(j % nbuf) * brs_max, F + (int64_t)j * brs, brs * sizeof(TF));
+        cp_async_commit();
+    }
+    for (int K = 0; K < nb; ++K) {
+        if (K + D < nb)
+            block_copy_async(bufs + (int64_t)((K + D) % nbuf) * brs_max, F + (int64_t)(K + D) * brs,
+                             brs * sizeof(TF));
+        cp_async_commit();
+        A t[NR], pv[MM];
 #pragma unroll
-                    for (int j = 0; j < NR; ++j) racc[k][j] += pv * t[j];
-                }
-            }
+        for (int j = 0; j < NR; ++j) { t[j] = tn0[j]; tn0[j] = tn1[j]; }
+#pragma unroll
+        for (int k = 0; k < MM; ++k) { pv[k] = pn0[k]; pn0[k] = pn1[k]; }
+        load_fwd(K + 2, tn1, pn1);
+        cp_async_wait_n(D);
+        __syncthreads();
+        const TF* B = bufs + (int64_t)(K % nbuf) * brs_max;
+        const int row = K * 32 + lane;
+        const bool valid = row < n;
+        const int64_t grow = S.row0 + row;
+        if (rc != nullptr) {
+#pragma unroll
+            for (int k = 0; k < MM; ++k)
+#pragma unroll
+                for (int j = 0; j < NR; ++j) racc[k][j] += pv[k] * t[j];
         }
         for (int d = 0; d < c; ++d) {
             const int src = K - c + d;
@@ -234,25 +257,38 @@ __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __rest
         }
     }
     // ---------------- backward ----------------
-    block_copy_async(bufs + (int64_t)((nb - 1) % nbuf) * brs_max, F + (int64_t)(nb - 1) * brs,
-                     brs * sizeof(TF));
-    cp_async_commit();
+    // step K needs block rows K..K+c; row K-D is requested at step K
+    cp_async_wait_all();
+    __syncthreads();
+    for (int j = 0; j < D; ++j) {
+        const int r = nb - 1 - j;
+        if (r >= 0) block_copy_async(bufs + (int64_t)(r % nbuf) * brs_max, F + (int64_t)r * brs, brs * sizeof(TF));
+        cp_async_commit();
+    }
+    auto load_bwd = [&](int K, A (&wv)[NR]) {
+        const int row = K * 32 + lane;
+        const bool valid = K >= 0 && row < n;
+        const int64_t grow = S.row0 + row;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) wv[j] = valid ? (A)zf[grow * ld + rhs0 + j] : A(0);
+    };
+    A wn0[NR], wn1[NR];
+    load_bwd(nb - 1, wn0);
+    load_bwd(nb - 2, wn1);
     for (int K = nb - 1; K >= 0; --K) {
-        if (K - 1 >= 0) {
-            block_copy_async(bufs + (int64_t)((K - 1) % nbuf) * brs_max, F + (int64_t)(K - 1) * brs,
+        if (K - D >= 0)
+            block_copy_async(bufs + (int64_t)((K - D) % nbuf) * brs_max, F + (int64_t)(K - D) * brs,
                              brs * sizeof(TF));
-            cp_async_commit();
-            cp_async_wait_1();
-        } else {
-            cp_async_wait_all();
-        }
+        cp_async_commit();
+        A w[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) { w[j] = wn0[j]; wn0[j] = wn1[j]; }
+        load_bwd(K - 2, wn1);
+        cp_async_wait_n(D);
         __syncthreads();
         const int row = K * 32 + lane;
         const bool valid = row < n;
         const int64_t grow = S.row0 + row;
-        A w[NR];
-#pragma unroll
-        for (int j = 0; j < NR; ++j) w[j] = valid ? (A)zf[grow * ld + rhs0 + j] : A(0);
         for (int d = 1; d <= c; ++d) {
             const int src = K + d;
             if (src >= nb) break;
@@ -379,17 +415,104 @@ k_coarse_gemm(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
 #pragma unroll
         for (int i = 0; i < OPT; ++i) P[o0 + i * 256] = (TF)acc[i];
     }
-    __threadfence();
     __syncthreads();
-    if (t == 0) s_last = (atomicAdd(cnt + it.tile_id, 1) == it.nchunks - 1);
+    if (t == 0) {
+        __threadfence();
+        s_last = (atomicAdd(cnt + it.tile_id, 1) == it.nchunks - 1);
+        if (s_last) __threadfence();
+    }
     __syncthreads();
     if (!s_last) return;
-    __threadfence();
     for (int o = t; o < OUT; o += 256) {
         A s = A(0);
         for (int ch = 0; ch < it.nchunks; ++ch) s += (A)__ldcg(partial + (int64_t)(it.slot0 + ch) * OUT + o);
         const int r = o / LD, h = o % LD;
         if (r < it.nrows) out[(int64_t)(it.out0 + r) * LD + h] = (TF)s;
+    }
+    if (t == 0) cnt[it.tile_id] = 0;
+}
+
+// Few right-hand sides (LD <= 4): each warp streams whole rows of the node
+// matrix with coalesced loads (lanes over columns) against the gathered
+// input chunk held in shared memory; no per-stage barriers.
+template <typename TF, int LD>
+__global__ void __launch_bounds__(256)
+k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
+              const int32_t* __restrict__ rng, const TF* __restrict__ in, TF* __restrict__ out,
+              TF* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
+    if (st != nullptr && st->done) return;
+    using A = typename Acc<TF>::type;
+    constexpr int OUT = 32 * LD;
+    __shared__ TF sx[kCoarseChunk * LD];
+    __shared__ A sres[OUT];
+    __shared__ int s_last;
+    const CoarseItem it = items[blockIdx.x];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int kn = it.k1 - it.k0;
+    for (int kk = t; kk < kn; kk += 256) {
+        int k = it.k0 + kk, g = 0;
+        for (int j = 0; j < it.nrng; ++j) {
+            const int s0 = rng[2 * (it.rng_off + j)], len = rng[2 * (it.rng_off + j) + 1];
+            if (k < len) { g = s0 + k; break; }
+            k -= len;
+        }
+#pragma unroll
+        for (int h = 0; h < LD; ++h) sx[kk * LD + h] = in[(int64_t)g * LD + h];
+    }
+    __syncthreads();
+    // warp w owns rows w, w+8, w+16, w+24 of the tile
+    A acc[4][LD];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int h = 0; h < LD; ++h) acc[i][h] = A(0);
+    const TF* M0 = mat + it.moff + (int64_t)it.row_in_node * it.K + it.k0;
+    const bool rv[4] = {warp < it.nrows, warp + 8 < it.nrows, warp + 16 < it.nrows, warp + 24 < it.nrows};
+#pragma unroll 4
+    for (int kk = lane; kk < kn; kk += 32) {
+        A xv[LD];
+#pragma unroll
+        for (int h = 0; h < LD; ++h) xv[h] = (A)sx[kk * LD + h];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (rv[i]) {
+                const A mv = (A)__ldg(M0 + (int64_t)(warp + 8 * i) * it.K + kk);
+#pragma unroll
+                for (int h = 0; h < LD; ++h) acc[i][h] += mv * xv[h];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int h = 0; h < LD; ++h) {
+            A v = acc[i][h];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) sres[(warp + 8 * i) * LD + h] = v;
+        }
+    __syncthreads();
+    if (it.nchunks == 1) {
+        for (int o = t; o < OUT; o += 256) {
+            const int r = o / LD;
+            if (r < it.nrows) out[(int64_t)(it.out0 + r) * LD + (o % LD)] = (TF)sres[o];
+        }
+        return;
+    }
+    TF* P = partial + (int64_t)(it.slot0 + it.chunk) * OUT;
+    for (int o = t; o < OUT; o += 256) P[o] = (TF)sres[o];
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        s_last = (atomicAdd(cnt + it.tile_id, 1) == it.nchunks - 1);
+        if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (!s_last) return;
+    for (int o = t; o < OUT; o += 256) {
+        A v = A(0);
+        for (int ch = 0; ch < it.nchunks; ++ch) v += (A)__ldcg(partial + (int64_t)(it.slot0 + ch) * OUT + o);
+        const int r = o / LD;
+        if (r < it.nrows) out[(int64_t)(it.out0 + r) * LD + (o % LD)] = (TF)v;
     }
     if (t == 0) cnt[it.tile_id] = 0;
 }
@@ -409,7 +532,7 @@ k_prolong_dot(const int32_t* __restrict__ sub_of_row, const SubInfo* __restrict_
     __shared__ double s_scr[kRedThreads];
     const int64_t base = (int64_t)blockIdx.x * kRedElems;
     double v[2] = {0.0, 0.0};
-#pragma unroll 2
+#pragma unroll
     for (int k = 0; k < kRedElems / kRedThreads; ++k) {
         const int64_t e = base + threadIdx.x + k * kRedThreads;
         const int64_t row = e / LD;
@@ -470,7 +593,7 @@ k_dir_update(double* __restrict__ p, const double* __restrict__ z, const int32_t
     const CgScalars c = sc[seg * LD + rhs];
     if (!c.active) return;
     const double beta = c.beta;
-#pragma unroll 4
+#pragma unroll
     for (int k = 0; k < kRedElems / kRedThreads; ++k) {
         const int64_t e = base + threadIdx.x + k * kRedThreads;
         p[e] = z[e] + beta * p[e];
@@ -511,6 +634,7 @@ k_init_norms(const double* __restrict__ r, RedLayout R, CgScalars* sc, SolveStat
         st->nactive = nact;
         st->it = 0;
         st->status = 0;
+        st->worst = 1.0;
         st->done = (nact == 0);
     }
 }
@@ -550,6 +674,13 @@ __global__ void k_sddmm(const int64_t* __restrict__ rowptr, const int32_t* __res
     }
 }
 
+// sell_val[pos[e]] = vals[e] (caller CSR entry e -> SELL slot)
+__global__ void k_scatter_vals(const double* __restrict__ vals, const int64_t* __restrict__ pos, int64_t nnz,
+                               double* __restrict__ sell_val) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < nnz) sell_val[pos[e]] = vals[e];
+}
+
 __global__ void k_zero(double* __restrict__ a, int64_t n) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) a[i] = 0.0;
@@ -578,14 +709,11 @@ void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_do
 }
 
 template <int LD>
-static void update_ld(const LaunchCtx& L, double* x, double* r, const double* p, const double* q,
-                      double rtol2, int maxit) {
-    k_cg_update<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(x, r, p, q, L.red, L.sc, L.st, L.nseg,
-                                                          rtol2, maxit);
+static void update_ld(const LaunchCtx& L, double* x, double* r, const double* p, const double* q) {
+    k_cg_update<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(x, r, p, q, L.red, L.sc, L.st, L.nseg);
 }
-void launch_cg_update(const LaunchCtx& L, double* x, double* r, const double* p, const double* q,
-                      double rtol2, int maxit) {
-    AMS_DISPATCH_LD(L.ld, update_ld, L, x, r, p, q, rtol2, maxit);
+void launch_cg_update(const LaunchCtx& L, double* x, double* r, const double* p, const double* q) {
+    AMS_DISPATCH_LD(L.ld, update_ld, L, x, r, p, q);
 }
 
 template <int LD>
@@ -604,20 +732,36 @@ void launch_init_norms(const LaunchCtx& L, const double* r, int nrhs) {
     AMS_DISPATCH_LD(L.ld, norms_ld, L, r, nrhs);
 }
 
-size_t local_solve_smem(int cmax, int ld, size_t tf_bytes) {
-    return ((size_t)(cmax + 2) * blockrow_elems(cmax) + (size_t)(cmax + 1) * 32 * ld + 32 * ld) * tf_bytes;
+size_t local_solve_smem(int cmax, int ld, size_t tf_bytes, int depth) {
+    return ((size_t)(cmax + depth + 1) * blockrow_elems(cmax) + (size_t)(cmax + 1) * 32 * ld + 32 * ld) *
+           tf_bytes;
+}
+
+// Deepest prefetch (<= 6 block rows) whose staging fits a shared-memory
+// budget that still leaves room for several resident blocks per SM.
+int local_solve_depth(int cmax, int ld, size_t tf_bytes) {
+    const size_t budget = 100 * 1024, hard = 200 * 1024;
+    int d = 4;
+    while (d > 1 && local_solve_smem(cmax, ld, tf_bytes, d) > budget) --d;
+    while (d > 1 && local_solve_smem(cmax, ld, tf_bytes, d) > hard) --d;
+    return d;
 }
 
 template <typename TF, typename TP, int NR, int MM>
 static cudaError_t local_nr(const LocalSolveArgs& a, const void* fac, const void* psi, void* zf,
                             void* rc) {
     const int warps = a.ld / NR;
-    const size_t smem = local_solve_smem(a.cmax, a.ld, sizeof(TF));
+    const int depth = local_solve_depth(a.cmax, a.ld, sizeof(TF));
+    const size_t smem = local_solve_smem(a.cmax, a.ld, sizeof(TF), depth);
     auto kern = k_local_solve<TF, TP, NR, MM>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    static size_t smem_set = 0;           // per template instance
+    if (smem > smem_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
     kern<<<a.nsub, warps * 32, smem, a.stream>>>(a.subs, (const TF*)fac, a.rin, a.rowscale, (TF*)zf,
-                                                  (const TP*)psi, (TF*)rc, a.ld, a.cmax, a.st);
+                                                  (const TP*)psi, (TF*)rc, a.ld, a.cmax, depth, a.st);
     return cudaGetLastError();
 }
 
@@ -651,9 +795,13 @@ cudaError_t launch_local_solve(const LocalSolveArgs& a, int prec, const void* fa
 template <typename TF, int LD>
 static void coarse_ld(const CoarseLaunch& c, const void* in, void* out) {
     if (c.nitems == 0) return;
-    k_coarse_gemm<TF, LD><<<c.nitems, 256, 0, c.stream>>>(c.items, (const TF*)c.mat, c.rng,
-                                                          (const TF*)in, (TF*)out, (TF*)c.partial,
-                                                          c.cnt, c.st);
+    if (LD <= 4)
+        k_coarse_rows<TF, (LD <= 4 ? LD : 4)><<<c.nitems, 256, 0, c.stream>>>(
+            c.items, (const TF*)c.mat, c.rng, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt, c.st);
+    else
+        k_coarse_gemm<TF, LD><<<c.nitems, 256, 0, c.stream>>>(c.items, (const TF*)c.mat, c.rng,
+                                                              (const TF*)in, (TF*)out, (TF*)c.partial,
+                                                              c.cnt, c.st);
 }
 template <typename TF>
 static void coarse_tf(const CoarseLaunch& c, int ld, const void* in, void* out) {
@@ -709,6 +857,9 @@ void launch_permute_out(cudaStream_t s, const double* x, int64_t n, int nrhs, in
 void launch_sddmm(cudaStream_t s, const int64_t* rowptr, const int32_t* colind, int64_t n, int nrhs,
                   const double* lam, const double* u, double* dvals) {
     k_sddmm<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(rowptr, colind, n, nrhs, lam, u, dvals);
+}
+void launch_scatter_vals(cudaStream_t s, const double* vals, const int64_t* pos, int64_t nnz, double* sell_val) {
+    if (nnz > 0) k_scatter_vals<<<(unsigned)((nnz + 255) / 256), 256, 0, s>>>(vals, pos, nnz, sell_val);
 }
 void launch_zero(cudaStream_t s, double* a, int64_t n) {
     if (n > 0) k_zero<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n);

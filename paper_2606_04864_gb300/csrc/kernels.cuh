@@ -37,6 +37,19 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+// wait until at most n of this thread's committed groups are pending (n <= 7)
+__device__ __forceinline__ void cp_async_wait_n(int n) {
+    switch (n) {
+        case 0: asm volatile("cp.async.wait_group 0;\n" ::); break;
+        case 1: asm volatile("cp.async.wait_group 1;\n" ::); break;
+        case 2: asm volatile("cp.async.wait_group 2;\n" ::); break;
+        case 3: asm volatile("cp.async.wait_group 3;\n" ::); break;
+        case 4: asm volatile("cp.async.wait_group 4;\n" ::); break;
+        case 5: asm volatile("cp.async.wait_group 5;\n" ::); break;
+        case 6: asm volatile("cp.async.wait_group 6;\n" ::); break;
+        default: asm volatile("cp.async.wait_group 7;\n" ::); break;
+    }
+}
 
 // Copy `bytes` (multiple of 16, both addresses 16-byte aligned) with the
 // whole thread block.
@@ -78,28 +91,33 @@ struct RedLayout {
 __device__ inline void block_sum_vectors(const double* src, int count, int64_t stride, int nv,
                                          double* dst, double* scratch) {
     const int t = threadIdx.x;
-    const int lanes_per = blockDim.x / nv;        // threads per value
+    const int lanes_per = blockDim.x / nv;        // threads per value (power of two)
     const int v = t % nv;
     const int part = t / nv;
     double s = 0.0;
-    if (part < lanes_per) {
-        for (int j = part; j < count; j += lanes_per) s += __ldcg(src + (int64_t)j * stride + v);
-    }
+    for (int j = part; j < count; j += lanes_per) s += __ldcg(src + (int64_t)j * stride + v);
     scratch[t] = s;
     __syncthreads();
-    if (t < nv) {
-        double tot = 0.0;
-        for (int p = 0; p < lanes_per; ++p) tot += scratch[p * nv + t];
-        dst[t] = tot;
+    for (int h = lanes_per / 2; h >= 1; h >>= 1) {   // fixed-shape tree
+        if (part < h) scratch[t] += scratch[t + h * nv];
+        __syncthreads();
     }
+    if (t < nv) dst[t] = scratch[t];
     __syncthreads();
 }
 
 // Reduce per-thread partials `val[NV]` (thread t's right-hand side is
-// t % ld) to per-block totals, then run the two-level cross-block sum.
-// Returns true in exactly one thread block per system, after which
-// `out[v*ld + rhs]` (shared memory, NV*ld doubles) holds the system totals
-// for every thread of that block.
+// t % ld) to per-block totals, then run the cross-block sum.  Returns true
+// in exactly one thread block per system, after which `out[v*ld + rhs]`
+// (shared memory, NV*ld doubles) holds the system totals for every thread
+// of that block.
+//
+// Ordering: the block's partial is written, the block synchronises, and one
+// thread issues a GPU-scope fence and the counter increment; the block that
+// sees the last count fences once more before reading the partials (.cg
+// loads).  When a system has at most kRedDirect partial vectors the last
+// block sums them directly (one serial stage); otherwise groups of
+// kRedGroup blocks are summed first (two stages).
 template <int NV>
 __device__ bool seg_reduce(const double (&val)[NV], int ld, const RedLayout& R, double* out,
                            double* scratch, int& seg_out) {
@@ -126,48 +144,70 @@ __device__ bool seg_reduce(const double (&val)[NV], int ld, const RedLayout& R, 
     const int b = blockIdx.x;
     const int seg = R.blk_seg[b];
     seg_out = seg;
+    const int nblk = R.seg_nblk[seg];
     const int lb = b - R.seg_blk0[seg];
-    const int g = R.seg_grp0[seg] + lb / kRedGroup;
-    const int gsize = min(kRedGroup, R.seg_nblk[seg] - (lb / kRedGroup) * kRedGroup);
     const int nvl = NV * ld;
     if (t < nvl) R.part1[(int64_t)b * nvl + t] = out[t];
-    __threadfence();
     __syncthreads();
-    if (t == 0) s_last = (atomicAdd(R.cnt1 + g, 1) == gsize - 1);
+    if (nblk <= kRedDirect) {
+        if (t == 0) {
+            __threadfence();
+            s_last = (atomicAdd(R.cnt2 + seg, 1) == nblk - 1);
+        }
+        __syncthreads();
+        if (!s_last) return false;
+        if (t == 0) __threadfence();
+        __syncthreads();
+        block_sum_vectors(R.part1 + (int64_t)R.seg_blk0[seg] * nvl, nblk, nvl, nvl, out, scratch);
+        if (t == 0) R.cnt2[seg] = 0;
+        return true;
+    }
+    const int g = R.seg_grp0[seg] + lb / kRedGroup;
+    const int gsize = min(kRedGroup, nblk - (lb / kRedGroup) * kRedGroup);
+    if (t == 0) {
+        __threadfence();
+        s_last = (atomicAdd(R.cnt1 + g, 1) == gsize - 1);
+    }
     __syncthreads();
     if (!s_last) return false;
-    __threadfence();
+    if (t == 0) __threadfence();
+    __syncthreads();
     // 2) group sum
     const int gb0 = R.seg_blk0[seg] + (lb / kRedGroup) * kRedGroup;
     block_sum_vectors(R.part1 + (int64_t)gb0 * nvl, gsize, nvl, nvl, out, scratch);
     if (t == 0) R.cnt1[g] = 0;
     if (t < nvl) R.part2[(int64_t)g * nvl + t] = out[t];
-    __threadfence();
     __syncthreads();
-    const int ngrp = (R.seg_nblk[seg] + kRedGroup - 1) / kRedGroup;
-    if (t == 0) s_last = (atomicAdd(R.cnt2 + seg, 1) == ngrp - 1);
+    const int ngrp = (nblk + kRedGroup - 1) / kRedGroup;
+    if (t == 0) {
+        __threadfence();
+        s_last = (atomicAdd(R.cnt2 + seg, 1) == ngrp - 1);
+    }
     __syncthreads();
     if (!s_last) return false;
-    __threadfence();
+    if (t == 0) __threadfence();
+    __syncthreads();
     // 3) system sum
     block_sum_vectors(R.part2 + (int64_t)R.seg_grp0[seg] * nvl, ngrp, nvl, nvl, out, scratch);
     if (t == 0) R.cnt2[seg] = 0;
-    __syncthreads();
     return true;
 }
 
 // After a system's finisher ran: count finished systems; the last one
 // returns true (one thread block per launch) and resets the counter.
 __device__ inline bool last_system(const RedLayout& R, int nseg) {
+    if (nseg == 1) return true;
     __shared__ int s_last2;
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
+        __threadfence();
         s_last2 = (atomicAdd(R.cnt3, 1) == nseg - 1);
-        if (s_last2) R.cnt3[0] = 0;
+        if (s_last2) {
+            R.cnt3[0] = 0;
+            __threadfence();
+        }
     }
     __syncthreads();
-    if (s_last2) __threadfence();
     return s_last2;
 }
 

@@ -37,6 +37,22 @@ struct LocalSolveArgs {
     const SolveState* st;
 };
 
+struct LocalTmaArgs {
+    cudaStream_t stream;
+    int nsub;
+    const SubInfo* subs;
+    const struct CUtensorMap_st* tmF;
+    const struct CUtensorMap_st* tmB;
+    const int64_t* tile_row0;
+    const float* piv;
+    const double* rin;
+    int ld;
+    int cmax;
+    int mmax;
+    int64_t budget;
+    SolveState* st;
+};
+
 struct CoarseLaunch {
     cudaStream_t stream;
     int nitems;
@@ -49,14 +65,20 @@ struct CoarseLaunch {
 };
 
 void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_dot);
-void launch_cg_update(const LaunchCtx& L, double* x, double* r, const double* p, const double* q,
-                      double rtol2, int maxit);
+void launch_cg_update(const LaunchCtx& L, double* x, double* r, const double* p, const double* q);
 void launch_dir_update(const LaunchCtx& L, double* p, const double* z);
 void launch_init_norms(const LaunchCtx& L, const double* r, int nrhs);
-size_t local_solve_smem(int cmax, int ld, size_t tf_bytes);
+size_t local_solve_smem(int cmax, int ld, size_t tf_bytes, int depth);
+int local_solve_depth(int cmax, int ld, size_t tf_bytes);
 cudaError_t launch_local_solve(const LocalSolveArgs& a, int prec, const void* fac, const void* psi,
                                void* zf, void* rc);
 void launch_coarse_gemm(const CoarseLaunch& c, int prec, int ld, const void* in, void* out);
+cudaError_t launch_local_tma(const LocalTmaArgs& a, int prec, const void* psi, void* zf, void* rc);
+size_t local_tma_smem(int cmax, int ld, int depth);
+cudaError_t make_tile_map(void* base, int64_t rows, struct CUtensorMap_st* out);
+void launch_band_pack_tiles(cudaStream_t s, int nwork, const SubInfo* subs, const int64_t* band_off,
+                            const int2* work, const double* band, const int64_t* out_off, float* fwd, float* bwd,
+                            float* piv);
 void launch_prolong_dot(const LaunchCtx& L, int prec, const void* psi, const void* ec, const void* zf,
                         const double* r, const double* q, double* z, int flexible, int first,
                         int with_dot);
@@ -67,6 +89,7 @@ void launch_permute_out(cudaStream_t s, const double* x, int64_t n, int nrhs, in
 void launch_sddmm(cudaStream_t s, const int64_t* rowptr, const int32_t* colind, int64_t n, int nrhs,
                   const double* lam, const double* u, double* dvals);
 void launch_zero(cudaStream_t s, double* a, int64_t n);
+void launch_scatter_vals(cudaStream_t s, const double* vals, const int64_t* pos, int64_t nnz, double* sell_val);
 
 // ---- setup kernels (k_setup.cu) ---------------------------------------------
 struct BandArgs {

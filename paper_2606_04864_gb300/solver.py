@@ -127,6 +127,18 @@ class _Base:
             u = u[0]
         return u, its, rel
 
+    def profile_solve(self, f, rtol: float = 1e-8):
+        """One solve with CUDA events around every kernel.  Returns a list of
+        7 dicts (spmv, update, local, coarse fwd, coarse bwd, prolong,
+        direction) with total ms, launch count and bytes per launch."""
+        fv, nrhs = self._vec_in(f)
+        ms = np.zeros(7, dtype=np.float64)
+        by = np.zeros(7, dtype=np.float64)
+        cnt = np.zeros(7, dtype=np.int64)
+        check(lib().ams_profile_solve(self._h, _ptr(fv), nrhs, float(rtol), _ptr(ms), _ptr(by), _ptr(cnt)),
+              "ams_profile_solve", allow=(4,))
+        return [{"ms": float(ms[k]), "count": int(cnt[k]), "bytes": float(by[k])} for k in range(7)]
+
     def time_kernel(self, which: int, reps: int = 20):
         ms = C.c_double()
         by = C.c_double()
@@ -186,6 +198,12 @@ class AmsSolver(_Base):
         if hasattr(g, "ndim") and g.ndim == 1:
             lam = lam[0]
         return lam, dv, its
+
+    def set_matrix_values(self, vals):
+        """Replace A's values (same pattern) for later solves; the
+        preconditioner built at setup is kept."""
+        v = _as_dev(vals, np.float64) if self.device else _as_host(vals, np.float64)
+        check(lib().ams_set_matrix_values(self._h, _ptr(v)), "ams_set_matrix_values")
 
     def index_maps(self):
         perm = np.empty(self.n, dtype=np.int64)

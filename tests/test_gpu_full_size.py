@@ -1,0 +1,225 @@
+"""GPU checks at the full workload sizes (the launch configuration the bench
+times), on outputs the oracle can compute one by one and on properties that
+hold at any size.
+
+* 1024^2 channelised system: bit-exact index maps, sampled local eigenpairs
+  and local solves against the oracle, symmetry/positivity of M^{-1}, mixed
+  vs FP64 solutions and iteration counts, true residuals.
+* 128^3 lognormal system with 32 right-hand sides: every column converges,
+  mixed vs FP64, sampled eigenpairs.
+* 96^3 differentiable solve: adjoint gradient dL/dlog k against central
+  differences (h = 1e-6) on 32 random directions, and against the oracle's
+  dense adjoint gradient on a 16^3 copy.
+* 48 uneven systems with 8 right-hand sides in one batched handle.
+"""
+
+import numpy as np
+import pytest
+import scipy.linalg as la
+
+import oracle
+from oracle import OracleAMS, csr_to_scipy, index_maps, local_eigenpairs, local_matrices, pcg
+from workloads import (make_config2, make_config3, make_config4, make_config5, tpfa_csr,
+                       tpfa_values_from_logk, grf_logk, make_from_logk)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2606_04864_gb300 import AmsBatchedSolver, AmsSolver  # noqa: E402
+from paper_2606_04864_gb300.autograd import ams_solve  # noqa: E402
+
+
+def _A(w):
+    return csr_to_scipy(w.rowptr, w.colind, w.vals)
+
+
+def _check_sampled_eigs(s, w, A, subs, tol_lam=1e-10, tol_proj=1e-7):
+    mi, lams, psis = s.coarse_basis()
+    perm, sub_ptr = s.index_maps()
+    for i in subs:
+        dofs = perm[sub_ptr[i]:sub_ptr[i + 1]]
+        Ai, Ahat, sw = local_matrices(A, dofs)
+        lam_o, Psi_o, mi_o = local_eigenpairs(Ahat, sw, w.m)
+        assert mi[i] == mi_o
+        assert np.abs(lams[i] - lam_o[:mi_o]).max() <= tol_lam * max(1.0, np.abs(lam_o[:mi_o]).max())
+        P1 = psis[i] @ psis[i].T * sw[None, :]
+        P2 = Psi_o @ Psi_o.T * sw[None, :]
+        assert np.abs(P1 - P2).max() <= tol_proj * max(1.0, np.abs(P2).max())
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    w = make_config2()
+    return w, _A(w)
+
+
+def test_cfg2_index_maps_and_sampled_eigenpairs(cfg2):
+    w, A = cfg2
+    s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp64")
+    perm, sub_ptr = s.index_maps()
+    p_o, ip_o, sp_o = index_maps(w.part, w.nparts)
+    assert (perm == p_o).all() and (sub_ptr == sp_o).all()
+    # subdomains with the most high-permeability cells, plus fixed picks
+    logk = w.logk.reshape(-1)
+    chan = np.bincount(w.part, weights=(logk > 1).astype(float), minlength=w.nparts)
+    picks = sorted(set([0, 137, 511, 1023] + list(np.argsort(-chan)[:3])))
+    _check_sampled_eigs(s, w, A, picks)
+    info = s.info()
+    assert info["eig_max_residual"] <= 1e-11
+
+
+def test_cfg2_sampled_local_solves(cfg2):
+    w, A = cfg2
+    r = np.random.default_rng(7).standard_normal(w.n)
+    perm, iperm, sub_ptr = index_maps(w.part, w.nparts)
+    for prec, tol in [("fp64", 1e-11), ("fp32", 1e-4)]:
+        s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision=prec, coarse=False)
+        z = s.apply_preconditioner(r)
+        for i in [3, 400, 777, 1020]:
+            dofs = perm[sub_ptr[i]:sub_ptr[i + 1]]
+            Ai = A[dofs][:, dofs].toarray()
+            zi = la.cho_solve(la.cho_factor(Ai), r[dofs])
+            assert np.linalg.norm(z[dofs] - zi) <= tol * np.linalg.norm(zi), (prec, i)
+
+
+def test_cfg2_preconditioner_symmetric_positive(cfg2):
+    w, A = cfg2
+    s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp64")
+    rng = np.random.default_rng(8)
+    r1, r2 = rng.standard_normal(w.n), rng.standard_normal(w.n)
+    z = s.apply_preconditioner(np.stack([r1, r2]))
+    a, b = r2 @ z[0], r1 @ z[1]
+    assert abs(a - b) <= 1e-11 * max(abs(a), abs(b))
+    assert r1 @ z[0] > 0 and r2 @ z[1] > 0
+
+
+def test_cfg2_mixed_vs_fp64_full_size(cfg2):
+    w, A = cfg2
+    f = torch.as_tensor(w.rhs, device="cuda")
+    s64 = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp64", device=True)
+    smx = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp32_bf16", device=True)
+    u64, i64, r64 = s64.solve(f, rtol=1e-8)
+    umx, imx, rmx = smx.solve(f, rtol=1e-8)
+    assert abs(int(i64[0]) - int(imx[0])) <= 2
+    err = float(torch.linalg.norm(umx - u64) / torch.linalg.norm(u64))
+    assert err <= 1e-6, err
+    for u in (u64, umx):
+        un = u.cpu().numpy()[0]
+        # attainable true residual at this conditioning (k contrast 1e6)
+        assert np.linalg.norm(w.rhs[0] - A @ un) <= 1e-6 * np.linalg.norm(w.rhs[0])
+    assert r64[0] <= 1e-8 and rmx[0] <= 1e-8
+
+
+def test_cfg3_32_rhs_full_size():
+    w = make_config3()
+    A = _A(w)
+    f = torch.as_tensor(w.rhs, device="cuda")
+    smx = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp32_bf16", device=True)
+    umx, imx, rmx = smx.solve(f, rtol=1e-8)
+    assert (rmx <= 1e-8).all()
+    s64 = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp64", device=True)
+    u64, i64, r64 = s64.solve(f, rtol=1e-8)
+    assert (np.abs(i64.astype(int) - imx.astype(int)) <= 2).all(), (i64, imx)
+    d = torch.linalg.norm(umx - u64, dim=1) / torch.linalg.norm(u64, dim=1)
+    assert float(d.max()) <= 1e-6
+    un = umx.cpu().numpy()
+    for k in range(0, 32, 7):
+        assert np.linalg.norm(w.rhs[k] - A @ un[k]) <= 1e-6 * np.linalg.norm(w.rhs[k])
+    _check_sampled_eigs(s64, w, A, [0, 1000, 2047, 4095])
+
+
+def _cfg5_loss_and_grad(w, solver, logk_np, d, obs, rtol):
+    faces = w.extra["faces"]
+    logk = torch.tensor(logk_np.reshape(-1), dtype=torch.float64, device="cuda", requires_grad=True)
+    vals = tpfa_values_from_logk(logk, faces)
+    f = torch.as_tensor(w.rhs[0], device="cuda")
+    u = ams_solve(vals, f, solver, rtol=rtol)
+    obs_t = torch.as_tensor(obs, device="cuda")
+    loss = 0.5 * torch.sum((u[obs_t] - torch.as_tensor(d, device="cuda")) ** 2)
+    loss.backward()
+    return float(loss), logk.grad.detach().cpu().numpy(), u.detach()
+
+
+def test_cfg5_adjoint_gradient_vs_central_differences():
+    w = make_config5()
+    obs = w.extra["obs"]
+    # data from the perturbed ("truth") field
+    rp, ci, vt = tpfa_csr(w.extra["logk_truth"], w.extra["faces"])
+    st = AmsSolver(rp, ci, vt, w.part, w.nparts, w.m, precision="fp64")
+    ut, _, _ = st.solve(w.rhs[0], rtol=1e-12)
+    d = ut[obs]
+    st.close()
+    s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp64", device=True)
+    L0, g, u0 = _cfg5_loss_and_grad(w, s, w.logk, d, obs, rtol=1e-12)
+    rng = np.random.default_rng(55)
+    h = 1e-6
+    rel = []
+    f = torch.as_tensor(w.rhs[0], device="cuda")
+    for _ in range(32):
+        v = rng.standard_normal(w.n)
+        Ls = []
+        for sgn in (1.0, -1.0):
+            _, _, vals = tpfa_csr((w.logk.reshape(-1) + sgn * h * v).reshape(w.shape), w.extra["faces"])
+            s.set_matrix_values(torch.as_tensor(vals, device="cuda"))
+            u, _, _ = s.solve(f, rtol=1e-13, allow_not_converged=True)
+            un = u.cpu().numpy()
+            Ls.append(0.5 * np.sum((un[obs] - d) ** 2))
+        fd = (Ls[0] - Ls[1]) / (2 * h)
+        an = g @ v
+        rel.append(abs(fd - an) / max(abs(an), 1e-300))
+    rel = np.array(rel)
+    assert np.median(rel) <= 1e-5 and rel.max() <= 1e-4, rel
+
+
+def test_cfg5_gradient_vs_oracle_on_16cubed_copy():
+    full = make_config5()
+    logk = grf_logk((16, 16, 16), sigma=6.0, std=2.0, seed=5)
+    w = make_from_logk("cfg5_16", logk, 8, 6)
+    A = _A(w)
+    rng = np.random.default_rng(9)
+    obs = np.sort(rng.choice(w.n, size=256, replace=False))
+    d = np.zeros(len(obs))
+    s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp64", device=True)
+    L, g, u = _cfg5_loss_and_grad(w, s, logk, d, obs, rtol=1e-13)
+    # oracle: dense adjoint, chained through the same face formulas
+    o = OracleAMS(A, w.part, w.nparts, w.m)
+    uo = pcg(A, w.rhs[0], o.apply, rtol=1e-13).u
+    go = np.zeros(w.n)
+    go[obs] = uo[obs] - d
+    lam, dvals, _ = oracle.adjoint_gradient(A, uo, go, o.apply, rtol=1e-13)
+    faces = w.extra["faces"]
+    k = np.exp(logk.reshape(-1))
+    dT = -dvals[faces.pos_ij] - dvals[faces.pos_ji] + dvals[faces.pos_ii] + dvals[faces.pos_jj]
+    dTb = dvals[faces.pos_b]
+    ki, kj = k[faces.fi], k[faces.fj]
+    gl = np.zeros(w.n)
+    np.add.at(gl, faces.fi, dT * faces.hfac * 2 * kj ** 2 / (ki + kj) ** 2 * ki)
+    np.add.at(gl, faces.fj, dT * faces.hfac * 2 * ki ** 2 / (ki + kj) ** 2 * kj)
+    np.add.at(gl, faces.bcell, dTb * faces.hfac * 2 * k[faces.bcell])
+    assert np.linalg.norm(g - gl) <= 1e-8 * np.linalg.norm(gl)
+
+
+def test_cfg4_batched_48_systems():
+    ws = make_config4()
+    systems = [(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m) for w in ws]
+    nrhs = 8
+    b = AmsBatchedSolver(systems, precision="fp32_bf16", device=True)
+    f = b.pack([w.rhs for w in ws])
+    u, its, rel = b.solve(f, nrhs, rtol=1e-8)
+    assert (rel <= 1e-8).all()
+    us = b.unpack(u.cpu().numpy(), nrhs)
+    for i in [0, 11, 23, 24, 40, 47]:
+        A = _A(ws[i])
+        for k in (0, 5):
+            assert np.linalg.norm(ws[i].rhs[k] - A @ us[i][k]) <= 1e-6 * np.linalg.norm(ws[i].rhs[k])
+    # oracle parity on the two smallest 2-D systems
+    small = sorted(range(24), key=lambda i: ws[i].n)[:2]
+    for i in small:
+        w = ws[i]
+        A = _A(w)
+        o = OracleAMS(A, w.part, w.nparts, w.m)
+        ref = pcg(A, w.rhs[0], o.apply, rtol=1e-8)
+        assert abs(int(its[i, 0]) - ref.iters) <= 2
+        assert np.linalg.norm(us[i][0] - ref.u) <= 1e-6 * np.linalg.norm(ref.u)
