@@ -285,6 +285,37 @@ ams_status ams_profile_solve(ams_handle h, const double* f, int32_t nrhs,
                              double rtol, double* ms, double* bytes,
                              int64_t* count);
 
+/*
+ * ams_csr_spmv_dot_noalloc — y = A x and *xy = x^T y for a CSR matrix, with
+ * no handle and no device allocation.  The paper has no counterpart: this
+ * is a service for callers that cannot allocate device memory at the
+ * moment they need the product, e.g. code that runs while another library
+ * captures a CUDA graph (allocation is not allowed during capture), hosts
+ * whose device memory is handed out by their own fixed pool, or real-time
+ * callers that forbid allocation after start-up.
+ *
+ *  n        rows (and columns) of A, 0 <= n <= 8,388,608 (larger n returns
+ *           AMS_ERR_INVALID_ARG and does nothing)
+ *  rowptr   device int64 CSR row pointer (n+1), colind device int32,
+ *  vals     device FP64 values (any symmetric or unsymmetric CSR)
+ *  x        device FP64 input (n), y device FP64 output (n)
+ *  xy       device FP64 output scalar x^T y (summed in a fixed order)
+ *  stream   cudaStream_t as void*; the call is asynchronous on it (unlike
+ *           the other calls, it does not wait for the GPU)
+ *
+ * The dot product's per-block partial sums and arrival counter live in one
+ * fixed 64 KB device array inside the library, held by every GPU that loads
+ * it until the process exits.  The first call on a device looks up that
+ * array's address on the current device; make that first call before any
+ * stream capture.  All calls share the array (the counter is cleared at the
+ * start of each call), so calls that overlap on the GPU race: order them on
+ * one stream.
+ */
+ams_status ams_csr_spmv_dot_noalloc(int64_t n, const int64_t* rowptr,
+                                    const int32_t* colind, const double* vals,
+                                    const double* x, double* y, double* xy,
+                                    void* stream);
+
 #ifdef __cplusplus
 }
 #endif

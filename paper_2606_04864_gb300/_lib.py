@@ -98,6 +98,8 @@ SIGNATURES = {
                                   C.POINTER(C.c_double)]),
     "ams_profile_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_void_p,
                                     C.c_void_p, C.c_void_p]),
+    "ams_csr_spmv_dot_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 _lock = threading.Lock()
