@@ -98,6 +98,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def slowest_rank(value: float, world: int, device=None) -> float:
+    """Max over ranks of a per-rank time (the whole job ends with the slowest
+    replica).  Uses whatever process group is initialised (NCCL on GPUs,
+    gloo in the CPU tests)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 # ---------------------------------------------------------------------------
 # CPU oracle leg (bounded sample)
 # ---------------------------------------------------------------------------
@@ -193,7 +206,8 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = make_config2()
+    from workloads import make_config3, make_config5
+    w = {"cfg2": make_config2, "cfg3": make_config3, "cfg5": make_config5}[args.workload]()
     f_dev = torch.as_tensor(w.rhs, device=dev)
     mixed = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp32_bf16",
                       device=True)
@@ -215,15 +229,12 @@ def run_gpu(args):
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = mixed.info()["kernel_launches"] - launches0
-    t_local = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
-    A_res = None
+    ms_max = slowest_rank(ms, world, dev)
     u_np = u.cpu().numpy()
     from scipy.sparse import csr_matrix
     A = csr_matrix((w.vals, w.colind, w.rowptr), shape=(w.n, w.n))
-    true_rel = float(np.linalg.norm(w.rhs[0] - A @ u_np[0]) / np.linalg.norm(w.rhs[0]))
+    true_rel = max(float(np.linalg.norm(w.rhs[k] - A @ u_np[k]) / np.linalg.norm(w.rhs[k]))
+                   for k in range(w.nrhs))
 
     # per-kernel device times measured inside a real solve: the library
     # records a CUDA event pair around every kernel on its stream during one
@@ -261,7 +272,7 @@ def run_gpu(args):
 
     # end to end through the public API with host buffers (pinned), copies timed
     host = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp32_bf16", device=False)
-    f_pin = torch.empty((1, w.n), dtype=torch.float64).pin_memory()
+    f_pin = torch.empty((w.nrhs, w.n), dtype=torch.float64).pin_memory()
     f_pin.copy_(torch.as_tensor(w.rhs))
     f_np = f_pin.numpy()
     host.solve(f_np, rtol=1e-8)
@@ -272,13 +283,10 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
     host.close()
-    t_e2e = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_e2e, op=dist.ReduceOp.MAX)
-    e2e_s = float(t_e2e.item())
+    e2e_s = slowest_rank(e2e_s, world, dev)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cfg2":
         smp = OracleSample(w)
         est, detail = smp.step(int(its[0]))
         cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
@@ -299,13 +307,13 @@ def run_gpu(args):
             "dtype": "f64+f32",
             "data": "synthetic",
             "config": {
-                "workload": w.name, "n": w.n, "nnz": w.nnz, "nparts": w.nparts, "m": w.m, "nrhs": 1,
+                "workload": w.name, "n": w.n, "nnz": w.nnz, "nparts": w.nparts, "m": w.m, "nrhs": w.nrhs,
                 "rtol": 1e-8, "precision": "fp32 apply + bf16 basis, flexible CG",
-                "iters": int(its[0]), "relres": float(rel[0]), "true_relres": true_rel,
+                "iters": int(its.max()), "relres": float(rel.max()), "true_relres": true_rel,
                 "ncoarse": info["ncoarse"], "setup_s": round(info["setup_seconds"], 3),
                 "eig_s": round(info["eig_seconds"], 3), "eig_iterations": info["eig_iterations"],
                 "l2": "working set > 129 MB L2 (no flush needed)",
-                "fp64": {"time_s": ms64 / 1e3, "iters": int(its64[0]),
+                "fp64": {"time_s": ms64 / 1e3, "iters": int(its64.max()),
                          "setup_s": round(info64["setup_seconds"], 3)},
                 "mixed_speedup_vs_fp64": ms64 / ms_max if ms_max > 0 else None,
                 "u_rel_diff_mixed_vs_fp64": rel_mixed_vs_fp64,
@@ -323,8 +331,8 @@ def run_gpu(args):
                 "timing": "CUDA events around every launch inside one profiled solve",
                 "algorithmic_bytes_per_launch": kern[dom]["bytes"],
             },
-            "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * w.n,
-                    "d2h_bytes_per_step": 8 * w.n + 12},
+            "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": 8 * w.n * w.nrhs,
+                    "d2h_bytes_per_step": 8 * w.n * w.nrhs + 12 * w.nrhs},
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
@@ -344,6 +352,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg5"],
+                    help="cfg2 (default, the headline line): 1024^2 channels; cfg3: 128^3 with 32 "
+                         "right-hand sides; cfg5: 96^3 single right-hand side")
     ap.add_argument("--ref-crop", type=int, default=256, help="oracle sample: crop side (cells)")
     ap.add_argument("--ref-iters", type=int, default=0,
                     help="oracle sample: iteration count of the full solve (0: the crop's own count)")

@@ -106,11 +106,11 @@ __device__ inline void block_sum_vectors(const double* src, int count, int64_t s
     __syncthreads();
 }
 
-// Reduce per-thread partials `val[NV]` (thread t's right-hand side is
-// t % ld) to per-block totals, then run the cross-block sum.  Returns true
-// in exactly one thread block per system, after which `out[v*ld + rhs]`
-// (shared memory, NV*ld doubles) holds the system totals for every thread
-// of that block.
+// seg_reduce: reduce per-thread partials `val[NV]` (thread t's right-hand
+// side is t % ld) to per-block totals, then run the cross-block sum.
+// Returns true in exactly one thread block per system, after which
+// `out[v*ld + rhs]` (shared memory, NV*ld doubles) holds the system totals
+// for every thread of that block.
 //
 // Ordering: the block's partial is written, the block synchronises, and one
 // thread issues a GPU-scope fence and the counter increment; the block that
@@ -118,35 +118,16 @@ __device__ inline void block_sum_vectors(const double* src, int count, int64_t s
 // loads).  When a system has at most kRedDirect partial vectors the last
 // block sums them directly (one serial stage); otherwise groups of
 // kRedGroup blocks are summed first (two stages).
-template <int NV>
-__device__ bool seg_reduce(const double (&val)[NV], int ld, const RedLayout& R, double* out,
-                           double* scratch, int& seg_out) {
+// Cross-block stage for block `b` of system `seg`, whose NV*ld totals are
+// in out[] (shared memory).  Returns true in exactly one block per system,
+// with the system totals in out[].  `scratch` holds blockDim.x doubles;
+// requires blockDim.x % nvl == 0.
+__device__ inline bool cross_blocks(int b, int seg, int nvl, const RedLayout& R, double* out,
+                                    double* scratch) {
     const int t = threadIdx.x;
-    const int lane = t & 31;
-    const int warp = t >> 5;
-    const int nwarp = blockDim.x >> 5;
     __shared__ int s_last;
-    // 1) block totals per (v, rhs)
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-        double x = val[v];
-        for (int off = 16; off >= ld; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
-        // lanes 0..ld-1 hold the warp sums for rhs = lane
-        if (lane < ld) scratch[warp * 32 + lane] = x;
-        __syncthreads();
-        if (t < ld) {
-            double s = 0.0;
-            for (int w = 0; w < nwarp; ++w) s += scratch[w * 32 + t];
-            out[v * ld + t] = s;
-        }
-        __syncthreads();
-    }
-    const int b = blockIdx.x;
-    const int seg = R.blk_seg[b];
-    seg_out = seg;
     const int nblk = R.seg_nblk[seg];
     const int lb = b - R.seg_blk0[seg];
-    const int nvl = NV * ld;
     if (t < nvl) R.part1[(int64_t)b * nvl + t] = out[t];
     __syncthreads();
     if (nblk <= kRedDirect) {
@@ -191,6 +172,34 @@ __device__ bool seg_reduce(const double (&val)[NV], int ld, const RedLayout& R, 
     block_sum_vectors(R.part2 + (int64_t)R.seg_grp0[seg] * nvl, ngrp, nvl, nvl, out, scratch);
     if (t == 0) R.cnt2[seg] = 0;
     return true;
+}
+
+template <int NV>
+__device__ bool seg_reduce(const double (&val)[NV], int ld, const RedLayout& R, double* out,
+                           double* scratch, int& seg_out) {
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int warp = t >> 5;
+    const int nwarp = blockDim.x >> 5;
+    // 1) block totals per (v, rhs)
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        double x = val[v];
+        for (int off = 16; off >= ld; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+        // lanes 0..ld-1 hold the warp sums for rhs = lane
+        if (lane < ld) scratch[warp * 32 + lane] = x;
+        __syncthreads();
+        if (t < ld) {
+            double s = 0.0;
+            for (int w = 0; w < nwarp; ++w) s += scratch[w * 32 + t];
+            out[v * ld + t] = s;
+        }
+        __syncthreads();
+    }
+    const int b = blockIdx.x;
+    const int seg = R.blk_seg[b];
+    seg_out = seg;
+    return cross_blocks(b, seg, NV * ld, R, out, scratch);
 }
 
 // After a system's finisher ran: count finished systems; the last one
