@@ -102,7 +102,7 @@ struct ams_handle_s {
     int64_t n_total = 0, n_pad = 0, nnz_total = 0;
     int32_t N = 0;
     int64_t Nc = 0;
-    int cmax = 1, mmax = 0;
+    int cmax = 1, mmax = 0, nbmax = 1;
     std::vector<SubInfo> h_subs;
     std::vector<double> h_lam;          // kept eigenvalues, subdomain-major
     std::vector<DevBuf> bufs;
@@ -598,8 +598,8 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
     // build all layouts first (host), then run factorisation + extraction per system
     struct SysChunks { int64_t d0, d1; };
     std::vector<SysChunks> sys_chunks(h->nsys);
-    auto add_items = [&](std::vector<CoarseItem>& items, int64_t moff, int64_t K, int64_t rows, int64_t out0,
-                         int32_t rng_off, int32_t nrng) {
+    auto add_items = [&](std::vector<CoarseItem>& items, int64_t moff, int64_t K, int64_t ldm, int64_t rows,
+                         int64_t out0, int32_t rng_off, int32_t nrng) {
         for (int64_t r0 = 0; r0 < rows; r0 += 32) {
             const int nr = (int)std::min<int64_t>(32, rows - r0);
             const int nch = (int)std::max<int64_t>(1, (K + KCHUNK - 1) / KCHUNK);
@@ -607,6 +607,7 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
                 CoarseItem it{};
                 it.moff = moff;
                 it.K = (int32_t)K;
+                it.ldm = (int32_t)ldm;
                 it.nrows = nr;
                 it.row_in_node = (int32_t)r0;
                 it.out0 = (int32_t)(out0 + r0);
@@ -636,12 +637,13 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
             const int32_t roff = (int32_t)(rng.size() / 2);
             rng.push_back((int32_t)cst);
             rng.push_back((int32_t)Kf);
-            add_items(fwd, Roff, Kf, nd.k, a, roff, 1);
-            for (int64_t e0 = 0; e0 < nd.k * Kf; e0 += ECHUNK) {
-                desc.insert(desc.end(), {Roff, Kf, 0, nd.a, nd.cstart, (int64_t)roff, e0,
-                                         std::min(nd.k * Kf, e0 + ECHUNK)});
+            const int64_t Kfp = (Kf + 3) & ~int64_t(3);
+            add_items(fwd, Roff, Kf, Kfp, nd.k, a, roff, 1);
+            for (int64_t e0 = 0; e0 < nd.k * Kfp; e0 += ECHUNK) {
+                desc.insert(desc.end(), {Roff, Kf | (Kfp << 32), 0, nd.a, nd.cstart, (int64_t)roff, e0,
+                                         std::min(nd.k * Kfp, e0 + ECHUNK)});
             }
-            Roff += nd.k * Kf;
+            Roff += nd.k * Kfp;
             // backward block: rows of the node x (own rows, then ancestors' rows)
             const int32_t boff = (int32_t)(rng.size() / 2);
             int64_t Kb = 0;
@@ -653,13 +655,14 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
                 Kb += S.nodes[q].k;
                 ++nrng;
             }
-            add_items(bwd, Qoff, Kb, nd.k, a, boff, nrng);
-            for (int64_t e0 = 0; e0 < nd.k * Kb; e0 += ECHUNK) {
-                desc.insert(desc.end(), {Qoff, Kb, 1, nd.a, nd.cstart,
+            const int64_t Kbp = (Kb + 3) & ~int64_t(3);
+            add_items(bwd, Qoff, Kb, Kbp, nd.k, a, boff, nrng);
+            for (int64_t e0 = 0; e0 < nd.k * Kbp; e0 += ECHUNK) {
+                desc.insert(desc.end(), {Qoff, Kb | (Kbp << 32), 1, nd.a, nd.cstart,
                                          (int64_t)boff | ((int64_t)nrng << 32), e0,
-                                         std::min(nd.k * Kb, e0 + ECHUNK)});
+                                         std::min(nd.k * Kbp, e0 + ECHUNK)});
             }
-            Qoff += nd.k * Kb;
+            Qoff += nd.k * Kbp;
         }
         sys_chunks[s].d1 = (int64_t)desc.size() / 8;
     }
@@ -842,6 +845,7 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
             I.row0 = S.row0 + S.sub_ptr[a];
             I.n = (int32_t)(S.sub_ptr[a + 1] - S.sub_ptr[a]);
             I.nb = (I.n + 31) / 32;
+            h->nbmax = std::max(h->nbmax, (int)I.nb);
             I.seg = s;
             I.m = 0;
             int64_t bw = 0;
@@ -1049,7 +1053,7 @@ static ams_status launch_local(ams_handle h, int ld, const double* r, bool with_
     const bool coarse = h->Nc > 0;
     if (h->use_tma) {
         LocalTmaArgs a{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, r, ld, h->cmax,
-                       std::max(1, h->mmax), int64_t(1) << 20, with_state ? h->d_st : nullptr};
+                       std::max(1, h->mmax), h->nbmax, int64_t(1) << 20, with_state ? h->d_st : nullptr};
         AMS_CUDA_TRY(launch_local_tma(a, h->prec, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
     } else {
         LocalSolveArgs la{h->stream, h->N, h->d_subs, r, nullptr, ld, h->cmax, std::max(1, h->mmax),

@@ -55,12 +55,13 @@ __host__ __device__ inline int64_t blockrow_elems(int c) { return (int64_t)c * 1
 __host__ __device__ inline int tile_idx(int r, int q) { return q * 32 + (r ^ q); }
 
 // ---- coarse inverse GEMM items ---------------------------------------------
-// out[out0 + r][:] = sum_k Mat[moff + (row_in_node + r)*K + k] * in[g(k)][:]
+// out[out0 + r][:] = sum_k Mat[moff + (row_in_node + r)*ldm + k] * in[g(k)][:]
 // over k in [k0, k1), where g maps a node-matrix column to an input row
 // through the gather ranges rng[rng_off .. rng_off+nrng) (start, len).
 struct CoarseItem {
     int64_t moff;
     int32_t K;
+    int32_t ldm;           // row stride of the node matrix (K rounded up to 4)
     int32_t nrows;
     int32_t row_in_node;
     int32_t out0;

@@ -189,7 +189,13 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
 #pragma unroll
         for (int j = 0; j < NR; ++j) racc[k][j] = 0.f;
 
-    // inputs of block row K, prefetched two block rows ahead
+    // Per-row inputs of block row K (r, basis row, pivot; y in the backward
+    // sweep) sit in PF rotating register buffers: the step that consumes
+    // buffer u reloads it with row K+PF (forward) or K-PF (backward), so
+    // every global load has PF steps to arrive.  The step loop is unrolled
+    // by PF so that buffer indices are compile-time constants.
+    constexpr int PF = (NR <= 2) ? 4 : 2;
+    float bt[PF][NR], bp[PF][MM], bv[PF];
     auto load_fwd = [&](int K, float (&tv)[NR], float (&pv)[MM], float& pvt) {
         const int row = K * 32 + lane;
         const bool valid = K < nb && row < n;
@@ -199,28 +205,23 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
 #pragma unroll
         for (int k = 0; k < MM; ++k)
             pv[k] = (rc != nullptr && valid && k < m) ? to_f(psi[S.psi_off + (int64_t)row * m + k]) : 0.f;
-        pvt = (K < nb) ? piv[S.row0 + min(row, n - 1)] : 1.f;
-        if (!valid) pvt = 1.f;
+        pvt = valid ? piv[grow] : 1.f;
     };
-    float tn0[NR], pn0[MM], tn1[NR], pn1[MM], pv0, pv1;
-    load_fwd(0, tn0, pn0, pv0);
-    load_fwd(1, tn1, pn1, pv1);
+#pragma unroll
+    for (int u = 0; u < PF; ++u) load_fwd(u, bt[u], bp[u], bv[u]);
 
-    // ---------------- forward ----------------
-    for (int j = 0; j < D && j < nb; ++j) issue(&tmF, j);
-    for (int K = 0; K < nb && ok; ++K) {
+    auto fwd_step = [&](int K, float (&tb)[NR], float (&pb)[MM], float& vb) {
         if (K + D < nb) issue(&tmF, K + D);
         float t[NR], pv[MM];
-        const float pvt = pv0;
+        const float pvt = vb;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) { t[j] = tn0[j]; tn0[j] = tn1[j]; }
+        for (int j = 0; j < NR; ++j) t[j] = tb[j];
 #pragma unroll
-        for (int k = 0; k < MM; ++k) { pv[k] = pn0[k]; pn0[k] = pn1[k]; }
-        pv0 = pv1;
-        load_fwd(K + 2, tn1, pn1, pv1);
+        for (int k = 0; k < MM; ++k) pv[k] = pb[k];
+        load_fwd(K + PF, tb, pb, vb);
         wait_slot(K);
         ok = __syncthreads_and(ok);      // uniform decision across the block
-        if (!ok) break;
+        if (!ok) return;
         const int row = K * 32 + lane;
         const bool valid = row < n;
         const int64_t grow = S.row0 + row;
@@ -252,6 +253,15 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
             for (int j = 0; j < NR; ++j) zf[grow * ld + rhs0 + j] = y[j];
         }
         __syncthreads();
+    };
+
+    // ---------------- forward ----------------
+    for (int j = 0; j < D && j < nb; ++j) issue(&tmF, j);
+#pragma unroll 1
+    for (int K0 = 0; K0 < nb && ok; K0 += PF) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u)
+            if (K0 + u < nb && ok) fwd_step(K0 + u, bt[u], bp[u], bv[u]);
     }
     if (rc != nullptr && ok) {
 #pragma unroll
@@ -272,23 +282,16 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
         for (int j = 0; j < NR; ++j) wv[j] = valid ? zf[grow * ld + rhs0 + j] : 0.f;
         pvt = valid ? piv[grow] : 1.f;
     };
-    float wn0[NR], wn1[NR], q0, q1;
-    if (ok) {
-        load_bwd(nb - 1, wn0, q0);
-        load_bwd(nb - 2, wn1, q1);
-        for (int j = 0; j < D && nb - 1 - j >= 0; ++j) issue(&tmB, nb - 1 - j);
-    }
-    for (int K = nb - 1; K >= 0 && ok; --K) {
+    auto bwd_step = [&](int K, float (&wb)[NR], float& vb) {
         if (K - D >= 0) issue(&tmB, K - D);
         float w[NR];
-        const float pvt = q0;
+        const float pvt = vb;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) { w[j] = wn0[j]; wn0[j] = wn1[j]; }
-        q0 = q1;
-        load_bwd(K - 2, wn1, q1);
+        for (int j = 0; j < NR; ++j) w[j] = wb[j];
+        load_bwd(K - PF, wb, vb);
         wait_slot(K);
         ok = __syncthreads_and(ok);
-        if (!ok) break;
+        if (!ok) return;
         const int row = K * 32 + lane;
         const bool valid = row < n;
         const int64_t grow = S.row0 + row;
@@ -317,6 +320,17 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
             for (int j = 0; j < NR; ++j) zf[grow * ld + rhs0 + j] = x[j];
         }
         __syncthreads();
+    };
+    if (ok) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) load_bwd(nb - 1 - u, bt[u], bv[u]);
+        for (int j = 0; j < D && nb - 1 - j >= 0; ++j) issue(&tmB, nb - 1 - j);
+    }
+#pragma unroll 1
+    for (int K0 = nb - 1; K0 >= 0 && ok; K0 -= PF) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u)
+            if (K0 - u >= 0 && ok) bwd_step(K0 - u, bt[u], bv[u]);
     }
     if (!ok) {
         // record the timeout and drain this block's copies in flight (bounded)
@@ -325,6 +339,286 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
             st->done = 1;
         }
         for (int i = 0; i < nbuf; ++i) mbar_wait(smem_u32(bars + i), (phase >> i) & 1u, budget);
+    }
+}
+
+
+// ---------------------------------------------------------------------------
+// One right-hand side: one warp per subdomain, forward tiles only.
+//
+// With a single vector each step is a chain of two dependent 32x32 products
+// (the off-diagonal update, then L_KK^{-1}), so the kernel is bound by the
+// latency of that chain and by the bytes of the factor, not by arithmetic.
+// This variant trims both:
+//   * the backward sweep reads the forward tiles by column (lane l reads
+//     column l of a tile: element (r, l) lies in bank ((l/4) ^ (r mod 8))*4
+//     + l mod 4 of row r, so the 32 lanes of a load hit 32 distinct banks),
+//     so the transposed copy is never read and the block rows that the
+//     forward sweep left in the ring are reused without a reload;
+//   * y stays in shared memory between the sweeps and x overwrites it in
+//     place (step K reads y_K and x_{K+1..K+c} only);
+//   * the row of M_K is loaded once for both of its parts; the triangular
+//     masks act per 4-column chunk (a 0/1 weight per chunk, plus the one
+//     chunk that holds the diagonal), and each 32-term dot is summed as a
+//     tree of eight 4-term dots.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float dot4(const float4& a, const float4& b) {
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
+}
+__device__ __forceinline__ float4 mul4(const float4& a, const float4& b) {
+    return make_float4(a.x * b.x, a.y * b.y, a.z * b.z, a.w * b.w);
+}
+__device__ __forceinline__ float sum8(const float (&c)[8]) {
+    return ((c[0] + c[1]) + (c[2] + c[3])) + ((c[4] + c[5]) + (c[6] + c[7]));
+}
+__device__ __forceinline__ float wsum8(const float (&w)[8], const float (&c)[8]) {
+    const float a = fmaf(w[1], c[1], w[0] * c[0]);
+    const float b = fmaf(w[3], c[3], w[2] * c[2]);
+    const float d = fmaf(w[5], c[5], w[4] * c[4]);
+    const float e = fmaf(w[7], c[7], w[6] * c[6]);
+    return (a + b) + (d + e);
+}
+// Column `lane` of a swizzled tile against a broadcast vector v[0..31]:
+// c[j] = sum_{r in chunk j} T[r][lane] v[r].
+__device__ __forceinline__ void col_chunks(const float* T, const int (&csw)[8], const float* v, float (&c)[8]) {
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float4 x = *reinterpret_cast<const float4*>(v + 4 * j);
+        const int r = 4 * j;
+        const float a0 = T[(r + 0) * 32 + csw[(r + 0) & 7]];
+        const float a1 = T[(r + 1) * 32 + csw[(r + 1) & 7]];
+        const float a2 = T[(r + 2) * 32 + csw[(r + 2) & 7]];
+        const float a3 = T[(r + 3) * 32 + csw[(r + 3) & 7]];
+        c[j] = fmaf(a3, x.w, fmaf(a2, x.z, fmaf(a1, x.y, a0 * x.x)));
+    }
+}
+
+template <typename TP, int MM>
+__global__ void __launch_bounds__(32, 8)
+k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict__ subs,
+             const int64_t* __restrict__ tile_row0, const float* __restrict__ piv,
+             const double* __restrict__ rin, float* __restrict__ zf, const TP* __restrict__ psi,
+             float* __restrict__ rc, int cmax, int nbmax, int depth, int64_t budget, SolveState* st) {
+    if (st != nullptr && st->done) return;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const SubInfo S = subs[blockIdx.x];
+    const int c = S.c, nb = S.nb, n = S.n, m = S.m;
+    const int D = depth;
+    const int nbuf = cmax + D + 1;
+    float* tiles = (float*)base;                                        // nbuf * cmax * 1024
+    uint64_t* bars = (uint64_t*)(tiles + (size_t)nbuf * cmax * 1024);    // nbuf (padded to even)
+    float* yv = (float*)(bars + ((nbuf + 1) & ~1));                      // nbmax * 32: y, then x
+    float* tmp = yv + (size_t)nbmax * 32;                                // 32
+    const int lane = threadIdx.x;
+    const int jr = lane >> 2, er = lane & 3;
+    const int64_t trow = tile_row0[blockIdx.x];
+    const uint32_t tile_bytes = 4096u * (uint32_t)c;
+    const size_t slot_floats = (size_t)cmax * 1024;
+    uint32_t phase = 0, pend = 0;   // parity per slot; slots with a copy in flight
+    bool ok = true;
+
+    // per-lane offsets and masks, fixed for the whole kernel
+    int rsw[8], csw[8], cdo[4];
+    float fhi[8], flo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        rsw[j] = lane * 32 + ((j ^ (lane & 7)) << 2);   // chunk j of tile row `lane`
+        csw[j] = ((jr ^ j) << 2) + er;                 // element (r, lane) sits at r*32 + csw[r & 7]
+        fhi[j] = j > jr ? 1.f : 0.f;
+        flo[j] = j < jr ? 1.f : 0.f;
+    }
+    const int dsw = rsw[0] ^ (jr << 2);              // chunk jr of tile row `lane`
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int r = 4 * jr + e;
+        cdo[e] = r * 32 + ((jr ^ (r & 7)) << 2) + er;
+    }
+    const float4 dge = make_float4(0 >= er, 1 >= er, 2 >= er, 3 >= er);   // q >= lane inside chunk jr
+    const float4 dlt = make_float4(0 < er, 1 < er, 2 < er, 3 < er);
+    const float4 dle = make_float4(0 <= er, 1 <= er, 2 <= er, 3 <= er);
+    const float4 dgt = make_float4(0 > er, 1 > er, 2 > er, 3 > er);
+
+    if (lane == 0) {
+        for (int i = 0; i < nbuf; ++i) mbar_init(smem_u32(bars + i), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncwarp();
+
+    auto issue = [&](int K) {
+        const int slot = K % nbuf;
+        if (lane == 0) {
+            const uint32_t bar = smem_u32(bars + slot);
+            mbar_expect_tx(bar, tile_bytes);
+            for (int d = 0; d < c; ++d)
+                tma_load_2d(smem_u32(tiles + slot * slot_floats + d * 1024), &tmF, 0,
+                            (int32_t)(trow + ((int64_t)K * c + d) * 32), bar);
+        }
+        pend |= 1u << slot;
+    };
+    auto wait_slot = [&](int K) {
+        const int slot = K % nbuf;
+        if (!mbar_wait(smem_u32(bars + slot), (phase >> slot) & 1u, budget)) ok = false;
+        phase ^= 1u << slot;
+        pend &= ~(1u << slot);
+    };
+    auto row_tiles = [&](int K) -> const float* { return tiles + (K % nbuf) * slot_floats; };
+
+    float racc[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) racc[k] = 0.f;
+
+    // per-row inputs of block row K+PF are loaded while step K runs
+    constexpr int PF = 4;
+    float bt[PF], bp[PF][MM], bv[PF];
+    auto load_fwd = [&](int K, float& tv, float (&pv)[MM], float& pvt) {
+        const int row = K * 32 + lane;
+        const bool valid = K < nb && row < n;
+        const int64_t grow = S.row0 + row;
+        tv = valid ? (float)rin[grow] : 0.f;
+#pragma unroll
+        for (int k = 0; k < MM; ++k)
+            pv[k] = (rc != nullptr && valid && k < m) ? to_f(psi[S.psi_off + (int64_t)row * m + k]) : 0.f;
+        pvt = valid ? piv[grow] : 1.f;
+    };
+#pragma unroll
+    for (int u = 0; u < PF; ++u) load_fwd(u, bt[u], bp[u], bv[u]);
+
+    auto fwd_step = [&](int K, float& tb, float (&pb)[MM], float& vb) {
+        if (K + D < nb) issue(K + D);
+        float t = tb;
+        const float pvt = vb;
+        if (rc != nullptr) {
+#pragma unroll
+            for (int k = 0; k < MM; ++k) racc[k] = fmaf(pb[k], t, racc[k]);
+        }
+        load_fwd(K + PF, tb, pb, vb);
+        wait_slot(K);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) return;
+        const float* T = row_tiles(K);
+        float4 mr[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) mr[j] = *reinterpret_cast<const float4*>(T + rsw[j]);
+        const float4 md = *reinterpret_cast<const float4*>(T + dsw);
+        // t = r_K - sum_d L_{K,K-c+d} y_{K-c+d}
+#pragma unroll 1
+        for (int d = 1; d < c; ++d) {
+            const int src = K - c + d;
+            if (src < 0) continue;
+            const float* Td = T + d * 1024;
+            const float* v = yv + src * 32;
+            float cj[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                cj[j] = dot4(*reinterpret_cast<const float4*>(Td + rsw[j]), *reinterpret_cast<const float4*>(v + 4 * j));
+            t -= sum8(cj);
+        }
+        if (K >= c) {   // upper part of M_K (q >= lane) is L_{K,K-c}
+            const float* v = yv + (K - c) * 32;
+            float cj[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) cj[j] = dot4(mr[j], *reinterpret_cast<const float4*>(v + 4 * j));
+            t -= wsum8(fhi, cj) + dot4(mul4(md, dge), *reinterpret_cast<const float4*>(v + 4 * jr));
+        }
+        tmp[lane] = t;
+        __syncwarp();
+        // y_K = L_KK^{-1} t: pivot times t plus the strict lower part of M_K
+        float y;
+        {
+            float cj[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) cj[j] = dot4(mr[j], *reinterpret_cast<const float4*>(tmp + 4 * j));
+            y = fmaf(pvt, t, wsum8(flo, cj) + dot4(mul4(md, dlt), *reinterpret_cast<const float4*>(tmp + 4 * jr)));
+        }
+        yv[K * 32 + lane] = y;
+        __syncwarp();
+    };
+
+    // ---------------- forward ----------------
+    for (int j = 0; j < D && j < nb; ++j) issue(j);
+#pragma unroll 1
+    for (int K0 = 0; K0 < nb && ok; K0 += PF) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u)
+            if (K0 + u < nb && ok) fwd_step(K0 + u, bt[u], bp[u], bv[u]);
+    }
+    if (rc != nullptr && ok) {
+#pragma unroll
+        for (int k = 0; k < MM; ++k) {
+            float v = racc[k];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+            if (lane == 0 && k < m) rc[S.coff + k] = v;
+        }
+    }
+
+    // ---------------- backward ----------------
+    // Block rows nb-nbuf .. nb-1 are still in the ring; older ones are
+    // reloaded D steps ahead of their use.
+    const int Rres = nb > nbuf ? nb - nbuf : 0;
+    auto load_bwd = [&](int K, float& pvt) {
+        const int row = K * 32 + lane;
+        pvt = (K >= 0 && row < n) ? piv[S.row0 + row] : 1.f;
+    };
+    auto bwd_step = [&](int K, float& vb) {
+        if (K - D >= 0 && K - D < Rres) issue(K - D);
+        const float pvt = vb;
+        load_bwd(K - PF, vb);
+        if (K < Rres) wait_slot(K);
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) return;
+        float w = yv[K * 32 + lane];
+        // w = y_K - sum_d L_{K+d,K}^T x_{K+d}
+#pragma unroll 1
+        for (int d = 1; d < c; ++d) {
+            const int src = K + d;
+            if (src >= nb) break;
+            float cj[8];
+            col_chunks(row_tiles(src) + (c - d) * 1024, csw, yv + src * 32, cj);
+            w -= sum8(cj);
+        }
+        if (K + c < nb) {   // L_{K+c,K}: upper part of M_{K+c}, rows r <= lane of column lane
+            const float* Tm = row_tiles(K + c);
+            const float* v = yv + (K + c) * 32;
+            float cj[8];
+            col_chunks(Tm, csw, v, cj);
+            const float4 ad = make_float4(Tm[cdo[0]], Tm[cdo[1]], Tm[cdo[2]], Tm[cdo[3]]);
+            w -= wsum8(flo, cj) + dot4(mul4(ad, dle), *reinterpret_cast<const float4*>(v + 4 * jr));
+        }
+        tmp[lane] = w;
+        __syncwarp();
+        // x_K = L_KK^{-T} w: rows r > lane of column lane of M_K
+        float x;
+        {
+            const float* Tm = row_tiles(K);
+            float cj[8];
+            col_chunks(Tm, csw, tmp, cj);
+            const float4 ad = make_float4(Tm[cdo[0]], Tm[cdo[1]], Tm[cdo[2]], Tm[cdo[3]]);
+            x = fmaf(pvt, w, wsum8(fhi, cj) + dot4(mul4(ad, dgt), *reinterpret_cast<const float4*>(tmp + 4 * jr)));
+        }
+        yv[K * 32 + lane] = x;
+        const int row = K * 32 + lane;
+        if (row < n) zf[S.row0 + row] = x;
+        __syncwarp();
+    };
+    if (ok) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u) load_bwd(nb - 1 - u, bv[u]);
+    }
+#pragma unroll 1
+    for (int K0 = nb - 1; K0 >= 0 && ok; K0 -= PF) {
+#pragma unroll
+        for (int u = 0; u < PF; ++u)
+            if (K0 - u >= 0 && ok) bwd_step(K0 - u, bv[u]);
+    }
+    if (!ok) {
+        // record the timeout and drain the copies still in flight (bounded)
+        if (lane == 0 && st != nullptr) {
+            atomicExch(&st->status, (int)AMS_ERR_DEVICE_TIMEOUT);
+            st->done = 1;
+        }
+        for (int i = 0; i < nbuf; ++i)
+            if ((pend >> i) & 1u) mbar_wait(smem_u32(bars + i), (phase >> i) & 1u, budget);
     }
 }
 
@@ -337,9 +631,14 @@ size_t local_tma_smem(int cmax, int ld, int depth) {
            ((size_t)(cmax + 1) * 32 * ld + 32 * ld) * sizeof(float);
 }
 
+// Prefetch depth: block rows in flight per subdomain.  Deeper rings hide
+// more TMA latency but cost shared memory; the single-warp blocks of the
+// one-right-hand-side case must stay small enough for about eight resident
+// blocks per SM.
 int local_tma_depth(int cmax, int ld) {
-    int d = 4;
-    while (d > 1 && local_tma_smem(cmax, ld, d) > 100 * 1024) --d;
+    const size_t budget = (ld == 1) ? 32 * 1024 : 100 * 1024;
+    int d = 6;
+    while (d > 1 && local_tma_smem(cmax, ld, d) > budget) --d;
     return d;
 }
 
@@ -380,7 +679,48 @@ static cudaError_t tma_tp(const LocalTmaArgs& a, const void* psi, void* zf, void
     }
 }
 
+size_t local_tma1_smem(int cmax, int nbmax, int depth) {
+    const int nbuf = cmax + depth + 1;
+    return 1024 /* alignment slack */ + (size_t)nbuf * cmax * 4096 + (size_t)((nbuf + 1) & ~1) * 8 +
+           ((size_t)nbmax * 32 + 32) * sizeof(float);
+}
+
+// Depth for the one-right-hand-side kernel: as deep as possible (at most 6)
+// while about seven single-warp blocks still fit on an SM.
+static int local_tma1_depth(int cmax, int nbmax) {
+    int d = 6;
+    while (d > 2 && local_tma1_smem(cmax, nbmax, d) > 31 * 1024) --d;
+    return d;
+}
+
+template <typename TP, int MM>
+static cudaError_t tma1(const LocalTmaArgs& a, const void* psi, void* zf, void* rc) {
+    const int depth = local_tma1_depth(a.cmax, a.nbmax);
+    const size_t smem = local_tma1_smem(a.cmax, a.nbmax, depth);
+    auto kern = k_local_tma1<TP, MM>;
+    static size_t smem_set = 0;
+    if (smem > smem_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        smem_set = smem;
+    }
+    kern<<<a.nsub, 32, smem, a.stream>>>(*a.tmF, a.subs, a.tile_row0, a.piv, a.rin, (float*)zf, (const TP*)psi,
+                                         (float*)rc, a.cmax, a.nbmax, depth, a.budget, a.st);
+    return cudaGetLastError();
+}
+
+// The one-right-hand-side kernel keeps y for a whole subdomain in shared
+// memory; wider subdomains use the general kernel.
+static bool use_tma1(const LocalTmaArgs& a) {
+    return a.ld == 1 && local_tma1_smem(a.cmax, a.nbmax, 2) <= 200 * 1024;
+}
+
 cudaError_t launch_local_tma(const LocalTmaArgs& a, int prec, const void* psi, void* zf, void* rc) {
+    if (use_tma1(a)) {
+        const bool big = a.mmax > 8;
+        if (prec == AMS_PREC_FP32) return big ? tma1<float, 16>(a, psi, zf, rc) : tma1<float, 8>(a, psi, zf, rc);
+        return big ? tma1<__nv_bfloat16, 16>(a, psi, zf, rc) : tma1<__nv_bfloat16, 8>(a, psi, zf, rc);
+    }
     if (prec == AMS_PREC_FP32) return tma_tp<float>(a, psi, zf, rc);
     return tma_tp<__nv_bfloat16>(a, psi, zf, rc);
 }

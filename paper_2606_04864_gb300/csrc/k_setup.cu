@@ -587,26 +587,29 @@ __global__ void k_extract(const int64_t* __restrict__ desc, const int32_t* __res
                           const double* __restrict__ Linv, int64_t ldL, double* __restrict__ out64,
                           float* __restrict__ out32) {
     const int64_t* D = desc + 8 * (int64_t)blockIdx.x;
-    const int64_t out_off = D[0], K = D[1], kind = D[2], a = D[3], cstart = D[4];
+    const int64_t out_off = D[0], K = D[1] & 0xffffffff, ldm = D[1] >> 32, kind = D[2], a = D[3], cstart = D[4];
     const int rng_off = (int)(D[5] & 0xffffffff), nrng = (int)(D[5] >> 32);
-    const int64_t e0 = D[6], e1 = D[7];
+    const int64_t e0 = D[6], e1 = D[7];   // element range over rows x ldm
     for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const int64_t r = e / K, kk = e % K;
-        int64_t i, j;
-        if (kind == 0) {            // forward: row a+r, column cstart+kk
-            i = a + r;
-            j = cstart + kk;
-        } else {                    // backward: row g(kk), column a+r
-            int64_t k2 = kk, g = 0;
-            for (int q = 0; q < nrng; ++q) {
-                const int64_t s0 = rng[2 * (rng_off + q)], len = rng[2 * (rng_off + q) + 1];
-                if (k2 < len) { g = s0 + k2; break; }
-                k2 -= len;
+        const int64_t r = e / ldm, kk = e % ldm;
+        double v = 0.0;
+        if (kk < K) {
+            int64_t i, j;
+            if (kind == 0) {            // forward: row a+r, column cstart+kk
+                i = a + r;
+                j = cstart + kk;
+            } else {                    // backward: row g(kk), column a+r
+                int64_t k2 = kk, g = 0;
+                for (int q = 0; q < nrng; ++q) {
+                    const int64_t s0 = rng[2 * (rng_off + q)], len = rng[2 * (rng_off + q) + 1];
+                    if (k2 < len) { g = s0 + k2; break; }
+                    k2 -= len;
+                }
+                i = g;
+                j = a + r;
             }
-            i = g;
-            j = a + r;
+            v = (i >= j) ? Linv[i + j * ldL] : 0.0;
         }
-        const double v = (i >= j) ? Linv[i + j * ldL] : 0.0;
         if (out64) out64[out_off + e] = v;
         if (out32) out32[out_off + e] = (float)v;
     }

@@ -9,6 +9,7 @@
 //   k_dir_update    p = z + beta p
 #include <cstdint>
 #include <cstdio>
+#include <type_traits>
 
 #include "ams_internal.h"
 #include "kernels.cuh"
@@ -356,12 +357,12 @@ k_coarse_gemm(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
     A acc[OPT];
 #pragma unroll
     for (int i = 0; i < OPT; ++i) acc[i] = A(0);
-    const TF* M0 = mat + it.moff + (int64_t)it.row_in_node * it.K;
+    const TF* M0 = mat + it.moff + (int64_t)it.row_in_node * it.ldm;
     for (int kb = it.k0; kb < it.k1; kb += KC) {
         const int kn = min(KC, it.k1 - kb);
         for (int i = t; i < 32 * KC; i += 256) {
             const int r = i / KC, kk = i % KC;
-            sM[r][kk] = (r < it.nrows && kk < kn) ? M0[(int64_t)r * it.K + kb + kk] : TF(0);
+            sM[r][kk] = (r < it.nrows && kk < kn) ? M0[(int64_t)r * it.ldm + kb + kk] : TF(0);
         }
         for (int i = t; i < KC * LD; i += 256) {
             const int kk = i / LD, h = i % LD;
@@ -433,8 +434,10 @@ k_coarse_gemm(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
 }
 
 // Few right-hand sides (LD <= 4): each warp streams whole rows of the node
-// matrix with coalesced loads (lanes over columns) against the gathered
-// input chunk held in shared memory; no per-stage barriers.
+// matrix with coalesced 16-byte loads (lane j covers columns 4j..4j+3 of
+// every 128-column group) against the gathered input chunk held in shared
+// memory; no per-stage barriers.  Node-matrix rows are padded with zeros to
+// a multiple of 4 columns, so every row starts 16-byte aligned.
 template <typename TF, int LD>
 __global__ void __launch_bounds__(256)
 k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
@@ -442,22 +445,37 @@ k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
               TF* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
     if (st != nullptr && st->done) return;
     using A = typename Acc<TF>::type;
+    using V4 = typename std::conditional<sizeof(TF) == 4, float4, double4>::type;
     constexpr int OUT = 32 * LD;
-    __shared__ TF sx[kCoarseChunk * LD];
+    constexpr int MAXR = 64;                  // gather ranges staged in shared memory
+    __shared__ __align__(16) TF sx[(kCoarseChunk + 4) * LD];
     __shared__ A sres[OUT];
+    __shared__ int srng[2 * MAXR];
     __shared__ int s_last;
     const CoarseItem it = items[blockIdx.x];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int kn = it.k1 - it.k0;
-    for (int kk = t; kk < kn; kk += 256) {
-        int k = it.k0 + kk, g = 0;
-        for (int j = 0; j < it.nrng; ++j) {
-            const int s0 = rng[2 * (it.rng_off + j)], len = rng[2 * (it.rng_off + j) + 1];
-            if (k < len) { g = s0 + k; break; }
-            k -= len;
+    const int kn4 = (kn + 3) & ~3;
+    const int nr = min(it.nrng, MAXR);
+    for (int i = t; i < 2 * nr; i += 256) srng[i] = rng[2 * it.rng_off + i];
+    __syncthreads();
+    for (int kk = t; kk < kn4; kk += 256) {
+        TF v[LD];
+#pragma unroll
+        for (int h = 0; h < LD; ++h) v[h] = TF(0);
+        if (kk < kn) {
+            int k = it.k0 + kk, g = 0;
+            for (int j = 0; j < it.nrng; ++j) {
+                const int s0 = j < MAXR ? srng[2 * j] : rng[2 * (it.rng_off + j)];
+                const int len = j < MAXR ? srng[2 * j + 1] : rng[2 * (it.rng_off + j) + 1];
+                if (k < len) { g = s0 + k; break; }
+                k -= len;
+            }
+#pragma unroll
+            for (int h = 0; h < LD; ++h) v[h] = in[(int64_t)g * LD + h];
         }
 #pragma unroll
-        for (int h = 0; h < LD; ++h) sx[kk * LD + h] = in[(int64_t)g * LD + h];
+        for (int h = 0; h < LD; ++h) sx[kk * LD + h] = v[h];
     }
     __syncthreads();
     // warp w owns rows w, w+8, w+16, w+24 of the tile
@@ -466,19 +484,26 @@ k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int h = 0; h < LD; ++h) acc[i][h] = A(0);
-    const TF* M0 = mat + it.moff + (int64_t)it.row_in_node * it.K + it.k0;
+    const TF* M0 = mat + it.moff + (int64_t)it.row_in_node * it.ldm + it.k0;
     const bool rv[4] = {warp < it.nrows, warp + 8 < it.nrows, warp + 16 < it.nrows, warp + 24 < it.nrows};
-#pragma unroll 4
-    for (int kk = lane; kk < kn; kk += 32) {
-        A xv[LD];
+#pragma unroll 2
+    for (int c4 = lane; 4 * c4 < kn4; c4 += 32) {
+        V4 mv[4];
 #pragma unroll
-        for (int h = 0; h < LD; ++h) xv[h] = (A)sx[kk * LD + h];
+        for (int i = 0; i < 4; ++i)
+            if (rv[i]) mv[i] = *reinterpret_cast<const V4*>(M0 + (int64_t)(warp + 8 * i) * it.ldm + 4 * c4);
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            if (rv[i]) {
-                const A mv = (A)__ldg(M0 + (int64_t)(warp + 8 * i) * it.K + kk);
+        for (int e = 0; e < 4; ++e) {
+            A xv[LD];
 #pragma unroll
-                for (int h = 0; h < LD; ++h) acc[i][h] += mv * xv[h];
+            for (int h = 0; h < LD; ++h) xv[h] = (A)sx[(4 * c4 + e) * LD + h];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                if (rv[i]) {
+                    const A m = (A)(e == 0 ? mv[i].x : e == 1 ? mv[i].y : e == 2 ? mv[i].z : mv[i].w);
+#pragma unroll
+                    for (int h = 0; h < LD; ++h) acc[i][h] += m * xv[h];
+                }
             }
         }
     }

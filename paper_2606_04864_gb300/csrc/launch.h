@@ -49,6 +49,7 @@ struct LocalTmaArgs {
     int ld;
     int cmax;
     int mmax;
+    int nbmax;          // largest number of 32-row block rows of a subdomain
     int64_t budget;
     SolveState* st;
 };
