@@ -262,13 +262,33 @@ ams_status ams_apply_preconditioner(ams_handle h, const double* r,
 ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y);
 
 /*
+ * The kernels of one CG iteration, in launch order (indices of
+ * ams_time_kernel and of the ams_profile_solve outputs):
+ *   AMS_KERNEL_SPMV        direction p = z + beta p_old, q = A p, p.q
+ *   AMS_KERNEL_LOCAL       local solves sum_i R_i^T A_i^{-1} R_i r' and the
+ *                          restriction R_0 r', with r' = r - alpha q
+ *   AMS_KERNEL_COARSE_FWD  y = L_c^{-1} r_c   (A_0 = L_c L_c^T)
+ *   AMS_KERNEL_COARSE_BWD  e_c = L_c^{-T} y
+ *   AMS_KERNEL_PROLONG     z = z_f + R_0^T e_c, r = r', x += alpha p, dots,
+ *                          convergence test and beta
+ * Without a coarse space (coarse = 0) the two coarse kernels do not run.
+ */
+enum {
+    AMS_KERNEL_SPMV = 0,
+    AMS_KERNEL_LOCAL = 1,
+    AMS_KERNEL_COARSE_FWD = 2,
+    AMS_KERNEL_COARSE_BWD = 3,
+    AMS_KERNEL_PROLONG = 4,
+    AMS_NUM_KERNELS = 5
+};
+
+/*
  * Time one kernel of the solve on the handle's current solve state (after
  * an ams_solve with nrhs right-hand sides): `reps` back-to-back launches on
- * the handle's stream between two CUDA events.  which: 0 SpMV+dot,
- * 1 CG update, 2 local solves + restriction, 3 coarse forward, 4 coarse
- * backward, 5 prolongation + dots, 6 direction update.  Outputs the mean
- * launch time (ms) and the kernel's algorithmic bytes per launch (each
- * operand read once, each output written once).
+ * the handle's stream between two CUDA events.  which: an AMS_KERNEL_*
+ * index.  Outputs the mean launch time (ms) and the kernel's algorithmic
+ * bytes per launch (each operand read once, each output written once).
+ * The launches overwrite the handle's solve work vectors.
  */
 ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps,
                            double* avg_ms, double* bytes);
@@ -277,9 +297,10 @@ ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps,
  * One solve (same arguments and result as ams_solve, output discarded) with
  * a CUDA event pair recorded around every kernel on the handle's stream, so
  * each kernel's device time is measured inside a real solve (cold caches,
- * real data).  Outputs per kernel (same order as ams_time_kernel): total
- * milliseconds `ms[7]`, launches `count[7]`, algorithmic bytes per launch
- * `bytes[7]`.  Host arrays; the solve runs without graph capture.
+ * real data).  Outputs per kernel (AMS_KERNEL_* order), host arrays of
+ * AMS_NUM_KERNELS entries: total milliseconds `ms`, launches `count`,
+ * algorithmic bytes per launch `bytes`.  The solve runs without graph
+ * capture.
  */
 ams_status ams_profile_solve(ams_handle h, const double* f, int32_t nrhs,
                              double rtol, double* ms, double* bytes,

@@ -20,6 +20,9 @@ STATUS_NAMES = {
     4: "AMS_ERR_NOT_CONVERGED", 5: "AMS_ERR_DEVICE_TIMEOUT", 6: "AMS_ERR_CUDA", 7: "AMS_ERR_OOM",
 }
 PREC = {"fp64": 0, "fp32": 1, "fp32_bf16": 2}
+# AMS_KERNEL_* indices of ams_time_kernel / ams_profile_solve, in launch order
+KERNEL_NAMES = ["spmv_direction", "local_solve_restrict", "coarse_fwd", "coarse_bwd", "prolong_update"]
+AMS_NUM_KERNELS = len(KERNEL_NAMES)
 CG = {"auto": -1, "pcg": 0, "fcg": 1}
 
 

@@ -81,8 +81,8 @@ using namespace ams;
 
 // per-kernel event timing of one solve (ams_profile_solve)
 struct KernelProfile {
-    double ms[7] = {0, 0, 0, 0, 0, 0, 0};
-    int64_t count[7] = {0, 0, 0, 0, 0, 0, 0};
+    double ms[AMS_NUM_KERNELS] = {};
+    int64_t count[AMS_NUM_KERNELS] = {};
     cudaEvent_t ev[32];
     int nev = 0;
     int which[16];
@@ -137,6 +137,7 @@ struct ams_handle_s {
     // solve work space (sized for ld_alloc)
     int ld_alloc = 0, ld_last = 0;
     double *d_x = nullptr, *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_z = nullptr;
+    double* d_p2 = nullptr;             // second direction buffer (iterations alternate p and p2)
     void *d_zf = nullptr, *d_rc = nullptr, *d_yc = nullptr, *d_ec = nullptr;
     double *d_stage_in = nullptr, *d_stage_out = nullptr, *d_stage_aux = nullptr;
     double* d_stage_dvals = nullptr;
@@ -224,8 +225,8 @@ static ams_status get_red(ams_handle h, int ld, RedCache** out) {
     AMS_TRY(upload(h, &rc.seg_blk0, seg_blk0));
     AMS_TRY(upload(h, &rc.seg_nblk, seg_nblk));
     AMS_TRY(upload(h, &rc.seg_grp0, seg_grp0));
-    AMS_TRY(h->alloc_t(&rc.part1, (size_t)rc.nblk * 2 * ld));
-    AMS_TRY(h->alloc_t(&rc.part2, (size_t)ngrp * 2 * ld));
+    AMS_TRY(h->alloc_t(&rc.part1, (size_t)rc.nblk * kRedMaxNV * ld));
+    AMS_TRY(h->alloc_t(&rc.part2, (size_t)ngrp * kRedMaxNV * ld));
     AMS_TRY(h->alloc_t(&rc.cnt1, (size_t)ngrp));
     AMS_TRY(h->alloc_t(&rc.cnt2, (size_t)h->nsys));
     AMS_TRY(h->alloc_t(&rc.cnt3, 1));
@@ -427,7 +428,7 @@ static ams_status setup_eigen(ams_handle h, const int64_t* d_rowptr, const int32
     }
     SubInfo* d_esubs = nullptr;
     AMS_TRY(upload(h, &d_esubs, esubs));
-    LocalSolveArgs la{h->stream, h->N, d_esubs, d_X, d_S, P, h->cmax, 0, nullptr};
+    LocalSolveArgs la{h->stream, h->N, d_esubs, ResidIn{d_X, nullptr, nullptr}, d_S, P, h->cmax, 0, nullptr};
     const int maxit = h->opt.eig_maxit > 0 ? h->opt.eig_maxit : 300;
     const double tol = h->opt.eig_tol > 0 ? h->opt.eig_tol : 1e-13;
     std::vector<double> res(h->N);
@@ -991,7 +992,7 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
 // ---------------------------------------------------------------------------
 static ams_status ensure_work(ams_handle h, int ld) {
     if (ld > h->ld_alloc) {
-        for (void* p : {(void*)h->d_x, (void*)h->d_r, (void*)h->d_p, (void*)h->d_q, (void*)h->d_z, h->d_zf, h->d_rc,
+        for (void* p : {(void*)h->d_x, (void*)h->d_r, (void*)h->d_p, (void*)h->d_p2, (void*)h->d_q, (void*)h->d_z, h->d_zf, h->d_rc,
                         h->d_yc, h->d_ec, (void*)h->d_stage_in, (void*)h->d_stage_out, (void*)h->d_stage_aux})
             h->release(p);
         const size_t nv = (size_t)h->n_pad * ld;
@@ -999,6 +1000,7 @@ static ams_status ensure_work(ams_handle h, int ld) {
         AMS_TRY(h->alloc_t(&h->d_x, nv));
         AMS_TRY(h->alloc_t(&h->d_r, nv));
         AMS_TRY(h->alloc_t(&h->d_p, nv));
+        AMS_TRY(h->alloc_t(&h->d_p2, nv));
         AMS_TRY(h->alloc_t(&h->d_q, nv));
         AMS_TRY(h->alloc_t(&h->d_z, nv));
         AMS_TRY(h->alloc(&h->d_zf, nv * h->tf_bytes()));
@@ -1013,7 +1015,7 @@ static ams_status ensure_work(ams_handle h, int ld) {
     }
     if (ld != h->ld_last) {
         const size_t nv = (size_t)h->n_pad * ld;
-        for (double* p : {h->d_x, h->d_r, h->d_p, h->d_q, h->d_z})
+        for (double* p : {h->d_x, h->d_r, h->d_p, h->d_p2, h->d_q, h->d_z})
             AMS_CUDA_TRY(cudaMemsetAsync(p, 0, nv * sizeof(double), h->stream));
         AMS_CUDA_TRY(cudaMemsetAsync(h->d_zf, 0, nv * h->tf_bytes(), h->stream));
         h->ld_last = ld;
@@ -1049,83 +1051,99 @@ static ams_status prof_flush(ams_handle h) {
 }
 
 // Fine-level local solves (+ restriction when the coarse space exists).
-static ams_status launch_local(ams_handle h, int ld, const double* r, bool with_state) {
+static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool with_state) {
     const bool coarse = h->Nc > 0;
     if (h->use_tma) {
-        LocalTmaArgs a{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, r, ld, h->cmax,
+        LocalTmaArgs a{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, in, ld, h->cmax,
                        std::max(1, h->mmax), h->nbmax, int64_t(1) << 20, with_state ? h->d_st : nullptr};
         AMS_CUDA_TRY(launch_local_tma(a, h->prec, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
     } else {
-        LocalSolveArgs la{h->stream, h->N, h->d_subs, r, nullptr, ld, h->cmax, std::max(1, h->mmax),
+        LocalSolveArgs la{h->stream, h->N, h->d_subs, in, nullptr, ld, h->cmax, std::max(1, h->mmax),
                           with_state ? h->d_st : nullptr};
         AMS_CUDA_TRY(launch_local_solve(la, h->prec, h->d_fac, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
     }
     return AMS_OK;
 }
 
-// z = M^{-1} r (internal layout); with_dot/first control the fused dots
-static ams_status apply_precond(ams_handle h, const LaunchCtx& L, const double* r, double* z, int first,
-                                int with_dot) {
+static void launch_coarse(ams_handle h, int ld, bool fwd, bool with_state) {
+    if (fwd) {
+        CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_partial, h->d_cnt,
+                        with_state ? h->d_st : nullptr};
+        launch_coarse_gemm(cf, h->prec, ld, h->d_rc, h->d_yc);
+    } else {
+        CoarseLaunch cb{h->stream, h->nbwd, h->d_bwd, h->d_Qmat, h->d_rng, h->d_partial, h->d_cnt,
+                        with_state ? h->d_st : nullptr};
+        launch_coarse_gemm(cb, h->prec, ld, h->d_yc, h->d_ec);
+    }
+}
+
+static ProlongArgs prolong_args(ams_handle h, int mode, const double* p) {
+    return ProlongArgs{h->d_psi, h->Nc > 0 ? h->d_ec : nullptr, h->d_zf, h->d_r, h->d_q, h->d_x, p, h->d_z,
+                       std::max(1, h->mmax), h->flexible, mode};
+}
+
+// z = M^{-1} r' (internal layout).  mode 0: plain application (r' = r, no
+// dots); mode 1: first application of a solve (r' = r, rho = r.z); mode 2:
+// inside an iteration (r' = r - alpha q formed by the local solves and
+// stored by the prolongation together with x += alpha p, the dots and the
+// convergence test).  p is the direction of the current iteration.
+static ams_status apply_precond(ams_handle h, const LaunchCtx& L, int mode, const double* p) {
     const bool coarse = h->Nc > 0;
-    prof_begin(h, 2);
-    AMS_TRY(launch_local(h, L.ld, r, with_dot != 0));
+    const bool with_state = mode != 0;
+    prof_begin(h, AMS_KERNEL_LOCAL);
+    AMS_TRY(launch_local(h, L.ld, ResidIn{h->d_r, mode == 2 ? h->d_q : nullptr, h->d_sc}, with_state));
     prof_end(h);
     h->launches += coarse ? 4 : 2;
     if (coarse) {
-        CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_partial, h->d_cnt,
-                        with_dot ? h->d_st : nullptr};
-        prof_begin(h, 3);
-        launch_coarse_gemm(cf, h->prec, L.ld, h->d_rc, h->d_yc);
+        prof_begin(h, AMS_KERNEL_COARSE_FWD);
+        launch_coarse(h, L.ld, true, with_state);
         prof_end(h);
-        CoarseLaunch cb{h->stream, h->nbwd, h->d_bwd, h->d_Qmat, h->d_rng, h->d_partial, h->d_cnt,
-                        with_dot ? h->d_st : nullptr};
-        prof_begin(h, 4);
-        launch_coarse_gemm(cb, h->prec, L.ld, h->d_yc, h->d_ec);
+        prof_begin(h, AMS_KERNEL_COARSE_BWD);
+        launch_coarse(h, L.ld, false, with_state);
         prof_end(h);
     }
     LaunchCtx L2 = L;
-    if (!with_dot) L2.st = nullptr;
-    prof_begin(h, 5);
-    launch_prolong_dot(L2, h->prec, h->d_psi, coarse ? h->d_ec : nullptr, h->d_zf, r, h->d_q, z, h->flexible,
-                       first, with_dot);
+    if (!with_state) L2.st = nullptr;
+    prof_begin(h, AMS_KERNEL_PROLONG);
+    launch_prolong_update(L2, h->prec, prolong_args(h, mode, p));
     prof_end(h);
     AMS_CUDA_TRY(cudaGetLastError());
     return AMS_OK;
 }
 
-static int launches_per_iteration(ams_handle h) { return h->Nc > 0 ? 7 : 5; }
+static int launches_per_iteration(ams_handle h) { return h->Nc > 0 ? 5 : 3; }
 
-static ams_status launch_iteration(ams_handle h, const LaunchCtx& L) {
-    h->launches += 3;
-    prof_begin(h, 0);
-    launch_spmv_dot(L, h->d_p, h->d_q, 1);
+// One CG iteration; `par` selects which direction buffer holds p_old.
+static ams_status launch_iteration(ams_handle h, const LaunchCtx& L, int par) {
+    double* p_old = par ? h->d_p2 : h->d_p;
+    double* p_new = par ? h->d_p : h->d_p2;
+    h->launches += 1;
+    prof_begin(h, AMS_KERNEL_SPMV);
+    launch_spmv_dir(L, h->d_z, p_old, p_new, h->d_q, 1);
     prof_end(h);
-    prof_begin(h, 1);
-    launch_cg_update(L, h->d_x, h->d_r, h->d_p, h->d_q);
-    prof_end(h);
-    AMS_TRY(apply_precond(h, L, h->d_r, h->d_z, 0, 1));
-    prof_begin(h, 6);
-    launch_dir_update(L, h->d_p, h->d_z);
-    prof_end(h);
-    return AMS_OK;
+    return apply_precond(h, L, 2, p_new);
 }
 
-// One PCG iteration captured as a CUDA graph (kernel arguments are fixed
-// device pointers; every scalar lives in device memory).
+// Two CG iterations (the direction buffers swap roles once each) captured
+// as a CUDA graph; kernel arguments are fixed device pointers and every
+// scalar lives in device memory.
 static ams_status get_iter_graph(ams_handle h, const LaunchCtx& L, cudaGraphExec_t* out) {
     auto it = h->iter_graph.find(L.ld);
     if (it != h->iter_graph.end()) {
         *out = it->second;
         return AMS_OK;
     }
-    // one un-captured iteration first: sets kernel attributes outside capture
     const int64_t saved = h->launches;
     cudaGraph_t g = nullptr;
     AMS_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    ams_status st = launch_iteration(h, L);
+    ams_status st = launch_iteration(h, L, 0);
+    if (st == AMS_OK) st = launch_iteration(h, L, 1);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     h->launches = saved;
-    if (st != AMS_OK) return st;
+    if (st != AMS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
     AMS_CUDA_TRY(e);
     cudaGraphExec_t ex = nullptr;
     e = cudaGraphInstantiate(&ex, g, 0);
@@ -1168,6 +1186,7 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
                               h->d_x);
         }
     }
+    // the first iteration reads p_old = 0 (beta = 0)
     AMS_CUDA_TRY(cudaMemsetAsync(h->d_p, 0, sizeof(double) * h->n_pad * ld, h->stream));
     {
         SolveState init{};
@@ -1175,10 +1194,9 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
         init.rtol2 = rtol * rtol;
         AMS_CUDA_TRY(cudaMemcpyAsync(h->d_st, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
     }
-    h->launches += 2 * h->nsys + 2;     // permutes in/out, norms, first direction
+    h->launches += 2 * h->nsys + 1;     // permutes in/out, norms
     launch_init_norms(L, h->d_r, nrhs);
-    AMS_TRY(apply_precond(h, L, h->d_r, h->d_z, 1, 1));
-    launch_dir_update(L, h->d_p, h->d_z);
+    AMS_TRY(apply_precond(h, L, 1, nullptr));
     AMS_CUDA_TRY(cudaGetLastError());
     AMS_TRY(prof_flush(h));
     cudaGraphExec_t graph = nullptr;
@@ -1192,13 +1210,16 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
     double w_prev = 1.0;
     const double target = rtol * rtol;
     while (true) {
-        for (int k = 0; k < chunk; ++k) {
+        // iterations run in pairs (one graph launch = two iterations)
+        for (int k = 0; k < (chunk + 1) / 2; ++k) {
             if (graph) {
                 AMS_CUDA_TRY(cudaGraphLaunch(graph, h->stream));
-                h->launches += launches_per_iteration(h);
+                h->launches += 2 * launches_per_iteration(h);
             } else {
-                AMS_TRY(launch_iteration(h, L));
-                AMS_TRY(prof_flush(h));
+                for (int par = 0; par < 2; ++par) {
+                    AMS_TRY(launch_iteration(h, L, par));
+                    AMS_TRY(prof_flush(h));
+                }
             }
         }
         AMS_CUDA_TRY(cudaMemcpyAsync(&st, h->d_st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
@@ -1308,22 +1329,25 @@ ams_status ams_destroy(ams_handle h) {
 
 // Algorithmic bytes of one launch of kernel `which` (each operand read once,
 // each output written once) at `ld` right-hand sides.
+// Algorithmic bytes of one launch: every operand read once, every output
+// written once (FP64 vectors, the stored factor and basis at their storage
+// precision).
 static double kernel_bytes(ams_handle h, int which, int ld) {
     const double n = (double)h->n_total, nl = n * ld;
     const double tf = (double)h->tf_bytes(), tp = (double)h->tp_bytes();
     switch (which) {
-        case 0: return 12.0 * (double)h->nnz_total + 16.0 * nl + 8.0 * (double)h->n_pad / 32;
-        case 1: return 48.0 * nl;
-        case 2: {
-            // factor read once (the TMA path stores it twice, once per sweep
-            // direction, and reads each copy once: 2x these factor bytes)
+        case AMS_KERNEL_SPMV:    // vals + cols, z and p_old in, p and q out, slice pointers
+            return 12.0 * (double)h->nnz_total + 32.0 * nl + 8.0 * (double)h->n_pad / 32;
+        case AMS_KERNEL_LOCAL: {
+            // factor once (tiles + pivots, or the packed factor), r and q in,
+            // z_f out, basis rows, r_c out
             const double fb = h->use_tma ? (double)h->tile_elems * 4.0 + 4.0 * n : (double)h->fac_elems * tf;
-            return fb + 8.0 * nl + tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf;
+            return fb + 16.0 * nl + tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf;
         }
-        case 3: return (double)h->R_elems * tf + 2.0 * (double)h->Nc * ld * tf;
-        case 4: return (double)h->Q_elems * tf + 2.0 * (double)h->Nc * ld * tf;
-        case 5: return tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf + 24.0 * nl;
-        case 6: return 24.0 * nl;
+        case AMS_KERNEL_COARSE_FWD: return (double)h->R_elems * tf + 2.0 * (double)h->Nc * ld * tf;
+        case AMS_KERNEL_COARSE_BWD: return (double)h->Q_elems * tf + 2.0 * (double)h->Nc * ld * tf;
+        case AMS_KERNEL_PROLONG:    // z_f, basis, e_c in; r, q, x, p in; r, x, z out
+            return tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf + 56.0 * nl;
     }
     return 0.0;
 }
@@ -1515,7 +1539,7 @@ ams_status ams_apply_preconditioner(ams_handle h, const double* r, int32_t nrhs,
     AMS_TRY(stage_in(h, r, nrhs, h->d_stage_in, &r_dev));
     launch_permute_in(h->stream, r_dev, h->n_total, nrhs, ld, h->d_int_row, h->d_r, nullptr);
     h->launches += 2;
-    AMS_TRY(apply_precond(h, L, h->d_r, h->d_z, 1, 0));
+    AMS_TRY(apply_precond(h, L, 0, nullptr));
     double* z_dev = h->opt.device_ptrs ? z : h->d_stage_out;
     launch_permute_out(h->stream, h->d_z, h->n_total, nrhs, ld, h->d_int_row, z_dev);
     AMS_CUDA_TRY(cudaGetLastError());
@@ -1541,7 +1565,7 @@ ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y) {
     const double* x_dev = nullptr;
     AMS_TRY(stage_in(h, x, nrhs, h->d_stage_in, &x_dev));
     launch_permute_in(h->stream, x_dev, h->n_total, nrhs, ld, h->d_int_row, h->d_p, nullptr);
-    launch_spmv_dot(L, h->d_p, h->d_q, 0);
+    launch_spmv_dir(L, h->d_p, nullptr, nullptr, h->d_q, 0);
     h->launches += 3;
     double* y_dev = h->opt.device_ptrs ? y : h->d_stage_out;
     launch_permute_out(h->stream, h->d_q, h->n_total, nrhs, ld, h->d_int_row, y_dev);
@@ -1554,7 +1578,7 @@ ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y) {
 
 ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* avg_ms, double* bytes) {
     g_last_error.clear();
-    if (!h || reps <= 0 || which < 0 || which > 6 || h->ld_last == 0) {
+    if (!h || reps <= 0 || which < 0 || which >= AMS_NUM_KERNELS || h->ld_last == 0) {
         set_error("invalid arguments (a solve must run first)");
         return AMS_ERR_INVALID_ARG;
     }
@@ -1579,28 +1603,19 @@ ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* av
         st.rtol2 = 0.0;
         AMS_CUDA_TRY(cudaMemcpy(h->d_st, &st, sizeof(st), cudaMemcpyHostToDevice));
     }
-    const bool coarse = h->Nc > 0;
     const double b = kernel_bytes(h, which, ld);
+    // Timed launches keep their solve-state argument (so they run the code
+    // path of a solve) but the state above never reports convergence.  The
+    // SpMV reads p and writes p2, the prolongation updates x and r in place.
     auto launch = [&]() -> ams_status {
         switch (which) {
-            case 0: launch_spmv_dot(L, h->d_p, h->d_q, 1); break;
-            case 1: launch_cg_update(L, h->d_x, h->d_r, h->d_p, h->d_q); break;
-            case 2: AMS_TRY(launch_local(h, ld, h->d_r, true)); break;
-            case 3: {
-                CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_partial, h->d_cnt, h->d_st};
-                launch_coarse_gemm(cf, h->prec, ld, h->d_rc, h->d_yc);
+            case AMS_KERNEL_SPMV: launch_spmv_dir(L, h->d_z, h->d_p, h->d_p2, h->d_q, 1); break;
+            case AMS_KERNEL_LOCAL:
+                AMS_TRY(launch_local(h, ld, ResidIn{h->d_r, h->d_q, h->d_sc}, true));
                 break;
-            }
-            case 4: {
-                CoarseLaunch cb{h->stream, h->nbwd, h->d_bwd, h->d_Qmat, h->d_rng, h->d_partial, h->d_cnt, h->d_st};
-                launch_coarse_gemm(cb, h->prec, ld, h->d_yc, h->d_ec);
-                break;
-            }
-            case 5:
-                launch_prolong_dot(L, h->prec, h->d_psi, coarse ? h->d_ec : nullptr, h->d_zf, h->d_r, h->d_q, h->d_z,
-                                   h->flexible, 0, 1);
-                break;
-            case 6: launch_dir_update(L, h->d_p, h->d_z); break;
+            case AMS_KERNEL_COARSE_FWD: launch_coarse(h, ld, true, true); break;
+            case AMS_KERNEL_COARSE_BWD: launch_coarse(h, ld, false, true); break;
+            case AMS_KERNEL_PROLONG: launch_prolong_update(L, h->prec, prolong_args(h, 2, h->d_p2)); break;
         }
         return AMS_OK;
     };
@@ -1642,7 +1657,7 @@ ams_status ams_profile_solve(ams_handle h, const double* f, int32_t nrhs, double
     for (auto& e : P.ev) cudaEventDestroy(e);
     if (st != AMS_OK && st != AMS_ERR_NOT_CONVERGED) return st;
     const int ld = pow2ceil(nrhs);
-    for (int k = 0; k < 7; ++k) {
+    for (int k = 0; k < AMS_NUM_KERNELS; ++k) {
         if (ms) ms[k] = P.ms[k];
         if (count) count[k] = P.count[k];
         if (bytes) bytes[k] = kernel_bytes(h, k, ld);

@@ -25,6 +25,7 @@ constexpr int kRedThreads = 256;       // threads of the reduction kernels
 constexpr int kRedElems = 1024;        // elements per reduction block
 constexpr int kRedGroup = 64;          // blocks summed per first-level group
 constexpr int kRedDirect = 2048;       // at most this many blocks: one-stage sum
+constexpr int kRedMaxNV = 4;           // values per right-hand side in one reduction
 constexpr int kMaxLd = 32;             // right-hand sides per solve call
 constexpr int kMaxM = 16;              // eigenvectors per subdomain (cap)
 constexpr int kCoarseChunk = 1024;     // node-matrix columns per coarse item

@@ -66,6 +66,14 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// 1024-byte aligned start of the dynamic shared memory (the 128-byte swizzle
+// pattern repeats every 1024 bytes).  Derived by pointer arithmetic, not an
+// integer round trip, so that the compiler still sees a shared-memory
+// pointer and emits shared-memory loads rather than generic ones.
+__device__ __forceinline__ unsigned char* smem_align1024(unsigned char* p) {
+    return p + ((1024u - (smem_u32(p) & 1023u)) & 1023u);
+}
+
 // Row r of a swizzled 32x32 FP32 tile: 16-byte chunk j (columns 4j..4j+3).
 __device__ __forceinline__ float4 tile_chunk(const float* tile, int r, int j) {
     return *reinterpret_cast<const float4*>(tile + r * 32 + ((j ^ (r & 7)) << 2));
@@ -134,13 +142,13 @@ template <typename TP, int NR, int MM>
 __global__ void __launch_bounds__(256)
 k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmB,
             const SubInfo* __restrict__ subs, const int64_t* __restrict__ tile_row0,
-            const float* __restrict__ piv, const double* __restrict__ rin, float* __restrict__ zf,
-            const TP* __restrict__ psi, float* __restrict__ rc, int ld, int cmax, int depth,
-            int64_t budget, SolveState* st) {
+            const float* __restrict__ piv, const double* __restrict__ rin, const double* __restrict__ qin,
+            const CgScalars* __restrict__ csc, float* __restrict__ zf, const TP* __restrict__ psi,
+            float* __restrict__ rc, int ld, int cmax, int depth, int64_t budget, SolveState* st) {
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned tile ring, then mbarriers, y/x ring, scratch
-    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* base = smem_align1024(smem_raw);
     const SubInfo S = subs[blockIdx.x];
     const int c = S.c, nb = S.nb, n = S.n;
     const int D = depth;
@@ -195,30 +203,62 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
     // every global load has PF steps to arrive.  The step loop is unrolled
     // by PF so that buffer indices are compile-time constants.
     constexpr int PF = (NR <= 2) ? 4 : 2;
-    float bt[PF][NR], bp[PF][MM], bv[PF];
-    auto load_fwd = [&](int K, float (&tv)[NR], float (&pv)[MM], float& pvt) {
+    // Loaded values stay in their loaded type until use (see the
+    // one-right-hand-side kernel below).
+    // r' = r - alpha q for (system, rhs) pairs still iterating
+    double al[NR];
+    bool upd[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        al[j] = 0.0;
+        upd[j] = false;
+        if (qin != nullptr) {
+            const CgScalars cj = csc[(int64_t)S.seg * ld + rhs0 + j];
+            upd[j] = cj.active != 0;
+            if (upd[j]) al[j] = cj.rho / cj.pq;
+        }
+    }
+    double bt[PF][NR], bq[PF][NR];
+    TP bp[PF][MM];
+    float bv[PF];
+    auto load_fwd = [&](int K, double (&tv)[NR], double (&qv)[NR], TP (&pv)[MM], float& pvt) {
         const int row = K * 32 + lane;
         const bool valid = K < nb && row < n;
         const int64_t grow = S.row0 + row;
+        pvt = 1.f;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) tv[j] = valid ? (float)rin[grow * ld + rhs0 + j] : 0.f;
+        for (int j = 0; j < NR; ++j) {
+            tv[j] = 0.0;
+            qv[j] = 0.0;
+        }
 #pragma unroll
-        for (int k = 0; k < MM; ++k)
-            pv[k] = (rc != nullptr && valid && k < m) ? to_f(psi[S.psi_off + (int64_t)row * m + k]) : 0.f;
-        pvt = valid ? piv[grow] : 1.f;
+        for (int k = 0; k < MM; ++k) pv[k] = TP(0.f);
+        if (valid) {
+            pvt = piv[grow];
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                tv[j] = rin[grow * ld + rhs0 + j];
+                if (upd[j]) qv[j] = qin[grow * ld + rhs0 + j];
+            }
+            if (rc != nullptr) {
+#pragma unroll
+                for (int k = 0; k < MM; ++k)
+                    if (k < m) pv[k] = psi[S.psi_off + (int64_t)row * m + k];
+            }
+        }
     };
 #pragma unroll
-    for (int u = 0; u < PF; ++u) load_fwd(u, bt[u], bp[u], bv[u]);
+    for (int u = 0; u < PF; ++u) load_fwd(u, bt[u], bq[u], bp[u], bv[u]);
 
-    auto fwd_step = [&](int K, float (&tb)[NR], float (&pb)[MM], float& vb) {
+    auto fwd_step = [&](int K, double (&tb)[NR], double (&qb)[NR], TP (&pb)[MM], float& vb) {
         if (K + D < nb) issue(&tmF, K + D);
         float t[NR], pv[MM];
         const float pvt = vb;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) t[j] = tb[j];
+        for (int j = 0; j < NR; ++j) t[j] = (float)(upd[j] ? fma(-al[j], qb[j], tb[j]) : tb[j]);
 #pragma unroll
-        for (int k = 0; k < MM; ++k) pv[k] = pb[k];
-        load_fwd(K + PF, tb, pb, vb);
+        for (int k = 0; k < MM; ++k) pv[k] = to_f(pb[k]);
+        load_fwd(K + PF, tb, qb, pb, vb);
         wait_slot(K);
         ok = __syncthreads_and(ok);      // uniform decision across the block
         if (!ok) return;
@@ -261,7 +301,7 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
     for (int K0 = 0; K0 < nb && ok; K0 += PF) {
 #pragma unroll
         for (int u = 0; u < PF; ++u)
-            if (K0 + u < nb && ok) fwd_step(K0 + u, bt[u], bp[u], bv[u]);
+            if (K0 + u < nb && ok) fwd_step(K0 + u, bt[u], bq[u], bp[u], bv[u]);
     }
     if (rc != nullptr && ok) {
 #pragma unroll
@@ -274,13 +314,19 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
             }
     }
     // ---------------- backward ----------------
+    float bw[PF][NR];
     auto load_bwd = [&](int K, float (&wv)[NR], float& pvt) {
         const int row = K * 32 + lane;
         const bool valid = K >= 0 && row < n;
         const int64_t grow = S.row0 + row;
+        pvt = 1.f;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) wv[j] = valid ? zf[grow * ld + rhs0 + j] : 0.f;
-        pvt = valid ? piv[grow] : 1.f;
+        for (int j = 0; j < NR; ++j) wv[j] = 0.f;
+        if (valid) {
+            pvt = piv[grow];
+#pragma unroll
+            for (int j = 0; j < NR; ++j) wv[j] = zf[grow * ld + rhs0 + j];
+        }
     };
     auto bwd_step = [&](int K, float (&wb)[NR], float& vb) {
         if (K - D >= 0) issue(&tmB, K - D);
@@ -323,14 +369,14 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
     };
     if (ok) {
 #pragma unroll
-        for (int u = 0; u < PF; ++u) load_bwd(nb - 1 - u, bt[u], bv[u]);
+        for (int u = 0; u < PF; ++u) load_bwd(nb - 1 - u, bw[u], bv[u]);
         for (int j = 0; j < D && nb - 1 - j >= 0; ++j) issue(&tmB, nb - 1 - j);
     }
 #pragma unroll 1
     for (int K0 = nb - 1; K0 >= 0 && ok; K0 -= PF) {
 #pragma unroll
         for (int u = 0; u < PF; ++u)
-            if (K0 - u >= 0 && ok) bwd_step(K0 - u, bt[u], bv[u]);
+            if (K0 - u >= 0 && ok) bwd_step(K0 - u, bw[u], bv[u]);
     }
     if (!ok) {
         // record the timeout and drain this block's copies in flight (bounded)
@@ -397,11 +443,12 @@ template <typename TP, int MM>
 __global__ void __launch_bounds__(32, 8)
 k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict__ subs,
              const int64_t* __restrict__ tile_row0, const float* __restrict__ piv,
-             const double* __restrict__ rin, float* __restrict__ zf, const TP* __restrict__ psi,
+             const double* __restrict__ rin, const double* __restrict__ qin,
+             const CgScalars* __restrict__ csc, float* __restrict__ zf, const TP* __restrict__ psi,
              float* __restrict__ rc, int cmax, int nbmax, int depth, int64_t budget, SolveState* st) {
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* base = smem_align1024(smem_raw);
     const SubInfo S = subs[blockIdx.x];
     const int c = S.c, nb = S.nb, n = S.n, m = S.m;
     const int D = depth;
@@ -468,31 +515,53 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
 #pragma unroll
     for (int k = 0; k < MM; ++k) racc[k] = 0.f;
 
-    // per-row inputs of block row K+PF are loaded while step K runs
+    // Per-row inputs of block row K+PF are loaded while step K runs.  They
+    // stay in the loaded type until the step that uses them: a conversion
+    // or a select right after the load would wait for it there.
+    // r' = r - alpha q when this subdomain's system is still iterating
+    double alpha = 0.0;
+    bool upd = false;
+    if (qin != nullptr) {
+        const CgScalars cs = csc[S.seg];
+        upd = cs.active != 0;
+        if (upd) alpha = cs.rho / cs.pq;
+    }
     constexpr int PF = 4;
-    float bt[PF], bp[PF][MM], bv[PF];
-    auto load_fwd = [&](int K, float& tv, float (&pv)[MM], float& pvt) {
+    double bt[PF], bq[PF];
+    TP bp[PF][MM];
+    float bv[PF];
+    auto load_fwd = [&](int K, double& tv, double& qv, TP (&pv)[MM], float& pvt) {
         const int row = K * 32 + lane;
         const bool valid = K < nb && row < n;
         const int64_t grow = S.row0 + row;
-        tv = valid ? (float)rin[grow] : 0.f;
+        tv = 0.0;
+        qv = 0.0;
+        pvt = 1.f;
 #pragma unroll
-        for (int k = 0; k < MM; ++k)
-            pv[k] = (rc != nullptr && valid && k < m) ? to_f(psi[S.psi_off + (int64_t)row * m + k]) : 0.f;
-        pvt = valid ? piv[grow] : 1.f;
+        for (int k = 0; k < MM; ++k) pv[k] = TP(0.f);
+        if (valid) {
+            tv = rin[grow];
+            if (upd) qv = qin[grow];
+            pvt = piv[grow];
+            if (rc != nullptr) {
+#pragma unroll
+                for (int k = 0; k < MM; ++k)
+                    if (k < m) pv[k] = psi[S.psi_off + (int64_t)row * m + k];
+            }
+        }
     };
 #pragma unroll
-    for (int u = 0; u < PF; ++u) load_fwd(u, bt[u], bp[u], bv[u]);
+    for (int u = 0; u < PF; ++u) load_fwd(u, bt[u], bq[u], bp[u], bv[u]);
 
-    auto fwd_step = [&](int K, float& tb, float (&pb)[MM], float& vb) {
+    auto fwd_step = [&](int K, double& tb, double& qb, TP (&pb)[MM], float& vb) {
         if (K + D < nb) issue(K + D);
-        float t = tb;
+        float t = (float)(upd ? fma(-alpha, qb, tb) : tb);
         const float pvt = vb;
         if (rc != nullptr) {
 #pragma unroll
-            for (int k = 0; k < MM; ++k) racc[k] = fmaf(pb[k], t, racc[k]);
+            for (int k = 0; k < MM; ++k) racc[k] = fmaf(to_f(pb[k]), t, racc[k]);
         }
-        load_fwd(K + PF, tb, pb, vb);
+        load_fwd(K + PF, tb, qb, pb, vb);
         wait_slot(K);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) return;
@@ -541,7 +610,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     for (int K0 = 0; K0 < nb && ok; K0 += PF) {
 #pragma unroll
         for (int u = 0; u < PF; ++u)
-            if (K0 + u < nb && ok) fwd_step(K0 + u, bt[u], bp[u], bv[u]);
+            if (K0 + u < nb && ok) fwd_step(K0 + u, bt[u], bq[u], bp[u], bv[u]);
     }
     if (rc != nullptr && ok) {
 #pragma unroll
@@ -558,7 +627,8 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     const int Rres = nb > nbuf ? nb - nbuf : 0;
     auto load_bwd = [&](int K, float& pvt) {
         const int row = K * 32 + lane;
-        pvt = (K >= 0 && row < n) ? piv[S.row0 + row] : 1.f;
+        pvt = 1.f;
+        if (K >= 0 && row < n) pvt = piv[S.row0 + row];
     };
     auto bwd_step = [&](int K, float& vb) {
         if (K - D >= 0 && K - D < Rres) issue(K - D);
@@ -654,8 +724,9 @@ static cudaError_t tma_nr(const LocalTmaArgs& a, const void* psi, void* zf, void
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    kern<<<a.nsub, warps * 32, smem, a.stream>>>(*a.tmF, *a.tmB, a.subs, a.tile_row0, a.piv, a.rin, (float*)zf,
-                                                  (const TP*)psi, (float*)rc, a.ld, a.cmax, depth, a.budget, a.st);
+    kern<<<a.nsub, warps * 32, smem, a.stream>>>(*a.tmF, *a.tmB, a.subs, a.tile_row0, a.piv, a.in.r, a.in.q, a.in.sc,
+                                                  (float*)zf, (const TP*)psi, (float*)rc, a.ld, a.cmax, depth,
+                                                  a.budget, a.st);
     return cudaGetLastError();
 }
 
@@ -704,8 +775,8 @@ static cudaError_t tma1(const LocalTmaArgs& a, const void* psi, void* zf, void* 
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    kern<<<a.nsub, 32, smem, a.stream>>>(*a.tmF, a.subs, a.tile_row0, a.piv, a.rin, (float*)zf, (const TP*)psi,
-                                         (float*)rc, a.cmax, a.nbmax, depth, a.budget, a.st);
+    kern<<<a.nsub, 32, smem, a.stream>>>(*a.tmF, a.subs, a.tile_row0, a.piv, a.in.r, a.in.q, a.in.sc, (float*)zf,
+                                         (const TP*)psi, (float*)rc, a.cmax, a.nbmax, depth, a.budget, a.st);
     return cudaGetLastError();
 }
 

@@ -1,12 +1,12 @@
 // Solve-phase kernels of the AMS-preconditioned CG (one GPU, sm_103a).
 //
-// Per iteration (Section 3.1 preconditioner inside CG):
-//   k_spmv_dot      q = A p and p.q                    (CSR SpMV, SELL-32 layout)
-//   k_cg_update     x += alpha p, r -= alpha q, r.r, convergence
-//   k_local_solve   z_f = sum_i R_i^T A_i^{-1} R_i r  and  r_c = R_0 r
-//   k_coarse_gemm   y = L_c^{-1} r_c, then e_c = L_c^{-T} y  (A_0 = L_c L_c^T)
-//   k_prolong_dot   z = z_f + R_0^T e_c, r.z (and z.q for flexible CG), beta
-//   k_dir_update    p = z + beta p
+// One CG iteration (Section 3.1 preconditioner inside CG) is five kernels:
+//   k_spmv_dir        p = z + beta p_old, q = A p and p.q     (SELL-32 SpMV)
+//   k_local_solve     z_f = sum_i R_i^T A_i^{-1} R_i r'  and  r_c = R_0 r',
+//   (k_local_tma*)    r' = r - alpha q formed on the fly       (alpha = rho/pq)
+//   k_coarse_gemm     y = L_c^{-1} r_c, then e_c = L_c^{-T} y  (A_0 = L_c L_c^T)
+//   k_prolong_update  z = z_f + R_0^T e_c, r = r', x += alpha p, r.z, r.r,
+//                     z.q, convergence test and beta
 #include <cstdint>
 #include <cstdio>
 #include <type_traits>
@@ -18,38 +18,76 @@
 namespace ams {
 
 // ===========================================================================
-// a1: SpMV q = A p with fused p.q  (SELL-32: slice s = rows 32s..32s+31,
-// entry j of lane l at sell_ptr[s] + 32 j + l; padded entries have value 0)
+// a1 + a7: direction update and SpMV (SELL-32: slice s = rows 32s..32s+31,
+// entry j of lane l at sell_ptr[s] + 32 j + l; padded entries have value 0
+// and a valid column).
+//
+// mode 1 (CG iteration): p_new = z + beta p_old for every element, q =
+// A p_new, and the dot p_new.q per (system, rhs).  A gathered entry
+// p_new[col] is recomputed from z and p_old with the same fused
+// multiply-add that produces the stored p_new[col], so q is exactly A times
+// the stored direction and no separate direction pass is needed.  p_old and
+// p_new are different buffers (successive iterations alternate them).
+// mode 0: q = A z (no direction, no dot, no solve state).
 // ===========================================================================
+__device__ __forceinline__ double dir_entry(const double* __restrict__ z, const double* __restrict__ p_old,
+                                            int64_t i, double beta, bool dir) {
+    return dir ? fma(beta, __ldg(p_old + i), __ldg(z + i)) : __ldg(z + i);
+}
+
 template <int LD>
 __global__ void __launch_bounds__(kRedThreads)
-k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sell_col,
-           const double* __restrict__ sell_val, const double* __restrict__ p,
-           double* __restrict__ q, RedLayout R, CgScalars* sc, SolveState* st, int nseg,
-           int with_dot) {
+k_spmv_dir(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sell_col,
+           const double* __restrict__ sell_val, const double* __restrict__ z,
+           const double* __restrict__ p_old, double* __restrict__ p_new, double* __restrict__ q,
+           RedLayout R, CgScalars* sc, SolveState* st, int mode) {
     if (st != nullptr && st->done) return;
-    __shared__ double s_out[2 * kMaxLd];
+    __shared__ double s_out[kRedMaxNV * kMaxLd];
     __shared__ double s_scr[kRedThreads];
+    constexpr int RPT = kRedElems / kRedThreads;     // elements per thread
+    constexpr int JU = 8;                            // row entries loaded before the first product
+    const bool dir = mode == 1;
     const int64_t base = (int64_t)blockIdx.x * kRedElems;
+    const int rhs = threadIdx.x % LD;                // kRedThreads is a multiple of LD
+    double beta = 0.0;
+    if (dir) beta = sc[R.blk_seg[blockIdx.x] * LD + rhs].beta;
     double dot[1] = {0.0};
 #pragma unroll
-    for (int k = 0; k < kRedElems / kRedThreads; ++k) {
+    for (int k = 0; k < RPT; ++k) {
         const int64_t e = base + threadIdx.x + k * kRedThreads;
         const int64_t row = e / LD;
-        const int rhs = (int)(e % LD);
         const int64_t s = row >> 5;
         const int lane = (int)(row & 31);
-        const int64_t b0 = __ldg(sell_ptr + s), b1 = __ldg(sell_ptr + s + 1);
-        const int w = (int)((b1 - b0) >> 5);
+        const int64_t b0 = __ldg(sell_ptr + s);
+        const int w = (int)((__ldg(sell_ptr + s + 1) - b0) >> 5);
+        int col[JU];
+        double val[JU];
+#pragma unroll
+        for (int j = 0; j < JU; ++j) {
+            col[j] = 0;
+            val[j] = 0.0;
+            if (j < w) {
+                col[j] = __ldg(sell_col + b0 + 32 * j + lane);
+                val[j] = __ldg(sell_val + b0 + 32 * j + lane);
+            }
+        }
         double acc = 0.0;
-        for (int j = 0; j < w; ++j) {
+#pragma unroll
+        for (int j = 0; j < JU; ++j)
+            if (j < w) acc = fma(val[j], dir_entry(z, p_old, (int64_t)col[j] * LD + rhs, beta, dir), acc);
+        for (int j = JU; j < w; ++j) {
             const int64_t o = b0 + 32 * j + lane;
-            acc += __ldg(sell_val + o) * __ldg(p + (int64_t)__ldg(sell_col + o) * LD + rhs);
+            acc = fma(__ldg(sell_val + o), dir_entry(z, p_old, (int64_t)__ldg(sell_col + o) * LD + rhs, beta, dir),
+                      acc);
         }
         q[e] = acc;
-        dot[0] += p[e] * acc;
+        if (dir) {
+            const double pe = dir_entry(z, p_old, e, beta, true);
+            p_new[e] = pe;
+            dot[0] = fma(pe, acc, dot[0]);
+        }
     }
-    if (!with_dot) return;
+    if (!dir) return;
     int seg;
     if (!seg_reduce<1>(dot, LD, R, s_out, s_scr, seg)) return;
     if (threadIdx.x < LD) {
@@ -59,63 +97,6 @@ k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
             st->status = AMS_ERR_BREAKDOWN;
             st->done = 1;
         }
-    }
-}
-
-// ===========================================================================
-// a2: x += alpha p ; r -= alpha q ; r.r ; convergence test per (system, rhs)
-// ===========================================================================
-template <int LD>
-__global__ void __launch_bounds__(kRedThreads)
-k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* __restrict__ p,
-            const double* __restrict__ q, RedLayout R, CgScalars* sc, SolveState* st, int nseg) {
-    if (st->done) return;
-    const double rtol2 = st->rtol2;
-    __shared__ double s_out[2 * kMaxLd];
-    __shared__ double s_scr[kRedThreads];
-    const int64_t base = (int64_t)blockIdx.x * kRedElems;
-    const int seg = R.blk_seg[blockIdx.x];
-    const int rhs = threadIdx.x % LD;
-    const CgScalars c = sc[seg * LD + rhs];
-    const double alpha = c.active ? c.rho / c.pq : 0.0;
-    double rr[1] = {0.0};
-#pragma unroll
-    for (int k = 0; k < kRedElems / kRedThreads; ++k) {
-        const int64_t e = base + threadIdx.x + k * kRedThreads;
-        x[e] += alpha * p[e];
-        const double rv = r[e] - alpha * q[e];
-        r[e] = rv;
-        rr[0] += rv * rv;
-    }
-    int sg;
-    if (!seg_reduce<1>(rr, LD, R, s_out, s_scr, sg)) return;
-    const int it = st->it;
-    if (threadIdx.x < LD) {
-        CgScalars& cs = sc[sg * LD + threadIdx.x];
-        cs.rr = s_out[threadIdx.x];
-        if (cs.active) {
-            cs.alpha = cs.rho / cs.pq;
-            cs.iters = it + 1;
-            if (!isfinite(cs.rr)) {
-                st->status = AMS_ERR_BREAKDOWN;
-                st->done = 1;
-            } else if (cs.rr <= rtol2 * cs.fnorm2) {
-                cs.active = 0;
-            }
-        }
-    }
-    if (!last_system(R, nseg)) return;
-    if (threadIdx.x == 0) {
-        int nact = 0;
-        double worst = 0.0;
-        for (int i = 0; i < nseg * LD; ++i) {
-            nact += sc[i].active;
-            if (sc[i].active) worst = fmax(worst, sc[i].rr / sc[i].fnorm2);
-        }
-        st->nactive = nact;
-        st->worst = worst;
-        st->it = it + 1;
-        if (nact == 0 || it + 1 >= st->maxit) st->done = 1;
     }
 }
 
@@ -136,7 +117,8 @@ k_cg_update(double* __restrict__ x, double* __restrict__ r, const double* __rest
 // ===========================================================================
 template <typename TF, typename TP, int NR, int MM>
 __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __restrict__ fac,
-                              const double* __restrict__ rin, const double* __restrict__ rowscale,
+                              const double* __restrict__ rin, const double* __restrict__ qin,
+                              const CgScalars* __restrict__ csc, const double* __restrict__ rowscale,
                               TF* __restrict__ zf, const TP* __restrict__ psi, TF* __restrict__ rc,
                               int ld, int cmax, int depth, const SolveState* st) {
     if (st != nullptr && st->done) return;
@@ -163,23 +145,53 @@ __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __rest
 #pragma unroll
         for (int j = 0; j < NR; ++j) racc[k][j] = A(0);
 
-    // inputs of block row K (r rows and basis rows), prefetched two block
-    // rows ahead into registers so their global-memory latency overlaps the
-    // substitution of the previous rows
-    auto load_fwd = [&](int K, A (&tv)[NR], A (&pv)[MM]) {
+    // r' = r - alpha q for (system, rhs) pairs still iterating (see ResidIn)
+    double al[NR];
+    bool upd[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        al[j] = 0.0;
+        upd[j] = false;
+        if (qin != nullptr) {
+            const CgScalars cj = csc[(int64_t)S.seg * ld + rhs0 + j];
+            upd[j] = cj.active != 0;
+            if (upd[j]) al[j] = cj.rho / cj.pq;
+        }
+    }
+    // Inputs of block row K (r and q rows, basis rows, row scale) are
+    // loaded two block rows ahead into alternating register buffers and
+    // kept in their loaded type until the step that uses them, so their
+    // global-memory latency overlaps the substitution of earlier rows.
+    auto load_fwd = [&](int K, double (&rv)[NR], double (&qv)[NR], TP (&pv)[MM], double& scv) {
         const int row = K * 32 + lane;
         const bool valid = K < nb && row < n;
         const int64_t grow = S.row0 + row;
-        const double sc = (rowscale != nullptr && valid) ? rowscale[grow] : 1.0;
+        scv = 1.0;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) tv[j] = valid ? (A)(rin[grow * ld + rhs0 + j] * sc) : A(0);
+        for (int j = 0; j < NR; ++j) {
+            rv[j] = 0.0;
+            qv[j] = 0.0;
+        }
 #pragma unroll
-        for (int k = 0; k < MM; ++k)
-            pv[k] = (rc != nullptr && valid && k < m) ? (A)to_d(psi[S.psi_off + (int64_t)row * m + k]) : A(0);
+        for (int k = 0; k < MM; ++k) pv[k] = TP(0.f);
+        if (valid) {
+            if (rowscale != nullptr) scv = rowscale[grow];
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                rv[j] = rin[grow * ld + rhs0 + j];
+                if (upd[j]) qv[j] = qin[grow * ld + rhs0 + j];
+            }
+            if (rc != nullptr) {
+#pragma unroll
+                for (int k = 0; k < MM; ++k)
+                    if (k < m) pv[k] = psi[S.psi_off + (int64_t)row * m + k];
+            }
+        }
     };
-    A tn0[NR], pn0[MM], tn1[NR], pn1[MM];
-    load_fwd(0, tn0, pn0);
-    load_fwd(1, tn1, pn1);
+    double rb[2][NR], qb[2][NR], sb[2];
+    TP pb[2][MM];
+    load_fwd(0, rb[0], qb[0], pb[0], sb[0]);
+    load_fwd(1, rb[1], qb[1], pb[1], sb[1]);
 
     // ---------------- forward ----------------
     // one commit group per block row; row K+D is requested at step K
@@ -187,17 +199,17 @@ __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __rest
         if (j < nb) block_copy_async(bufs + (int64_t)(j % nbuf) * brs_max, F + (int64_t)j * brs, brs * sizeof(TF));
         cp_async_commit();
     }
-    for (int K = 0; K < nb; ++K) {
+    auto fwd_step = [&](int K, double (&rv)[NR], double (&qv)[NR], TP (&pb_)[MM], double& scv) {
         if (K + D < nb)
             block_copy_async(bufs + (int64_t)((K + D) % nbuf) * brs_max, F + (int64_t)(K + D) * brs,
                              brs * sizeof(TF));
         cp_async_commit();
         A t[NR], pv[MM];
 #pragma unroll
-        for (int j = 0; j < NR; ++j) { t[j] = tn0[j]; tn0[j] = tn1[j]; }
+        for (int j = 0; j < NR; ++j) t[j] = (A)((upd[j] ? fma(-al[j], qv[j], rv[j]) : rv[j]) * scv);
 #pragma unroll
-        for (int k = 0; k < MM; ++k) { pv[k] = pn0[k]; pn0[k] = pn1[k]; }
-        load_fwd(K + 2, tn1, pn1);
+        for (int k = 0; k < MM; ++k) pv[k] = (A)to_d(pb_[k]);
+        load_fwd(K + 2, rv, qv, pb_, scv);
         cp_async_wait_n(D);
         __syncthreads();
         const TF* B = bufs + (int64_t)(K % nbuf) * brs_max;
@@ -244,6 +256,11 @@ __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __rest
             for (int j = 0; j < NR; ++j) zf[grow * ld + rhs0 + j] = (TF)y[j];
         }
         __syncthreads();
+    };
+#pragma unroll 1
+    for (int K = 0; K < nb; K += 2) {
+        fwd_step(K, rb[0], qb[0], pb[0], sb[0]);
+        if (K + 1 < nb) fwd_step(K + 1, rb[1], qb[1], pb[1], sb[1]);
     }
     // restriction: reduce over lanes, lane 0 writes r_c rows of this subdomain
     if (rc != nullptr) {
@@ -266,25 +283,29 @@ __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __rest
         if (r >= 0) block_copy_async(bufs + (int64_t)(r % nbuf) * brs_max, F + (int64_t)r * brs, brs * sizeof(TF));
         cp_async_commit();
     }
-    auto load_bwd = [&](int K, A (&wv)[NR]) {
+    auto load_bwd = [&](int K, TF (&wv)[NR]) {
         const int row = K * 32 + lane;
         const bool valid = K >= 0 && row < n;
         const int64_t grow = S.row0 + row;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) wv[j] = valid ? (A)zf[grow * ld + rhs0 + j] : A(0);
+        for (int j = 0; j < NR; ++j) wv[j] = TF(0);
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < NR; ++j) wv[j] = zf[grow * ld + rhs0 + j];
+        }
     };
-    A wn0[NR], wn1[NR];
-    load_bwd(nb - 1, wn0);
-    load_bwd(nb - 2, wn1);
-    for (int K = nb - 1; K >= 0; --K) {
+    TF wb[2][NR];
+    load_bwd(nb - 1, wb[0]);
+    load_bwd(nb - 2, wb[1]);
+    auto bwd_step = [&](int K, TF (&wv)[NR]) {
         if (K - D >= 0)
             block_copy_async(bufs + (int64_t)((K - D) % nbuf) * brs_max, F + (int64_t)(K - D) * brs,
                              brs * sizeof(TF));
         cp_async_commit();
         A w[NR];
 #pragma unroll
-        for (int j = 0; j < NR; ++j) { w[j] = wn0[j]; wn0[j] = wn1[j]; }
-        load_bwd(K - 2, wn1);
+        for (int j = 0; j < NR; ++j) w[j] = (A)wv[j];
+        load_bwd(K - 2, wv);
         cp_async_wait_n(D);
         __syncthreads();
         const int row = K * 32 + lane;
@@ -326,6 +347,11 @@ __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __rest
             for (int j = 0; j < NR; ++j) zf[grow * ld + rhs0 + j] = (TF)x[j];
         }
         __syncthreads();
+    };
+#pragma unroll 1
+    for (int K = nb - 1; K >= 0; K -= 2) {
+        bwd_step(K, wb[0]);
+        if (K - 1 >= 0) bwd_step(K - 1, wb[1]);
     }
 }
 
@@ -543,85 +569,123 @@ k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
 }
 
 // ===========================================================================
-// a6+a7: z = z_f + Psi e_c ; r.z and (flexible CG) z.q ; beta
+// a6 + a2: z = z_f + R_0^T e_c with the CG update and the dots.
+//
+// mode 0: z only (a plain preconditioner application).
+// mode 1: first application of a solve: z and rho = r.z (beta = 0).
+// mode 2: CG iteration.  For (system, rhs) pairs still iterating,
+//         r <- r - alpha q and x <- x + alpha p with alpha = rho / pq (the
+//         local solves applied the same fused multiply-add to r on the fly),
+//         then r.z, r.r and, for flexible CG, z.q; the last block of a
+//         system applies the convergence test and sets beta: rho'/rho (PCG)
+//         or -(z.q)/(p.q) (flexible CG).
 // ===========================================================================
-template <typename TF, typename TP, int LD>
+template <typename TF, typename TP, int LD, int MM>
 __global__ void __launch_bounds__(kRedThreads)
-k_prolong_dot(const int32_t* __restrict__ sub_of_row, const SubInfo* __restrict__ subs,
-              const TP* __restrict__ psi, const TF* __restrict__ ec, const TF* __restrict__ zf,
-              const double* __restrict__ r, const double* __restrict__ q, double* __restrict__ z,
-              RedLayout R, CgScalars* sc, SolveState* st, int nseg, int flexible, int first,
-              int with_dot) {
+k_prolong_update(const int32_t* __restrict__ sub_of_row, const SubInfo* __restrict__ subs,
+                 const TP* __restrict__ psi, const TF* __restrict__ ec, const TF* __restrict__ zf,
+                 double* __restrict__ r, const double* __restrict__ q, double* __restrict__ x,
+                 const double* __restrict__ p, double* __restrict__ z, RedLayout R, CgScalars* sc,
+                 SolveState* st, int nseg, int flexible, int mode) {
     if (st != nullptr && st->done) return;
-    __shared__ double s_out[2 * kMaxLd];
+    using AT = typename Acc<TF>::type;
+    __shared__ double s_out[kRedMaxNV * kMaxLd];
     __shared__ double s_scr[kRedThreads];
+    constexpr int RPT = kRedElems / kRedThreads;
     const int64_t base = (int64_t)blockIdx.x * kRedElems;
-    double v[2] = {0.0, 0.0};
+    const int rhs = threadIdx.x % LD;
+    double alpha = 0.0;
+    bool upd = false;
+    if (mode == 2) {
+        const CgScalars c = sc[R.blk_seg[blockIdx.x] * LD + rhs];
+        upd = c.active != 0;
+        if (upd) alpha = c.rho / c.pq;
+    }
+    int sub[RPT];
 #pragma unroll
-    for (int k = 0; k < kRedElems / kRedThreads; ++k) {
+    for (int k = 0; k < RPT; ++k) sub[k] = __ldg(sub_of_row + (base + threadIdx.x + k * kRedThreads) / LD);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
         const int64_t e = base + threadIdx.x + k * kRedThreads;
-        const int64_t row = e / LD;
-        const int rhs = (int)(e % LD);
-        const int s = sub_of_row[row];
         double zv = 0.0;
-        if (s >= 0) {
-            const SubInfo S = subs[s];
-            const int64_t lr = row - S.row0;
-            double acc = to_d(zf[e]);
+        if (sub[k] >= 0) {
+            const SubInfo* S = subs + sub[k];
+            const int64_t lr = e / LD - S->row0;
+            AT acc = (AT)zf[e];
             if (ec != nullptr) {
-                const TP* pr = psi + S.psi_off + lr * S.m;
-                const TF* er = ec + S.coff * LD + rhs;
-                typename Acc<TF>::type pe = 0;
-                for (int kk = 0; kk < S.m; ++kk) pe += (typename Acc<TF>::type)to_d(pr[kk]) * er[(int64_t)kk * LD];
-                acc += (double)pe;
+                const int m = S->m;
+                const TP* pr = psi + S->psi_off + lr * m;
+                const TF* er = ec + (int64_t)S->coff * LD + rhs;
+                AT pe = AT(0);
+#pragma unroll
+                for (int kk = 0; kk < MM; ++kk)
+                    if (kk < m) pe += (AT)to_d(pr[kk]) * er[(int64_t)kk * LD];
+                zv = (double)acc + (double)pe;
+            } else {
+                zv = (double)acc;
             }
-            zv = acc;
         }
         z[e] = zv;
-        if (with_dot) {
-            v[0] += r[e] * zv;
-            if (flexible && !first) v[1] += zv * q[e];
+        if (mode != 0) {
+            double rv = r[e];
+            if (upd) {
+                rv = fma(-alpha, q[e], rv);
+                r[e] = rv;
+                x[e] = fma(alpha, p[e], x[e]);
+            }
+            v[0] = fma(rv, zv, v[0]);
+            v[1] = fma(rv, rv, v[1]);
+            if (flexible && mode == 2) v[2] = fma(zv, q[e], v[2]);
         }
     }
-    if (!with_dot) return;
+    if (mode == 0) return;
     int sg;
-    if (!seg_reduce<2>(v, LD, R, s_out, s_scr, sg)) return;
+    if (!seg_reduce<4>(v, LD, R, s_out, s_scr, sg)) return;
+    const int it = st->it;
     if (threadIdx.x < LD) {
         CgScalars& c = sc[sg * LD + threadIdx.x];
         const double rz = s_out[threadIdx.x];
-        const double zq = s_out[LD + threadIdx.x];
-        if (first) {
+        const double rr = s_out[LD + threadIdx.x];
+        const double zq = s_out[2 * LD + threadIdx.x];
+        if (mode == 1) {
+            c.rho = rz;
             c.beta = 0.0;
+            c.zq = 0.0;
+            if (c.active && !isfinite(rz)) {
+                st->status = AMS_ERR_BREAKDOWN;
+                st->done = 1;
+            }
         } else if (c.active) {
-            c.beta = flexible ? -(c.rho / c.pq) * zq / c.rho : rz / c.rho;
-        } else {
-            c.beta = 0.0;
+            c.alpha = c.rho / c.pq;
+            c.rr = rr;
+            c.iters = it + 1;
+            if (!isfinite(rr) || !isfinite(rz)) {
+                st->status = AMS_ERR_BREAKDOWN;
+                st->done = 1;
+            } else if (rr <= st->rtol2 * c.fnorm2) {
+                c.active = 0;
+                c.beta = 0.0;
+            } else {
+                c.beta = flexible ? -zq / c.pq : rz / c.rho;
+            }
+            c.zq = zq;
+            c.rho = rz;
         }
-        if (c.active && !isfinite(rz)) {
-            st->status = AMS_ERR_BREAKDOWN;
-            st->done = 1;
-        }
-        c.zq = zq;
-        c.rho = rz;
     }
-}
-
-// p = z + beta p  (first application: p = z)
-template <int LD>
-__global__ void __launch_bounds__(kRedThreads)
-k_dir_update(double* __restrict__ p, const double* __restrict__ z, const int32_t* __restrict__ blk_seg,
-             const CgScalars* sc, const SolveState* st) {
-    if (st->done) return;
-    const int64_t base = (int64_t)blockIdx.x * kRedElems;
-    const int seg = blk_seg[blockIdx.x];
-    const int rhs = threadIdx.x % LD;
-    const CgScalars c = sc[seg * LD + rhs];
-    if (!c.active) return;
-    const double beta = c.beta;
-#pragma unroll
-    for (int k = 0; k < kRedElems / kRedThreads; ++k) {
-        const int64_t e = base + threadIdx.x + k * kRedThreads;
-        p[e] = z[e] + beta * p[e];
+    if (mode != 2) return;
+    if (!last_system(R, nseg)) return;
+    if (threadIdx.x == 0) {
+        int nact = 0;
+        double worst = 0.0;
+        for (int i = 0; i < nseg * LD; ++i) {
+            nact += sc[i].active;
+            if (sc[i].active) worst = fmax(worst, sc[i].rr / sc[i].fnorm2);
+        }
+        st->nactive = nact;
+        st->worst = worst;
+        st->it = it + 1;
+        if (nact == 0 || it + 1 >= st->maxit) st->done = 1;
     }
 }
 
@@ -630,7 +694,7 @@ template <int LD>
 __global__ void __launch_bounds__(kRedThreads)
 k_init_norms(const double* __restrict__ r, RedLayout R, CgScalars* sc, SolveState* st, int nseg,
              int nrhs) {
-    __shared__ double s_out[2 * kMaxLd];
+    __shared__ double s_out[kRedMaxNV * kMaxLd];
     __shared__ double s_scr[kRedThreads];
     const int64_t base = (int64_t)blockIdx.x * kRedElems;
     double v[1] = {0.0};
@@ -725,28 +789,13 @@ __global__ void k_zero(double* __restrict__ a, int64_t n) {
     }
 
 template <int LD>
-static void spmv_ld(const LaunchCtx& L, const double* p, double* q, int with_dot) {
-    k_spmv_dot<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(L.sell_ptr, L.sell_col, L.sell_val, p, q,
-                                                         L.red, L.sc, L.st, L.nseg, with_dot);
+static void spmv_ld(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* q, int mode) {
+    k_spmv_dir<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(L.sell_ptr, L.sell_col, L.sell_val, z, p_old, p_new, q,
+                                                         L.red, L.sc, mode ? L.st : nullptr, mode);
 }
-void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_dot) {
-    AMS_DISPATCH_LD(L.ld, spmv_ld, L, p, q, with_dot);
-}
-
-template <int LD>
-static void update_ld(const LaunchCtx& L, double* x, double* r, const double* p, const double* q) {
-    k_cg_update<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(x, r, p, q, L.red, L.sc, L.st, L.nseg);
-}
-void launch_cg_update(const LaunchCtx& L, double* x, double* r, const double* p, const double* q) {
-    AMS_DISPATCH_LD(L.ld, update_ld, L, x, r, p, q);
-}
-
-template <int LD>
-static void dir_ld(const LaunchCtx& L, double* p, const double* z) {
-    k_dir_update<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(p, z, L.red.blk_seg, L.sc, L.st);
-}
-void launch_dir_update(const LaunchCtx& L, double* p, const double* z) {
-    AMS_DISPATCH_LD(L.ld, dir_ld, L, p, z);
+void launch_spmv_dir(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* q,
+                     int mode) {
+    AMS_DISPATCH_LD(L.ld, spmv_ld, L, z, p_old, p_new, q, mode);
 }
 
 template <int LD>
@@ -785,7 +834,7 @@ static cudaError_t local_nr(const LocalSolveArgs& a, const void* fac, const void
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    kern<<<a.nsub, warps * 32, smem, a.stream>>>(a.subs, (const TF*)fac, a.rin, a.rowscale, (TF*)zf,
+    kern<<<a.nsub, warps * 32, smem, a.stream>>>(a.subs, (const TF*)fac, a.in.r, a.in.q, a.in.sc, a.rowscale, (TF*)zf,
                                                   (const TP*)psi, (TF*)rc, a.ld, a.cmax, depth, a.st);
     return cudaGetLastError();
 }
@@ -845,30 +894,31 @@ void launch_coarse_gemm(const CoarseLaunch& c, int prec, int ld, const void* in,
 }
 
 template <typename TF, typename TP, int LD>
-static void prolong_ld(const LaunchCtx& L, const void* psi, const void* ec, const void* zf,
-                       const double* r, const double* q, double* z, int flexible, int first, int with_dot) {
-    k_prolong_dot<TF, TP, LD><<<L.nblk, kRedThreads, 0, L.stream>>>(
-        L.sub_of_row, L.subs, (const TP*)psi, (const TF*)ec, (const TF*)zf, r, q, z, L.red, L.sc, L.st,
-        L.nseg, flexible, first, with_dot);
+static void prolong_ld(const LaunchCtx& L, const ProlongArgs& a) {
+    if (a.mmax > 8)
+        k_prolong_update<TF, TP, LD, kMaxM><<<L.nblk, kRedThreads, 0, L.stream>>>(
+            L.sub_of_row, L.subs, (const TP*)a.psi, (const TF*)a.ec, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z,
+            L.red, L.sc, L.st, L.nseg, a.flexible, a.mode);
+    else
+        k_prolong_update<TF, TP, LD, 8><<<L.nblk, kRedThreads, 0, L.stream>>>(
+            L.sub_of_row, L.subs, (const TP*)a.psi, (const TF*)a.ec, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z,
+            L.red, L.sc, L.st, L.nseg, a.flexible, a.mode);
 }
 template <typename TF, typename TP>
-static void prolong_tp(const LaunchCtx& L, const void* psi, const void* ec, const void* zf,
-                       const double* r, const double* q, double* z, int flexible, int first, int with_dot) {
+static void prolong_tp(const LaunchCtx& L, const ProlongArgs& a) {
     switch (L.ld) {
-        case 1: prolong_ld<TF, TP, 1>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
-        case 2: prolong_ld<TF, TP, 2>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
-        case 4: prolong_ld<TF, TP, 4>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
-        case 8: prolong_ld<TF, TP, 8>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
-        case 16: prolong_ld<TF, TP, 16>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
-        default: prolong_ld<TF, TP, 32>(L, psi, ec, zf, r, q, z, flexible, first, with_dot); break;
+        case 1: prolong_ld<TF, TP, 1>(L, a); break;
+        case 2: prolong_ld<TF, TP, 2>(L, a); break;
+        case 4: prolong_ld<TF, TP, 4>(L, a); break;
+        case 8: prolong_ld<TF, TP, 8>(L, a); break;
+        case 16: prolong_ld<TF, TP, 16>(L, a); break;
+        default: prolong_ld<TF, TP, 32>(L, a); break;
     }
 }
-void launch_prolong_dot(const LaunchCtx& L, int prec, const void* psi, const void* ec, const void* zf,
-                        const double* r, const double* q, double* z, int flexible, int first,
-                        int with_dot) {
-    if (prec == AMS_PREC_FP64) prolong_tp<double, double>(L, psi, ec, zf, r, q, z, flexible, first, with_dot);
-    else if (prec == AMS_PREC_FP32) prolong_tp<float, float>(L, psi, ec, zf, r, q, z, flexible, first, with_dot);
-    else prolong_tp<float, __nv_bfloat16>(L, psi, ec, zf, r, q, z, flexible, first, with_dot);
+void launch_prolong_update(const LaunchCtx& L, int prec, const ProlongArgs& a) {
+    if (prec == AMS_PREC_FP64) prolong_tp<double, double>(L, a);
+    else if (prec == AMS_PREC_FP32) prolong_tp<float, float>(L, a);
+    else prolong_tp<float, __nv_bfloat16>(L, a);
 }
 
 void launch_permute_in(cudaStream_t s, const double* f, int64_t n, int nrhs, int ld,

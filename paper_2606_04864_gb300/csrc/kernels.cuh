@@ -87,22 +87,36 @@ struct RedLayout {
 
 // Sum `count` vectors of `nv` doubles (vector j at src + j*stride) in a
 // fixed order using all threads of the block; result lands in dst[0..nv).
-// Requires nv <= blockDim.x.  Uses `scratch` (blockDim.x doubles).
+// nv is a power of two <= blockDim.x (a power of two).  Thread t adds the
+// vectors j = t/nv, t/nv + blockDim.x/nv, ... of component t % nv; threads
+// of one warp that share a component combine by xor shuffles, and the
+// per-warp (or, for nv >= 32, per-thread) partials are added in index order
+// after a single barrier.  Uses `scratch` (blockDim.x doubles).
 __device__ inline void block_sum_vectors(const double* src, int count, int64_t stride, int nv,
                                          double* dst, double* scratch) {
     const int t = threadIdx.x;
-    const int lanes_per = blockDim.x / nv;        // threads per value (power of two)
+    const int lanes_per = blockDim.x / nv;        // threads per component
     const int v = t % nv;
-    const int part = t / nv;
     double s = 0.0;
-    for (int j = part; j < count; j += lanes_per) s += __ldcg(src + (int64_t)j * stride + v);
-    scratch[t] = s;
-    __syncthreads();
-    for (int h = lanes_per / 2; h >= 1; h >>= 1) {   // fixed-shape tree
-        if (part < h) scratch[t] += scratch[t + h * nv];
+    for (int j = t / nv; j < count; j += lanes_per) s += __ldcg(src + (int64_t)j * stride + v);
+    if (nv < 32) {
+        for (int off = 16; off >= nv; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if ((t & 31) < nv) scratch[(t >> 5) * nv + v] = s;
         __syncthreads();
+        if (t < nv) {
+            double a = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += scratch[w * nv + t];
+            dst[t] = a;
+        }
+    } else {
+        scratch[t] = s;
+        __syncthreads();
+        if (t < nv) {
+            double a = 0.0;
+            for (int k = 0; k < lanes_per; ++k) a += scratch[k * nv + t];
+            dst[t] = a;
+        }
     }
-    if (t < nv) dst[t] = scratch[t];
     __syncthreads();
 }
 
@@ -177,6 +191,7 @@ __device__ inline bool cross_blocks(int b, int seg, int nvl, const RedLayout& R,
 template <int NV>
 __device__ bool seg_reduce(const double (&val)[NV], int ld, const RedLayout& R, double* out,
                            double* scratch, int& seg_out) {
+    static_assert(NV <= kRedMaxNV, "partial buffers hold kRedMaxNV values per right-hand side");
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;

@@ -25,12 +25,21 @@ struct LaunchCtx {
     const SubInfo* subs;
 };
 
+// Residual used by the local solves: r' = r - alpha q (alpha = rho / pq of
+// the subdomain's (system, rhs)) for pairs still iterating when q is
+// non-NULL, r itself otherwise.
+struct ResidIn {
+    const double* r;
+    const double* q;         // NULL: no update
+    const CgScalars* sc;     // [nseg][ld]
+};
+
 struct LocalSolveArgs {
     cudaStream_t stream;
     int nsub;
     const SubInfo* subs;
-    const double* rin;
-    const double* rowscale;  // NULL or per-row scale applied to rin
+    ResidIn in;
+    const double* rowscale;  // NULL or per-row scale applied to the input
     int ld;
     int cmax;
     int mmax;
@@ -45,7 +54,7 @@ struct LocalTmaArgs {
     const struct CUtensorMap_st* tmB;
     const int64_t* tile_row0;
     const float* piv;
-    const double* rin;
+    ResidIn in;
     int ld;
     int cmax;
     int mmax;
@@ -65,9 +74,9 @@ struct CoarseLaunch {
     const SolveState* st;
 };
 
-void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_dot);
-void launch_cg_update(const LaunchCtx& L, double* x, double* r, const double* p, const double* q);
-void launch_dir_update(const LaunchCtx& L, double* p, const double* z);
+// mode 1: p_new = z + beta p_old, q = A p_new, p_new.q; mode 0: q = A z
+void launch_spmv_dir(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* q,
+                     int mode);
 void launch_init_norms(const LaunchCtx& L, const double* r, int nrhs);
 size_t local_solve_smem(int cmax, int ld, size_t tf_bytes, int depth);
 int local_solve_depth(int cmax, int ld, size_t tf_bytes);
@@ -80,9 +89,20 @@ cudaError_t make_tile_map(void* base, int64_t rows, struct CUtensorMap_st* out);
 void launch_band_pack_tiles(cudaStream_t s, int nwork, const SubInfo* subs, const int64_t* band_off,
                             const int2* work, const double* band, const int64_t* out_off, float* fwd, float* bwd,
                             float* piv);
-void launch_prolong_dot(const LaunchCtx& L, int prec, const void* psi, const void* ec, const void* zf,
-                        const double* r, const double* q, double* z, int flexible, int first,
-                        int with_dot);
+struct ProlongArgs {
+    const void* psi;
+    const void* ec;          // NULL without a coarse space
+    const void* zf;
+    double* r;
+    const double* q;
+    double* x;
+    const double* p;
+    double* z;
+    int mmax;
+    int flexible;
+    int mode;                // 0 apply only, 1 first application, 2 CG iteration
+};
+void launch_prolong_update(const LaunchCtx& L, int prec, const ProlongArgs& a);
 void launch_permute_in(cudaStream_t s, const double* f, int64_t n, int nrhs, int ld,
                        const int64_t* int_row, double* r, double* x);
 void launch_permute_out(cudaStream_t s, const double* x, int64_t n, int nrhs, int ld,

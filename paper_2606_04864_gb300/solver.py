@@ -23,7 +23,7 @@ from typing import List, Optional, Sequence
 import numpy as np
 
 from . import _lib
-from ._lib import AmsError, ams_info, ams_options, ams_system_desc, check, lib
+from ._lib import AMS_NUM_KERNELS, KERNEL_NAMES, AmsError, ams_info, ams_options, ams_system_desc, check, lib
 
 
 def _torch():
@@ -128,16 +128,19 @@ class _Base:
         return u, its, rel
 
     def profile_solve(self, f, rtol: float = 1e-8):
-        """One solve with CUDA events around every kernel.  Returns a list of
-        7 dicts (spmv, update, local, coarse fwd, coarse bwd, prolong,
-        direction) with total ms, launch count and bytes per launch."""
+        """One solve with CUDA events around every kernel.  Returns one dict
+        per kernel of the iteration (``KERNEL_NAMES`` order: SpMV with the
+        direction update, local solves, coarse forward, coarse backward,
+        prolongation with the CG update) with total ms, launch count and
+        algorithmic bytes per launch."""
         fv, nrhs = self._vec_in(f)
-        ms = np.zeros(7, dtype=np.float64)
-        by = np.zeros(7, dtype=np.float64)
-        cnt = np.zeros(7, dtype=np.int64)
+        ms = np.zeros(AMS_NUM_KERNELS, dtype=np.float64)
+        by = np.zeros(AMS_NUM_KERNELS, dtype=np.float64)
+        cnt = np.zeros(AMS_NUM_KERNELS, dtype=np.int64)
         check(lib().ams_profile_solve(self._h, _ptr(fv), nrhs, float(rtol), _ptr(ms), _ptr(by), _ptr(cnt)),
               "ams_profile_solve", allow=(4,))
-        return [{"ms": float(ms[k]), "count": int(cnt[k]), "bytes": float(by[k])} for k in range(7)]
+        return [{"name": KERNEL_NAMES[k], "ms": float(ms[k]), "count": int(cnt[k]), "bytes": float(by[k])}
+                for k in range(AMS_NUM_KERNELS)]
 
     def time_kernel(self, which: int, reps: int = 20):
         ms = C.c_double()
