@@ -264,7 +264,8 @@ ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y);
 /*
  * The kernels of one CG iteration, in launch order (indices of
  * ams_time_kernel and of the ams_profile_solve outputs):
- *   AMS_KERNEL_SPMV        direction p = z + beta p_old, q = A p, p.q
+ *   AMS_KERNEL_SPMV        direction p = z + beta p_old, then q = A p and
+ *                          p.q (two launches, timed together)
  *   AMS_KERNEL_LOCAL       local solves sum_i R_i^T A_i^{-1} R_i r' and the
  *                          restriction R_0 r', with r' = r - alpha q
  *   AMS_KERNEL_COARSE_FWD  y = L_c^{-1} r_c   (A_0 = L_c L_c^T)

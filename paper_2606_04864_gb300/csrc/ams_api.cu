@@ -56,6 +56,7 @@ struct RedCache {
     int ld = 0;
     int64_t nblk = 0;
     int ngrp = 0;
+    int64_t* blk_lo = nullptr;
     int32_t *blk_seg = nullptr, *seg_blk0 = nullptr, *seg_nblk = nullptr, *seg_grp0 = nullptr;
     double *part1 = nullptr, *part2 = nullptr;
     int32_t *cnt1 = nullptr, *cnt2 = nullptr, *cnt3 = nullptr;
@@ -103,6 +104,7 @@ struct ams_handle_s {
     int32_t N = 0;
     int64_t Nc = 0;
     int cmax = 1, mmax = 0, nbmax = 1;
+    int num_sms = 1;                    // SMs of the handle's device
     std::vector<SubInfo> h_subs;
     std::vector<double> h_lam;          // kept eigenvalues, subdomain-major
     std::vector<DevBuf> bufs;
@@ -143,7 +145,8 @@ struct ams_handle_s {
     double* d_stage_dvals = nullptr;
     CgScalars* d_sc = nullptr;
     SolveState* d_st = nullptr;
-    std::map<int, RedCache> red;
+    std::map<int, RedCache> red;        // element blocks, per ld
+    std::map<int, RedCache> red_sub;    // one block per subdomain, per ld
     ams_info info{};
     int64_t launches = 0;               // kernels launched by solve-time entry points
 
@@ -200,59 +203,132 @@ static double now_s() {
 // ---------------------------------------------------------------------------
 // reduction layout for a given ld
 // ---------------------------------------------------------------------------
-static ams_status get_red(ams_handle h, int ld, RedCache** out) {
-    auto it = h->red.find(ld);
-    if (it != h->red.end()) {
-        *out = &it->second;
-        return AMS_OK;
-    }
-    RedCache rc;
+// Blocks [blk0[s], blk0[s] + nblk[s]) belong to system s; block b covers
+// the range [blk_lo[b], blk_lo[b+1]).
+static ams_status build_red(ams_handle h, int ld, const std::vector<int64_t>& blk_lo,
+                            const std::vector<int32_t>& blk_seg, const std::vector<int32_t>& seg_blk0,
+                            const std::vector<int32_t>& seg_nblk, RedCache& rc) {
     rc.ld = ld;
-    rc.nblk = h->n_pad * ld / kRedElems;
-    std::vector<int32_t> blk_seg(rc.nblk), seg_blk0(h->nsys), seg_nblk(h->nsys), seg_grp0(h->nsys);
+    rc.nblk = (int64_t)blk_seg.size();
+    std::vector<int32_t> seg_grp0(h->nsys);
     int ngrp = 0;
     for (int s = 0; s < h->nsys; ++s) {
-        const int64_t b0 = h->sys[s].row0 * ld / kRedElems;
-        const int64_t nb = h->sys[s].npad * ld / kRedElems;
-        seg_blk0[s] = (int32_t)b0;
-        seg_nblk[s] = (int32_t)nb;
         seg_grp0[s] = ngrp;
-        ngrp += (int)((nb + kRedGroup - 1) / kRedGroup);
-        for (int64_t b = b0; b < b0 + nb; ++b) blk_seg[b] = s;
+        ngrp += (seg_nblk[s] + kRedGroup - 1) / kRedGroup;
     }
     rc.ngrp = ngrp;
+    AMS_TRY(upload(h, &rc.blk_lo, blk_lo));
     AMS_TRY(upload(h, &rc.blk_seg, blk_seg));
     AMS_TRY(upload(h, &rc.seg_blk0, seg_blk0));
     AMS_TRY(upload(h, &rc.seg_nblk, seg_nblk));
     AMS_TRY(upload(h, &rc.seg_grp0, seg_grp0));
-    AMS_TRY(h->alloc_t(&rc.part1, (size_t)rc.nblk * kRedMaxNV * ld));
-    AMS_TRY(h->alloc_t(&rc.part2, (size_t)ngrp * kRedMaxNV * ld));
-    AMS_TRY(h->alloc_t(&rc.cnt1, (size_t)ngrp));
+    AMS_TRY(h->alloc_t(&rc.part1, (size_t)std::max<int64_t>(rc.nblk, 1) * kRedMaxNV * ld));
+    AMS_TRY(h->alloc_t(&rc.part2, (size_t)std::max(ngrp, 1) * kRedMaxNV * ld));
+    AMS_TRY(h->alloc_t(&rc.cnt1, (size_t)std::max(ngrp, 1)));
     AMS_TRY(h->alloc_t(&rc.cnt2, (size_t)h->nsys));
     AMS_TRY(h->alloc_t(&rc.cnt3, 1));
-    AMS_CUDA_TRY(cudaMemsetAsync(rc.cnt1, 0, sizeof(int32_t) * ngrp, h->stream));
+    AMS_CUDA_TRY(cudaMemsetAsync(rc.cnt1, 0, sizeof(int32_t) * std::max(ngrp, 1), h->stream));
     AMS_CUDA_TRY(cudaMemsetAsync(rc.cnt2, 0, sizeof(int32_t) * h->nsys, h->stream));
     AMS_CUDA_TRY(cudaMemsetAsync(rc.cnt3, 0, sizeof(int32_t), h->stream));
-    h->red[ld] = rc;
-    *out = &h->red[ld];
     return AMS_OK;
 }
 
-static LaunchCtx make_ctx(ams_handle h, const RedCache& rc) {
+// Split `work[i]` (i = 0..count-1, one system) into `nb` consecutive ranges of
+// about equal total work; appends the range starts (offset by `first`).
+static void split_ranges(const std::vector<int64_t>& work, int nb, int64_t first, std::vector<int64_t>& lo) {
+    const int64_t count = (int64_t)work.size();
+    double tot = 0.0;
+    for (int64_t w : work) tot += (double)w;
+    int64_t i = 0;
+    double acc = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        lo.push_back(first + i);
+        const double target = tot * (double)(b + 1) / nb;
+        const int64_t left = nb - 1 - b;   // later ranges each keep at least one item
+        while (i < count - left && (acc < target || i == lo.back() - first)) acc += (double)work[i++];
+    }
+}
+
+// Reduction layouts for a given ld, sized to about kRedBlocksPerSM blocks per
+// SM: blocks of whole kRedElems-element chunks of one system, and blocks of
+// consecutive subdomains of one system (balanced by rows).
+static ams_status get_red(ams_handle h, int ld, RedCache** out, RedCache** out_sub) {
+    const int target = std::max(1, kRedBlocksPerSM * h->num_sms);
+    if (h->red.find(ld) == h->red.end()) {
+        const int64_t nchunk_tot = h->n_pad * ld / kRedElems;
+        std::vector<int64_t> blk_lo;
+        std::vector<int32_t> blk_seg, seg_blk0(h->nsys), seg_nblk(h->nsys);
+        for (int s = 0; s < h->nsys; ++s) {
+            const int64_t c0 = h->sys[s].row0 * ld / kRedElems;
+            const int64_t nc = h->sys[s].npad * ld / kRedElems;
+            int nb = (int)std::llround((double)target * (double)nc / (double)nchunk_tot);
+            nb = (int)std::max<int64_t>(1, std::min<int64_t>(nb, nc));
+            seg_blk0[s] = (int32_t)blk_seg.size();
+            seg_nblk[s] = nb;
+            std::vector<int64_t> work(nc, 1), lo;
+            split_ranges(work, nb, c0, lo);
+            for (int64_t c : lo) {
+                blk_lo.push_back(c * kRedElems);
+                blk_seg.push_back(s);
+            }
+        }
+        blk_lo.push_back(h->n_pad * ld);
+        RedCache rc;
+        AMS_TRY(build_red(h, ld, blk_lo, blk_seg, seg_blk0, seg_nblk, rc));
+        h->red[ld] = rc;
+    }
+    if (h->red_sub.find(ld) == h->red_sub.end()) {
+        std::vector<int64_t> blk_lo;
+        std::vector<int32_t> blk_seg, seg_blk0(h->nsys), seg_nblk(h->nsys);
+        for (int s = 0; s < h->nsys; ++s) {
+            const SystemHost& S = h->sys[s];
+            int nb = (int)std::llround((double)target * (double)S.n / (double)std::max<int64_t>(1, h->n_total));
+            nb = std::max(1, std::min(nb, S.nparts));
+            seg_blk0[s] = (int32_t)blk_seg.size();
+            seg_nblk[s] = nb;
+            std::vector<int64_t> work(S.nparts), lo;
+            for (int a = 0; a < S.nparts; ++a) work[a] = std::max<int64_t>(1, h->h_subs[S.sub0 + a].n);
+            split_ranges(work, nb, S.sub0, lo);
+            for (int64_t b : lo) {
+                blk_lo.push_back(b);
+                blk_seg.push_back(s);
+            }
+        }
+        blk_lo.push_back(h->N);
+        RedCache rc;
+        AMS_TRY(build_red(h, ld, blk_lo, blk_seg, seg_blk0, seg_nblk, rc));
+        h->red_sub[ld] = rc;
+    }
+    *out = &h->red[ld];
+    if (out_sub) *out_sub = &h->red_sub[ld];
+    return AMS_OK;
+}
+
+static RedLayout layout_of(const RedCache& rc) {
+    RedLayout R;
+    R.blk_lo = rc.blk_lo;
+    R.blk_seg = rc.blk_seg;
+    R.seg_blk0 = rc.seg_blk0;
+    R.seg_nblk = rc.seg_nblk;
+    R.seg_grp0 = rc.seg_grp0;
+    R.part1 = rc.part1;
+    R.part2 = rc.part2;
+    R.cnt1 = rc.cnt1;
+    R.cnt2 = rc.cnt2;
+    R.cnt3 = rc.cnt3;
+    return R;
+}
+
+static LaunchCtx make_ctx(ams_handle h, const RedCache& rc, const RedCache& rcs) {
     LaunchCtx L;
     L.stream = h->stream;
     L.ld = rc.ld;
     L.nblk = rc.nblk;
     L.nseg = h->nsys;
-    L.red.blk_seg = rc.blk_seg;
-    L.red.seg_blk0 = rc.seg_blk0;
-    L.red.seg_nblk = rc.seg_nblk;
-    L.red.seg_grp0 = rc.seg_grp0;
-    L.red.part1 = rc.part1;
-    L.red.part2 = rc.part2;
-    L.red.cnt1 = rc.cnt1;
-    L.red.cnt2 = rc.cnt2;
-    L.red.cnt3 = rc.cnt3;
+    L.red = layout_of(rc);
+    L.red_sub = layout_of(rcs);
+    L.nblk_sub = rcs.nblk;
+    L.nsub = h->N;
     L.sc = h->d_sc;
     L.st = h->d_st;
     L.sell_ptr = h->d_sell_ptr;
@@ -787,6 +863,11 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     h->flexible = h->opt.cg_variant == AMS_CG_AUTO ? (h->prec != AMS_PREC_FP64) : (h->opt.cg_variant == AMS_CG_FCG);
     h->ustream = (cudaStream_t)stream;
     AMS_CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    {
+        int dev = 0;
+        AMS_CUDA_TRY(cudaGetDevice(&dev));
+        AMS_CUDA_TRY(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    }
     AMS_CUDA_TRY(cudaEventCreateWithFlags(&h->ev_enter, cudaEventDisableTiming));
     AMS_CUDA_TRY(cudaEventRecord(h->ev_enter, h->ustream));
     AMS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_enter, 0));
@@ -1111,15 +1192,20 @@ static ams_status apply_precond(ams_handle h, const LaunchCtx& L, int mode, cons
     return AMS_OK;
 }
 
-static int launches_per_iteration(ams_handle h) { return h->Nc > 0 ? 5 : 3; }
+static int launches_per_iteration(ams_handle h) { return h->Nc > 0 ? 6 : 4; }
+
+static void launch_direction_spmv(ams_handle h, const LaunchCtx& L, const double* p_old, double* p_new) {
+    launch_dir_update(L, h->d_z, p_old, p_new);
+    launch_spmv_dot(L, p_new, h->d_q, 1);
+}
 
 // One CG iteration; `par` selects which direction buffer holds p_old.
 static ams_status launch_iteration(ams_handle h, const LaunchCtx& L, int par) {
     double* p_old = par ? h->d_p2 : h->d_p;
     double* p_new = par ? h->d_p : h->d_p2;
-    h->launches += 1;
+    h->launches += 2;
     prof_begin(h, AMS_KERNEL_SPMV);
-    launch_spmv_dir(L, h->d_z, p_old, p_new, h->d_q, 1);
+    launch_direction_spmv(h, L, p_old, p_new);
     prof_end(h);
     return apply_precond(h, L, 2, p_new);
 }
@@ -1169,9 +1255,9 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
                       double* relres) {
     const int ld = pow2ceil(nrhs);
     AMS_TRY(ensure_work(h, ld));
-    RedCache* rc = nullptr;
-    AMS_TRY(get_red(h, ld, &rc));
-    LaunchCtx L = make_ctx(h, *rc);
+    RedCache *rc = nullptr, *rcs = nullptr;
+    AMS_TRY(get_red(h, ld, &rc, &rcs));
+    LaunchCtx L = make_ctx(h, *rc, *rcs);
     // caller order -> internal rows (each system's block is contiguous in f)
     for (int s = 0; s < h->nsys; ++s) {
         const SystemHost& S = h->sys[s];
@@ -1532,9 +1618,9 @@ ams_status ams_apply_preconditioner(ams_handle h, const double* r, int32_t nrhs,
     }
     const int ld = pow2ceil(nrhs);
     AMS_TRY(ensure_work(h, ld));
-    RedCache* rc = nullptr;
-    AMS_TRY(get_red(h, ld, &rc));
-    LaunchCtx L = make_ctx(h, *rc);
+    RedCache *rc = nullptr, *rcs = nullptr;
+    AMS_TRY(get_red(h, ld, &rc, &rcs));
+    LaunchCtx L = make_ctx(h, *rc, *rcs);
     const double* r_dev = nullptr;
     AMS_TRY(stage_in(h, r, nrhs, h->d_stage_in, &r_dev));
     launch_permute_in(h->stream, r_dev, h->n_total, nrhs, ld, h->d_int_row, h->d_r, nullptr);
@@ -1558,14 +1644,14 @@ ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y) {
     }
     const int ld = pow2ceil(nrhs);
     AMS_TRY(ensure_work(h, ld));
-    RedCache* rc = nullptr;
-    AMS_TRY(get_red(h, ld, &rc));
-    LaunchCtx L = make_ctx(h, *rc);
+    RedCache *rc = nullptr, *rcs = nullptr;
+    AMS_TRY(get_red(h, ld, &rc, &rcs));
+    LaunchCtx L = make_ctx(h, *rc, *rcs);
     L.st = nullptr;
     const double* x_dev = nullptr;
     AMS_TRY(stage_in(h, x, nrhs, h->d_stage_in, &x_dev));
     launch_permute_in(h->stream, x_dev, h->n_total, nrhs, ld, h->d_int_row, h->d_p, nullptr);
-    launch_spmv_dir(L, h->d_p, nullptr, nullptr, h->d_q, 0);
+    launch_spmv_dot(L, h->d_p, h->d_q, 0);
     h->launches += 3;
     double* y_dev = h->opt.device_ptrs ? y : h->d_stage_out;
     launch_permute_out(h->stream, h->d_q, h->n_total, nrhs, ld, h->d_int_row, y_dev);
@@ -1584,9 +1670,9 @@ ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* av
     }
     AMS_TRY(enter(h));
     const int ld = h->ld_last;
-    RedCache* rc = nullptr;
-    AMS_TRY(get_red(h, ld, &rc));
-    LaunchCtx L = make_ctx(h, *rc);
+    RedCache *rc = nullptr, *rcs = nullptr;
+    AMS_TRY(get_red(h, ld, &rc, &rcs));
+    LaunchCtx L = make_ctx(h, *rc, *rcs);
     // keep every (system, rhs) active and never converge while timing
     {
         std::vector<CgScalars> sc((size_t)h->nsys * ld);
@@ -1609,7 +1695,7 @@ ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* av
     // SpMV reads p and writes p2, the prolongation updates x and r in place.
     auto launch = [&]() -> ams_status {
         switch (which) {
-            case AMS_KERNEL_SPMV: launch_spmv_dir(L, h->d_z, h->d_p, h->d_p2, h->d_q, 1); break;
+            case AMS_KERNEL_SPMV: launch_direction_spmv(h, L, h->d_p, h->d_p2); break;
             case AMS_KERNEL_LOCAL:
                 AMS_TRY(launch_local(h, ld, ResidIn{h->d_r, h->d_q, h->d_sc}, true));
                 break;

@@ -22,10 +22,11 @@ namespace ams {
 constexpr int kTile = 32;              // rows per block row of a local factor
 constexpr int kRowAlign = 2048;        // row padding of each system
 constexpr int kRedThreads = 256;       // threads of the reduction kernels
-constexpr int kRedElems = 1024;        // elements per reduction block
+constexpr int kRedElems = 256;         // elements per reduction block (one per thread)
 constexpr int kRedGroup = 64;          // blocks summed per first-level group
 constexpr int kRedDirect = 2048;       // at most this many blocks: one-stage sum
 constexpr int kRedMaxNV = 4;           // values per right-hand side in one reduction
+constexpr int kRedBlocksPerSM = 4;     // reduction-kernel grid: about this many blocks per SM
 constexpr int kMaxLd = 32;             // right-hand sides per solve call
 constexpr int kMaxM = 16;              // eigenvectors per subdomain (cap)
 constexpr int kCoarseChunk = 1024;     // node-matrix columns per coarse item

@@ -1,7 +1,8 @@
 // Solve-phase kernels of the AMS-preconditioned CG (one GPU, sm_103a).
 //
-// One CG iteration (Section 3.1 preconditioner inside CG) is five kernels:
-//   k_spmv_dir        p = z + beta p_old, q = A p and p.q     (SELL-32 SpMV)
+// One CG iteration (Section 3.1 preconditioner inside CG) is six kernels:
+//   k_dir_update      p = z + beta p_old
+//   k_spmv_dot        q = A p and p.q                          (SELL-32 SpMV)
 //   k_local_solve     z_f = sum_i R_i^T A_i^{-1} R_i r'  and  r_c = R_0 r',
 //   (k_local_tma*)    r' = r - alpha q formed on the fly       (alpha = rho/pq)
 //   k_coarse_gemm     y = L_c^{-1} r_c, then e_c = L_c^{-T} y  (A_0 = L_c L_c^T)
@@ -18,48 +19,33 @@
 namespace ams {
 
 // ===========================================================================
-// a1 + a7: direction update and SpMV (SELL-32: slice s = rows 32s..32s+31,
-// entry j of lane l at sell_ptr[s] + 32 j + l; padded entries have value 0
-// and a valid column).
-//
-// mode 1 (CG iteration): p_new = z + beta p_old for every element, q =
-// A p_new, and the dot p_new.q per (system, rhs).  A gathered entry
-// p_new[col] is recomputed from z and p_old with the same fused
-// multiply-add that produces the stored p_new[col], so q is exactly A times
-// the stored direction and no separate direction pass is needed.  p_old and
-// p_new are different buffers (successive iterations alternate them).
-// mode 0: q = A z (no direction, no dot, no solve state).
+// a1: SpMV q = A p and the dot p.q per (system, rhs) (SELL-32: slice s =
+// rows 32s..32s+31, entry j of lane l at sell_ptr[s] + 32 j + l; padded
+// entries have value 0 and a valid column).  One element (row, rhs) per
+// thread per step; the first JU entries of the row are loaded before any
+// product, so their loads and then their gathers are in flight together.
+// FP64 arithmetic is scarce on this GPU (about 1/64 of the FP32 rate), so
+// the direction update p = z + beta p_old runs as its own streaming pass
+// (k_dir_update) rather than being recomputed for every gathered entry.
+// with_dot = 0: plain product (no dot, no solve state).
 // ===========================================================================
-__device__ __forceinline__ double dir_entry(const double* __restrict__ z, const double* __restrict__ p_old,
-                                            int64_t i, double beta, bool dir) {
-    return dir ? fma(beta, __ldg(p_old + i), __ldg(z + i)) : __ldg(z + i);
-}
-
-template <int LD>
+template <int LD, int JU>
 __global__ void __launch_bounds__(kRedThreads)
-k_spmv_dir(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sell_col,
-           const double* __restrict__ sell_val, const double* __restrict__ z,
-           const double* __restrict__ p_old, double* __restrict__ p_new, double* __restrict__ q,
-           RedLayout R, CgScalars* sc, SolveState* st, int mode) {
+k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sell_col,
+           const double* __restrict__ sell_val, const double* __restrict__ p, double* __restrict__ q,
+           RedLayout R, CgScalars* sc, SolveState* st, int with_dot) {
     if (st != nullptr && st->done) return;
     __shared__ double s_out[kRedMaxNV * kMaxLd];
     __shared__ double s_scr[kRedThreads];
-    constexpr int RPT = kRedElems / kRedThreads;     // elements per thread
-    constexpr int JU = 8;                            // row entries loaded before the first product
-    const bool dir = mode == 1;
-    const int64_t base = (int64_t)blockIdx.x * kRedElems;
     const int rhs = threadIdx.x % LD;                // kRedThreads is a multiple of LD
-    double beta = 0.0;
-    if (dir) beta = sc[R.blk_seg[blockIdx.x] * LD + rhs].beta;
+    const int64_t lo = R.blk_lo[blockIdx.x], hi = R.blk_lo[blockIdx.x + 1];
     double dot[1] = {0.0};
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int64_t e = base + threadIdx.x + k * kRedThreads;
+    for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) {
         const int64_t row = e / LD;
-        const int64_t s = row >> 5;
+        const int64_t sl = row >> 5;
         const int lane = (int)(row & 31);
-        const int64_t b0 = __ldg(sell_ptr + s);
-        const int w = (int)((__ldg(sell_ptr + s + 1) - b0) >> 5);
+        const int64_t b0 = __ldg(sell_ptr + sl);
+        const int w = (int)((__ldg(sell_ptr + sl + 1) - b0) >> 5);
         int col[JU];
         double val[JU];
 #pragma unroll
@@ -71,23 +57,24 @@ k_spmv_dir(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
                 val[j] = __ldg(sell_val + b0 + 32 * j + lane);
             }
         }
+        double xv[JU];
+#pragma unroll
+        for (int j = 0; j < JU; ++j) {
+            xv[j] = 0.0;
+            if (j < w) xv[j] = __ldg(p + (int64_t)col[j] * LD + rhs);
+        }
         double acc = 0.0;
 #pragma unroll
         for (int j = 0; j < JU; ++j)
-            if (j < w) acc = fma(val[j], dir_entry(z, p_old, (int64_t)col[j] * LD + rhs, beta, dir), acc);
+            if (j < w) acc = fma(val[j], xv[j], acc);
         for (int j = JU; j < w; ++j) {
             const int64_t o = b0 + 32 * j + lane;
-            acc = fma(__ldg(sell_val + o), dir_entry(z, p_old, (int64_t)__ldg(sell_col + o) * LD + rhs, beta, dir),
-                      acc);
+            acc = fma(__ldg(sell_val + o), __ldg(p + (int64_t)__ldg(sell_col + o) * LD + rhs), acc);
         }
         q[e] = acc;
-        if (dir) {
-            const double pe = dir_entry(z, p_old, e, beta, true);
-            p_new[e] = pe;
-            dot[0] = fma(pe, acc, dot[0]);
-        }
+        if (with_dot) dot[0] = fma(__ldg(p + e), acc, dot[0]);
     }
-    if (!dir) return;
+    if (!with_dot) return;
     int seg;
     if (!seg_reduce<1>(dot, LD, R, s_out, s_scr, seg)) return;
     if (threadIdx.x < LD) {
@@ -98,6 +85,19 @@ k_spmv_dir(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
             st->done = 1;
         }
     }
+}
+
+// a7: p_new = z + beta p_old per (system, rhs); p_old and p_new are
+// different buffers (successive iterations alternate them)
+template <int LD>
+__global__ void __launch_bounds__(kRedThreads)
+k_dir_update(const double* __restrict__ z, const double* __restrict__ p_old, double* __restrict__ p_new,
+             RedLayout R, const CgScalars* sc, const SolveState* st) {
+    if (st->done) return;
+    const double beta = sc[R.blk_seg[blockIdx.x] * LD + threadIdx.x % LD].beta;
+    const int64_t lo = R.blk_lo[blockIdx.x], hi = R.blk_lo[blockIdx.x + 1];
+#pragma unroll 4
+    for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) p_new[e] = fma(beta, p_old[e], z[e]);
 }
 
 // ===========================================================================
@@ -569,7 +569,11 @@ k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
 }
 
 // ===========================================================================
-// a6 + a2: z = z_f + R_0^T e_c with the CG update and the dots.
+// a6 + a2: z = z_f + R_0^T e_c with the CG update and the dots.  A thread
+// block takes a range of consecutive subdomains of one system; per
+// subdomain its rows are contiguous, its basis rows are contiguous, and its
+// m coarse values are staged once in shared memory.
+// Padded rows belong to no subdomain: their z stays 0 and r, q, x are 0.
 //
 // mode 0: z only (a plain preconditioner application).
 // mode 1: first application of a solve: z and rho = r.z (beta = 0).
@@ -580,63 +584,83 @@ k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
 //         system applies the convergence test and sets beta: rho'/rho (PCG)
 //         or -(z.q)/(p.q) (flexible CG).
 // ===========================================================================
+// Basis row of `m` entries into registers; one 16-byte load per 16 bytes
+// when the row is 16-byte aligned and m == MM.
+template <typename TP, int MM>
+__device__ __forceinline__ void load_basis_row(const TP* __restrict__ pr, int m, bool vec, TP (&v)[MM]) {
+    constexpr int PER = 16 / sizeof(TP);
+    if (MM % PER == 0 && vec) {
+#pragma unroll
+        for (int k = 0; k < MM; k += PER) {
+            const uint4 u = __ldg(reinterpret_cast<const uint4*>(pr + k));
+            const TP* t = reinterpret_cast<const TP*>(&u);
+#pragma unroll
+            for (int i = 0; i < PER; ++i) v[k + i] = t[i];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < MM; ++k) v[k] = (k < m) ? pr[k] : TP(0.f);
+    }
+}
+
 template <typename TF, typename TP, int LD, int MM>
 __global__ void __launch_bounds__(kRedThreads)
-k_prolong_update(const int32_t* __restrict__ sub_of_row, const SubInfo* __restrict__ subs,
-                 const TP* __restrict__ psi, const TF* __restrict__ ec, const TF* __restrict__ zf,
-                 double* __restrict__ r, const double* __restrict__ q, double* __restrict__ x,
-                 const double* __restrict__ p, double* __restrict__ z, RedLayout R, CgScalars* sc,
-                 SolveState* st, int nseg, int flexible, int mode) {
+k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, const TF* __restrict__ ec,
+                 const TF* __restrict__ zf, double* __restrict__ r, const double* __restrict__ q,
+                 double* __restrict__ x, const double* __restrict__ p, double* __restrict__ z, RedLayout R,
+                 CgScalars* sc, SolveState* st, int nseg, int flexible, int mode) {
     if (st != nullptr && st->done) return;
     using AT = typename Acc<TF>::type;
     __shared__ double s_out[kRedMaxNV * kMaxLd];
     __shared__ double s_scr[kRedThreads];
-    constexpr int RPT = kRedElems / kRedThreads;
-    const int64_t base = (int64_t)blockIdx.x * kRedElems;
+    __shared__ AT s_ec[MM * LD];
     const int rhs = threadIdx.x % LD;
     double alpha = 0.0;
     bool upd = false;
     if (mode == 2) {
-        const CgScalars c = sc[R.blk_seg[blockIdx.x] * LD + rhs];
+        const CgScalars c = sc[(int64_t)R.blk_seg[blockIdx.x] * LD + rhs];
         upd = c.active != 0;
         if (upd) alpha = c.rho / c.pq;
     }
-    int sub[RPT];
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) sub[k] = __ldg(sub_of_row + (base + threadIdx.x + k * kRedThreads) / LD);
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-#pragma unroll
-    for (int k = 0; k < RPT; ++k) {
-        const int64_t e = base + threadIdx.x + k * kRedThreads;
-        double zv = 0.0;
-        if (sub[k] >= 0) {
-            const SubInfo* S = subs + sub[k];
-            const int64_t lr = e / LD - S->row0;
+    const int64_t s_lo = R.blk_lo[blockIdx.x], s_hi = R.blk_lo[blockIdx.x + 1];
+    for (int64_t si = s_lo; si < s_hi; ++si) {
+        const SubInfo S = subs[si];
+        const int m = S.m;
+        const bool coarse = ec != nullptr && m > 0;
+        __syncthreads();                 // s_ec of the previous subdomain is no longer read
+        if (coarse)
+            for (int i = threadIdx.x; i < MM * LD; i += kRedThreads)
+                s_ec[i] = (i < m * LD) ? (AT)ec[(int64_t)S.coff * LD + i] : AT(0);
+        __syncthreads();
+        const bool vec = (m == MM) && ((reinterpret_cast<uintptr_t>(psi + S.psi_off) & 15) == 0);
+        const int64_t ne = (int64_t)S.n * LD;
+        const int64_t g0 = S.row0 * LD;
+#pragma unroll 2
+        for (int64_t le = threadIdx.x; le < ne; le += kRedThreads) {
+            const int64_t e = g0 + le;
             AT acc = (AT)zf[e];
-            if (ec != nullptr) {
-                const int m = S->m;
-                const TP* pr = psi + S->psi_off + lr * m;
-                const TF* er = ec + (int64_t)S->coff * LD + rhs;
-                AT pe = AT(0);
+            AT pe = AT(0);
+            if (coarse) {
+                TP pv[MM];
+                load_basis_row<TP, MM>(psi + S.psi_off + (le / LD) * m, m, vec, pv);
 #pragma unroll
-                for (int kk = 0; kk < MM; ++kk)
-                    if (kk < m) pe += (AT)to_d(pr[kk]) * er[(int64_t)kk * LD];
-                zv = (double)acc + (double)pe;
-            } else {
-                zv = (double)acc;
+                for (int k = 0; k < MM; ++k) pe += (AT)to_d(pv[k]) * s_ec[k * LD + rhs];
             }
-        }
-        z[e] = zv;
-        if (mode != 0) {
-            double rv = r[e];
-            if (upd) {
-                rv = fma(-alpha, q[e], rv);
-                r[e] = rv;
-                x[e] = fma(alpha, p[e], x[e]);
+            const double zv = (double)(acc + pe);   // z in the apply precision, stored as FP64
+            z[e] = zv;
+            if (mode != 0) {
+                double rv = r[e];
+                const double qv = (upd || (flexible && mode == 2)) ? q[e] : 0.0;
+                if (upd) {
+                    rv = fma(-alpha, qv, rv);
+                    r[e] = rv;
+                    x[e] = fma(alpha, p[e], x[e]);
+                }
+                v[0] = fma(rv, zv, v[0]);
+                v[1] = fma(rv, rv, v[1]);
+                if (flexible && mode == 2) v[2] = fma(zv, qv, v[2]);
             }
-            v[0] = fma(rv, zv, v[0]);
-            v[1] = fma(rv, rv, v[1]);
-            if (flexible && mode == 2) v[2] = fma(zv, q[e], v[2]);
         }
     }
     if (mode == 0) return;
@@ -696,12 +720,9 @@ k_init_norms(const double* __restrict__ r, RedLayout R, CgScalars* sc, SolveStat
              int nrhs) {
     __shared__ double s_out[kRedMaxNV * kMaxLd];
     __shared__ double s_scr[kRedThreads];
-    const int64_t base = (int64_t)blockIdx.x * kRedElems;
     double v[1] = {0.0};
-    for (int k = 0; k < kRedElems / kRedThreads; ++k) {
-        const int64_t e = base + threadIdx.x + k * kRedThreads;
-        v[0] += r[e] * r[e];
-    }
+    for (int64_t e = R.blk_lo[blockIdx.x] + threadIdx.x; e < R.blk_lo[blockIdx.x + 1]; e += kRedThreads)
+        v[0] = fma(r[e], r[e], v[0]);
     int sg;
     if (!seg_reduce<1>(v, LD, R, s_out, s_scr, sg)) return;
     if (threadIdx.x < LD) {
@@ -789,13 +810,20 @@ __global__ void k_zero(double* __restrict__ a, int64_t n) {
     }
 
 template <int LD>
-static void spmv_ld(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* q, int mode) {
-    k_spmv_dir<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(L.sell_ptr, L.sell_col, L.sell_val, z, p_old, p_new, q,
-                                                         L.red, L.sc, mode ? L.st : nullptr, mode);
+static void spmv_ld(const LaunchCtx& L, const double* p, double* q, int with_dot) {
+    k_spmv_dot<LD, 8><<<L.nblk, kRedThreads, 0, L.stream>>>(L.sell_ptr, L.sell_col, L.sell_val, p, q, L.red, L.sc,
+                                                            with_dot ? L.st : nullptr, with_dot);
 }
-void launch_spmv_dir(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* q,
-                     int mode) {
-    AMS_DISPATCH_LD(L.ld, spmv_ld, L, z, p_old, p_new, q, mode);
+void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_dot) {
+    AMS_DISPATCH_LD(L.ld, spmv_ld, L, p, q, with_dot);
+}
+
+template <int LD>
+static void dir_ld(const LaunchCtx& L, const double* z, const double* p_old, double* p_new) {
+    k_dir_update<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(z, p_old, p_new, L.red, L.sc, L.st);
+}
+void launch_dir_update(const LaunchCtx& L, const double* z, const double* p_old, double* p_new) {
+    AMS_DISPATCH_LD(L.ld, dir_ld, L, z, p_old, p_new);
 }
 
 template <int LD>
@@ -895,14 +923,15 @@ void launch_coarse_gemm(const CoarseLaunch& c, int prec, int ld, const void* in,
 
 template <typename TF, typename TP, int LD>
 static void prolong_ld(const LaunchCtx& L, const ProlongArgs& a) {
+    if (L.nsub == 0) return;
     if (a.mmax > 8)
-        k_prolong_update<TF, TP, LD, kMaxM><<<L.nblk, kRedThreads, 0, L.stream>>>(
-            L.sub_of_row, L.subs, (const TP*)a.psi, (const TF*)a.ec, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z,
-            L.red, L.sc, L.st, L.nseg, a.flexible, a.mode);
+        k_prolong_update<TF, TP, LD, kMaxM><<<L.nblk_sub, kRedThreads, 0, L.stream>>>(
+            L.subs, (const TP*)a.psi, (const TF*)a.ec, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z, L.red_sub, L.sc,
+            L.st, L.nseg, a.flexible, a.mode);
     else
-        k_prolong_update<TF, TP, LD, 8><<<L.nblk, kRedThreads, 0, L.stream>>>(
-            L.sub_of_row, L.subs, (const TP*)a.psi, (const TF*)a.ec, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z,
-            L.red, L.sc, L.st, L.nseg, a.flexible, a.mode);
+        k_prolong_update<TF, TP, LD, 8><<<L.nblk_sub, kRedThreads, 0, L.stream>>>(
+            L.subs, (const TP*)a.psi, (const TF*)a.ec, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z, L.red_sub, L.sc,
+            L.st, L.nseg, a.flexible, a.mode);
 }
 template <typename TF, typename TP>
 static void prolong_tp(const LaunchCtx& L, const ProlongArgs& a) {

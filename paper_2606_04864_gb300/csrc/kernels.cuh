@@ -63,9 +63,10 @@ __device__ __forceinline__ void block_copy_async(void* smem, const void* gmem, i
 // ---------------------------------------------------------------------------
 // Deterministic segmented reduction.
 //
-// A "reduction block" covers kRedElems consecutive elements of a node-major
-// vector (rows of a single system, since systems are padded to kRowAlign
-// rows).  Each thread block of a reduction kernel handles one reduction
+// A "reduction block" covers a contiguous range of elements of a node-major
+// vector (whole kRedElems-element chunks of a single system, since systems
+// are padded to kRowAlign rows), or a contiguous range of subdomains of a
+// single system; a system's blocks are consecutive.  Each thread block of a reduction kernel handles one reduction
 // block and produces NV partial values per right-hand side.  Partials are
 // summed in a fixed order in two levels: groups of kRedGroup blocks (the
 // last block of a group to finish sums the group), then all groups of a
@@ -74,6 +75,7 @@ __device__ __forceinline__ void block_copy_async(void* smem, const void* gmem, i
 // reproducible.
 // ---------------------------------------------------------------------------
 struct RedLayout {
+    const int64_t* blk_lo;     // block b covers [blk_lo[b], blk_lo[b+1]) (elements or subdomains)
     const int32_t* blk_seg;    // reduction block -> system
     const int32_t* seg_blk0;   // system -> first reduction block
     const int32_t* seg_nblk;   // system -> number of reduction blocks

@@ -13,9 +13,12 @@ namespace ams {
 struct LaunchCtx {
     cudaStream_t stream;
     int ld;                  // right-hand-side stride (power of two)
-    int64_t nblk;            // reduction blocks (n_pad * ld / kRedElems)
+    int64_t nblk;            // blocks of red
     int nseg;                // systems
-    RedLayout red;
+    RedLayout red;           // element blocks
+    RedLayout red_sub;       // blocks of consecutive subdomains
+    int64_t nblk_sub;        // blocks of red_sub
+    int nsub;                // subdomains
     CgScalars* sc;           // [nseg][ld]
     SolveState* st;
     const int64_t* sell_ptr;
@@ -74,9 +77,10 @@ struct CoarseLaunch {
     const SolveState* st;
 };
 
-// mode 1: p_new = z + beta p_old, q = A p_new, p_new.q; mode 0: q = A z
-void launch_spmv_dir(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* q,
-                     int mode);
+// q = A p, and p.q per (system, rhs) when with_dot
+void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_dot);
+// p_new = z + beta p_old (per system and right-hand side)
+void launch_dir_update(const LaunchCtx& L, const double* z, const double* p_old, double* p_new);
 void launch_init_norms(const LaunchCtx& L, const double* r, int nrhs);
 size_t local_solve_smem(int cmax, int ld, size_t tf_bytes, int depth);
 int local_solve_depth(int cmax, int ld, size_t tf_bytes);
