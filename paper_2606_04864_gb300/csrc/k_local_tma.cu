@@ -439,7 +439,36 @@ __device__ __forceinline__ void col_chunks(const float* T, const int (&csw)[8], 
     }
 }
 
+// Basis row of one subdomain row (m <= MM entries) as raw 16-byte words when
+// the row is 16-byte aligned and m == MM, element by element otherwise.
 template <typename TP, int MM>
+struct BasisRow {
+    static constexpr int PER = 16 / (int)sizeof(TP);
+    static constexpr int NW = (MM * (int)sizeof(TP) + 15) / 16;
+    uint4 w[NW];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int i = 0; i < NW; ++i) w[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __device__ __forceinline__ void load(const TP* __restrict__ pr, int m, bool vec) {
+        if (MM % PER == 0 && vec) {
+#pragma unroll
+            for (int i = 0; i < NW; ++i) w[i] = __ldg(reinterpret_cast<const uint4*>(pr) + i);
+        } else {
+            TP* e = reinterpret_cast<TP*>(w);
+#pragma unroll
+            for (int k = 0; k < MM; ++k)
+                if (k < m) e[k] = pr[k];
+        }
+    }
+    __device__ __forceinline__ float get(int k) const { return to_f(reinterpret_cast<const TP*>(w)[k]); }
+};
+
+// C1: every subdomain has c == 1 (one 32x32 tile per block row).  The
+// backward sweep then keeps column `lane` of M_K in registers after step K
+// and forms the step K-1 term sum_{r <= lane} M_K[r][lane] x_K[r] at once,
+// so every tile column is read from shared memory once.
+template <typename TP, int MM, bool C1>
 __global__ void __launch_bounds__(32, 8)
 k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict__ subs,
              const int64_t* __restrict__ tile_row0, const float* __restrict__ piv,
@@ -450,7 +479,8 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_align1024(smem_raw);
     const SubInfo S = subs[blockIdx.x];
-    const int c = S.c, nb = S.nb, n = S.n, m = S.m;
+    const int c = C1 ? 1 : S.c;
+    const int nb = S.nb, n = S.n, m = S.m;
     const int D = depth;
     const int nbuf = cmax + D + 1;
     float* tiles = (float*)base;                                        // nbuf * cmax * 1024
@@ -461,7 +491,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     const int jr = lane >> 2, er = lane & 3;
     const int64_t trow = tile_row0[blockIdx.x];
     const uint32_t tile_bytes = 4096u * (uint32_t)c;
-    const size_t slot_floats = (size_t)cmax * 1024;
+    const int slot_floats = cmax * 1024;
     uint32_t phase = 0, pend = 0;   // parity per slot; slots with a copy in flight
     bool ok = true;
 
@@ -492,8 +522,10 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     }
     __syncwarp();
 
-    auto issue = [&](int K) {
-        const int slot = K % nbuf;
+    // ring slots are tracked incrementally (no division in the step loop)
+    auto wrap_up = [&](int sl) { return sl >= nbuf ? sl - nbuf : sl; };
+    auto wrap_dn = [&](int sl) { return sl < 0 ? sl + nbuf : sl; };
+    auto issue = [&](int K, int slot) {
         if (lane == 0) {
             const uint32_t bar = smem_u32(bars + slot);
             mbar_expect_tx(bar, tile_bytes);
@@ -503,21 +535,16 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
         }
         pend |= 1u << slot;
     };
-    auto wait_slot = [&](int K) {
-        const int slot = K % nbuf;
+    auto wait_slot = [&](int slot) {
         if (!mbar_wait(smem_u32(bars + slot), (phase >> slot) & 1u, budget)) ok = false;
         phase ^= 1u << slot;
         pend &= ~(1u << slot);
     };
-    auto row_tiles = [&](int K) -> const float* { return tiles + (K % nbuf) * slot_floats; };
 
     float racc[MM];
 #pragma unroll
     for (int k = 0; k < MM; ++k) racc[k] = 0.f;
 
-    // Per-row inputs of block row K+PF are loaded while step K runs.  They
-    // stay in the loaded type until the step that uses them: a conversion
-    // or a select right after the load would wait for it there.
     // r' = r - alpha q when this subdomain's system is still iterating
     double alpha = 0.0;
     bool upd = false;
@@ -526,62 +553,67 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
         upd = cs.active != 0;
         if (upd) alpha = cs.rho / cs.pq;
     }
+    // Per-row inputs of block row K+PF are loaded while step K runs.  They
+    // stay in the loaded type until the step that uses them: a conversion
+    // or a select right after the load would wait for it there.
     constexpr int PF = 4;
+    const double* rp = rin + S.row0 + lane;
+    const double* qp = upd ? qin + S.row0 + lane : nullptr;
+    const float* vp = piv + S.row0 + lane;
+    const bool vec = (m == MM) && ((reinterpret_cast<uintptr_t>(psi + S.psi_off) & 15) == 0);
+    const TP* pp = rc != nullptr ? psi + S.psi_off + (int64_t)lane * m : nullptr;
     double bt[PF], bq[PF];
-    TP bp[PF][MM];
+    BasisRow<TP, MM> bp[PF];
     float bv[PF];
-    auto load_fwd = [&](int K, double& tv, double& qv, TP (&pv)[MM], float& pvt) {
+    auto load_fwd = [&](int K, double& tv, double& qv, BasisRow<TP, MM>& pv, float& pvt) {
         const int row = K * 32 + lane;
-        const bool valid = K < nb && row < n;
-        const int64_t grow = S.row0 + row;
         tv = 0.0;
         qv = 0.0;
         pvt = 1.f;
-#pragma unroll
-        for (int k = 0; k < MM; ++k) pv[k] = TP(0.f);
-        if (valid) {
-            tv = rin[grow];
-            if (upd) qv = qin[grow];
-            pvt = piv[grow];
-            if (rc != nullptr) {
-#pragma unroll
-                for (int k = 0; k < MM; ++k)
-                    if (k < m) pv[k] = psi[S.psi_off + (int64_t)row * m + k];
-            }
+        pv.clear();
+        if (K < nb && row < n) {
+            tv = rp[K * 32];
+            if (upd) qv = qp[K * 32];
+            pvt = vp[K * 32];
+            if (rc != nullptr) pv.load(pp + (int64_t)K * 32 * m, m, vec);
         }
     };
 #pragma unroll
     for (int u = 0; u < PF; ++u) load_fwd(u, bt[u], bq[u], bp[u], bv[u]);
 
-    auto fwd_step = [&](int K, double& tb, double& qb, TP (&pb)[MM], float& vb) {
-        if (K + D < nb) issue(K + D);
+    int sK = 0;   // slot of block row K
+    auto fwd_step = [&](int K, double& tb, double& qb, BasisRow<TP, MM>& pb, float& vb) {
+        if (K + D < nb) issue(K + D, wrap_up(sK + D));
         float t = (float)(upd ? fma(-alpha, qb, tb) : tb);
         const float pvt = vb;
         if (rc != nullptr) {
 #pragma unroll
-            for (int k = 0; k < MM; ++k) racc[k] = fmaf(to_f(pb[k]), t, racc[k]);
+            for (int k = 0; k < MM; ++k) racc[k] = fmaf(pb.get(k), t, racc[k]);
         }
         load_fwd(K + PF, tb, qb, pb, vb);
-        wait_slot(K);
+        wait_slot(sK);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) return;
-        const float* T = row_tiles(K);
+        const float* T = tiles + sK * slot_floats;
         float4 mr[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) mr[j] = *reinterpret_cast<const float4*>(T + rsw[j]);
         const float4 md = *reinterpret_cast<const float4*>(T + dsw);
         // t = r_K - sum_d L_{K,K-c+d} y_{K-c+d}
+        if (!C1) {
 #pragma unroll 1
-        for (int d = 1; d < c; ++d) {
-            const int src = K - c + d;
-            if (src < 0) continue;
-            const float* Td = T + d * 1024;
-            const float* v = yv + src * 32;
-            float cj[8];
+            for (int d = 1; d < c; ++d) {
+                const int src = K - c + d;
+                if (src < 0) continue;
+                const float* Td = T + d * 1024;
+                const float* v = yv + src * 32;
+                float cj[8];
 #pragma unroll
-            for (int j = 0; j < 8; ++j)
-                cj[j] = dot4(*reinterpret_cast<const float4*>(Td + rsw[j]), *reinterpret_cast<const float4*>(v + 4 * j));
-            t -= sum8(cj);
+                for (int j = 0; j < 8; ++j)
+                    cj[j] = dot4(*reinterpret_cast<const float4*>(Td + rsw[j]),
+                                 *reinterpret_cast<const float4*>(v + 4 * j));
+                t -= sum8(cj);
+            }
         }
         if (K >= c) {   // upper part of M_K (q >= lane) is L_{K,K-c}
             const float* v = yv + (K - c) * 32;
@@ -601,11 +633,12 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
             y = fmaf(pvt, t, wsum8(flo, cj) + dot4(mul4(md, dlt), *reinterpret_cast<const float4*>(tmp + 4 * jr)));
         }
         yv[K * 32 + lane] = y;
+        sK = wrap_up(sK + 1);
         __syncwarp();
     };
 
     // ---------------- forward ----------------
-    for (int j = 0; j < D && j < nb; ++j) issue(j);
+    for (int j = 0; j < D && j < nb; ++j) issue(j, j);
 #pragma unroll 1
     for (int K0 = 0; K0 < nb && ok; K0 += PF) {
 #pragma unroll
@@ -628,48 +661,73 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     auto load_bwd = [&](int K, float& pvt) {
         const int row = K * 32 + lane;
         pvt = 1.f;
-        if (K >= 0 && row < n) pvt = piv[S.row0 + row];
+        if (K >= 0 && row < n) pvt = vp[K * 32];
     };
+    float ucarry = 0.f;   // C1: sum_{r <= lane} M_{K+1}[r][lane] x_{K+1}[r] for the next step
+    sK = (nb - 1) % nbuf;
     auto bwd_step = [&](int K, float& vb) {
-        if (K - D >= 0 && K - D < Rres) issue(K - D);
+        if (K - D >= 0 && K - D < Rres) issue(K - D, wrap_dn(sK - D));
         const float pvt = vb;
         load_bwd(K - PF, vb);
-        if (K < Rres) wait_slot(K);
+        if (K < Rres) wait_slot(sK);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) return;
         float w = yv[K * 32 + lane];
-        // w = y_K - sum_d L_{K+d,K}^T x_{K+d}
+        const float* Tm = tiles + sK * slot_floats;   // M_K
+        if (C1) {
+            w -= ucarry;
+        } else {
+            // w = y_K - sum_d L_{K+d,K}^T x_{K+d}
 #pragma unroll 1
-        for (int d = 1; d < c; ++d) {
-            const int src = K + d;
-            if (src >= nb) break;
-            float cj[8];
-            col_chunks(row_tiles(src) + (c - d) * 1024, csw, yv + src * 32, cj);
-            w -= sum8(cj);
-        }
-        if (K + c < nb) {   // L_{K+c,K}: upper part of M_{K+c}, rows r <= lane of column lane
-            const float* Tm = row_tiles(K + c);
-            const float* v = yv + (K + c) * 32;
-            float cj[8];
-            col_chunks(Tm, csw, v, cj);
-            const float4 ad = make_float4(Tm[cdo[0]], Tm[cdo[1]], Tm[cdo[2]], Tm[cdo[3]]);
-            w -= wsum8(flo, cj) + dot4(mul4(ad, dle), *reinterpret_cast<const float4*>(v + 4 * jr));
+            for (int d = 1; d < c; ++d) {
+                const int src = K + d;
+                if (src >= nb) break;
+                float cj[8];
+                col_chunks(tiles + wrap_up(sK + d) * slot_floats + (c - d) * 1024, csw, yv + src * 32, cj);
+                w -= sum8(cj);
+            }
+            if (K + c < nb) {   // L_{K+c,K}: upper part of M_{K+c}, rows r <= lane of column lane
+                const float* Tc = tiles + wrap_up(sK + c) * slot_floats;
+                const float* v = yv + (K + c) * 32;
+                float cj[8];
+                col_chunks(Tc, csw, v, cj);
+                const float4 ad = make_float4(Tc[cdo[0]], Tc[cdo[1]], Tc[cdo[2]], Tc[cdo[3]]);
+                w -= wsum8(flo, cj) + dot4(mul4(ad, dle), *reinterpret_cast<const float4*>(v + 4 * jr));
+            }
         }
         tmp[lane] = w;
         __syncwarp();
         // x_K = L_KK^{-T} w: rows r > lane of column lane of M_K
+        float a[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) a[r] = Tm[r * 32 + csw[r & 7]];
+        const float4 ad = make_float4(Tm[cdo[0]], Tm[cdo[1]], Tm[cdo[2]], Tm[cdo[3]]);
         float x;
         {
-            const float* Tm = row_tiles(K);
             float cj[8];
-            col_chunks(Tm, csw, tmp, cj);
-            const float4 ad = make_float4(Tm[cdo[0]], Tm[cdo[1]], Tm[cdo[2]], Tm[cdo[3]]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float4 v = *reinterpret_cast<const float4*>(tmp + 4 * j);
+                cj[j] = fmaf(a[4 * j + 3], v.w, fmaf(a[4 * j + 2], v.z, fmaf(a[4 * j + 1], v.y, a[4 * j] * v.x)));
+            }
             x = fmaf(pvt, w, wsum8(fhi, cj) + dot4(mul4(ad, dgt), *reinterpret_cast<const float4*>(tmp + 4 * jr)));
         }
         yv[K * 32 + lane] = x;
         const int row = K * 32 + lane;
         if (row < n) zf[S.row0 + row] = x;
         __syncwarp();
+        if (C1 && K > 0) {
+            // term of step K-1: L_{K,K-1} is the upper part of M_K (rows r <= lane of column lane)
+            const float* v = yv + K * 32;
+            float cj[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float4 xv = *reinterpret_cast<const float4*>(v + 4 * j);
+                cj[j] = fmaf(a[4 * j + 3], xv.w, fmaf(a[4 * j + 2], xv.z, fmaf(a[4 * j + 1], xv.y, a[4 * j] * xv.x)));
+            }
+            ucarry = wsum8(flo, cj) + dot4(mul4(ad, dle), *reinterpret_cast<const float4*>(v + 4 * jr));
+        }
+        sK = wrap_dn(sK - 1);
     };
     if (ok) {
 #pragma unroll
@@ -764,11 +822,11 @@ static int local_tma1_depth(int cmax, int nbmax) {
     return d;
 }
 
-template <typename TP, int MM>
+template <typename TP, int MM, bool C1>
 static cudaError_t tma1(const LocalTmaArgs& a, const void* psi, void* zf, void* rc) {
     const int depth = local_tma1_depth(a.cmax, a.nbmax);
     const size_t smem = local_tma1_smem(a.cmax, a.nbmax, depth);
-    auto kern = k_local_tma1<TP, MM>;
+    auto kern = k_local_tma1<TP, MM, C1>;
     static size_t smem_set = 0;
     if (smem > smem_set) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -788,9 +846,14 @@ static bool use_tma1(const LocalTmaArgs& a) {
 
 cudaError_t launch_local_tma(const LocalTmaArgs& a, int prec, const void* psi, void* zf, void* rc) {
     if (use_tma1(a)) {
-        const bool big = a.mmax > 8;
-        if (prec == AMS_PREC_FP32) return big ? tma1<float, 16>(a, psi, zf, rc) : tma1<float, 8>(a, psi, zf, rc);
-        return big ? tma1<__nv_bfloat16, 16>(a, psi, zf, rc) : tma1<__nv_bfloat16, 8>(a, psi, zf, rc);
+        const bool big = a.mmax > 8, c1 = a.cmax == 1;
+        if (prec == AMS_PREC_FP32) {
+            if (big) return c1 ? tma1<float, 16, true>(a, psi, zf, rc) : tma1<float, 16, false>(a, psi, zf, rc);
+            return c1 ? tma1<float, 8, true>(a, psi, zf, rc) : tma1<float, 8, false>(a, psi, zf, rc);
+        }
+        if (big)
+            return c1 ? tma1<__nv_bfloat16, 16, true>(a, psi, zf, rc) : tma1<__nv_bfloat16, 16, false>(a, psi, zf, rc);
+        return c1 ? tma1<__nv_bfloat16, 8, true>(a, psi, zf, rc) : tma1<__nv_bfloat16, 8, false>(a, psi, zf, rc);
     }
     if (prec == AMS_PREC_FP32) return tma_tp<float>(a, psi, zf, rc);
     return tma_tp<__nv_bfloat16>(a, psi, zf, rc);
