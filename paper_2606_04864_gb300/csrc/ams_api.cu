@@ -105,6 +105,7 @@ struct ams_handle_s {
     int64_t Nc = 0;
     int cmax = 1, mmax = 0, nbmax = 1;
     int num_sms = 1;                    // SMs of the handle's device
+    bool use_pdl = false;               // solve-loop kernels overlap their prologue with the previous kernel
     std::vector<SubInfo> h_subs;
     std::vector<double> h_lam;          // kept eigenvalues, subdomain-major
     std::vector<DevBuf> bufs;
@@ -336,6 +337,7 @@ static LaunchCtx make_ctx(ams_handle h, const RedCache& rc, const RedCache& rcs)
     L.sell_val = h->d_sell_val;
     L.sub_of_row = h->d_sub_of_row;
     L.subs = h->d_subs;
+    L.pdl = h->use_pdl;
     return L;
 }
 
@@ -504,7 +506,7 @@ static ams_status setup_eigen(ams_handle h, const int64_t* d_rowptr, const int32
     }
     SubInfo* d_esubs = nullptr;
     AMS_TRY(upload(h, &d_esubs, esubs));
-    LocalSolveArgs la{h->stream, h->N, d_esubs, ResidIn{d_X, nullptr, nullptr}, d_S, P, h->cmax, 0, nullptr};
+    LocalSolveArgs la{h->stream, h->N, d_esubs, ResidIn{d_X, nullptr, nullptr}, d_S, P, h->cmax, 0, nullptr, false};
     const int maxit = h->opt.eig_maxit > 0 ? h->opt.eig_maxit : 300;
     const double tol = h->opt.eig_tol > 0 ? h->opt.eig_tol : 1e-13;
     std::vector<double> res(h->N);
@@ -1136,11 +1138,12 @@ static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool wit
     const bool coarse = h->Nc > 0;
     if (h->use_tma) {
         LocalTmaArgs a{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, in, ld, h->cmax,
-                       std::max(1, h->mmax), h->nbmax, int64_t(1) << 20, with_state ? h->d_st : nullptr};
+                       std::max(1, h->mmax), h->nbmax, int64_t(1) << 20, with_state ? h->d_st : nullptr,
+                       h->use_pdl};
         AMS_CUDA_TRY(launch_local_tma(a, h->prec, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
     } else {
         LocalSolveArgs la{h->stream, h->N, h->d_subs, in, nullptr, ld, h->cmax, std::max(1, h->mmax),
-                          with_state ? h->d_st : nullptr};
+                          with_state ? h->d_st : nullptr, h->use_pdl};
         AMS_CUDA_TRY(launch_local_solve(la, h->prec, h->d_fac, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
     }
     return AMS_OK;
@@ -1149,11 +1152,11 @@ static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool wit
 static void launch_coarse(ams_handle h, int ld, bool fwd, bool with_state) {
     if (fwd) {
         CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_partial, h->d_cnt,
-                        with_state ? h->d_st : nullptr};
+                        with_state ? h->d_st : nullptr, h->use_pdl};
         launch_coarse_gemm(cf, h->prec, ld, h->d_rc, h->d_yc);
     } else {
         CoarseLaunch cb{h->stream, h->nbwd, h->d_bwd, h->d_Qmat, h->d_rng, h->d_partial, h->d_cnt,
-                        with_state ? h->d_st : nullptr};
+                        with_state ? h->d_st : nullptr, h->use_pdl};
         launch_coarse_gemm(cb, h->prec, ld, h->d_yc, h->d_ec);
     }
 }

@@ -145,6 +145,7 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
             const float* __restrict__ piv, const double* __restrict__ rin, const double* __restrict__ qin,
             const CgScalars* __restrict__ csc, float* __restrict__ zf, const TP* __restrict__ psi,
             float* __restrict__ rc, int ld, int cmax, int depth, int64_t budget, SolveState* st) {
+    pdl_wait();
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned tile ring, then mbarriers, y/x ring, scratch
@@ -313,6 +314,7 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
                 if (lane == 0 && k < m) rc[(S.coff + k) * ld + rhs0 + j] = v;
             }
     }
+    pdl_trigger();
     // ---------------- backward ----------------
     float bw[PF][NR];
     auto load_bwd = [&](int K, float (&wv)[NR], float& pvt) {
@@ -475,7 +477,6 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
              const double* __restrict__ rin, const double* __restrict__ qin,
              const CgScalars* __restrict__ csc, float* __restrict__ zf, const TP* __restrict__ psi,
              float* __restrict__ rc, int cmax, int nbmax, int depth, int64_t budget, SolveState* st) {
-    if (st != nullptr && st->done) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_align1024(smem_raw);
     const SubInfo S = subs[blockIdx.x];
@@ -545,6 +546,38 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
 #pragma unroll
     for (int k = 0; k < MM; ++k) racc[k] = 0.f;
 
+    // Per-row inputs of block row K+PF are loaded while step K runs.  They
+    // stay in the loaded type until the step that uses them: a conversion
+    // or a select right after the load would wait for it there.  Basis rows
+    // and pivots are setup data; r and q are written by the previous
+    // kernels and are read only after pdl_wait().
+    constexpr int PF = 4;
+    const float* vp = piv + S.row0 + lane;
+    const bool vec = (m == MM) && ((reinterpret_cast<uintptr_t>(psi + S.psi_off) & 15) == 0);
+    const TP* pp = rc != nullptr ? psi + S.psi_off + (int64_t)lane * m : nullptr;
+    double bt[PF], bq[PF];
+    BasisRow<TP, MM> bp[PF];
+    float bv[PF];
+    auto load_static = [&](int K, BasisRow<TP, MM>& pv, float& pvt) {
+        const int row = K * 32 + lane;
+        pvt = 1.f;
+        pv.clear();
+        if (K < nb && row < n) {
+            pvt = vp[K * 32];
+            if (rc != nullptr) pv.load(pp + (int64_t)K * 32 * m, m, vec);
+        }
+    };
+    // first block rows of the factor and their setup inputs, ahead of the wait
+    for (int j = 0; j < D && j < nb; ++j) issue(j, j);
+#pragma unroll
+    for (int u = 0; u < PF; ++u) load_static(u, bp[u], bv[u]);
+    pdl_wait();
+    if (st != nullptr && st->done) ok = false;
+    if (!ok) {
+        for (int i = 0; i < nbuf; ++i)
+            if ((pend >> i) & 1u) mbar_wait(smem_u32(bars + i), (phase >> i) & 1u, budget);
+        return;
+    }
     // r' = r - alpha q when this subdomain's system is still iterating
     double alpha = 0.0;
     bool upd = false;
@@ -553,33 +586,19 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
         upd = cs.active != 0;
         if (upd) alpha = cs.rho / cs.pq;
     }
-    // Per-row inputs of block row K+PF are loaded while step K runs.  They
-    // stay in the loaded type until the step that uses them: a conversion
-    // or a select right after the load would wait for it there.
-    constexpr int PF = 4;
     const double* rp = rin + S.row0 + lane;
     const double* qp = upd ? qin + S.row0 + lane : nullptr;
-    const float* vp = piv + S.row0 + lane;
-    const bool vec = (m == MM) && ((reinterpret_cast<uintptr_t>(psi + S.psi_off) & 15) == 0);
-    const TP* pp = rc != nullptr ? psi + S.psi_off + (int64_t)lane * m : nullptr;
-    double bt[PF], bq[PF];
-    BasisRow<TP, MM> bp[PF];
-    float bv[PF];
-    auto load_fwd = [&](int K, double& tv, double& qv, BasisRow<TP, MM>& pv, float& pvt) {
+    auto load_dyn = [&](int K, double& tv, double& qv) {
         const int row = K * 32 + lane;
         tv = 0.0;
         qv = 0.0;
-        pvt = 1.f;
-        pv.clear();
         if (K < nb && row < n) {
             tv = rp[K * 32];
             if (upd) qv = qp[K * 32];
-            pvt = vp[K * 32];
-            if (rc != nullptr) pv.load(pp + (int64_t)K * 32 * m, m, vec);
         }
     };
 #pragma unroll
-    for (int u = 0; u < PF; ++u) load_fwd(u, bt[u], bq[u], bp[u], bv[u]);
+    for (int u = 0; u < PF; ++u) load_dyn(u, bt[u], bq[u]);
 
     int sK = 0;   // slot of block row K
     auto fwd_step = [&](int K, double& tb, double& qb, BasisRow<TP, MM>& pb, float& vb) {
@@ -590,7 +609,8 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
 #pragma unroll
             for (int k = 0; k < MM; ++k) racc[k] = fmaf(pb.get(k), t, racc[k]);
         }
-        load_fwd(K + PF, tb, qb, pb, vb);
+        load_static(K + PF, pb, vb);
+        load_dyn(K + PF, tb, qb);
         wait_slot(sK);
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) return;
@@ -638,13 +658,13 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     };
 
     // ---------------- forward ----------------
-    for (int j = 0; j < D && j < nb; ++j) issue(j, j);
 #pragma unroll 1
     for (int K0 = 0; K0 < nb && ok; K0 += PF) {
 #pragma unroll
         for (int u = 0; u < PF; ++u)
             if (K0 + u < nb && ok) fwd_step(K0 + u, bt[u], bq[u], bp[u], bv[u]);
     }
+    pdl_trigger();
     if (rc != nullptr && ok) {
 #pragma unroll
         for (int k = 0; k < MM; ++k) {
@@ -782,10 +802,9 @@ static cudaError_t tma_nr(const LocalTmaArgs& a, const void* psi, void* zf, void
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    kern<<<a.nsub, warps * 32, smem, a.stream>>>(*a.tmF, *a.tmB, a.subs, a.tile_row0, a.piv, a.in.r, a.in.q, a.in.sc,
-                                                  (float*)zf, (const TP*)psi, (float*)rc, a.ld, a.cmax, depth,
-                                                  a.budget, a.st);
-    return cudaGetLastError();
+    return launch_kernel(a.pdl, kern, dim3(a.nsub), dim3(warps * 32), smem, a.stream, *a.tmF, *a.tmB, a.subs,
+                         a.tile_row0, a.piv, a.in.r, a.in.q, a.in.sc, (float*)zf, (const TP*)psi, (float*)rc, a.ld,
+                         a.cmax, depth, a.budget, a.st);
 }
 
 template <typename TP>
@@ -833,9 +852,9 @@ static cudaError_t tma1(const LocalTmaArgs& a, const void* psi, void* zf, void* 
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    kern<<<a.nsub, 32, smem, a.stream>>>(*a.tmF, a.subs, a.tile_row0, a.piv, a.in.r, a.in.q, a.in.sc, (float*)zf,
-                                         (const TP*)psi, (float*)rc, a.cmax, a.nbmax, depth, a.budget, a.st);
-    return cudaGetLastError();
+    return launch_kernel(a.pdl, kern, dim3(a.nsub), dim3(32), smem, a.stream, *a.tmF, a.subs, a.tile_row0, a.piv,
+                         a.in.r, a.in.q, a.in.sc, (float*)zf, (const TP*)psi, (float*)rc, a.cmax, a.nbmax, depth,
+                         a.budget, a.st);
 }
 
 // The one-right-hand-side kernel keeps y for a whole subdomain in shared

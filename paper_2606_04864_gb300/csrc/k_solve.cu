@@ -34,20 +34,21 @@ __global__ void __launch_bounds__(kRedThreads)
 k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sell_col,
            const double* __restrict__ sell_val, const double* __restrict__ p, double* __restrict__ q,
            RedLayout R, CgScalars* sc, SolveState* st, int with_dot) {
-    if (st != nullptr && st->done) return;
     __shared__ double s_out[kRedMaxNV * kMaxLd];
     __shared__ double s_scr[kRedThreads];
     const int rhs = threadIdx.x % LD;                // kRedThreads is a multiple of LD
     const int64_t lo = R.blk_lo[blockIdx.x], hi = R.blk_lo[blockIdx.x + 1];
-    double dot[1] = {0.0};
-    for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) {
+    int64_t b0 = 0;
+    int w = 0, lane = 0;
+    int col[JU];
+    double val[JU];
+    // matrix entries of one element (setup data: may be read before pdl_wait)
+    auto load_row = [&](int64_t e) {
         const int64_t row = e / LD;
         const int64_t sl = row >> 5;
-        const int lane = (int)(row & 31);
-        const int64_t b0 = __ldg(sell_ptr + sl);
-        const int w = (int)((__ldg(sell_ptr + sl + 1) - b0) >> 5);
-        int col[JU];
-        double val[JU];
+        lane = (int)(row & 31);
+        b0 = __ldg(sell_ptr + sl);
+        w = (int)((__ldg(sell_ptr + sl + 1) - b0) >> 5);
 #pragma unroll
         for (int j = 0; j < JU; ++j) {
             col[j] = 0;
@@ -57,6 +58,13 @@ k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
                 val[j] = __ldg(sell_val + b0 + 32 * j + lane);
             }
         }
+    };
+    int64_t e = lo + threadIdx.x;
+    if (e < hi) load_row(e);
+    pdl_wait();
+    if (st != nullptr && st->done) return;
+    double dot[1] = {0.0};
+    while (e < hi) {
         double xv[JU];
 #pragma unroll
         for (int j = 0; j < JU; ++j) {
@@ -73,7 +81,10 @@ k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
         }
         q[e] = acc;
         if (with_dot) dot[0] = fma(__ldg(p + e), acc, dot[0]);
+        e += kRedThreads;
+        if (e < hi) load_row(e);
     }
+    pdl_trigger();
     if (!with_dot) return;
     int seg;
     if (!seg_reduce<1>(dot, LD, R, s_out, s_scr, seg)) return;
@@ -93,7 +104,9 @@ template <int LD>
 __global__ void __launch_bounds__(kRedThreads)
 k_dir_update(const double* __restrict__ z, const double* __restrict__ p_old, double* __restrict__ p_new,
              RedLayout R, const CgScalars* sc, const SolveState* st) {
+    pdl_wait();
     if (st->done) return;
+    pdl_trigger();
     const double beta = sc[R.blk_seg[blockIdx.x] * LD + threadIdx.x % LD].beta;
     const int64_t lo = R.blk_lo[blockIdx.x], hi = R.blk_lo[blockIdx.x + 1];
 #pragma unroll 4
@@ -121,6 +134,7 @@ __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __rest
                               const CgScalars* __restrict__ csc, const double* __restrict__ rowscale,
                               TF* __restrict__ zf, const TP* __restrict__ psi, TF* __restrict__ rc,
                               int ld, int cmax, int depth, const SolveState* st) {
+    pdl_wait();
     if (st != nullptr && st->done) return;
     using A = typename Acc<TF>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -262,6 +276,7 @@ __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __rest
         fwd_step(K, rb[0], qb[0], pb[0], sb[0]);
         if (K + 1 < nb) fwd_step(K + 1, rb[1], qb[1], pb[1], sb[1]);
     }
+    pdl_trigger();
     // restriction: reduce over lanes, lane 0 writes r_c rows of this subdomain
     if (rc != nullptr) {
 #pragma unroll
@@ -366,7 +381,9 @@ __global__ void __launch_bounds__(256)
 k_coarse_gemm(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
               const int32_t* __restrict__ rng, const TF* __restrict__ in, TF* __restrict__ out,
               TF* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
+    pdl_wait();
     if (st != nullptr && st->done) return;
+    pdl_trigger();
     using A = typename Acc<TF>::type;
     constexpr int KC = 64;                                   // columns per stage
     constexpr int OUT = 32 * LD;                             // outputs of a tile
@@ -469,7 +486,6 @@ __global__ void __launch_bounds__(256)
 k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
               const int32_t* __restrict__ rng, const TF* __restrict__ in, TF* __restrict__ out,
               TF* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
-    if (st != nullptr && st->done) return;
     using A = typename Acc<TF>::type;
     using V4 = typename std::conditional<sizeof(TF) == 4, float4, double4>::type;
     constexpr int OUT = 32 * LD;
@@ -483,7 +499,23 @@ k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
     const int kn = it.k1 - it.k0;
     const int kn4 = (kn + 3) & ~3;
     const int nr = min(it.nrng, MAXR);
+    const TF* M0 = mat + it.moff + (int64_t)it.row_in_node * it.ldm + it.k0;
+    const bool rv[4] = {warp < it.nrows, warp + 8 < it.nrows, warp + 16 < it.nrows, warp + 24 < it.nrows};
+    // warp w owns rows w, w+8, w+16, w+24 of the tile; lane takes 4 columns
+    // per step.  The first two steps of the (setup-data) tile are loaded
+    // before the input gather so both memory trips overlap.
+    auto load_cols = [&](int c4, V4 (&mv)[4]) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (rv[i] && 4 * c4 < kn4) mv[i] = *reinterpret_cast<const V4*>(M0 + (int64_t)(warp + 8 * i) * it.ldm + 4 * c4);
+    };
+    V4 pre0[4], pre1[4];
+    load_cols(lane, pre0);
+    load_cols(lane + 32, pre1);
     for (int i = t; i < 2 * nr; i += 256) srng[i] = rng[2 * it.rng_off + i];
+    pdl_wait();
+    if (st != nullptr && st->done) return;
+    pdl_trigger();
     __syncthreads();
     for (int kk = t; kk < kn4; kk += 256) {
         TF v[LD];
@@ -504,20 +536,13 @@ k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
         for (int h = 0; h < LD; ++h) sx[kk * LD + h] = v[h];
     }
     __syncthreads();
-    // warp w owns rows w, w+8, w+16, w+24 of the tile
     A acc[4][LD];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int h = 0; h < LD; ++h) acc[i][h] = A(0);
-    const TF* M0 = mat + it.moff + (int64_t)it.row_in_node * it.ldm + it.k0;
-    const bool rv[4] = {warp < it.nrows, warp + 8 < it.nrows, warp + 16 < it.nrows, warp + 24 < it.nrows};
-#pragma unroll 2
-    for (int c4 = lane; 4 * c4 < kn4; c4 += 32) {
-        V4 mv[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (rv[i]) mv[i] = *reinterpret_cast<const V4*>(M0 + (int64_t)(warp + 8 * i) * it.ldm + 4 * c4);
+    auto step = [&](int c4, const V4 (&mv)[4]) {
+        if (4 * c4 >= kn4) return;
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             A xv[LD];
@@ -532,6 +557,14 @@ k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
                 }
             }
         }
+    };
+    step(lane, pre0);
+    step(lane + 32, pre1);
+#pragma unroll 2
+    for (int c4 = lane + 64; 4 * c4 < kn4; c4 += 32) {
+        V4 mv[4];
+        load_cols(c4, mv);
+        step(c4, mv);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i)
@@ -609,7 +642,9 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
                  const TF* __restrict__ zf, double* __restrict__ r, const double* __restrict__ q,
                  double* __restrict__ x, const double* __restrict__ p, double* __restrict__ z, RedLayout R,
                  CgScalars* sc, SolveState* st, int nseg, int flexible, int mode) {
+    pdl_wait();
     if (st != nullptr && st->done) return;
+    pdl_trigger();
     using AT = typename Acc<TF>::type;
     __shared__ double s_out[kRedMaxNV * kMaxLd];
     __shared__ double s_scr[kRedThreads];
@@ -811,8 +846,8 @@ __global__ void k_zero(double* __restrict__ a, int64_t n) {
 
 template <int LD>
 static void spmv_ld(const LaunchCtx& L, const double* p, double* q, int with_dot) {
-    k_spmv_dot<LD, 8><<<L.nblk, kRedThreads, 0, L.stream>>>(L.sell_ptr, L.sell_col, L.sell_val, p, q, L.red, L.sc,
-                                                            with_dot ? L.st : nullptr, with_dot);
+    launch_kernel(L.pdl, k_spmv_dot<LD, 8>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream, L.sell_ptr,
+                  L.sell_col, L.sell_val, p, q, L.red, L.sc, with_dot ? L.st : nullptr, with_dot);
 }
 void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_dot) {
     AMS_DISPATCH_LD(L.ld, spmv_ld, L, p, q, with_dot);
@@ -820,7 +855,8 @@ void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_do
 
 template <int LD>
 static void dir_ld(const LaunchCtx& L, const double* z, const double* p_old, double* p_new) {
-    k_dir_update<LD><<<L.nblk, kRedThreads, 0, L.stream>>>(z, p_old, p_new, L.red, L.sc, L.st);
+    launch_kernel(L.pdl, k_dir_update<LD>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream, z, p_old, p_new,
+                  L.red, (const CgScalars*)L.sc, (const SolveState*)L.st);
 }
 void launch_dir_update(const LaunchCtx& L, const double* z, const double* p_old, double* p_new) {
     AMS_DISPATCH_LD(L.ld, dir_ld, L, z, p_old, p_new);
@@ -862,9 +898,8 @@ static cudaError_t local_nr(const LocalSolveArgs& a, const void* fac, const void
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    kern<<<a.nsub, warps * 32, smem, a.stream>>>(a.subs, (const TF*)fac, a.in.r, a.in.q, a.in.sc, a.rowscale, (TF*)zf,
-                                                  (const TP*)psi, (TF*)rc, a.ld, a.cmax, depth, a.st);
-    return cudaGetLastError();
+    return launch_kernel(a.pdl, kern, dim3(a.nsub), dim3(warps * 32), smem, a.stream, a.subs, (const TF*)fac, a.in.r,
+                         a.in.q, a.in.sc, a.rowscale, (TF*)zf, (const TP*)psi, (TF*)rc, a.ld, a.cmax, depth, a.st);
 }
 
 template <typename TF, typename TP>
@@ -898,12 +933,11 @@ template <typename TF, int LD>
 static void coarse_ld(const CoarseLaunch& c, const void* in, void* out) {
     if (c.nitems == 0) return;
     if (LD <= 4)
-        k_coarse_rows<TF, (LD <= 4 ? LD : 4)><<<c.nitems, 256, 0, c.stream>>>(
-            c.items, (const TF*)c.mat, c.rng, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt, c.st);
+        launch_kernel(c.pdl, k_coarse_rows<TF, (LD <= 4 ? LD : 4)>, dim3(c.nitems), dim3(256), 0, c.stream, c.items,
+                      (const TF*)c.mat, c.rng, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt, c.st);
     else
-        k_coarse_gemm<TF, LD><<<c.nitems, 256, 0, c.stream>>>(c.items, (const TF*)c.mat, c.rng,
-                                                              (const TF*)in, (TF*)out, (TF*)c.partial,
-                                                              c.cnt, c.st);
+        launch_kernel(c.pdl, k_coarse_gemm<TF, LD>, dim3(c.nitems), dim3(256), 0, c.stream, c.items,
+                      (const TF*)c.mat, c.rng, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt, c.st);
 }
 template <typename TF>
 static void coarse_tf(const CoarseLaunch& c, int ld, const void* in, void* out) {
@@ -924,14 +958,10 @@ void launch_coarse_gemm(const CoarseLaunch& c, int prec, int ld, const void* in,
 template <typename TF, typename TP, int LD>
 static void prolong_ld(const LaunchCtx& L, const ProlongArgs& a) {
     if (L.nsub == 0) return;
-    if (a.mmax > 8)
-        k_prolong_update<TF, TP, LD, kMaxM><<<L.nblk_sub, kRedThreads, 0, L.stream>>>(
-            L.subs, (const TP*)a.psi, (const TF*)a.ec, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z, L.red_sub, L.sc,
-            L.st, L.nseg, a.flexible, a.mode);
-    else
-        k_prolong_update<TF, TP, LD, 8><<<L.nblk_sub, kRedThreads, 0, L.stream>>>(
-            L.subs, (const TP*)a.psi, (const TF*)a.ec, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z, L.red_sub, L.sc,
-            L.st, L.nseg, a.flexible, a.mode);
+    auto kern = a.mmax > 8 ? k_prolong_update<TF, TP, LD, kMaxM> : k_prolong_update<TF, TP, LD, 8>;
+    launch_kernel(L.pdl, kern, dim3((unsigned)L.nblk_sub), dim3(kRedThreads), 0, L.stream, L.subs, (const TP*)a.psi,
+                  (const TF*)a.ec, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z, L.red_sub, L.sc, L.st, L.nseg,
+                  a.flexible, a.mode);
 }
 template <typename TF, typename TP>
 static void prolong_tp(const LaunchCtx& L, const ProlongArgs& a) {

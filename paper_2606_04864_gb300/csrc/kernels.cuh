@@ -28,6 +28,20 @@ template <> __device__ __forceinline__ float from_d<float>(double v) { return (f
 template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch.  Kernels of the solve loop are launched so
+// that they may start while the previous kernel on the stream drains: work
+// that reads only setup data (matrix, factor tiles, basis) runs first, then
+// pdl_wait() blocks until the previous grid has completed and its writes
+// are visible.  Every such kernel calls pdl_wait() before it reads anything
+// another solve kernel writes (including the solve state) and before any
+// early exit, so completion stays transitive along the stream.
+// pdl_trigger() lets the next kernel launch once every block of this one
+// has passed it.  Both are no-ops for a normal launch.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
 // cp.async (16-byte, L2-only) staging into shared memory
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {

@@ -10,6 +10,25 @@
 namespace ams {
 
 // Everything the per-row reduction kernels need for one solve shape.
+// Launch `kern` on `stream`; with pdl the launch carries the programmatic
+// stream serialization attribute (the kernel must call pdl_wait(), see
+// kernels.cuh).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_kernel(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                 cudaStream_t stream, Args... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 struct LaunchCtx {
     cudaStream_t stream;
     int ld;                  // right-hand-side stride (power of two)
@@ -21,6 +40,7 @@ struct LaunchCtx {
     int nsub;                // subdomains
     CgScalars* sc;           // [nseg][ld]
     SolveState* st;
+    bool pdl;                // solve-loop kernels: programmatic dependent launch
     const int64_t* sell_ptr;
     const int32_t* sell_col;
     const double* sell_val;
@@ -47,6 +67,7 @@ struct LocalSolveArgs {
     int cmax;
     int mmax;
     const SolveState* st;
+    bool pdl;
 };
 
 struct LocalTmaArgs {
@@ -64,6 +85,7 @@ struct LocalTmaArgs {
     int nbmax;          // largest number of 32-row block rows of a subdomain
     int64_t budget;
     SolveState* st;
+    bool pdl;
 };
 
 struct CoarseLaunch {
@@ -75,6 +97,7 @@ struct CoarseLaunch {
     void* partial;
     int32_t* cnt;
     const SolveState* st;
+    bool pdl;
 };
 
 // q = A p, and p.q per (system, rhs) when with_dot
