@@ -308,6 +308,19 @@ ams_status ams_profile_solve(ams_handle h, const double* f, int32_t nrhs,
                              int64_t* count);
 
 /*
+ * Diagnostic.  The solve kernels convert between FP32 and FP64 with integer
+ * instructions (FP64 instructions are scarce on this GPU).  This call
+ * checks those conversions against the hardware conversions for n device
+ * FP64 values x: *narrow_bad counts values whose FP64 -> FP32 result
+ * differs bitwise (round to nearest even; NaNs compared as NaN), and
+ * *widen_bad those whose FP32 -> FP64 widening of the hardware-rounded value
+ * differs.  Both are 0 when the conversions agree.  Synchronous on the
+ * current device's default stream; allocates 16 bytes of device memory.
+ * Errors: AMS_ERR_INVALID_ARG (n < 0, NULL pointers), AMS_ERR_CUDA.
+ */
+ams_status ams_check_conversions(const double* x, int64_t n, int64_t* narrow_bad, int64_t* widen_bad);
+
+/*
  * ams_csr_spmv_dot_noalloc — y = A x and *xy = x^T y for a CSR matrix, with
  * no handle and no device allocation.  The paper has no counterpart: this
  * is a service for callers that cannot allocate device memory at the

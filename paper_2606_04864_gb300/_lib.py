@@ -103,6 +103,7 @@ SIGNATURES = {
                                     C.c_void_p, C.c_void_p]),
     "ams_csr_spmv_dot_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ams_check_conversions": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
 }
 
 _lock = threading.Lock()

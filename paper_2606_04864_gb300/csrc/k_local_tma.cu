@@ -256,7 +256,7 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
         float t[NR], pv[MM];
         const float pvt = vb;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) t[j] = (float)(upd[j] ? fma(-al[j], qb[j], tb[j]) : tb[j]);
+        for (int j = 0; j < NR; ++j) t[j] = f64_to_f32(upd[j] ? fma(-al[j], qb[j], tb[j]) : tb[j]);
 #pragma unroll
         for (int k = 0; k < MM; ++k) pv[k] = to_f(pb[k]);
         load_fwd(K + PF, tb, qb, pb, vb);
@@ -603,7 +603,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     int sK = 0;   // slot of block row K
     auto fwd_step = [&](int K, double& tb, double& qb, BasisRow<TP, MM>& pb, float& vb) {
         if (K + D < nb) issue(K + D, wrap_up(sK + D));
-        float t = (float)(upd ? fma(-alpha, qb, tb) : tb);
+        float t = f64_to_f32(upd ? fma(-alpha, qb, tb) : tb);
         const float pvt = vb;
         if (rc != nullptr) {
 #pragma unroll

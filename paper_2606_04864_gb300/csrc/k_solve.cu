@@ -682,7 +682,7 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
 #pragma unroll
                 for (int k = 0; k < MM; ++k) pe += (AT)to_d(pv[k]) * s_ec[k * LD + rhs];
             }
-            const double zv = (double)(acc + pe);   // z in the apply precision, stored as FP64
+            const double zv = widen(acc + pe);   // z in the apply precision, stored as FP64
             z[e] = zv;
             if (mode != 0) {
                 double rv = r[e];

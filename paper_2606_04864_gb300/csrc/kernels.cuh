@@ -20,6 +20,35 @@ __device__ __forceinline__ double to_d(float v) { return (double)v; }
 __device__ __forceinline__ double to_d(double v) { return v; }
 __device__ __forceinline__ double to_d(__nv_bfloat16 v) { return (double)__bfloat162float(v); }
 
+// FP32 <-> FP64 conversions on the integer pipe.  FP64 instructions are
+// scarce on this GPU (about 1/64 of the FP32 rate) and a conversion between
+// the two formats occupies the FP64 pipe.  For inputs whose result is a
+// normal number the bit manipulation below gives exactly the IEEE results
+// (widening is exact; narrowing rounds to nearest, ties to even, and a
+// carry out of the mantissa moves into the exponent, up to infinity); every
+// other input (zero, subnormal, infinity, NaN, out of range) takes the
+// hardware conversion.
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const uint64_t d = ((uint64_t)(u >> 31) << 63) | ((uint64_t)(e + 896u) << 52) |
+                       ((uint64_t)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+__device__ __forceinline__ float f64_to_f32(double x) {
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t e = (uint32_t)(b >> 52) & 0x7ffu;
+    if (e < 897u || e > 1150u) return (float)x;        // result not a normal float before rounding
+    const uint64_t m = b & 0xfffffffffffffull;
+    uint32_t r = ((uint32_t)(b >> 63) << 31) | ((e - 896u) << 23) | (uint32_t)(m >> 29);
+    const uint32_t rem = (uint32_t)(m & 0x1fffffffu);
+    r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ double widen(float v) { return f32_to_f64(v); }
+__device__ __forceinline__ double widen(double v) { return v; }
+
 template <typename T> struct Acc { using type = float; };
 template <> struct Acc<double> { using type = double; };
 
