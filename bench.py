@@ -36,6 +36,31 @@ if ROOT not in sys.path:
 METRIC = "PCG time-to-solution at rtol 1e-8 (s), iters, HBM GB/s; mixed vs FP64"
 
 
+# Kernel behind each timed solve step, for the ncu traffic lookup.
+STEP_KERNELS = {"local_solve_restrict": "k_local_tma1"}
+
+
+def _profiled_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary under
+    profiles/, or None when no summary matches the kernel's current source
+    (the counters describe only the source they were taken from)."""
+    import glob
+    import hashlib
+    import re
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        for line in open(path, errors="replace"):
+            m = re.match(r"traffic_bytes_per_launch: (\d+) kernel: (\S+) source: (\S+) sha256_16: ([0-9a-f]{16})",
+                         line.strip())
+            if not m or m.group(2) != kernel:
+                continue
+            src = os.path.join(ROOT, m.group(3))
+            if not os.path.exists(src):
+                continue
+            if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == m.group(4):
+                return int(m.group(1)), os.path.relpath(path, ROOT)
+    return None, None
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -248,6 +273,9 @@ def run_gpu(args):
     for v in kern.values():
         v["share"] = v["ms_total"] / tot if tot > 0 else None
     dom = max(kern, key=lambda n: kern[n]["ms_total"])
+    traffic, traffic_src = (None, None)
+    if args.workload == "cfg2" and dom in STEP_KERNELS:
+        traffic, traffic_src = _profiled_traffic(STEP_KERNELS[dom])
     peak, peak_kind = _peaks()
     iter_bytes = sum(v["bytes"] for v in kern.values())
     it_ms = sum(v["ms"] for v in kern.values())
@@ -325,7 +353,8 @@ def run_gpu(args):
             "roofline": {
                 "bound": "hbm", "kernel": dom,
                 "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
-                "frac": kern[dom]["gbs"] / peak, "traffic": None,
+                "frac": kern[dom]["gbs"] / peak, "traffic": traffic,
+                "traffic_source": traffic_src,
                 "peak_source": f"{peak_kind} hbm_gbs (copy burst)",
                 "timing": "CUDA events around every launch inside one profiled solve",
                 "algorithmic_bytes_per_launch": kern[dom]["bytes"],
@@ -347,7 +376,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
