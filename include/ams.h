@@ -268,19 +268,21 @@ ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y);
  *                          p.q (two launches, timed together)
  *   AMS_KERNEL_LOCAL       local solves sum_i R_i^T A_i^{-1} R_i r' and the
  *                          restriction R_0 r', with r' = r - alpha q
- *   AMS_KERNEL_COARSE_FWD  y = L_c^{-1} r_c   (A_0 = L_c L_c^T)
- *   AMS_KERNEL_COARSE_BWD  e_c = L_c^{-T} y
- *   AMS_KERNEL_PROLONG     z = z_f + R_0^T e_c, r = r', x += alpha p, dots,
- *                          convergence test and beta
- * Without a coarse space (coarse = 0) the two coarse kernels do not run.
+ *   AMS_KERNEL_COARSE      forward substitution y = L_c^{-1} r_c
+ *                          (A_0 = L_c L_c^T); with more than four
+ *                          right-hand sides also the backward substitution
+ *                          e_c = L_c^{-T} y (a second launch)
+ *   AMS_KERNEL_PROLONG     (up to four right-hand sides: the backward
+ *                          substitution,) z = z_f + R_0^T e_c, r = r',
+ *                          x += alpha p, dots, convergence test and beta
+ * Without a coarse space (coarse = 0) AMS_KERNEL_COARSE does not run.
  */
 enum {
     AMS_KERNEL_SPMV = 0,
     AMS_KERNEL_LOCAL = 1,
-    AMS_KERNEL_COARSE_FWD = 2,
-    AMS_KERNEL_COARSE_BWD = 3,
-    AMS_KERNEL_PROLONG = 4,
-    AMS_NUM_KERNELS = 5
+    AMS_KERNEL_COARSE = 2,
+    AMS_KERNEL_PROLONG = 3,
+    AMS_NUM_KERNELS = 4
 };
 
 /*

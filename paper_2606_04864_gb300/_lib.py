@@ -21,7 +21,7 @@ STATUS_NAMES = {
 }
 PREC = {"fp64": 0, "fp32": 1, "fp32_bf16": 2}
 # AMS_KERNEL_* indices of ams_time_kernel / ams_profile_solve, in launch order
-KERNEL_NAMES = ["spmv_direction", "local_solve_restrict", "coarse_fwd", "coarse_bwd", "prolong_update"]
+KERNEL_NAMES = ["spmv_direction", "local_solve_restrict", "coarse_solve", "prolong_update"]
 AMS_NUM_KERNELS = len(KERNEL_NAMES)
 CG = {"auto": -1, "pcg": 0, "fcg": 1}
 

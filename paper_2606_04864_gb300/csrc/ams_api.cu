@@ -133,6 +133,8 @@ struct ams_handle_s {
     CoarseItem *d_fwd = nullptr, *d_bwd = nullptr;
     int nfwd = 0, nbwd = 0;
     void *d_Rmat = nullptr, *d_Qmat = nullptr;
+    CoarseRef* d_cref = nullptr;        // per subdomain: its rows of the backward blocks
+    int32_t* d_gat = nullptr;           // per ND node: backward column gather lists
     int64_t R_elems = 0, Q_elems = 0;
     int32_t* d_rng = nullptr;
     void* d_partial = nullptr;
@@ -670,6 +672,8 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
     std::vector<CoarseItem> fwd, bwd;
     std::vector<int32_t> rng;
     std::vector<int64_t> desc;   // extraction chunks, 8 per chunk
+    std::vector<int32_t> gat;
+    std::vector<CoarseRef> cref(h->N, CoarseRef{0, 0, 0, 4});
     int64_t Roff = 0, Qoff = 0;
     int32_t tile_id = 0, slot = 0;
     const int KCHUNK = kCoarseChunk;
@@ -736,6 +740,21 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
             }
             const int64_t Kbp = (Kb + 3) & ~int64_t(3);
             add_items(bwd, Qoff, Kb, Kbp, nd.k, a, boff, nrng);
+            // fused backward substitution: gather list of the node's columns
+            // and the rows of each of its subdomains
+            const int64_t goff = (int64_t)gat.size();
+            for (int32_t r = 0; r < nrng; ++r) {
+                const int32_t st0 = rng[2 * (boff + r)], len = rng[2 * (boff + r) + 1];
+                for (int32_t i = 0; i < len; ++i) gat.push_back(st0 + i);
+            }
+            for (int32_t sa : nd.subs) {
+                const SubInfo& I = h->h_subs[S.sub0 + sa];
+                CoarseRef& cr = cref[S.sub0 + sa];
+                cr.q_off = Qoff + (I.coff - a) * Kbp;
+                cr.gat_off = goff;
+                cr.K = (int32_t)Kb;
+                cr.ldm = (int32_t)Kbp;
+            }
             for (int64_t e0 = 0; e0 < nd.k * Kbp; e0 += ECHUNK) {
                 desc.insert(desc.end(), {Qoff, Kb | (Kbp << 32), 1, nd.a, nd.cstart,
                                          (int64_t)boff | ((int64_t)nrng << 32), e0,
@@ -765,6 +784,9 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
     AMS_TRY(upload(h, &h->d_fwd, fwd));
     AMS_TRY(upload(h, &h->d_bwd, bwd));
     AMS_TRY(upload(h, &h->d_rng, rng));
+    if (gat.empty()) gat.push_back(0);
+    AMS_TRY(upload(h, &h->d_gat, gat));
+    AMS_TRY(upload(h, &h->d_cref, cref));
     AMS_TRY(h->alloc(&h->d_partial, (size_t)std::max<int32_t>(slot, 1) * 32 * kMaxLd * tfb));
     AMS_TRY(h->alloc_t(&h->d_cnt, (size_t)std::max<int32_t>(tile_id, 1)));
     AMS_CUDA_TRY(cudaMemsetAsync(h->d_cnt, 0, sizeof(int32_t) * std::max<int32_t>(tile_id, 1), h->stream));
@@ -1149,21 +1171,30 @@ static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool wit
     return AMS_OK;
 }
 
-static void launch_coarse(ams_handle h, int ld, bool fwd, bool with_state) {
-    if (fwd) {
-        CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_partial, h->d_cnt,
-                        with_state ? h->d_st : nullptr, h->use_pdl};
-        launch_coarse_gemm(cf, h->prec, ld, h->d_rc, h->d_yc);
-    } else {
-        CoarseLaunch cb{h->stream, h->nbwd, h->d_bwd, h->d_Qmat, h->d_rng, h->d_partial, h->d_cnt,
-                        with_state ? h->d_st : nullptr, h->use_pdl};
-        launch_coarse_gemm(cb, h->prec, ld, h->d_yc, h->d_ec);
-    }
+// Up to four right-hand sides the backward coarse substitution runs inside
+// the prolongation (each subdomain multiplies its rows of the backward block
+// with y); with more, the per-subdomain gathers of y cost more than the
+// separate backward launch.
+static bool fused_backward(int ld) { return ld <= 4; }
+
+// forward coarse substitution y = L_c^{-1} r_c, and the backward one when it
+// is not fused
+static int launch_coarse(ams_handle h, int ld, bool with_state) {
+    CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_partial, h->d_cnt,
+                    with_state ? h->d_st : nullptr, h->use_pdl};
+    launch_coarse_gemm(cf, h->prec, ld, h->d_rc, h->d_yc);
+    if (fused_backward(ld)) return 1;
+    CoarseLaunch cb{h->stream, h->nbwd, h->d_bwd, h->d_Qmat, h->d_rng, h->d_partial, h->d_cnt,
+                    with_state ? h->d_st : nullptr, h->use_pdl};
+    launch_coarse_gemm(cb, h->prec, ld, h->d_yc, h->d_ec);
+    return 2;
 }
 
-static ProlongArgs prolong_args(ams_handle h, int mode, const double* p) {
-    return ProlongArgs{h->d_psi, h->Nc > 0 ? h->d_ec : nullptr, h->d_zf, h->d_r, h->d_q, h->d_x, p, h->d_z,
-                       std::max(1, h->mmax), h->flexible, mode};
+static ProlongArgs prolong_args(ams_handle h, int mode, const double* p, int ld) {
+    const bool coarse = h->Nc > 0, fused = fused_backward(ld);
+    return ProlongArgs{h->d_psi, coarse && !fused ? h->d_ec : nullptr, coarse && fused ? h->d_yc : nullptr,
+                       coarse && fused ? h->d_Qmat : nullptr, h->d_cref, h->d_gat, h->d_zf, h->d_r, h->d_q, h->d_x,
+                       p, h->d_z, std::max(1, h->mmax), h->flexible, mode};
 }
 
 // z = M^{-1} r' (internal layout).  mode 0: plain application (r' = r, no
@@ -1177,25 +1208,24 @@ static ams_status apply_precond(ams_handle h, const LaunchCtx& L, int mode, cons
     prof_begin(h, AMS_KERNEL_LOCAL);
     AMS_TRY(launch_local(h, L.ld, ResidIn{h->d_r, mode == 2 ? h->d_q : nullptr, h->d_sc}, with_state));
     prof_end(h);
-    h->launches += coarse ? 4 : 2;
+    h->launches += 2;
     if (coarse) {
-        prof_begin(h, AMS_KERNEL_COARSE_FWD);
-        launch_coarse(h, L.ld, true, with_state);
-        prof_end(h);
-        prof_begin(h, AMS_KERNEL_COARSE_BWD);
-        launch_coarse(h, L.ld, false, with_state);
+        prof_begin(h, AMS_KERNEL_COARSE);
+        h->launches += launch_coarse(h, L.ld, with_state);
         prof_end(h);
     }
     LaunchCtx L2 = L;
     if (!with_state) L2.st = nullptr;
     prof_begin(h, AMS_KERNEL_PROLONG);
-    launch_prolong_update(L2, h->prec, prolong_args(h, mode, p));
+    launch_prolong_update(L2, h->prec, prolong_args(h, mode, p, L.ld));
     prof_end(h);
     AMS_CUDA_TRY(cudaGetLastError());
     return AMS_OK;
 }
 
-static int launches_per_iteration(ams_handle h) { return h->Nc > 0 ? 6 : 4; }
+static int launches_per_iteration(ams_handle h, int ld) {
+    return 4 + (h->Nc > 0 ? (fused_backward(ld) ? 1 : 2) : 0);
+}
 
 static void launch_direction_spmv(ams_handle h, const LaunchCtx& L, const double* p_old, double* p_new) {
     launch_dir_update(L, h->d_z, p_old, p_new);
@@ -1303,7 +1333,7 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
         for (int k = 0; k < (chunk + 1) / 2; ++k) {
             if (graph) {
                 AMS_CUDA_TRY(cudaGraphLaunch(graph, h->stream));
-                h->launches += 2 * launches_per_iteration(h);
+                h->launches += 2 * launches_per_iteration(h, ld);
             } else {
                 for (int par = 0; par < 2; ++par) {
                     AMS_TRY(launch_iteration(h, L, par));
@@ -1433,10 +1463,12 @@ static double kernel_bytes(ams_handle h, int which, int ld) {
             const double fb = h->use_tma ? (double)h->tile_elems * 4.0 + 4.0 * n : (double)h->fac_elems * tf;
             return fb + 16.0 * nl + tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf;
         }
-        case AMS_KERNEL_COARSE_FWD: return (double)h->R_elems * tf + 2.0 * (double)h->Nc * ld * tf;
-        case AMS_KERNEL_COARSE_BWD: return (double)h->Q_elems * tf + 2.0 * (double)h->Nc * ld * tf;
-        case AMS_KERNEL_PROLONG:    // z_f, basis, e_c in; r, q, x, p in; r, x, z out
-            return tf * nl + (double)h->psi_elems * tp + (double)h->Nc * ld * tf + 56.0 * nl;
+        case AMS_KERNEL_COARSE:     // forward blocks, r_c in, y out (+ the backward pass when separate)
+            return (double)h->R_elems * tf + 2.0 * (double)h->Nc * ld * tf +
+                   (fused_backward(ld) ? 0.0 : (double)h->Q_elems * tf + 2.0 * (double)h->Nc * ld * tf);
+        case AMS_KERNEL_PROLONG:    // (backward blocks, y) or e_c; z_f, basis; r, q, x, p in; r, x, z out
+            return (fused_backward(ld) ? (double)h->Q_elems * tf : 0.0) + (double)h->Nc * ld * tf + tf * nl +
+                   (double)h->psi_elems * tp + 56.0 * nl;
     }
     return 0.0;
 }
@@ -1702,9 +1734,8 @@ ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* av
             case AMS_KERNEL_LOCAL:
                 AMS_TRY(launch_local(h, ld, ResidIn{h->d_r, h->d_q, h->d_sc}, true));
                 break;
-            case AMS_KERNEL_COARSE_FWD: launch_coarse(h, ld, true, true); break;
-            case AMS_KERNEL_COARSE_BWD: launch_coarse(h, ld, false, true); break;
-            case AMS_KERNEL_PROLONG: launch_prolong_update(L, h->prec, prolong_args(h, 2, h->d_p2)); break;
+            case AMS_KERNEL_COARSE: launch_coarse(h, ld, true); break;
+            case AMS_KERNEL_PROLONG: launch_prolong_update(L, h->prec, prolong_args(h, 2, h->d_p2, ld)); break;
         }
         return AMS_OK;
     };

@@ -75,6 +75,16 @@ struct CoarseItem {
     int32_t slot0;         // first partial slot of this tile
 };
 
+// Backward coarse substitution, fused into the prolongation: the rows of
+// L_c^{-T} that belong to one subdomain (m_i consecutive rows of its ND
+// node's backward block) and the node's column gather list into y.
+struct CoarseRef {
+    int64_t q_off;         // first element of the subdomain's rows in the backward blocks
+    int64_t gat_off;       // first entry of the node's gather list
+    int32_t K;             // columns: the node's own coarse rows, then its ancestors'
+    int32_t ldm;           // row stride (K rounded up to 4)
+};
+
 // ---- per (system, rhs) CG scalars -----------------------------------------
 struct CgScalars {
     double fnorm2;     // ||f||^2

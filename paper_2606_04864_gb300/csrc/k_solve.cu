@@ -1,13 +1,13 @@
 // Solve-phase kernels of the AMS-preconditioned CG (one GPU, sm_103a).
 //
-// One CG iteration (Section 3.1 preconditioner inside CG) is six kernels:
+// One CG iteration (Section 3.1 preconditioner inside CG) is five kernels:
 //   k_dir_update      p = z + beta p_old
 //   k_spmv_dot        q = A p and p.q                          (SELL-32 SpMV)
 //   k_local_solve     z_f = sum_i R_i^T A_i^{-1} R_i r'  and  r_c = R_0 r',
 //   (k_local_tma*)    r' = r - alpha q formed on the fly       (alpha = rho/pq)
-//   k_coarse_gemm     y = L_c^{-1} r_c, then e_c = L_c^{-T} y  (A_0 = L_c L_c^T)
-//   k_prolong_update  z = z_f + R_0^T e_c, r = r', x += alpha p, r.z, r.r,
-//                     z.q, convergence test and beta
+//   k_coarse_rows     y = L_c^{-1} r_c                        (A_0 = L_c L_c^T)
+//   k_prolong_update  e_c = L_c^{-T} y, z = z_f + R_0^T e_c, r = r',
+//                     x += alpha p, r.z, r.r, z.q, convergence test, beta
 #include <cstdint>
 #include <cstdio>
 #include <type_traits>
@@ -602,11 +602,17 @@ k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
 }
 
 // ===========================================================================
-// a6 + a2: z = z_f + R_0^T e_c with the CG update and the dots.  A thread
-// block takes a range of consecutive subdomains of one system; per
-// subdomain its rows are contiguous, its basis rows are contiguous, and its
-// m coarse values are staged once in shared memory.
-// Padded rows belong to no subdomain: their z stays 0 and r, q, x are 0.
+// a5 (backward substitution) + a6 + a2: e_c = L_c^{-T} y, z = z_f + R_0^T e_c,
+// the CG update and the dots.  A thread block takes a range of consecutive
+// subdomains of one system.  Per subdomain: its m_i rows of e_c are the
+// product of its rows of the backward block of its nested-dissection node
+// (L_c^{-T} restricted to the node's rows and the columns of the node and
+// its ancestors) with y gathered at those columns; the block reduces them
+// in a fixed order into shared memory, then prolongates over the
+// subdomain's contiguous rows (basis rows by 16-byte loads).  With many
+// right-hand sides the per-subdomain gathers of y cost more than a separate
+// backward launch: then e_c comes in precomputed (ec != NULL).  Padded rows
+// belong to no subdomain: their z stays 0 and r, q, x are 0.
 //
 // mode 0: z only (a plain preconditioner application).
 // mode 1: first application of a solve: z and rho = r.z (beta = 0).
@@ -639,17 +645,24 @@ __device__ __forceinline__ void load_basis_row(const TP* __restrict__ pr, int m,
 template <typename TF, typename TP, int LD, int MM>
 __global__ void __launch_bounds__(kRedThreads)
 k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, const TF* __restrict__ ec,
+                 const TF* __restrict__ yc, const TF* __restrict__ qmat, const CoarseRef* __restrict__ cref, const int32_t* __restrict__ gat,
                  const TF* __restrict__ zf, double* __restrict__ r, const double* __restrict__ q,
                  double* __restrict__ x, const double* __restrict__ p, double* __restrict__ z, RedLayout R,
                  CgScalars* sc, SolveState* st, int nseg, int flexible, int mode) {
-    pdl_wait();
-    if (st != nullptr && st->done) return;
-    pdl_trigger();
     using AT = typename Acc<TF>::type;
+    using V4 = typename std::conditional<sizeof(TF) == 4, float4, double4>::type;
+    constexpr int NCG = kRedThreads / LD;            // column groups of the backward product
+    constexpr int NW = kRedThreads / 32;
     __shared__ double s_out[kRedMaxNV * kMaxLd];
     __shared__ double s_scr[kRedThreads];
     __shared__ AT s_ec[MM * LD];
+    __shared__ AT s_part[NW * MM * LD];
+    pdl_wait();
+    if (st != nullptr && st->done) return;
+    pdl_trigger();
     const int rhs = threadIdx.x % LD;
+    const int cg = threadIdx.x / LD;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double alpha = 0.0;
     bool upd = false;
     if (mode == 2) {
@@ -662,11 +675,47 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
     for (int64_t si = s_lo; si < s_hi; ++si) {
         const SubInfo S = subs[si];
         const int m = S.m;
-        const bool coarse = ec != nullptr && m > 0;
-        __syncthreads();                 // s_ec of the previous subdomain is no longer read
-        if (coarse)
+        const bool coarse = (ec != nullptr || qmat != nullptr) && m > 0;
+        if (coarse && ec != nullptr) {
+            // e_c computed by a separate backward-substitution launch
             for (int i = threadIdx.x; i < MM * LD; i += kRedThreads)
                 s_ec[i] = (i < m * LD) ? (AT)ec[(int64_t)S.coff * LD + i] : AT(0);
+        } else if (coarse) {
+            // e_c rows of this subdomain: acc[k] = sum_j Q[k][j] y[gat[j]] over this thread's columns
+            const CoarseRef cr = cref[si];
+            const TF* Q = qmat + cr.q_off;
+            const int32_t* G = gat + cr.gat_off;
+            AT acc[MM];
+#pragma unroll
+            for (int k = 0; k < MM; ++k) acc[k] = AT(0);
+            for (int c4 = cg; 4 * c4 < cr.K; c4 += NCG) {
+                const int j0 = 4 * c4;
+                AT yv[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    yv[e] = (j0 + e < cr.K) ? (AT)yc[(int64_t)__ldg(G + j0 + e) * LD + rhs] : AT(0);
+#pragma unroll
+                for (int k = 0; k < MM; ++k) {
+                    if (k < m) {
+                        const V4 qv = *reinterpret_cast<const V4*>(Q + (int64_t)k * cr.ldm + j0);
+                        acc[k] += (AT)qv.x * yv[0] + (AT)qv.y * yv[1] + (AT)qv.z * yv[2] + (AT)qv.w * yv[3];
+                    }
+                }
+            }
+            // sum over column groups: lanes of a warp with the same rhs, then warps in order
+#pragma unroll
+            for (int k = 0; k < MM; ++k) {
+                AT a = acc[k];
+                for (int off = 16; off >= LD; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+                if (lane < LD) s_part[(warp * MM + k) * LD + lane] = a;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < MM * LD; i += kRedThreads) {
+                AT a = AT(0);
+                for (int w = 0; w < NW; ++w) a += s_part[w * MM * LD + i];
+                s_ec[i] = a;
+            }
+        }
         __syncthreads();
         const bool vec = (m == MM) && ((reinterpret_cast<uintptr_t>(psi + S.psi_off) & 15) == 0);
         const int64_t ne = (int64_t)S.n * LD;
@@ -697,6 +746,7 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
                 if (flexible && mode == 2) v[2] = fma(zv, qv, v[2]);
             }
         }
+        __syncthreads();                 // s_ec / s_part are reused by the next subdomain
     }
     if (mode == 0) return;
     int sg;
@@ -960,8 +1010,8 @@ static void prolong_ld(const LaunchCtx& L, const ProlongArgs& a) {
     if (L.nsub == 0) return;
     auto kern = a.mmax > 8 ? k_prolong_update<TF, TP, LD, kMaxM> : k_prolong_update<TF, TP, LD, 8>;
     launch_kernel(L.pdl, kern, dim3((unsigned)L.nblk_sub), dim3(kRedThreads), 0, L.stream, L.subs, (const TP*)a.psi,
-                  (const TF*)a.ec, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z, L.red_sub, L.sc, L.st, L.nseg,
-                  a.flexible, a.mode);
+                  (const TF*)a.ec, (const TF*)a.yc, (const TF*)a.qmat, a.cref, a.gat, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z,
+                  L.red_sub, L.sc, L.st, L.nseg, a.flexible, a.mode);
 }
 template <typename TF, typename TP>
 static void prolong_tp(const LaunchCtx& L, const ProlongArgs& a) {

@@ -118,7 +118,11 @@ void launch_band_pack_tiles(cudaStream_t s, int nwork, const SubInfo* subs, cons
                             float* piv);
 struct ProlongArgs {
     const void* psi;
-    const void* ec;          // NULL without a coarse space
+    const void* ec;          // coarse correction from a separate backward launch, or NULL
+    const void* yc;          // forward coarse substitution output (NULL without a coarse space)
+    const void* qmat;        // backward blocks of L_c^{-1} (NULL without a coarse space)
+    const CoarseRef* cref;
+    const int32_t* gat;
     const void* zf;
     double* r;
     const double* q;

@@ -129,10 +129,11 @@ class _Base:
 
     def profile_solve(self, f, rtol: float = 1e-8):
         """One solve with CUDA events around every kernel.  Returns one dict
-        per kernel of the iteration (``KERNEL_NAMES`` order: SpMV with the
-        direction update, local solves, coarse forward, coarse backward,
-        prolongation with the CG update) with total ms, launch count and
-        algorithmic bytes per launch."""
+        per kernel slot of the iteration (``KERNEL_NAMES`` order: SpMV with
+        the direction update; local solves; coarse forward substitution,
+        plus the backward one above four right-hand sides; prolongation with
+        the CG update, plus the backward substitution up to four right-hand
+        sides) with total ms, launch count and algorithmic bytes per launch."""
         fv, nrhs = self._vec_in(f)
         ms = np.zeros(AMS_NUM_KERNELS, dtype=np.float64)
         by = np.zeros(AMS_NUM_KERNELS, dtype=np.float64)
