@@ -75,7 +75,11 @@ typedef struct {
     int32_t cg_variant;          /* AMS_CG_*; default AMS_CG_AUTO */
     int32_t maxit;               /* outer iteration cap; default 10000 */
     int32_t device_ptrs;         /* 0 host pointers (default), 1 device pointers */
-    int32_t autotune;            /* 1: time SpMV launch shapes during setup (default 1) */
+    int32_t autotune;            /* 1 (default): at the first solve with a given
+                                    number of right-hand sides, time candidate
+                                    launch shapes (blocks per SM of the SpMV and
+                                    prolongation grids, local-solve ring depth)
+                                    on that right-hand side and keep the fastest */
     int32_t coarse;              /* 1: two-level (default); 0: local solves only */
     double eig_shift;            /* shift sigma of the local eigensolver; 0 = default 1e-2 */
     int32_t eig_maxit;           /* local eigensolver iteration cap; 0 = default 300 */

@@ -62,6 +62,14 @@ struct RedCache {
     int32_t *cnt1 = nullptr, *cnt2 = nullptr, *cnt3 = nullptr;
 };
 
+// Launch shapes of the solve kernels for one ld.
+struct TuneCfg {
+    int bps_elem = kRedBlocksPerSM;     // element-layout blocks per SM (direction update, SpMV)
+    int bps_sub = kRedBlocksPerSM;      // subdomain-layout blocks per SM (prolongation)
+    int depth = 0;                      // local-solve ring depth; 0: chosen from the band width
+    bool done = false;                  // autotuned
+};
+
 struct SystemHost {
     int64_t n = 0, nnz = 0;
     int64_t caller0 = 0;       // offset of this system in caller vectors
@@ -148,8 +156,9 @@ struct ams_handle_s {
     double* d_stage_dvals = nullptr;
     CgScalars* d_sc = nullptr;
     SolveState* d_st = nullptr;
-    std::map<int, RedCache> red;        // element blocks, per ld
-    std::map<int, RedCache> red_sub;    // one block per subdomain, per ld
+    std::map<std::pair<int, int>, RedCache> red;      // element blocks, per (ld, blocks per SM)
+    std::map<std::pair<int, int>, RedCache> red_sub;  // subdomain ranges, per (ld, blocks per SM)
+    std::map<int, TuneCfg> tune;        // launch shapes per ld (autotuned or defaults)
     ams_info info{};
     int64_t launches = 0;               // kernels launched by solve-time entry points
 
@@ -252,15 +261,22 @@ static void split_ranges(const std::vector<int64_t>& work, int nb, int64_t first
     }
 }
 
-// Reduction layouts for a given ld, sized to about kRedBlocksPerSM blocks per
-// SM: blocks of whole kRedElems-element chunks of one system, and blocks of
+// Reduction layouts for a given ld, sized to about `bps` blocks per SM:
+// blocks of whole kRedElems-element chunks of one system, and blocks of
 // consecutive subdomains of one system (balanced by rows).
-static ams_status get_red(ams_handle h, int ld, RedCache** out, RedCache** out_sub) {
-    const int target = std::max(1, kRedBlocksPerSM * h->num_sms);
-    if (h->red.find(ld) == h->red.end()) {
+static ams_status get_layout(ams_handle h, int ld, int bps, bool sub, RedCache** out) {
+    auto& cache = sub ? h->red_sub : h->red;
+    const auto key = std::make_pair(ld, bps);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *out = &it->second;
+        return AMS_OK;
+    }
+    const int target = std::max(1, bps * h->num_sms);
+    std::vector<int64_t> blk_lo;
+    std::vector<int32_t> blk_seg, seg_blk0(h->nsys), seg_nblk(h->nsys);
+    if (!sub) {
         const int64_t nchunk_tot = h->n_pad * ld / kRedElems;
-        std::vector<int64_t> blk_lo;
-        std::vector<int32_t> blk_seg, seg_blk0(h->nsys), seg_nblk(h->nsys);
         for (int s = 0; s < h->nsys; ++s) {
             const int64_t c0 = h->sys[s].row0 * ld / kRedElems;
             const int64_t nc = h->sys[s].npad * ld / kRedElems;
@@ -276,13 +292,7 @@ static ams_status get_red(ams_handle h, int ld, RedCache** out, RedCache** out_s
             }
         }
         blk_lo.push_back(h->n_pad * ld);
-        RedCache rc;
-        AMS_TRY(build_red(h, ld, blk_lo, blk_seg, seg_blk0, seg_nblk, rc));
-        h->red[ld] = rc;
-    }
-    if (h->red_sub.find(ld) == h->red_sub.end()) {
-        std::vector<int64_t> blk_lo;
-        std::vector<int32_t> blk_seg, seg_blk0(h->nsys), seg_nblk(h->nsys);
+    } else {
         for (int s = 0; s < h->nsys; ++s) {
             const SystemHost& S = h->sys[s];
             int nb = (int)std::llround((double)target * (double)S.n / (double)std::max<int64_t>(1, h->n_total));
@@ -298,13 +308,19 @@ static ams_status get_red(ams_handle h, int ld, RedCache** out, RedCache** out_s
             }
         }
         blk_lo.push_back(h->N);
-        RedCache rc;
-        AMS_TRY(build_red(h, ld, blk_lo, blk_seg, seg_blk0, seg_nblk, rc));
-        h->red_sub[ld] = rc;
     }
-    *out = &h->red[ld];
-    if (out_sub) *out_sub = &h->red_sub[ld];
+    RedCache rc;
+    AMS_TRY(build_red(h, ld, blk_lo, blk_seg, seg_blk0, seg_nblk, rc));
+    cache[key] = rc;
+    *out = &cache[key];
     return AMS_OK;
+}
+
+// The layouts of the current launch shapes for ld.
+static ams_status get_red(ams_handle h, int ld, RedCache** out, RedCache** out_sub) {
+    const TuneCfg& T = h->tune[ld];
+    AMS_TRY(get_layout(h, ld, T.bps_elem, false, out));
+    return get_layout(h, ld, T.bps_sub, true, out_sub);
 }
 
 static RedLayout layout_of(const RedCache& rc) {
@@ -508,7 +524,8 @@ static ams_status setup_eigen(ams_handle h, const int64_t* d_rowptr, const int32
     }
     SubInfo* d_esubs = nullptr;
     AMS_TRY(upload(h, &d_esubs, esubs));
-    LocalSolveArgs la{h->stream, h->N, d_esubs, ResidIn{d_X, nullptr, nullptr}, d_S, P, h->cmax, 0, nullptr, false};
+    LocalSolveArgs la{h->stream, h->N, d_esubs, ResidIn{d_X, nullptr, nullptr}, d_S, P, h->cmax, 0, nullptr, false,
+                      0};
     const int maxit = h->opt.eig_maxit > 0 ? h->opt.eig_maxit : 300;
     const double tol = h->opt.eig_tol > 0 ? h->opt.eig_tol : 1e-13;
     std::vector<double> res(h->N);
@@ -1156,16 +1173,20 @@ static ams_status prof_flush(ams_handle h) {
 }
 
 // Fine-level local solves (+ restriction when the coarse space exists).
+static LocalTmaArgs local_tma_args(ams_handle h, int ld, const ResidIn& in, bool with_state) {
+    return LocalTmaArgs{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, in, ld, h->cmax,
+                        std::max(1, h->mmax), h->nbmax, int64_t(1) << 20, with_state ? h->d_st : nullptr,
+                        h->use_pdl, h->tune[ld].depth};
+}
+
 static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool with_state) {
     const bool coarse = h->Nc > 0;
     if (h->use_tma) {
-        LocalTmaArgs a{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, in, ld, h->cmax,
-                       std::max(1, h->mmax), h->nbmax, int64_t(1) << 20, with_state ? h->d_st : nullptr,
-                       h->use_pdl};
+        LocalTmaArgs a = local_tma_args(h, ld, in, with_state);
         AMS_CUDA_TRY(launch_local_tma(a, h->prec, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
     } else {
         LocalSolveArgs la{h->stream, h->N, h->d_subs, in, nullptr, ld, h->cmax, std::max(1, h->mmax),
-                          with_state ? h->d_st : nullptr, h->use_pdl};
+                          with_state ? h->d_st : nullptr, h->use_pdl, h->tune[ld].depth};
         AMS_CUDA_TRY(launch_local_solve(la, h->prec, h->d_fac, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
     }
     return AMS_OK;
@@ -1284,18 +1305,11 @@ static ams_status stage_in(ams_handle h, const double* src, int nrhs, double* ds
     return AMS_OK;
 }
 
-static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, double* u_dev, int32_t* iters,
-                      double* relres) {
-    const int ld = pow2ceil(nrhs);
-    AMS_TRY(ensure_work(h, ld));
-    RedCache *rc = nullptr, *rcs = nullptr;
-    AMS_TRY(get_red(h, ld, &rc, &rcs));
-    LaunchCtx L = make_ctx(h, *rc, *rcs);
-    // caller order -> internal rows (each system's block is contiguous in f)
-    for (int s = 0; s < h->nsys; ++s) {
-        const SystemHost& S = h->sys[s];
-        (void)S;
-    }
+// Internal state at the start of a solve: r = f (internal order), x = 0,
+// p = 0, ||f||^2, and the first preconditioner application (z, rho).
+static ams_status start_solve(ams_handle h, const LaunchCtx& L, const double* f_dev, int nrhs, int32_t maxit,
+                              double rtol2) {
+    const int ld = L.ld;
     if (h->nsys == 1) {
         launch_permute_in(h->stream, f_dev, h->n_total, nrhs, ld, h->d_int_row, h->d_r, h->d_x);
     } else {
@@ -1307,16 +1321,128 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
     }
     // the first iteration reads p_old = 0 (beta = 0)
     AMS_CUDA_TRY(cudaMemsetAsync(h->d_p, 0, sizeof(double) * h->n_pad * ld, h->stream));
-    {
-        SolveState init{};
-        init.maxit = h->opt.maxit;
-        init.rtol2 = rtol * rtol;
-        AMS_CUDA_TRY(cudaMemcpyAsync(h->d_st, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
-    }
+    SolveState init{};
+    init.maxit = maxit;
+    init.rtol2 = rtol2;
+    AMS_CUDA_TRY(cudaMemcpyAsync(h->d_st, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
     h->launches += 2 * h->nsys + 1;     // permutes in/out, norms
     launch_init_norms(L, h->d_r, nrhs);
     AMS_TRY(apply_precond(h, L, 1, nullptr));
     AMS_CUDA_TRY(cudaGetLastError());
+    return AMS_OK;
+}
+
+// Autotuning (opt.autotune): at the first solve with a given ld, time the
+// candidate launch shapes on the caller's right-hand side and keep the
+// fastest for this handle: blocks per SM of the element layout (direction
+// update + SpMV), the local-solve ring depth, and blocks per SM of the
+// subdomain layout (prolongation).  Each candidate runs once untimed, then
+// three times between CUDA events, inside a solve state that never
+// reports convergence; the real solve starts afresh afterwards.
+static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) {
+    TuneCfg& T = h->tune[ld];
+    struct Restore {                    // tuning launches are not part of a profiled solve
+        ams_handle h;
+        KernelProfile* prof;
+        int64_t launches;
+        ~Restore() {
+            h->prof = prof;
+            h->launches = launches;
+        }
+    } restore{h, h->prof, h->launches};
+    h->prof = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    AMS_CUDA_TRY(cudaEventCreate(&e0));
+    AMS_CUDA_TRY(cudaEventCreate(&e1));
+    std::unique_ptr<CUevent_st, decltype(&cudaEventDestroy)> g0(e0, cudaEventDestroy), g1(e1, cudaEventDestroy);
+    auto ctx = [&](LaunchCtx* L) -> ams_status {
+        RedCache *rc = nullptr, *rcs = nullptr;
+        AMS_TRY(get_red(h, ld, &rc, &rcs));
+        *L = make_ctx(h, *rc, *rcs);
+        return AMS_OK;
+    };
+    auto timed = [&](auto&& launch, float* ms) -> ams_status {
+        AMS_TRY(launch());
+        AMS_CUDA_TRY(cudaEventRecord(e0, h->stream));
+        for (int k = 0; k < 3; ++k) AMS_TRY(launch());
+        AMS_CUDA_TRY(cudaEventRecord(e1, h->stream));
+        AMS_CUDA_TRY(cudaEventSynchronize(e1));
+        AMS_CUDA_TRY(cudaGetLastError());
+        AMS_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+        return AMS_OK;
+    };
+    LaunchCtx L;
+    AMS_TRY(ctx(&L));
+    AMS_TRY(start_solve(h, L, f_dev, nrhs, 0x7fffffff, 0.0));
+    const int cand_bps[] = {3, 4, 6};
+    {   // element layout: direction update + SpMV
+        float best = 1e30f;
+        int arg = T.bps_elem;
+        for (int bps : cand_bps) {
+            T.bps_elem = bps;
+            AMS_TRY(ctx(&L));
+            float ms = 0.f;
+            AMS_TRY(timed([&]() -> ams_status { launch_direction_spmv(h, L, h->d_p, h->d_p2); return AMS_OK; }, &ms));
+            if (ms < best) {
+                best = ms;
+                arg = bps;
+            }
+        }
+        T.bps_elem = arg;
+    }
+    {   // local-solve ring depth, among the depths whose staging fits 200 KB
+        const ResidIn in{h->d_r, h->d_q, h->d_sc};
+        float best = 1e30f;
+        int arg = 0;
+        for (int d = 1; d <= 6; ++d) {
+            const size_t smem = h->use_tma ? local_tma_launch_smem(local_tma_args(h, ld, in, true), d)
+                                           : local_solve_smem(h->cmax, ld, h->tf_bytes(), d);
+            if (smem > 200 * 1024 || (h->use_tma && d < 2)) continue;
+            T.depth = d;
+            float ms = 0.f;
+            AMS_TRY(timed([&]() -> ams_status { return launch_local(h, ld, in, true); }, &ms));
+            if (ms < best) {
+                best = ms;
+                arg = d;
+            }
+        }
+        T.depth = arg;
+    }
+    {   // subdomain layout: prolongation (updates x and r of this throw-away state)
+        float best = 1e30f;
+        int arg = T.bps_sub;
+        for (int bps : cand_bps) {
+            T.bps_sub = bps;
+            AMS_TRY(ctx(&L));
+            float ms = 0.f;
+            AMS_TRY(timed([&]() -> ams_status {
+                launch_prolong_update(L, h->prec, prolong_args(h, 2, h->d_p2, ld));
+                return AMS_OK;
+            }, &ms));
+            if (ms < best) {
+                best = ms;
+                arg = bps;
+            }
+        }
+        T.bps_sub = arg;
+    }
+    T.done = true;
+    return AMS_OK;
+}
+
+static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, double* u_dev, int32_t* iters,
+                      double* relres) {
+    const int ld = pow2ceil(nrhs);
+    AMS_TRY(ensure_work(h, ld));
+    RedCache *rc = nullptr, *rcs = nullptr;
+    AMS_TRY(get_red(h, ld, &rc, &rcs));
+    LaunchCtx L = make_ctx(h, *rc, *rcs);
+    if (h->opt.autotune && !h->tune[ld].done) {
+        AMS_TRY(autotune(h, f_dev, nrhs, ld));
+        AMS_TRY(get_red(h, ld, &rc, &rcs));
+        L = make_ctx(h, *rc, *rcs);
+    }
+    AMS_TRY(start_solve(h, L, f_dev, nrhs, h->opt.maxit, rtol * rtol));
     AMS_TRY(prof_flush(h));
     cudaGraphExec_t graph = nullptr;
     if (!h->prof) AMS_TRY(get_iter_graph(h, L, &graph));

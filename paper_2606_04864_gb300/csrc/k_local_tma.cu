@@ -793,7 +793,7 @@ int local_tma_depth(int cmax, int ld) {
 template <typename TP, int NR, int MM>
 static cudaError_t tma_nr(const LocalTmaArgs& a, const void* psi, void* zf, void* rc) {
     const int warps = a.ld / NR;
-    const int depth = local_tma_depth(a.cmax, a.ld);
+    const int depth = a.depth > 0 ? a.depth : local_tma_depth(a.cmax, a.ld);
     const size_t smem = local_tma_smem(a.cmax, a.ld, depth);
     auto kern = k_local_tma<TP, NR, MM>;
     static size_t smem_set = 0;
@@ -843,7 +843,7 @@ static int local_tma1_depth(int cmax, int nbmax) {
 
 template <typename TP, int MM, bool C1>
 static cudaError_t tma1(const LocalTmaArgs& a, const void* psi, void* zf, void* rc) {
-    const int depth = local_tma1_depth(a.cmax, a.nbmax);
+    const int depth = a.depth > 0 ? a.depth : local_tma1_depth(a.cmax, a.nbmax);
     const size_t smem = local_tma1_smem(a.cmax, a.nbmax, depth);
     auto kern = k_local_tma1<TP, MM, C1>;
     static size_t smem_set = 0;
@@ -861,6 +861,10 @@ static cudaError_t tma1(const LocalTmaArgs& a, const void* psi, void* zf, void* 
 // memory; wider subdomains use the general kernel.
 static bool use_tma1(const LocalTmaArgs& a) {
     return a.ld == 1 && local_tma1_smem(a.cmax, a.nbmax, 2) <= 200 * 1024;
+}
+
+size_t local_tma_launch_smem(const LocalTmaArgs& a, int depth) {
+    return use_tma1(a) ? local_tma1_smem(a.cmax, a.nbmax, depth) : local_tma_smem(a.cmax, a.ld, depth);
 }
 
 cudaError_t launch_local_tma(const LocalTmaArgs& a, int prec, const void* psi, void* zf, void* rc) {

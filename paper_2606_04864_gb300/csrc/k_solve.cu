@@ -939,7 +939,7 @@ template <typename TF, typename TP, int NR, int MM>
 static cudaError_t local_nr(const LocalSolveArgs& a, const void* fac, const void* psi, void* zf,
                             void* rc) {
     const int warps = a.ld / NR;
-    const int depth = local_solve_depth(a.cmax, a.ld, sizeof(TF));
+    const int depth = a.depth > 0 ? a.depth : local_solve_depth(a.cmax, a.ld, sizeof(TF));
     const size_t smem = local_solve_smem(a.cmax, a.ld, sizeof(TF), depth);
     auto kern = k_local_solve<TF, TP, NR, MM>;
     static size_t smem_set = 0;           // per template instance

@@ -68,6 +68,7 @@ struct LocalSolveArgs {
     int mmax;
     const SolveState* st;
     bool pdl;
+    int depth;               // ring depth (block rows in flight); 0: chosen from the band width
 };
 
 struct LocalTmaArgs {
@@ -86,6 +87,7 @@ struct LocalTmaArgs {
     int64_t budget;
     SolveState* st;
     bool pdl;
+    int depth;               // ring depth (block rows in flight); 0: chosen from the band width
 };
 
 struct CoarseLaunch {
@@ -112,6 +114,8 @@ cudaError_t launch_local_solve(const LocalSolveArgs& a, int prec, const void* fa
 void launch_coarse_gemm(const CoarseLaunch& c, int prec, int ld, const void* in, void* out);
 cudaError_t launch_local_tma(const LocalTmaArgs& a, int prec, const void* psi, void* zf, void* rc);
 size_t local_tma_smem(int cmax, int ld, int depth);
+// Shared memory the TMA local-solve launch for `a` needs at ring depth `depth`.
+size_t local_tma_launch_smem(const LocalTmaArgs& a, int depth);
 cudaError_t make_tile_map(void* base, int64_t rows, struct CUtensorMap_st* out);
 void launch_band_pack_tiles(cudaStream_t s, int nwork, const SubInfo* subs, const int64_t* band_off,
                             const int2* work, const double* band, const int64_t* out_off, float* fwd, float* bwd,

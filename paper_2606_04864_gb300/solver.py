@@ -161,7 +161,7 @@ class AmsSolver(_Base):
 
     def __init__(self, rowptr, colind, vals, part, nparts: int, m: int, precision="fp32_bf16",
                  cg="auto", maxit=10000, device: bool = False, coarse=True, eig_shift=0.0,
-                 eig_maxit=0, eig_tol=0.0):
+                 eig_maxit=0, eig_tol=0.0, autotune=True):
         self.device = bool(device)
         conv = _as_dev if self.device else _as_host
         self._rowptr = conv(rowptr, np.int64)
@@ -172,7 +172,8 @@ class AmsSolver(_Base):
         self.nnz = int(self._colind.shape[0])
         self.nparts = int(nparts)
         self.nsys = 1
-        self.opts = make_options(precision, cg, maxit, self.device, coarse, eig_shift, eig_maxit, eig_tol)
+        self.opts = make_options(precision, cg, maxit, self.device, coarse, eig_shift, eig_maxit, eig_tol,
+                                 autotune)
         h = C.c_void_p()
         st = lib().ams_setup(self.n, _ptr(self._rowptr), _ptr(self._colind), _ptr(self._vals),
                              _ptr(self._part), self.nparts, int(m), C.byref(self.opts),
@@ -263,7 +264,7 @@ class AmsBatchedSolver(_Base):
     """
 
     def __init__(self, systems: Sequence, precision="fp32_bf16", cg="auto", maxit=10000,
-                 device: bool = False, coarse=True):
+                 device: bool = False, coarse=True, autotune=True):
         self.device = bool(device)
         conv = _as_dev if self.device else _as_host
         keep = []
@@ -279,7 +280,7 @@ class AmsBatchedSolver(_Base):
                                        int(nparts), int(m))
         self.n = int(sum(self.sizes))
         self.nsys = len(systems)
-        self.opts = make_options(precision, cg, maxit, self.device, coarse)
+        self.opts = make_options(precision, cg, maxit, self.device, coarse, autotune=autotune)
         h = C.c_void_p()
         st = lib().ams_setup_batched(self.nsys, descs, C.byref(self.opts), _stream_ptr(self.device),
                                      C.byref(h))

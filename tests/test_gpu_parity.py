@@ -276,3 +276,20 @@ def test_invalid_inputs_are_rejected():
     with pytest.raises(AmsError) as e:
         AmsSolver(w.rowptr, w.colind, ind, w.part, w.nparts, 2)
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_bf16"])
+def test_autotuned_launch_shapes_give_the_same_solve(prec):
+    """Launch shapes change block ranges and ring depths, not the arithmetic
+    of any row: an autotuned handle and one on the default shapes agree."""
+    w = make_small_2d(side=96, bs=16, m=4, std=2.0, sigma=3.0, seed=43, nrhs=3, rhs_kind="normal")
+    a = _solver(w, precision=prec, autotune=True)
+    b = _solver(w, precision=prec, autotune=False)
+    ua, ia, _ = a.solve(w.rhs, rtol=1e-8)
+    ub, ib, _ = b.solve(w.rhs, rtol=1e-8)
+    assert (np.abs(ia.astype(int) - ib.astype(int)) <= 2).all()
+    tol = 1e-10 if prec == "fp64" else 1e-6
+    assert np.linalg.norm(ua - ub) <= tol * np.linalg.norm(ub)
+    # a second solve reuses the tuned shapes
+    ua2, ia2, _ = a.solve(w.rhs, rtol=1e-8)
+    assert (ia2 == ia).all() and np.array_equal(ua2, ua)
