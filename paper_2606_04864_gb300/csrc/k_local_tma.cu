@@ -441,6 +441,31 @@ __device__ __forceinline__ void col_chunks(const float* T, const int (&csw)[8], 
     }
 }
 
+// Packed FP32 pairs (FFMA2, sm_100 and later): a 32-term dot product in
+// 16 two-wide fused multiply-adds on four independent accumulators.
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float pdot16(const float2 (&a)[16], const float* v) {
+    float2 s0 = make_float2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+        const float4 v0 = *reinterpret_cast<const float4*>(v + 4 * j);
+        const float4 v1 = *reinterpret_cast<const float4*>(v + 4 * j + 4);
+        s0 = __ffma2_rn(a[2 * j], lo2(v0), s0);
+        s1 = __ffma2_rn(a[2 * j + 1], hi2(v0), s1);
+        s2 = __ffma2_rn(a[2 * j + 2], lo2(v1), s2);
+        s3 = __ffma2_rn(a[2 * j + 3], hi2(v1), s3);
+    }
+    const float2 s = __fadd2_rn(__fadd2_rn(s0, s1), __fadd2_rn(s2, s3));
+    return s.x + s.y;
+}
+// Column `lane` of a swizzled tile as 16 row pairs (2i, 2i+1).
+__device__ __forceinline__ void col_pairs(const float* T, const int (&csw)[8], float2 (&c)[16]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        c[i] = make_float2(T[(2 * i) * 32 + csw[(2 * i) & 7]], T[(2 * i + 1) * 32 + csw[(2 * i + 1) & 7]]);
+}
+
 // Basis row of one subdomain row (m <= MM entries) as raw 16-byte words when
 // the row is 16-byte aligned and m == MM, element by element otherwise.
 template <typename TP, int MM>
@@ -497,25 +522,19 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     bool ok = true;
 
     // per-lane offsets and masks, fixed for the whole kernel
-    int rsw[8], csw[8], cdo[4];
-    float fhi[8], flo[8];
+    int rsw[8], csw[8];
+    float2 mk[16], mg[16];                           // 1 where index >= lane / index > lane, pairs (2i, 2i+1)
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         rsw[j] = lane * 32 + ((j ^ (lane & 7)) << 2);   // chunk j of tile row `lane`
         csw[j] = ((jr ^ j) << 2) + er;                 // element (r, lane) sits at r*32 + csw[r & 7]
-        fhi[j] = j > jr ? 1.f : 0.f;
-        flo[j] = j < jr ? 1.f : 0.f;
     }
-    const int dsw = rsw[0] ^ (jr << 2);              // chunk jr of tile row `lane`
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-        const int r = 4 * jr + e;
-        cdo[e] = r * 32 + ((jr ^ (r & 7)) << 2) + er;
+    for (int i = 0; i < 16; ++i) {
+        mk[i] = make_float2(2 * i >= lane ? 1.f : 0.f, 2 * i + 1 >= lane ? 1.f : 0.f);
+        mg[i] = make_float2(2 * i > lane ? 1.f : 0.f, 2 * i + 1 > lane ? 1.f : 0.f);
     }
-    const float4 dge = make_float4(0 >= er, 1 >= er, 2 >= er, 3 >= er);   // q >= lane inside chunk jr
-    const float4 dlt = make_float4(0 < er, 1 < er, 2 < er, 3 < er);
-    const float4 dle = make_float4(0 <= er, 1 <= er, 2 <= er, 3 <= er);
-    const float4 dgt = make_float4(0 > er, 1 > er, 2 > er, 3 > er);
+    const float2 neg1 = make_float2(-1.f, -1.f);
 
     if (lane == 0) {
         for (int i = 0; i < nbuf; ++i) mbar_init(smem_u32(bars + i), 1);
@@ -615,10 +634,17 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
         ok = __all_sync(0xffffffffu, ok);
         if (!ok) return;
         const float* T = tiles + sK * slot_floats;
-        float4 mr[8];
+        // row `lane` of M_K split exactly into its two triangles: mu (q >= lane,
+        // from L_{K,K-c}) and ml (q < lane, from L_KK^{-1})
+        float2 mu[16], ml[16];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) mr[j] = *reinterpret_cast<const float4*>(T + rsw[j]);
-        const float4 md = *reinterpret_cast<const float4*>(T + dsw);
+        for (int j = 0; j < 8; ++j) {
+            const float4 m4 = *reinterpret_cast<const float4*>(T + rsw[j]);
+            mu[2 * j] = __fmul2_rn(lo2(m4), mk[2 * j]);
+            mu[2 * j + 1] = __fmul2_rn(hi2(m4), mk[2 * j + 1]);
+            ml[2 * j] = __ffma2_rn(mu[2 * j], neg1, lo2(m4));
+            ml[2 * j + 1] = __ffma2_rn(mu[2 * j + 1], neg1, hi2(m4));
+        }
         // t = r_K - sum_d L_{K,K-c+d} y_{K-c+d}
         if (!C1) {
 #pragma unroll 1
@@ -626,32 +652,21 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
                 const int src = K - c + d;
                 if (src < 0) continue;
                 const float* Td = T + d * 1024;
-                const float* v = yv + src * 32;
-                float cj[8];
+                float2 dp[16];
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    cj[j] = dot4(*reinterpret_cast<const float4*>(Td + rsw[j]),
-                                 *reinterpret_cast<const float4*>(v + 4 * j));
-                t -= sum8(cj);
+                for (int j = 0; j < 8; ++j) {
+                    const float4 m4 = *reinterpret_cast<const float4*>(Td + rsw[j]);
+                    dp[2 * j] = lo2(m4);
+                    dp[2 * j + 1] = hi2(m4);
+                }
+                t -= pdot16(dp, yv + src * 32);
             }
         }
-        if (K >= c) {   // upper part of M_K (q >= lane) is L_{K,K-c}
-            const float* v = yv + (K - c) * 32;
-            float cj[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) cj[j] = dot4(mr[j], *reinterpret_cast<const float4*>(v + 4 * j));
-            t -= wsum8(fhi, cj) + dot4(mul4(md, dge), *reinterpret_cast<const float4*>(v + 4 * jr));
-        }
+        if (K >= c) t -= pdot16(mu, yv + (K - c) * 32);
         tmp[lane] = t;
         __syncwarp();
         // y_K = L_KK^{-1} t: pivot times t plus the strict lower part of M_K
-        float y;
-        {
-            float cj[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) cj[j] = dot4(mr[j], *reinterpret_cast<const float4*>(tmp + 4 * j));
-            y = fmaf(pvt, t, wsum8(flo, cj) + dot4(mul4(md, dlt), *reinterpret_cast<const float4*>(tmp + 4 * jr)));
-        }
+        const float y = fmaf(pvt, t, pdot16(ml, tmp));
         yv[K * 32 + lane] = y;
         sK = wrap_up(sK + 1);
         __syncwarp();
@@ -702,50 +717,41 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
             for (int d = 1; d < c; ++d) {
                 const int src = K + d;
                 if (src >= nb) break;
-                float cj[8];
-                col_chunks(tiles + wrap_up(sK + d) * slot_floats + (c - d) * 1024, csw, yv + src * 32, cj);
-                w -= sum8(cj);
+                float2 cp[16];
+                col_pairs(tiles + wrap_up(sK + d) * slot_floats + (c - d) * 1024, csw, cp);
+                w -= pdot16(cp, yv + src * 32);
             }
             if (K + c < nb) {   // L_{K+c,K}: upper part of M_{K+c}, rows r <= lane of column lane
                 const float* Tc = tiles + wrap_up(sK + c) * slot_floats;
                 const float* v = yv + (K + c) * 32;
-                float cj[8];
-                col_chunks(Tc, csw, v, cj);
-                const float4 ad = make_float4(Tc[cdo[0]], Tc[cdo[1]], Tc[cdo[2]], Tc[cdo[3]]);
-                w -= wsum8(flo, cj) + dot4(mul4(ad, dle), *reinterpret_cast<const float4*>(v + 4 * jr));
+                float2 cp[16], cl[16];
+                col_pairs(Tc, csw, cp);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) cl[i] = __ffma2_rn(__fmul2_rn(cp[i], mg[i]), neg1, cp[i]);
+                w -= pdot16(cl, v);
             }
         }
         tmp[lane] = w;
         __syncwarp();
-        // x_K = L_KK^{-T} w: rows r > lane of column lane of M_K
-        float a[32];
+        // x_K = L_KK^{-T} w: rows r > lane of column lane of M_K.  Column
+        // `lane` splits exactly into au (rows r > lane, from L_KK^{-1}) and
+        // al (rows r <= lane, from L_{K,K-c}).
+        float2 au[16], al[16];
+        col_pairs(Tm, csw, au);
 #pragma unroll
-        for (int r = 0; r < 32; ++r) a[r] = Tm[r * 32 + csw[r & 7]];
-        const float4 ad = make_float4(Tm[cdo[0]], Tm[cdo[1]], Tm[cdo[2]], Tm[cdo[3]]);
-        float x;
-        {
-            float cj[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float4 v = *reinterpret_cast<const float4*>(tmp + 4 * j);
-                cj[j] = fmaf(a[4 * j + 3], v.w, fmaf(a[4 * j + 2], v.z, fmaf(a[4 * j + 1], v.y, a[4 * j] * v.x)));
-            }
-            x = fmaf(pvt, w, wsum8(fhi, cj) + dot4(mul4(ad, dgt), *reinterpret_cast<const float4*>(tmp + 4 * jr)));
+        for (int i = 0; i < 16; ++i) {
+            const float2 a2 = au[i];
+            au[i] = __fmul2_rn(a2, mg[i]);
+            al[i] = __ffma2_rn(au[i], neg1, a2);
         }
+        const float x = fmaf(pvt, w, pdot16(au, tmp));
         yv[K * 32 + lane] = x;
         const int row = K * 32 + lane;
         if (row < n) zf[S.row0 + row] = x;
         __syncwarp();
         if (C1 && K > 0) {
             // term of step K-1: L_{K,K-1} is the upper part of M_K (rows r <= lane of column lane)
-            const float* v = yv + K * 32;
-            float cj[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float4 xv = *reinterpret_cast<const float4*>(v + 4 * j);
-                cj[j] = fmaf(a[4 * j + 3], xv.w, fmaf(a[4 * j + 2], xv.z, fmaf(a[4 * j + 1], xv.y, a[4 * j] * xv.x)));
-            }
-            ucarry = wsum8(flo, cj) + dot4(mul4(ad, dle), *reinterpret_cast<const float4*>(v + 4 * jr));
+            ucarry = pdot16(al, yv + K * 32);
         }
         sK = wrap_dn(sK - 1);
     };
