@@ -29,7 +29,7 @@ constexpr int kRedMaxNV = 4;           // values per right-hand side in one redu
 constexpr int kRedBlocksPerSM = 4;     // reduction-kernel grid: about this many blocks per SM
 constexpr int kMaxLd = 32;             // right-hand sides per solve call
 constexpr int kMaxM = 16;              // eigenvectors per subdomain (cap)
-constexpr int kCoarseChunk = 1024;     // node-matrix columns per coarse item
+constexpr int kCoarseChunk = 512;      // node-matrix columns per coarse item
 
 // ---- per-subdomain descriptor (device array) ------------------------------
 struct SubInfo {
