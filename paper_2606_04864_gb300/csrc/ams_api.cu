@@ -699,7 +699,7 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
     struct SysChunks { int64_t d0, d1; };
     std::vector<SysChunks> sys_chunks(h->nsys);
     auto add_items = [&](std::vector<CoarseItem>& items, int64_t moff, int64_t K, int64_t ldm, int64_t rows,
-                         int64_t out0, int32_t rng_off, int32_t nrng) {
+                         int64_t out0, int32_t rng_off, int32_t nrng, int64_t gat_off) {
         for (int64_t r0 = 0; r0 < rows; r0 += 32) {
             const int nr = (int)std::min<int64_t>(32, rows - r0);
             const int nch = (int)std::max<int64_t>(1, (K + KCHUNK - 1) / KCHUNK);
@@ -719,6 +719,7 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
                 it.nchunks = nch;
                 it.chunk = ch;
                 it.slot0 = slot;
+                it.gat_off = gat_off;
                 items.push_back(it);
             }
             if (nch > 1) slot += nch;
@@ -738,7 +739,7 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
             rng.push_back((int32_t)cst);
             rng.push_back((int32_t)Kf);
             const int64_t Kfp = (Kf + 3) & ~int64_t(3);
-            add_items(fwd, Roff, Kf, Kfp, nd.k, a, roff, 1);
+            add_items(fwd, Roff, Kf, Kfp, nd.k, a, roff, 1, -1);
             for (int64_t e0 = 0; e0 < nd.k * Kfp; e0 += ECHUNK) {
                 desc.insert(desc.end(), {Roff, Kf | (Kfp << 32), 0, nd.a, nd.cstart, (int64_t)roff, e0,
                                          std::min(nd.k * Kfp, e0 + ECHUNK)});
@@ -756,10 +757,10 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
                 ++nrng;
             }
             const int64_t Kbp = (Kb + 3) & ~int64_t(3);
-            add_items(bwd, Qoff, Kb, Kbp, nd.k, a, boff, nrng);
-            // fused backward substitution: gather list of the node's columns
-            // and the rows of each of its subdomains
+            // gather list of the node's columns (the backward items and the
+            // fused backward substitution read y through it)
             const int64_t goff = (int64_t)gat.size();
+            add_items(bwd, Qoff, Kb, Kbp, nd.k, a, boff, nrng, goff);
             for (int32_t r = 0; r < nrng; ++r) {
                 const int32_t st0 = rng[2 * (boff + r)], len = rng[2 * (boff + r) + 1];
                 for (int32_t i = 0; i < len; ++i) gat.push_back(st0 + i);
@@ -1201,11 +1202,11 @@ static bool fused_backward(int ld) { return ld <= 4; }
 // forward coarse substitution y = L_c^{-1} r_c, and the backward one when it
 // is not fused
 static int launch_coarse(ams_handle h, int ld, bool with_state) {
-    CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_partial, h->d_cnt,
+    CoarseLaunch cf{h->stream, h->nfwd, h->d_fwd, h->d_Rmat, h->d_rng, h->d_gat, h->d_partial, h->d_cnt,
                     with_state ? h->d_st : nullptr, h->use_pdl};
     launch_coarse_gemm(cf, h->prec, ld, h->d_rc, h->d_yc);
     if (fused_backward(ld)) return 1;
-    CoarseLaunch cb{h->stream, h->nbwd, h->d_bwd, h->d_Qmat, h->d_rng, h->d_partial, h->d_cnt,
+    CoarseLaunch cb{h->stream, h->nbwd, h->d_bwd, h->d_Qmat, h->d_rng, h->d_gat, h->d_partial, h->d_cnt,
                     with_state ? h->d_st : nullptr, h->use_pdl};
     launch_coarse_gemm(cb, h->prec, ld, h->d_yc, h->d_ec);
     return 2;

@@ -73,6 +73,7 @@ struct CoarseItem {
     int32_t nchunks;       // chunks of this tile
     int32_t chunk;         // this item's chunk
     int32_t slot0;         // first partial slot of this tile
+    int64_t gat_off;       // backward items: the node's column gather list (-1: one contiguous range)
 };
 
 // Backward coarse substitution, fused into the prolongation: the rows of

@@ -379,86 +379,110 @@ __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __rest
 template <typename TF, int LD>
 __global__ void __launch_bounds__(256)
 k_coarse_gemm(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
-              const int32_t* __restrict__ rng, const TF* __restrict__ in, TF* __restrict__ out,
-              TF* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
+              const int32_t* __restrict__ rng, const int32_t* __restrict__ gat, const TF* __restrict__ in,
+              TF* __restrict__ out, TF* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
+    // Many right-hand sides (LD >= 8): thread (h = t % LD, row group t / LD)
+    // accumulates RPT consecutive rows of the 32-row tile for right-hand side
+    // h.  Per stage of KC columns the tile (transposed, so one aligned load
+    // gives a thread its RPT rows at one column) and the gathered input go
+    // through shared memory; the next stage's global loads are issued into
+    // registers before the current stage is computed.
     pdl_wait();
     if (st != nullptr && st->done) return;
     pdl_trigger();
     using A = typename Acc<TF>::type;
+    using V4 = typename std::conditional<sizeof(TF) == 4, float4, double4>::type;
+    static_assert(LD >= 8 && LD <= 32, "k_coarse_gemm serves 8 to 32 right-hand sides");
     constexpr int KC = 64;                                   // columns per stage
     constexpr int OUT = 32 * LD;                             // outputs of a tile
-    constexpr int KG = OUT >= 256 ? 1 : 256 / OUT;           // k-groups (small LD)
-    constexpr int OPT = OUT >= 256 ? OUT / 256 : 1;          // outputs per thread
-    __shared__ TF sM[32][KC + 1];
+    constexpr int NRG = 256 / LD;                            // row groups
+    constexpr int RPT = 32 / NRG;                            // rows per thread (1, 2 or 4)
+    constexpr int TP = 32 + 4;                               // padded transposed row
+    constexpr int MV = 32 * KC / 4 / 256;                    // 4-column tile pieces per thread (2)
+    constexpr int XV = KC * LD / 256;                        // input values per thread
+    __shared__ __align__(32) TF sMT[KC][TP];
     __shared__ TF sX[KC][LD];
-    __shared__ A sRed[256];
     __shared__ int s_last;
     const CoarseItem it = items[blockIdx.x];
     const int t = threadIdx.x;
-    const int kg = t / (OUT >= 256 ? 256 : OUT);
-    const int o0 = t % (OUT >= 256 ? 256 : OUT);
-    A acc[OPT];
-#pragma unroll
-    for (int i = 0; i < OPT; ++i) acc[i] = A(0);
+    const int h = t % LD, r0 = (t / LD) * RPT;
     const TF* M0 = mat + it.moff + (int64_t)it.row_in_node * it.ldm;
-    for (int kb = it.k0; kb < it.k1; kb += KC) {
+    const int g0 = (it.gat_off < 0) ? rng[2 * it.rng_off] : 0;
+    const int32_t* G = gat + (it.gat_off < 0 ? 0 : it.gat_off);
+    V4 mreg[MV];
+    TF xreg[XV];
+    auto load_stage = [&](int kb) {
         const int kn = min(KC, it.k1 - kb);
-        for (int i = t; i < 32 * KC; i += 256) {
-            const int r = i / KC, kk = i % KC;
-            sM[r][kk] = (r < it.nrows && kk < kn) ? M0[(int64_t)r * it.ldm + kb + kk] : TF(0);
+#pragma unroll
+        for (int u = 0; u < MV; ++u) {
+            const int i = t + 256 * u;
+            const int r = i / (KC / 4), c4 = i % (KC / 4);
+            mreg[u] = V4{};
+            if (r < it.nrows && 4 * c4 < kn)
+                mreg[u] = *reinterpret_cast<const V4*>(M0 + (int64_t)r * it.ldm + kb + 4 * c4);
         }
-        for (int i = t; i < KC * LD; i += 256) {
-            const int kk = i / LD, h = i % LD;
-            TF v = TF(0);
+#pragma unroll
+        for (int u = 0; u < XV; ++u) {
+            const int i = t + 256 * u;
+            const int kk = i / LD, hh = i % LD;
+            xreg[u] = TF(0);
             if (kk < kn) {
-                int k = kb + kk, g = -1;
-                for (int j = 0; j < it.nrng; ++j) {
-                    const int s0 = rng[2 * (it.rng_off + j)], len = rng[2 * (it.rng_off + j) + 1];
-                    if (k < len) { g = s0 + k; break; }
-                    k -= len;
-                }
-                v = in[(int64_t)g * LD + h];
+                const int k = kb + kk;
+                const int g = (it.gat_off < 0) ? g0 + k : __ldg(G + k);
+                xreg[u] = in[(int64_t)g * LD + hh];
             }
-            sX[kk][h] = v;
         }
-        __syncthreads();
+    };
+    auto store_stage = [&]() {
 #pragma unroll
-        for (int i = 0; i < OPT; ++i) {
-            const int o = o0 + i * 256;
-            const int r = o / LD, h = o % LD;
-            A s = acc[i];
-            for (int kk = kg; kk < KC; kk += KG) s += (A)sM[r][kk] * (A)sX[kk][h];
-            acc[i] = s;
+        for (int u = 0; u < MV; ++u) {
+            const int i = t + 256 * u;
+            const int r = i / (KC / 4), c4 = i % (KC / 4);
+            sMT[4 * c4 + 0][r] = mreg[u].x;
+            sMT[4 * c4 + 1][r] = mreg[u].y;
+            sMT[4 * c4 + 2][r] = mreg[u].z;
+            sMT[4 * c4 + 3][r] = mreg[u].w;
         }
-        __syncthreads();
-    }
-    if (KG > 1) {
-        sRed[t] = acc[0];
-        __syncthreads();
-        if (t < OUT) {
-            A s = A(0);
-            for (int g = 0; g < KG; ++g) s += sRed[g * OUT + t];
-            acc[0] = s;
+#pragma unroll
+        for (int u = 0; u < XV; ++u) {
+            const int i = t + 256 * u;
+            sX[i / LD][i % LD] = xreg[u];
         }
+    };
+    A acc[RPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i) acc[i] = A(0);
+    load_stage(it.k0);
+    for (int kb = it.k0; kb < it.k1; kb += KC) {
+        __syncthreads();                     // the previous stage is no longer read
+        store_stage();
         __syncthreads();
+        if (kb + KC < it.k1) load_stage(kb + KC);
+#pragma unroll 8
+        for (int kk = 0; kk < KC; ++kk) {
+            const A x = (A)sX[kk][h];
+            if (RPT == 4) {
+                const V4 m = *reinterpret_cast<const V4*>(&sMT[kk][r0]);
+                acc[0] += (A)m.x * x;
+                acc[RPT > 1 ? 1 : 0] += (A)m.y * x;
+                acc[RPT > 2 ? 2 : 0] += (A)m.z * x;
+                acc[RPT > 3 ? 3 : 0] += (A)m.w * x;
+            } else {
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) acc[i] += (A)sMT[kk][r0 + i] * x;
+            }
+        }
     }
-    const bool owner = (KG > 1) ? (t < OUT) : true;
     if (it.nchunks == 1) {
-        if (owner) {
 #pragma unroll
-            for (int i = 0; i < OPT; ++i) {
-                const int o = o0 + i * 256;
-                const int r = o / LD, h = o % LD;
-                if (r < it.nrows) out[(int64_t)(it.out0 + r) * LD + h] = (TF)acc[i];
-            }
-        }
+        for (int i = 0; i < RPT; ++i)
+            if (r0 + i < it.nrows) out[(int64_t)(it.out0 + r0 + i) * LD + h] = (TF)acc[i];
         return;
     }
     TF* P = partial + (int64_t)(it.slot0 + it.chunk) * OUT;
-    if (owner) {
 #pragma unroll
-        for (int i = 0; i < OPT; ++i) P[o0 + i * 256] = (TF)acc[i];
-    }
+    for (int i = 0; i < RPT; ++i) P[(r0 + i) * LD + h] = (TF)acc[i];
+
     __syncthreads();
     if (t == 0) {
         __threadfence();
@@ -470,8 +494,8 @@ k_coarse_gemm(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
     for (int o = t; o < OUT; o += 256) {
         A s = A(0);
         for (int ch = 0; ch < it.nchunks; ++ch) s += (A)__ldcg(partial + (int64_t)(it.slot0 + ch) * OUT + o);
-        const int r = o / LD, h = o % LD;
-        if (r < it.nrows) out[(int64_t)(it.out0 + r) * LD + h] = (TF)s;
+        const int rr = o / LD, hh = o % LD;
+        if (rr < it.nrows) out[(int64_t)(it.out0 + rr) * LD + hh] = (TF)s;
     }
     if (t == 0) cnt[it.tile_id] = 0;
 }
@@ -986,8 +1010,9 @@ static void coarse_ld(const CoarseLaunch& c, const void* in, void* out) {
         launch_kernel(c.pdl, k_coarse_rows<TF, (LD <= 4 ? LD : 4)>, dim3(c.nitems), dim3(256), 0, c.stream, c.items,
                       (const TF*)c.mat, c.rng, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt, c.st);
     else
-        launch_kernel(c.pdl, k_coarse_gemm<TF, LD>, dim3(c.nitems), dim3(256), 0, c.stream, c.items,
-                      (const TF*)c.mat, c.rng, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt, c.st);
+        launch_kernel(c.pdl, k_coarse_gemm<TF, (LD >= 8 ? LD : 8)>, dim3(c.nitems), dim3(256), 0, c.stream,
+                      c.items, (const TF*)c.mat, c.rng, c.gat, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt,
+                      c.st);
 }
 template <typename TF>
 static void coarse_tf(const CoarseLaunch& c, int ld, const void* in, void* out) {

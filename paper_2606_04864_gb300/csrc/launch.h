@@ -96,6 +96,7 @@ struct CoarseLaunch {
     const CoarseItem* items;
     const void* mat;
     const int32_t* rng;
+    const int32_t* gat;      // per-node column gather lists (backward items)
     void* partial;
     int32_t* cnt;
     const SolveState* st;
