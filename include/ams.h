@@ -78,8 +78,10 @@ typedef struct {
     int32_t autotune;            /* 1 (default): at the first solve with a given
                                     number of right-hand sides, time candidate
                                     launch shapes (blocks per SM of the SpMV and
-                                    prolongation grids, local-solve ring depth)
-                                    on that right-hand side and keep the fastest */
+                                    prolongation grids, local-solve ring depth,
+                                    right-hand sides per warp of the several-RHS
+                                    local solve) on that right-hand side and keep
+                                    the fastest */
     int32_t coarse;              /* 1: two-level (default); 0: local solves only */
     double eig_shift;            /* shift sigma of the local eigensolver; 0 = default 1e-2 */
     int32_t eig_maxit;           /* local eigensolver iteration cap; 0 = default 300 */

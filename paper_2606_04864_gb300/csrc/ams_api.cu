@@ -67,6 +67,7 @@ struct TuneCfg {
     int bps_elem = kRedBlocksPerSM;     // element-layout blocks per SM (direction update, SpMV)
     int bps_sub = kRedBlocksPerSM;      // subdomain-layout blocks per SM (prolongation)
     int depth = 0;                      // local-solve ring depth; 0: chosen from the band width
+    int nr = 0;                         // several-RHS local solve: right-hand sides per warp; 0: default
     bool done = false;                  // autotuned
 };
 
@@ -1177,7 +1178,7 @@ static ams_status prof_flush(ams_handle h) {
 static LocalTmaArgs local_tma_args(ams_handle h, int ld, const ResidIn& in, bool with_state) {
     return LocalTmaArgs{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, in, ld, h->cmax,
                         std::max(1, h->mmax), h->nbmax, int64_t(1) << 20, with_state ? h->d_st : nullptr,
-                        h->use_pdl, h->tune[ld].depth};
+                        h->use_pdl, h->tune[ld].depth, h->tune[ld].nr};
 }
 
 static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool with_state) {
@@ -1408,6 +1409,22 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
             }
         }
         T.depth = arg;
+    }
+    if (h->use_tma && ld > 1) {   // several-RHS local solve: right-hand sides per warp
+        const ResidIn in{h->d_r, h->d_q, h->d_sc};
+        float best = 1e30f;
+        int arg = 0;
+        for (int nr = 8; nr >= 2; nr /= 2) {
+            if (nr > ld || ld / nr > 8) continue;    // at most 8 warps per block
+            T.nr = nr;
+            float ms = 0.f;
+            AMS_TRY(timed([&]() -> ams_status { return launch_local(h, ld, in, true); }, &ms));
+            if (ms < best) {
+                best = ms;
+                arg = nr;
+            }
+        }
+        T.nr = arg;
     }
     {   // subdomain layout: prolongation (updates x and r of this throw-away state)
         float best = 1e30f;

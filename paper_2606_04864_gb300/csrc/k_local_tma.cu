@@ -817,7 +817,9 @@ template <typename TP>
 static cudaError_t tma_tp(const LocalTmaArgs& a, const void* psi, void* zf, void* rc) {
     const bool big = a.mmax > 8;
     const int nrmax = big ? 4 : 8;
-    const int nr = a.ld < nrmax ? a.ld : nrmax;
+    int nr = a.ld < nrmax ? a.ld : nrmax;
+    // fewer right-hand sides per warp: more warps per block (at most 8, the kernel's launch bound)
+    if (a.nr > 0 && a.nr < nr && a.ld / a.nr <= 8) nr = a.nr;
     if (big) {
         switch (nr) {
             case 1: return tma_nr<TP, 1, 16>(a, psi, zf, rc);

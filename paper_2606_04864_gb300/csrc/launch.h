@@ -88,6 +88,7 @@ struct LocalTmaArgs {
     SolveState* st;
     bool pdl;
     int depth;               // ring depth (block rows in flight); 0: chosen from the band width
+    int nr;                  // several-RHS kernel: right-hand sides per warp (1, 2, 4, 8); 0: default
 };
 
 struct CoarseLaunch {
