@@ -74,6 +74,27 @@ __device__ __forceinline__ unsigned char* smem_align1024(unsigned char* p) {
     return p + ((1024u - (smem_u32(p) & 1023u)) & 1023u);
 }
 
+// Row stride (floats) of the y/x ring of the several-RHS kernel: ld + 4 for
+// ld >= 2 (conflict-free per-lane row stores, 16-byte aligned rows); one
+// right-hand side keeps a contiguous vector.
+__host__ __device__ __forceinline__ int local_tma_row_stride(int ld) { return ld >= 2 ? ld + 4 : 1; }
+
+// NR consecutive floats of one ring row (16-byte stores when NR % 4 == 0:
+// eight lanes of a quarter warp then cover all 32 banks).
+template <int NR>
+__device__ __forceinline__ void store_row(float* p, const float (&v)[NR]) {
+    if (NR % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < NR; k += 4)
+            *reinterpret_cast<float4*>(p + k) = make_float4(v[k], v[(k + 1) % NR], v[(k + 2) % NR], v[(k + 3) % NR]);
+    } else if (NR == 2) {
+        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1 % NR]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) p[j] = v[j];
+    }
+}
+
 // Row r of a swizzled 32x32 FP32 tile: 16-byte chunk j (columns 4j..4j+3).
 __device__ __forceinline__ float4 tile_chunk(const float* tile, int r, int j) {
     return *reinterpret_cast<const float4*>(tile + r * 32 + ((j ^ (r & 7)) << 2));
@@ -156,8 +177,12 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
     const int nbuf = cmax + D + 1;
     float* tiles = (float*)base;                                        // nbuf * cmax * 1024
     uint64_t* bars = (uint64_t*)(tiles + (size_t)nbuf * cmax * 1024);    // nbuf (padded to even)
-    float* ring = (float*)(bars + ((nbuf + 1) & ~1));                    // (cmax+1)*32*ld
-    float* tmp = ring + (size_t)(cmax + 1) * 32 * ld;                    // 32*ld
+    // y/x ring and scratch: rows of lds = ld + 4 floats, so that the 32 lanes
+    // storing their own rows hit distinct banks (a row stride of ld floats
+    // put every lane on the same bank) while rows stay 16-byte aligned
+    const int lds = local_tma_row_stride(ld);
+    float* ring = (float*)(bars + ((nbuf + 1) & ~1));                    // (cmax+1)*32*lds
+    float* tmp = ring + (size_t)(cmax + 1) * 32 * lds;                   // 32*lds
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rhs0 = warp * NR;
     const int m = S.m;
@@ -275,20 +300,18 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
         for (int d = 0; d < c; ++d) {
             const int src = K - c + d;
             if (src < 0) continue;
-            const float* ys = ring + (size_t)(src % (c + 1)) * 32 * ld;
-            if (d == 0) tile_rowdot<NR, 1>(slot_tile(K, d), lane, ys, ld, rhs0, -1.f, t);
-            else tile_rowdot<NR, 0>(slot_tile(K, d), lane, ys, ld, rhs0, -1.f, t);
+            const float* ys = ring + (size_t)(src % (c + 1)) * 32 * lds;
+            if (d == 0) tile_rowdot<NR, 1>(slot_tile(K, d), lane, ys, lds, rhs0, -1.f, t);
+            else tile_rowdot<NR, 0>(slot_tile(K, d), lane, ys, lds, rhs0, -1.f, t);
         }
-#pragma unroll
-        for (int j = 0; j < NR; ++j) tmp[lane * ld + rhs0 + j] = t[j];
+        store_row<NR>(tmp + lane * lds + rhs0, t);
         __syncwarp();
         float y[NR];
 #pragma unroll
         for (int j = 0; j < NR; ++j) y[j] = pvt * t[j];
-        tile_rowdot<NR, 2>(slot_tile(K, 0), lane, tmp, ld, rhs0, 1.f, y);
-        float* yr = ring + (size_t)(K % (c + 1)) * 32 * ld;
-#pragma unroll
-        for (int j = 0; j < NR; ++j) yr[lane * ld + rhs0 + j] = y[j];
+        tile_rowdot<NR, 2>(slot_tile(K, 0), lane, tmp, lds, rhs0, 1.f, y);
+        float* yr = ring + (size_t)(K % (c + 1)) * 32 * lds;
+        store_row<NR>(yr + lane * lds + rhs0, y);
         if (valid) {
 #pragma unroll
             for (int j = 0; j < NR; ++j) zf[grow * ld + rhs0 + j] = y[j];
@@ -346,23 +369,21 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
         for (int d = 1; d <= c; ++d) {
             const int src = K + d;
             if (src >= nb) break;
-            const float* xs = ring + (size_t)(src % (c + 1)) * 32 * ld;
+            const float* xs = ring + (size_t)(src % (c + 1)) * 32 * lds;
             // transposed tile of L_{K+d,K}: dense tile c-d of block row K+d,
             // or (d == c) the upper part of M_{K+c} (rows r <= lane of M^T)
-            if (d < c) tile_rowdot<NR, 0>(slot_tile(src, c - d), lane, xs, ld, rhs0, -1.f, w);
-            else tile_rowdot<NR, 3>(slot_tile(src, 0), lane, xs, ld, rhs0, -1.f, w);
+            if (d < c) tile_rowdot<NR, 0>(slot_tile(src, c - d), lane, xs, lds, rhs0, -1.f, w);
+            else tile_rowdot<NR, 3>(slot_tile(src, 0), lane, xs, lds, rhs0, -1.f, w);
         }
-#pragma unroll
-        for (int j = 0; j < NR; ++j) tmp[lane * ld + rhs0 + j] = w[j];
+        store_row<NR>(tmp + lane * lds + rhs0, w);
         __syncwarp();
         float x[NR];
 #pragma unroll
         for (int j = 0; j < NR; ++j) x[j] = pvt * w[j];
         // L_KK^{-T}: strict lower part of M_K read as row `lane` of M_K^T (r > lane)
-        tile_rowdot<NR, 4>(slot_tile(K, 0), lane, tmp, ld, rhs0, 1.f, x);
-        float* xr = ring + (size_t)(K % (c + 1)) * 32 * ld;
-#pragma unroll
-        for (int j = 0; j < NR; ++j) xr[lane * ld + rhs0 + j] = x[j];
+        tile_rowdot<NR, 4>(slot_tile(K, 0), lane, tmp, lds, rhs0, 1.f, x);
+        float* xr = ring + (size_t)(K % (c + 1)) * 32 * lds;
+        store_row<NR>(xr + lane * lds + rhs0, x);
         if (valid) {
 #pragma unroll
             for (int j = 0; j < NR; ++j) zf[grow * ld + rhs0 + j] = x[j];
@@ -781,8 +802,9 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
 // ---------------------------------------------------------------------------
 size_t local_tma_smem(int cmax, int ld, int depth) {
     const int nbuf = cmax + depth + 1;
+    const int lds = local_tma_row_stride(ld);
     return 1024 /* alignment slack */ + (size_t)nbuf * cmax * 4096 + (size_t)((nbuf + 1) & ~1) * 8 +
-           ((size_t)(cmax + 1) * 32 * ld + 32 * ld) * sizeof(float);
+           ((size_t)(cmax + 1) * 32 * lds + 32 * lds) * sizeof(float);
 }
 
 // Prefetch depth: block rows in flight per subdomain.  Deeper rings hide

@@ -293,3 +293,27 @@ def test_autotuned_launch_shapes_give_the_same_solve(prec):
     # a second solve reuses the tuned shapes
     ua2, ia2, _ = a.solve(w.rhs, rtol=1e-8)
     assert (ia2 == ia).all() and np.array_equal(ua2, ua)
+
+
+def test_profile_and_time_kernel_report_every_slot():
+    """ams_profile_solve times every kernel slot of a real solve (one launch
+    per slot and iteration, plus the first application), and ams_time_kernel
+    times each slot on the solve state; both report the slot's algorithmic
+    bytes."""
+    from paper_2606_04864_gb300._lib import AMS_NUM_KERNELS, KERNEL_NAMES
+    w = make_small_2d(side=64, bs=8, m=4, std=2.0, seed=44)
+    s = _solver(w, precision="fp32_bf16")
+    u, its, _ = s.solve(w.rhs[0], rtol=1e-8)
+    prof = s.profile_solve(w.rhs[0], rtol=1e-8)
+    assert [p["name"] for p in prof] == KERNEL_NAMES and len(prof) == AMS_NUM_KERNELS
+    n_it = int(its[0])
+    for k, p in enumerate(prof):
+        # the direction slot runs once per iteration, the others also once for
+        # z_0; iterations are launched in chunks, and launches after
+        # convergence (at most one chunk of 64) return at once but are timed
+        expect = n_it if k == 0 else n_it + 1
+        assert expect <= p["count"] <= expect + 66, (p["name"], p["count"], expect)
+        assert p["ms"] > 0 and p["bytes"] > 0
+    for k in range(AMS_NUM_KERNELS):
+        ms, by = s.time_kernel(k, 3)
+        assert ms > 0 and by > 0
