@@ -236,11 +236,15 @@ def run_gpu(args):
                       device=True)
     info = mixed.info()
     stream = torch.cuda.current_stream()
+    if args.launch_shape:
+        mixed.set_launch_shape(w.nrhs, **dict(zip(("bps_elem", "bps_sub", "depth", "nr", "l2mode", "l2keep"),
+                                                  (int(v) for v in args.launch_shape.split(",")))))
 
     # warm-up
     for _ in range(args.warmup):
         u, its, rel = mixed.solve(f_dev, rtol=1e-8)
     launches0 = mixed.info()["kernel_launches"]
+    shape = mixed.launch_shape(w.nrhs)
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -258,6 +262,21 @@ def run_gpu(args):
     A = csr_matrix((w.vals, w.colind, w.rowptr), shape=(w.n, w.n))
     true_rel = max(float(np.linalg.norm(w.rhs[k] - A @ u_np[k]) / np.linalg.norm(w.rhs[k]))
                    for k in range(w.nrhs))
+
+    # adjoint (a8), outside the timed region: for L = |u|^2 / 2, dL/du = u;
+    # lambda = A^{-1} u by the same preconditioned CG, then dL/dA on A's pattern
+    lam, dv, its_adj = mixed.solve_adjoint(u, u, rtol=1e-8)
+    torch.cuda.synchronize()
+    ea0 = torch.cuda.Event(enable_timing=True)
+    ea1 = torch.cuda.Event(enable_timing=True)
+    nadj = max(1, min(args.steps, 3))
+    ea0.record(stream)
+    for _ in range(nadj):
+        lam, dv, its_adj = mixed.solve_adjoint(u, u, rtol=1e-8)
+    ea1.record(stream)
+    torch.cuda.synchronize()
+    adjoint = {"time_s": ea0.elapsed_time(ea1) / nadj / 1e3, "iters": int(np.max(its_adj)),
+               "loss": "L = |u|^2/2 (g = u); lambda = A^-1 g, dL/dA_ij = -lambda_i u_j on A's pattern"}
 
     # per-kernel device times measured inside a real solve: the library
     # records a CUDA event pair around every kernel on its stream during one
@@ -343,6 +362,8 @@ def run_gpu(args):
                 "fp64": {"time_s": ms64 / 1e3, "iters": int(its64.max()),
                          "setup_s": round(info64["setup_seconds"], 3)},
                 "mixed_speedup_vs_fp64": ms64 / ms_max if ms_max > 0 else None,
+                "adjoint": adjoint,
+                "launch_shape": {**shape, "source": "--launch-shape" if args.launch_shape else "autotuned"},
                 "u_rel_diff_mixed_vs_fp64": rel_mixed_vs_fp64,
                 "iteration_ms": it_ms, "iteration_gbs": iter_bytes / (it_ms * 1e-3) / 1e9,
                 "kernels": {n: {"ms_per_launch": round(v["ms"], 5), "launches": v["launches"],
@@ -383,6 +404,11 @@ def main():
     ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg5"],
                     help="cfg2 (default, the headline line): 1024^2 channels; cfg3: 128^3 with 32 "
                          "right-hand sides; cfg5: 96^3 single right-hand side")
+    ap.add_argument("--launch-shape", default="",
+                    help="fix the mixed solver's launch shapes instead of autotuning them: "
+                         "bps_elem,bps_sub,depth,nr,l2mode,l2keep (as reported in config.launch_shape); for "
+                         "profiling one configuration under ncu, where autotuning timings are "
+                         "distorted by the replays")
     ap.add_argument("--ref-crop", type=int, default=256, help="oracle sample: crop side (cells)")
     ap.add_argument("--ref-iters", type=int, default=0,
                     help="oracle sample: iteration count of the full solve (0: the crop's own count)")

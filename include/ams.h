@@ -80,8 +80,9 @@ typedef struct {
                                     launch shapes (blocks per SM of the SpMV and
                                     prolongation grids, local-solve ring depth,
                                     right-hand sides per warp of the several-RHS
-                                    local solve) on that right-hand side and keep
-                                    the fastest */
+                                    local solve, L2 priorities of the one-RHS
+                                    local solve's tile copies) on that right-hand
+                                    side and keep the fastest */
     int32_t coarse;              /* 1: two-level (default); 0: local solves only */
     double eig_shift;            /* shift sigma of the local eigensolver; 0 = default 1e-2 */
     int32_t eig_maxit;           /* local eigensolver iteration cap; 0 = default 300 */
@@ -229,6 +230,33 @@ typedef struct {
 } ams_info;
 
 ams_status ams_get_info(ams_handle h, ams_info* info);
+
+/*
+ * Launch shapes of the solve kernels for solves with nrhs right-hand sides
+ * (1 <= nrhs <= 32; shapes are kept per nrhs rounded up to a power of two).
+ * shape[0]  blocks per SM of the element-layout grids (direction update, SpMV)
+ * shape[1]  blocks per SM of the subdomain-layout grid (prolongation)
+ * shape[2]  local-solve ring depth in band tiles; 0 = derived from the band width
+ * shape[3]  right-hand sides per warp of the several-RHS local solve; 0 = default
+ * shape[4]  L2 priorities of the one-RHS local solve's factor-tile copies:
+ *           0 none (default); 1 evict-first on copies that read a block row
+ *           for the last time; 2 as 1, plus evict-last on the kept copies
+ * shape[5]  kept copies: the forward loads of this many block rows below
+ *           the ones that stay in the staging ring (the rows the backward
+ *           sweep reloads soonest) are not marked evict-first
+ * shape[6]  (get only) 1 once the shapes are fixed, by the autotuner or by
+ *           ams_set_launch_shape; 0 while they are the defaults
+ * ams_get_launch_shape writes 7 entries to host memory.  ams_set_launch_shape
+ * reads shape[0..5], fixes them (the autotuner then leaves this count alone)
+ * and drops the iteration graph captured with the previous shapes; call it
+ * between solves.  Errors: AMS_ERR_INVALID_ARG (NULL, nrhs out of range,
+ * blocks per SM outside 1..8, depth outside 0..6, below 2 with TMA staging or
+ * needing more than 200 KB of shared memory, right-hand sides per warp not
+ * 0/2/4/8, above the rounded count or leaving more than 8 warps per block,
+ * L2 mode outside 0..2, negative kept rows).
+ */
+ams_status ams_get_launch_shape(ams_handle h, int32_t nrhs, int32_t* shape);
+ams_status ams_set_launch_shape(ams_handle h, int32_t nrhs, const int32_t* shape);
 
 /*
  * Index maps (Section 3.1): perm[k] = global dof at position k of the

@@ -68,6 +68,8 @@ struct TuneCfg {
     int bps_sub = kRedBlocksPerSM;      // subdomain-layout blocks per SM (prolongation)
     int depth = 0;                      // local-solve ring depth; 0: chosen from the band width
     int nr = 0;                         // several-RHS local solve: right-hand sides per warp; 0: default
+    int l2mode = 0;                     // one-RHS local solve: L2 priorities of the factor tiles (0 none)
+    int l2keep = 0;                     // block rows whose forward load keeps its L2 priority
     bool done = false;                  // autotuned
 };
 
@@ -1178,7 +1180,7 @@ static ams_status prof_flush(ams_handle h) {
 static LocalTmaArgs local_tma_args(ams_handle h, int ld, const ResidIn& in, bool with_state) {
     return LocalTmaArgs{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, in, ld, h->cmax,
                         std::max(1, h->mmax), h->nbmax, int64_t(1) << 20, with_state ? h->d_st : nullptr,
-                        h->use_pdl, h->tune[ld].depth, h->tune[ld].nr};
+                        h->use_pdl, h->tune[ld].depth, h->tune[ld].nr, h->tune[ld].l2mode, h->tune[ld].l2keep};
 }
 
 static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool with_state) {
@@ -1373,6 +1375,38 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
         AMS_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
         return AMS_OK;
     };
+    // Local-solve candidates are timed each right after an SpMV, as they run
+    // in a solve: the SpMV streams the matrix through L2, so a candidate finds
+    // there what it finds inside an iteration (back-to-back launches of one
+    // kernel would find part of their own factor tiles and favour deep rings).
+    cudaEvent_t ev[6] = {};
+    struct Events {
+        cudaEvent_t* e;
+        ~Events() {
+            for (int k = 0; k < 6; ++k)
+                if (e[k]) cudaEventDestroy(e[k]);
+        }
+    } ev_guard{ev};
+    for (auto& e : ev) AMS_CUDA_TRY(cudaEventCreate(&e));
+    auto timed_after = [&](auto&& pre, auto&& launch, float* ms) -> ams_status {
+        AMS_TRY(pre());
+        AMS_TRY(launch());
+        for (int k = 0; k < 3; ++k) {
+            AMS_TRY(pre());
+            AMS_CUDA_TRY(cudaEventRecord(ev[2 * k], h->stream));
+            AMS_TRY(launch());
+            AMS_CUDA_TRY(cudaEventRecord(ev[2 * k + 1], h->stream));
+        }
+        AMS_CUDA_TRY(cudaEventSynchronize(ev[5]));
+        AMS_CUDA_TRY(cudaGetLastError());
+        *ms = 0.f;
+        for (int k = 0; k < 3; ++k) {
+            float t = 0.f;
+            AMS_CUDA_TRY(cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]));
+            *ms += t;
+        }
+        return AMS_OK;
+    };
     LaunchCtx L;
     AMS_TRY(ctx(&L));
     AMS_TRY(start_solve(h, L, f_dev, nrhs, 0x7fffffff, 0.0));
@@ -1391,7 +1425,12 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
             }
         }
         T.bps_elem = arg;
+        AMS_TRY(ctx(&L));
     }
+    auto spmv = [&]() -> ams_status {
+        launch_direction_spmv(h, L, h->d_p, h->d_p2);
+        return AMS_OK;
+    };
     {   // local-solve ring depth, among the depths whose staging fits 200 KB
         const ResidIn in{h->d_r, h->d_q, h->d_sc};
         float best = 1e30f;
@@ -1402,13 +1441,31 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
             if (smem > 200 * 1024 || (h->use_tma && d < 2)) continue;
             T.depth = d;
             float ms = 0.f;
-            AMS_TRY(timed([&]() -> ams_status { return launch_local(h, ld, in, true); }, &ms));
+            AMS_TRY(timed_after(spmv, [&]() -> ams_status { return launch_local(h, ld, in, true); }, &ms));
             if (ms < best) {
                 best = ms;
                 arg = d;
             }
         }
         T.depth = arg;
+    }
+    if (h->use_tma && ld == 1) {   // one-RHS local solve: L2 priorities of the factor tiles
+        const ResidIn in{h->d_r, h->d_q, h->d_sc};
+        const int cand[][2] = {{0, 0}, {1, 4}, {1, 8}, {1, 16}, {1, 1 << 20}, {2, 4}, {2, 8}, {2, 16}};
+        float best = 1e30f;
+        int arg = 0;
+        for (int i = 0; i < (int)(sizeof(cand) / sizeof(cand[0])); ++i) {
+            T.l2mode = cand[i][0];
+            T.l2keep = cand[i][1];
+            float ms = 0.f;
+            AMS_TRY(timed_after(spmv, [&]() -> ams_status { return launch_local(h, ld, in, true); }, &ms));
+            if (ms < best) {
+                best = ms;
+                arg = i;
+            }
+        }
+        T.l2mode = cand[arg][0];
+        T.l2keep = cand[arg][1];
     }
     if (h->use_tma && ld > 1) {   // several-RHS local solve: right-hand sides per warp
         const ResidIn in{h->d_r, h->d_q, h->d_sc};
@@ -1418,7 +1475,7 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
             if (nr > ld || ld / nr > 8) continue;    // at most 8 warps per block
             T.nr = nr;
             float ms = 0.f;
-            AMS_TRY(timed([&]() -> ams_status { return launch_local(h, ld, in, true); }, &ms));
+            AMS_TRY(timed_after(spmv, [&]() -> ams_status { return launch_local(h, ld, in, true); }, &ms));
             if (ms < best) {
                 best = ms;
                 arg = nr;
@@ -1729,6 +1786,71 @@ ams_status ams_get_info(ams_handle h, ams_info* info) {
     }
     *info = h->info;
     info->kernel_launches = h->launches;
+    return AMS_OK;
+}
+
+ams_status ams_get_launch_shape(ams_handle h, int32_t nrhs, int32_t* shape) {
+    if (!h || !shape || nrhs < 1 || nrhs > kMaxLd) {
+        set_error("null argument or nrhs outside [1, 32]");
+        return AMS_ERR_INVALID_ARG;
+    }
+    const TuneCfg& T = h->tune[pow2ceil(nrhs)];
+    shape[0] = T.bps_elem;
+    shape[1] = T.bps_sub;
+    shape[2] = T.depth;
+    shape[3] = T.nr;
+    shape[4] = T.l2mode;
+    shape[5] = T.l2keep;
+    shape[6] = T.done ? 1 : 0;
+    return AMS_OK;
+}
+
+ams_status ams_set_launch_shape(ams_handle h, int32_t nrhs, const int32_t* shape) {
+    if (!h || !shape || nrhs < 1 || nrhs > kMaxLd) {
+        set_error("null argument or nrhs outside [1, 32]");
+        return AMS_ERR_INVALID_ARG;
+    }
+    const int ld = pow2ceil(nrhs);
+    const int bps_e = shape[0], bps_s = shape[1], depth = shape[2], nr = shape[3];
+    const int l2mode = shape[4], l2keep = shape[5];
+    if (bps_e < 1 || bps_e > 8 || bps_s < 1 || bps_s > 8) {
+        set_error("blocks per SM must be in [1, 8]");
+        return AMS_ERR_INVALID_ARG;
+    }
+    if (depth < 0 || depth > 6) {
+        set_error("ring depth must be in [0, 6]");
+        return AMS_ERR_INVALID_ARG;
+    }
+    if (depth > 0) {
+        const ResidIn in{nullptr, nullptr, nullptr};
+        const size_t smem = h->use_tma ? local_tma_launch_smem(local_tma_args(h, ld, in, false), depth)
+                                       : local_solve_smem(h->cmax, ld, h->tf_bytes(), depth);
+        if ((h->use_tma && depth < 2) || smem > 200 * 1024) {
+            set_error("ring depth too small for the TMA staging or its shared memory above 200 KB");
+            return AMS_ERR_INVALID_ARG;
+        }
+    }
+    if (nr != 0 && ((nr != 2 && nr != 4 && nr != 8) || nr > ld || ld / nr > 8)) {
+        set_error("right-hand sides per warp must be 0, or 2, 4 or 8 with at most 8 warps per block");
+        return AMS_ERR_INVALID_ARG;
+    }
+    if (l2mode < 0 || l2mode > 2 || l2keep < 0) {
+        set_error("L2 mode must be 0, 1 or 2 and the kept block rows non-negative");
+        return AMS_ERR_INVALID_ARG;
+    }
+    TuneCfg& T = h->tune[ld];
+    T.l2mode = l2mode;
+    T.l2keep = l2keep;
+    T.bps_elem = bps_e;
+    T.bps_sub = bps_s;
+    T.depth = depth;
+    T.nr = nr;
+    T.done = true;
+    auto g = h->iter_graph.find(ld);   // captured with the previous shapes
+    if (g != h->iter_graph.end()) {
+        AMS_CUDA_TRY(cudaGraphExecDestroy(g->second));
+        h->iter_graph.erase(g);
+    }
     return AMS_OK;
 }
 

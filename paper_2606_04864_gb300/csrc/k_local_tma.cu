@@ -66,6 +66,31 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// The same copy with an L2 eviction-priority hint (a createpolicy value).
+__device__ __forceinline__ void tma_load_2d_hint(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
+                                                 uint32_t bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%2, %3}], [%4], %5;\n"
+        ::"r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_normal() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+    return p;
+}
+
 // 1024-byte aligned start of the dynamic shared memory (the 128-byte swizzle
 // pattern repeats every 1024 bytes).  Derived by pointer arithmetic, not an
 // integer round trip, so that the compiler still sees a shared-memory
@@ -522,7 +547,8 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
              const int64_t* __restrict__ tile_row0, const float* __restrict__ piv,
              const double* __restrict__ rin, const double* __restrict__ qin,
              const CgScalars* __restrict__ csc, float* __restrict__ zf, const TP* __restrict__ psi,
-             float* __restrict__ rc, int cmax, int nbmax, int depth, int64_t budget, SolveState* st) {
+             float* __restrict__ rc, int cmax, int nbmax, int depth, int l2mode, int l2keep, int64_t budget,
+             SolveState* st) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_align1024(smem_raw);
     const SubInfo S = subs[blockIdx.x];
@@ -530,6 +556,9 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     const int nb = S.nb, n = S.n, m = S.m;
     const int D = depth;
     const int nbuf = cmax + D + 1;
+    // Block rows nb-nbuf .. nb-1 stay in the ring from the forward sweep to
+    // the backward one; rows below Rres are loaded twice.
+    const int Rres = nb > nbuf ? nb - nbuf : 0;
     float* tiles = (float*)base;                                        // nbuf * cmax * 1024
     uint64_t* bars = (uint64_t*)(tiles + (size_t)nbuf * cmax * 1024);    // nbuf (padded to even)
     float* yv = (float*)(bars + ((nbuf + 1) & ~1));                      // nbmax * 32: y, then x
@@ -566,13 +595,30 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     // ring slots are tracked incrementally (no division in the step loop)
     auto wrap_up = [&](int sl) { return sl >= nbuf ? sl - nbuf : sl; };
     auto wrap_dn = [&](int sl) { return sl < 0 ? sl + nbuf : sl; };
-    auto issue = [&](int K, int slot) {
+    // L2 priorities of the tile copies (l2mode > 0): a copy that reads a
+    // block row for the last time (a resident row's forward load, a backward
+    // reload, a forward load whose reload is far away) is evict-first; the
+    // forward loads of the l2keep rows below Rres, which the backward sweep
+    // reloads soonest, keep normal (l2mode 1) or evict-last (2) priority.
+    uint64_t pol_dead = 0, pol_keep = 0;
+    if (l2mode > 0 && lane == 0) {
+        pol_dead = l2_policy_evict_first();
+        pol_keep = l2mode == 2 ? l2_policy_evict_last() : l2_policy_evict_normal();
+    }
+    auto issue = [&](int K, int slot, bool reload) {
         if (lane == 0) {
             const uint32_t bar = smem_u32(bars + slot);
             mbar_expect_tx(bar, tile_bytes);
-            for (int d = 0; d < c; ++d)
-                tma_load_2d(smem_u32(tiles + slot * slot_floats + d * 1024), &tmF, 0,
-                            (int32_t)(trow + ((int64_t)K * c + d) * 32), bar);
+            const bool keep = !reload && K < Rres && K >= Rres - l2keep;
+            const uint64_t pol = keep ? pol_keep : pol_dead;
+            for (int d = 0; d < c; ++d) {
+                const uint32_t dst = smem_u32(tiles + slot * slot_floats + d * 1024);
+                const int32_t y = (int32_t)(trow + ((int64_t)K * c + d) * 32);
+                if (l2mode > 0)
+                    tma_load_2d_hint(dst, &tmF, 0, y, bar, pol);
+                else
+                    tma_load_2d(dst, &tmF, 0, y, bar);
+            }
         }
         pend |= 1u << slot;
     };
@@ -608,7 +654,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
         }
     };
     // first block rows of the factor and their setup inputs, ahead of the wait
-    for (int j = 0; j < D && j < nb; ++j) issue(j, j);
+    for (int j = 0; j < D && j < nb; ++j) issue(j, j, false);
 #pragma unroll
     for (int u = 0; u < PF; ++u) load_static(u, bp[u], bv[u]);
     pdl_wait();
@@ -642,7 +688,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
 
     int sK = 0;   // slot of block row K
     auto fwd_step = [&](int K, double& tb, double& qb, BasisRow<TP, MM>& pb, float& vb) {
-        if (K + D < nb) issue(K + D, wrap_up(sK + D));
+        if (K + D < nb) issue(K + D, wrap_up(sK + D), false);
         float t = f64_to_f32(upd ? fma(-alpha, qb, tb) : tb);
         const float pvt = vb;
         if (rc != nullptr) {
@@ -711,9 +757,8 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     }
 
     // ---------------- backward ----------------
-    // Block rows nb-nbuf .. nb-1 are still in the ring; older ones are
+    // Block rows Rres .. nb-1 are still in the ring; older ones are
     // reloaded D steps ahead of their use.
-    const int Rres = nb > nbuf ? nb - nbuf : 0;
     auto load_bwd = [&](int K, float& pvt) {
         const int row = K * 32 + lane;
         pvt = 1.f;
@@ -722,7 +767,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     float ucarry = 0.f;   // C1: sum_{r <= lane} M_{K+1}[r][lane] x_{K+1}[r] for the next step
     sK = (nb - 1) % nbuf;
     auto bwd_step = [&](int K, float& vb) {
-        if (K - D >= 0 && K - D < Rres) issue(K - D, wrap_dn(sK - D));
+        if (K - D >= 0 && K - D < Rres) issue(K - D, wrap_dn(sK - D), true);
         const float pvt = vb;
         load_bwd(K - PF, vb);
         if (K < Rres) wait_slot(sK);
@@ -884,7 +929,7 @@ static cudaError_t tma1(const LocalTmaArgs& a, const void* psi, void* zf, void* 
     }
     return launch_kernel(a.pdl, kern, dim3(a.nsub), dim3(32), smem, a.stream, *a.tmF, a.subs, a.tile_row0, a.piv,
                          a.in.r, a.in.q, a.in.sc, (float*)zf, (const TP*)psi, (float*)rc, a.cmax, a.nbmax, depth,
-                         a.budget, a.st);
+                         a.l2mode, a.l2keep, a.budget, a.st);
 }
 
 // The one-right-hand-side kernel keeps y for a whole subdomain in shared

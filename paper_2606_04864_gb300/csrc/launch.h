@@ -89,6 +89,10 @@ struct LocalTmaArgs {
     bool pdl;
     int depth;               // ring depth (block rows in flight); 0: chosen from the band width
     int nr;                  // several-RHS kernel: right-hand sides per warp (1, 2, 4, 8); 0: default
+    int l2mode;              // one-RHS kernel, L2 priority of factor tiles: 0 none, 1 evict-first on
+                             // tiles read for the last time, 2 as 1 plus evict-last on kept tiles
+    int l2keep;              // block rows below the ring's resident ones whose forward load is
+                             // kept (not marked evict-first): the backward sweep reloads them soonest
 };
 
 struct CoarseLaunch {

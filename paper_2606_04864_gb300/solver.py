@@ -97,6 +97,28 @@ class _Base:
         check(lib().ams_get_info(self._h, C.byref(i)), "ams_get_info")
         return {f: getattr(i, f) for f, _ in ams_info._fields_}
 
+    _SHAPE_KEYS = ("bps_elem", "bps_sub", "depth", "nr", "l2mode", "l2keep")
+
+    def launch_shape(self, nrhs: int = 1) -> dict:
+        """Launch shapes used for solves with `nrhs` right-hand sides: blocks
+        per SM of the element and subdomain grids, local-solve ring depth
+        (0 = derived from the band width), right-hand sides per warp of the
+        several-RHS local solve (0 = default), L2 priorities of the one-RHS
+        local solve's tile copies (mode 0/1/2 and kept block rows), and
+        whether they are fixed."""
+        a = np.zeros(7, dtype=np.int32)
+        check(lib().ams_get_launch_shape(self._h, int(nrhs), _ptr(a)), "ams_get_launch_shape")
+        d = dict(zip(self._SHAPE_KEYS, (int(v) for v in a[:6])))
+        d["fixed"] = bool(a[6])
+        return d
+
+    def set_launch_shape(self, nrhs: int = 1, **shape):
+        """Fix the launch shapes for `nrhs` right-hand sides (keys as returned
+        by launch_shape; missing keys keep their current value)."""
+        cur = self.launch_shape(nrhs)
+        a = np.array([int(shape.get(k, cur[k])) for k in self._SHAPE_KEYS], dtype=np.int32)
+        check(lib().ams_set_launch_shape(self._h, int(nrhs), _ptr(a)), "ams_set_launch_shape")
+
     def _vec_in(self, v, nrhs_expected=None):
         if self.device:
             t = _as_dev(v, np.float64)

@@ -295,6 +295,52 @@ def test_autotuned_launch_shapes_give_the_same_solve(prec):
     assert (ia2 == ia).all() and np.array_equal(ua2, ua)
 
 
+def test_set_launch_shape_is_validated_and_kept():
+    """A fixed launch shape is reported back, survives the first solve (the
+    autotuner leaves it), replaces the captured iteration graph, and gives
+    the solve of the default shapes; invalid shapes are refused."""
+    from paper_2606_04864_gb300._lib import AmsError
+    w = make_small_2d(side=96, bs=16, m=4, std=2.0, sigma=3.0, seed=45, nrhs=3, rhs_kind="normal")
+    a = _solver(w, precision="fp32_bf16", autotune=True)
+    assert not a.launch_shape(3)["fixed"]
+    a.set_launch_shape(3, bps_elem=3, bps_sub=6, depth=2, nr=2)
+    assert a.launch_shape(4) == {"bps_elem": 3, "bps_sub": 6, "depth": 2, "nr": 2, "l2mode": 0, "l2keep": 0,
+                                 "fixed": True}
+    ua, ia, _ = a.solve(w.rhs, rtol=1e-8)
+    assert a.launch_shape(3) == {"bps_elem": 3, "bps_sub": 6, "depth": 2, "nr": 2, "l2mode": 0, "l2keep": 0,
+                                 "fixed": True}
+    a.set_launch_shape(3, bps_elem=6, depth=3, nr=4)
+    ub, ib, _ = a.solve(w.rhs, rtol=1e-8)
+    ref = _solver(w, precision="fp32_bf16", autotune=False)
+    ur, ir, _ = ref.solve(w.rhs, rtol=1e-8)
+    for u, i in ((ua, ia), (ub, ib)):
+        assert (np.abs(i.astype(int) - ir.astype(int)) <= 2).all()
+        assert np.linalg.norm(u - ur) <= 1e-6 * np.linalg.norm(ur)
+    for bad in ({"bps_elem": 0}, {"bps_sub": 9}, {"depth": 7}, {"depth": -1}, {"nr": 3}, {"nr": 8},
+                {"l2mode": 3}, {"l2keep": -1}):
+        with pytest.raises(AmsError):
+            a.set_launch_shape(3, **bad)
+    with pytest.raises(AmsError):
+        a.launch_shape(33)
+    assert a.launch_shape(3)["depth"] == 3
+
+
+def test_l2_priorities_leave_the_solve_bitwise_unchanged():
+    """The L2 eviction priorities of the one-RHS local solve's tile copies
+    change where the tiles are cached, not a single value: with the other
+    shapes fixed, every priority setting gives the same bits."""
+    w = make_small_2d(side=128, bs=32, m=4, std=2.0, seed=46)   # 32 block rows per subdomain
+    s = _solver(w, precision="fp32_bf16", autotune=False)
+    base = None
+    for mode, keep in ((0, 0), (1, 0), (1, 3), (1, 1 << 20), (2, 3), (2, 1 << 20)):
+        s.set_launch_shape(1, bps_elem=4, bps_sub=4, depth=2, nr=0, l2mode=mode, l2keep=keep)
+        u, its, _ = s.solve(w.rhs[0], rtol=1e-8)
+        if base is None:
+            base = (u.copy(), its.copy())
+        else:
+            assert np.array_equal(u, base[0]) and np.array_equal(its, base[1]), (mode, keep)
+
+
 def test_profile_and_time_kernel_report_every_slot():
     """ams_profile_solve times every kernel slot of a real solve (one launch
     per slot and iteration, plus the first application), and ams_time_kernel
