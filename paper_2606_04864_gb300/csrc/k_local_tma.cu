@@ -535,6 +535,15 @@ struct BasisRow {
         }
     }
     __device__ __forceinline__ float get(int k) const { return to_f(reinterpret_cast<const TP*>(w)[k]); }
+    // entries 2i and 2i+1 (a BF16 pair is widened with two integer operations)
+    __device__ __forceinline__ float2 get2(int i) const {
+        if constexpr (sizeof(TP) == 2) {
+            const uint32_t u = reinterpret_cast<const uint32_t*>(w)[i];
+            return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+        } else {
+            return make_float2(get(2 * i), get(2 * i + 1));
+        }
+    }
 };
 
 // C1: every subdomain has c == 1 (one 32x32 tile per block row).  The
@@ -543,7 +552,8 @@ struct BasisRow {
 // so every tile column is read from shared memory once.
 template <typename TP, int MM, bool C1>
 __global__ void __launch_bounds__(32, 8)
-k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict__ subs,
+k_local_tma1(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmB,
+             const SubInfo* __restrict__ subs,
              const int64_t* __restrict__ tile_row0, const float* __restrict__ piv,
              const double* __restrict__ rin, const double* __restrict__ qin,
              const CgScalars* __restrict__ csc, float* __restrict__ zf, const TP* __restrict__ psi,
@@ -605,19 +615,23 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
         pol_dead = l2_policy_evict_first();
         pol_keep = l2mode == 2 ? l2_policy_evict_last() : l2_policy_evict_normal();
     }
+    // C1: a backward reload copies the transposed tile (row `lane` of M_K^T
+    // is column `lane` of M_K), so the backward step reads it by rows.
+    const CUtensorMap* map_reload = C1 ? &tmB : &tmF;
     auto issue = [&](int K, int slot, bool reload) {
         if (lane == 0) {
             const uint32_t bar = smem_u32(bars + slot);
             mbar_expect_tx(bar, tile_bytes);
             const bool keep = !reload && K < Rres && K >= Rres - l2keep;
             const uint64_t pol = keep ? pol_keep : pol_dead;
+            const CUtensorMap* map = reload ? map_reload : &tmF;
             for (int d = 0; d < c; ++d) {
                 const uint32_t dst = smem_u32(tiles + slot * slot_floats + d * 1024);
                 const int32_t y = (int32_t)(trow + ((int64_t)K * c + d) * 32);
                 if (l2mode > 0)
-                    tma_load_2d_hint(dst, &tmF, 0, y, bar, pol);
+                    tma_load_2d_hint(dst, map, 0, y, bar, pol);
                 else
-                    tma_load_2d(dst, &tmF, 0, y, bar);
+                    tma_load_2d(dst, map, 0, y, bar);
             }
         }
         pend |= 1u << slot;
@@ -628,9 +642,10 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
         pend &= ~(1u << slot);
     };
 
-    float racc[MM];
+    static_assert(MM % 2 == 0, "basis rows are accumulated in pairs");
+    float2 racc[MM / 2];
 #pragma unroll
-    for (int k = 0; k < MM; ++k) racc[k] = 0.f;
+    for (int k = 0; k < MM / 2; ++k) racc[k] = make_float2(0.f, 0.f);
 
     // Per-row inputs of block row K+PF are loaded while step K runs.  They
     // stay in the loaded type until the step that uses them: a conversion
@@ -689,11 +704,14 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     int sK = 0;   // slot of block row K
     auto fwd_step = [&](int K, double& tb, double& qb, BasisRow<TP, MM>& pb, float& vb) {
         if (K + D < nb) issue(K + D, wrap_up(sK + D), false);
-        float t = f64_to_f32(upd ? fma(-alpha, qb, tb) : tb);
+        // the FP64 pipe is nearly idle in this kernel: the hardware narrowing
+        // is one instruction where the integer-pipe one is about a dozen
+        float t = __double2float_rn(upd ? fma(-alpha, qb, tb) : tb);
         const float pvt = vb;
         if (rc != nullptr) {
+            const float2 t2 = make_float2(t, t);
 #pragma unroll
-            for (int k = 0; k < MM; ++k) racc[k] = fmaf(pb.get(k), t, racc[k]);
+            for (int k = 0; k < MM / 2; ++k) racc[k] = __ffma2_rn(pb.get2(k), t2, racc[k]);
         }
         load_static(K + PF, pb, vb);
         load_dyn(K + PF, tb, qb);
@@ -750,7 +768,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     if (rc != nullptr && ok) {
 #pragma unroll
         for (int k = 0; k < MM; ++k) {
-            float v = racc[k];
+            float v = (k & 1) ? racc[k / 2].y : racc[k / 2].x;
             for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
             if (lane == 0 && k < m) rc[S.coff + k] = v;
         }
@@ -801,9 +819,19 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
         __syncwarp();
         // x_K = L_KK^{-T} w: rows r > lane of column lane of M_K.  Column
         // `lane` splits exactly into au (rows r > lane, from L_KK^{-1}) and
-        // al (rows r <= lane, from L_{K,K-c}).
+        // al (rows r <= lane, from L_{K,K-c}).  A reloaded C1 tile is M_K^T
+        // and gives the column as row `lane`.
         float2 au[16], al[16];
-        col_pairs(Tm, csw, au);
+        if (C1 && K < Rres) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float4 m4 = *reinterpret_cast<const float4*>(Tm + rsw[j]);
+                au[2 * j] = lo2(m4);
+                au[2 * j + 1] = hi2(m4);
+            }
+        } else {
+            col_pairs(Tm, csw, au);
+        }
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const float2 a2 = au[i];
@@ -927,7 +955,8 @@ static cudaError_t tma1(const LocalTmaArgs& a, const void* psi, void* zf, void* 
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    return launch_kernel(a.pdl, kern, dim3(a.nsub), dim3(32), smem, a.stream, *a.tmF, a.subs, a.tile_row0, a.piv,
+    return launch_kernel(a.pdl, kern, dim3(a.nsub), dim3(32), smem, a.stream, *a.tmF, *a.tmB, a.subs, a.tile_row0,
+                         a.piv,
                          a.in.r, a.in.q, a.in.sc, (float*)zf, (const TP*)psi, (float*)rc, a.cmax, a.nbmax, depth,
                          a.l2mode, a.l2keep, a.budget, a.st);
 }
