@@ -101,7 +101,9 @@ void ams_options_default(ams_options* opt);
  *  colind   CSR column indices, rowptr[n] entries, strictly ascending per row
  *  vals     CSR values (FP64); A must be symmetric (pattern and values equal
  *           to the last bit) with a positive diagonal
- *  part     subdomain id of each dof, in [0, nparts); no subdomain may be empty
+ *  part     subdomain id of each dof, in [0, nparts); no subdomain may be empty;
+ *           NULL = the built-in partition of the pattern (ams_partition with
+ *           the default imbalance and seed 0)
  *  nparts   number of subdomains N
  *  m        eigenvectors per subdomain; the library keeps m_i = min(m, n_i)
  *           and grows m_i while lambda_{m_i+1} equals lambda_{m_i} to a
@@ -120,6 +122,34 @@ ams_status ams_setup(int64_t n, const int64_t* rowptr, const int32_t* colind,
                      const double* vals, const int32_t* part, int32_t nparts,
                      int32_t m, const ams_options* opt, void* stream,
                      ams_handle* out);
+
+/*
+ * ams_partition — split the dofs into nparts subdomains from the matrix
+ * pattern alone.  The method takes a non-overlapping partition as given
+ * (Section 3.1; the paper's experiments use METIS, Section 5); this
+ * built-in one is a multilevel recursive bisection of the pattern's graph
+ * (heavy-edge matching, region growing on the coarsest graph,
+ * Fiduccia-Mattheyses refinement on every level) for callers with no
+ * partitioner of their own.  Host code only: no GPU, no CUDA context.
+ *
+ *  n, rowptr, colind  CSR pattern as for ams_setup (host memory); diagonal
+ *                     entries are ignored and the pattern is symmetrised
+ *  nparts             1 <= nparts <= n
+ *  imbalance          every part has at most about (1 + imbalance) n/nparts
+ *                     dofs (one dof of rounding per bisection level);
+ *                     0 = default 0.03
+ *  seed               the result depends on the seed alone
+ *  part               out, host, n entries in [0, nparts); every part is
+ *                     non-empty; parts need not be connected
+ *  edge_cut           out (NULL allowed): undirected pattern edges {i, j},
+ *                     i != j, whose endpoints lie in different parts
+ *
+ * Errors: AMS_ERR_INVALID_ARG (NULL arrays, n out of range, nparts outside
+ * [1, n], negative or non-finite imbalance, rowptr not starting at 0 or
+ * decreasing, column index out of range).
+ */
+ams_status ams_partition(int64_t n, const int64_t* rowptr, const int32_t* colind, int32_t nparts,
+                         double imbalance, uint64_t seed, int32_t* part, int64_t* edge_cut);
 
 /* One independent system of a batch (same meaning as ams_setup's arguments). */
 typedef struct {

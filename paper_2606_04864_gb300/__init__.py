@@ -4,6 +4,6 @@ subdomain solves plus a spectral coarse correction, all in hand-written
 CUDA for sm_103a behind the C ABI in ``include/ams.h``."""
 
 from ._lib import AmsError, lib  # noqa: F401
-from .solver import AmsBatchedSolver, AmsSolver  # noqa: F401
+from .solver import AmsBatchedSolver, AmsSolver, partition  # noqa: F401
 
-__all__ = ["AmsSolver", "AmsBatchedSolver", "AmsError", "lib"]
+__all__ = ["AmsSolver", "AmsBatchedSolver", "AmsError", "lib", "partition"]

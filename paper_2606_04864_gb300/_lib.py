@@ -94,6 +94,8 @@ SIGNATURES = {
     "ams_get_info": (C.c_int, [C.c_void_p, C.POINTER(ams_info)]),
     "ams_get_index_maps": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "ams_get_launch_shape": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
+    "ams_partition": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_uint64,
+                                C.c_void_p, C.c_void_p]),
     "ams_set_launch_shape": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "ams_get_coarse_basis": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ams_get_coarse_matrix": (C.c_int, [C.c_void_p, C.c_void_p]),

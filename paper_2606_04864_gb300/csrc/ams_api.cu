@@ -373,7 +373,7 @@ struct SysInput {
 };
 
 static ams_status read_inputs(const ams_system_desc& d, int device_ptrs, SysInput& in) {
-    if (d.n <= 0 || !d.rowptr || !d.colind || !d.vals || !d.part) {
+    if (d.n <= 0 || !d.rowptr || !d.colind || !d.vals) {
         set_error("null pointer or non-positive n");
         return AMS_ERR_INVALID_ARG;
     }
@@ -395,7 +395,12 @@ static ams_status read_inputs(const ams_system_desc& d, int device_ptrs, SysInpu
     in.A.vals.resize(nnz);
     AMS_CUDA_TRY(cudaMemcpy(in.A.colind.data(), d.colind, sizeof(int32_t) * nnz, kind));
     AMS_CUDA_TRY(cudaMemcpy(in.A.vals.data(), d.vals, sizeof(double) * nnz, kind));
-    AMS_CUDA_TRY(cudaMemcpy(in.part.data(), d.part, sizeof(int32_t) * d.n, kind));
+    if (d.part) {
+        AMS_CUDA_TRY(cudaMemcpy(in.part.data(), d.part, sizeof(int32_t) * d.n, kind));
+    } else {   // no partition given: the built-in one of the matrix pattern
+        AMS_TRY(partition_graph(d.n, in.A.rowptr.data(), in.A.colind.data(), d.nparts, 0.0, 0, in.part.data(),
+                                nullptr));
+    }
     in.nparts = d.nparts;
     in.m = d.m;
     return validate_system(in.A, in.part.data(), d.nparts);

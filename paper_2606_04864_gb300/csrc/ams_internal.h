@@ -112,6 +112,11 @@ struct SolveState {    // device-resident control block
 // ---- error bookkeeping ------------------------------------------------------
 void set_error(const std::string& msg);
 
+// Multilevel recursive bisection of the matrix pattern's graph into nparts
+// parts (partition.cpp; behind ams_partition).
+ams_status partition_graph(int64_t n, const int64_t* rowptr, const int32_t* colind, int32_t nparts,
+                           double imbalance, uint64_t seed, int32_t* part, int64_t* edge_cut);
+
 #define AMS_CUDA_TRY(expr)                                                     \
     do {                                                                       \
         cudaError_t _e = (expr);                                               \

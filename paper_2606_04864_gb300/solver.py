@@ -173,12 +173,27 @@ class _Base:
         return ms.value, by.value
 
 
+def partition(rowptr, colind, nparts: int, imbalance: float = 0.0, seed: int = 0):
+    """Built-in partition of a CSR pattern into `nparts` subdomains
+    (``ams_partition``: multilevel recursive bisection, host code).  Returns
+    (part int32[n], edge_cut)."""
+    rp = np.ascontiguousarray(np.asarray(rowptr), dtype=np.int64)
+    ci = np.ascontiguousarray(np.asarray(colind), dtype=np.int32)
+    n = int(rp.shape[0] - 1)
+    part = np.empty(max(n, 0), dtype=np.int32)
+    cut = C.c_int64(0)
+    check(lib().ams_partition(n, _ptr(rp), _ptr(ci), int(nparts), float(imbalance), int(seed), _ptr(part),
+                              C.byref(cut)), "ams_partition")
+    return part, int(cut.value)
+
+
 class AmsSolver(_Base):
     """Two-level AMS preconditioner + CG on one sparse SPD matrix.
 
     Parameters follow ``ams_setup``: CSR arrays (rowptr int64, colind int32,
-    vals float64), ``part`` (int32 subdomain id per dof), ``nparts`` and
-    ``m`` eigenvectors per subdomain.
+    vals float64), ``part`` (int32 subdomain id per dof, or None for the
+    built-in partition of the pattern), ``nparts`` and ``m`` eigenvectors
+    per subdomain.
     """
 
     def __init__(self, rowptr, colind, vals, part, nparts: int, m: int, precision="fp32_bf16",
@@ -189,7 +204,7 @@ class AmsSolver(_Base):
         self._rowptr = conv(rowptr, np.int64)
         self._colind = conv(colind, np.int32)
         self._vals = conv(vals, np.float64)
-        self._part = conv(part, np.int32)
+        self._part = conv(part, np.int32) if part is not None else None
         self.n = int(self._rowptr.shape[0] - 1)
         self.nnz = int(self._colind.shape[0])
         self.nparts = int(nparts)
@@ -198,7 +213,8 @@ class AmsSolver(_Base):
                                  autotune)
         h = C.c_void_p()
         st = lib().ams_setup(self.n, _ptr(self._rowptr), _ptr(self._colind), _ptr(self._vals),
-                             _ptr(self._part), self.nparts, int(m), C.byref(self.opts),
+                             _ptr(self._part) if self._part is not None else None, self.nparts, int(m),
+                             C.byref(self.opts),
                              _stream_ptr(self.device), C.byref(h))
         check(st, "ams_setup")
         self._h = h

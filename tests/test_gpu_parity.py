@@ -341,6 +341,24 @@ def test_l2_priorities_leave_the_solve_bitwise_unchanged():
             assert np.array_equal(u, base[0]) and np.array_equal(its, base[1]), (mode, keep)
 
 
+def test_built_in_partition_when_none_is_given():
+    """Without a partition the setup splits the pattern with ams_partition
+    (seed 0, default imbalance): its subdomains are exactly that
+    partition's parts, and PCG on them converges."""
+    import scipy.sparse as sp
+    from paper_2606_04864_gb300 import partition
+    w = make_small_2d(side=96, bs=16, m=4, std=2.0, sigma=3.0, seed=47)
+    part, _ = partition(w.rowptr, w.colind, 20)
+    s = AmsSolver(w.rowptr, w.colind, w.vals, None, 20, 4, precision="fp32_bf16")
+    perm, sub_ptr = s.index_maps()
+    for i in range(20):
+        assert np.array_equal(perm[sub_ptr[i]:sub_ptr[i + 1]], np.flatnonzero(part == i))
+    u, its, rel = s.solve(w.rhs[0], rtol=1e-8)
+    A = sp.csr_matrix((w.vals, w.colind, w.rowptr), shape=(w.n, w.n))
+    assert rel[0] <= 1e-8
+    assert np.linalg.norm(w.rhs[0] - A @ u) <= 1e-6 * np.linalg.norm(w.rhs[0])
+
+
 def test_profile_and_time_kernel_report_every_slot():
     """ams_profile_solve times every kernel slot of a real solve (one launch
     per slot and iteration, plus the first application), and ams_time_kernel
