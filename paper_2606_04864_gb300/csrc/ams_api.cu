@@ -1360,30 +1360,19 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
         }
     } restore{h, h->prof, h->launches};
     h->prof = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    AMS_CUDA_TRY(cudaEventCreate(&e0));
-    AMS_CUDA_TRY(cudaEventCreate(&e1));
-    std::unique_ptr<CUevent_st, decltype(&cudaEventDestroy)> g0(e0, cudaEventDestroy), g1(e1, cudaEventDestroy);
     auto ctx = [&](LaunchCtx* L) -> ams_status {
         RedCache *rc = nullptr, *rcs = nullptr;
         AMS_TRY(get_red(h, ld, &rc, &rcs));
         *L = make_ctx(h, *rc, *rcs);
         return AMS_OK;
     };
-    auto timed = [&](auto&& launch, float* ms) -> ams_status {
-        AMS_TRY(launch());
-        AMS_CUDA_TRY(cudaEventRecord(e0, h->stream));
-        for (int k = 0; k < 3; ++k) AMS_TRY(launch());
-        AMS_CUDA_TRY(cudaEventRecord(e1, h->stream));
-        AMS_CUDA_TRY(cudaEventSynchronize(e1));
-        AMS_CUDA_TRY(cudaGetLastError());
-        AMS_CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
-        return AMS_OK;
-    };
-    // Local-solve candidates are timed each right after an SpMV, as they run
-    // in a solve: the SpMV streams the matrix through L2, so a candidate finds
-    // there what it finds inside an iteration (back-to-back launches of one
-    // kernel would find part of their own factor tiles and favour deep rings).
+    // Every candidate launch is timed right after a launch that streams other
+    // data through L2, as in a solve: the SpMV and the prolongation after a
+    // local solve, the local solve after an SpMV.  Back-to-back launches of
+    // one kernel find part of their own operands still in L2 and favour the
+    // wrong shapes (deep rings; three blocks per SM for the SpMV).  Each
+    // candidate: one warm pair, then the faster of two rounds of three (one
+    // round let a clock or L2 hiccup pick a slower shape).
     cudaEvent_t ev[6] = {};
     struct Events {
         cudaEvent_t* e;
@@ -1396,19 +1385,23 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
     auto timed_after = [&](auto&& pre, auto&& launch, float* ms) -> ams_status {
         AMS_TRY(pre());
         AMS_TRY(launch());
-        for (int k = 0; k < 3; ++k) {
-            AMS_TRY(pre());
-            AMS_CUDA_TRY(cudaEventRecord(ev[2 * k], h->stream));
-            AMS_TRY(launch());
-            AMS_CUDA_TRY(cudaEventRecord(ev[2 * k + 1], h->stream));
-        }
-        AMS_CUDA_TRY(cudaEventSynchronize(ev[5]));
-        AMS_CUDA_TRY(cudaGetLastError());
-        *ms = 0.f;
-        for (int k = 0; k < 3; ++k) {
-            float t = 0.f;
-            AMS_CUDA_TRY(cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]));
-            *ms += t;
+        *ms = 1e30f;
+        for (int round = 0; round < 2; ++round) {
+            for (int k = 0; k < 3; ++k) {
+                AMS_TRY(pre());
+                AMS_CUDA_TRY(cudaEventRecord(ev[2 * k], h->stream));
+                AMS_TRY(launch());
+                AMS_CUDA_TRY(cudaEventRecord(ev[2 * k + 1], h->stream));
+            }
+            AMS_CUDA_TRY(cudaEventSynchronize(ev[5]));
+            AMS_CUDA_TRY(cudaGetLastError());
+            float sum = 0.f;
+            for (int k = 0; k < 3; ++k) {
+                float t = 0.f;
+                AMS_CUDA_TRY(cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]));
+                sum += t;
+            }
+            *ms = std::min(*ms, sum);
         }
         return AMS_OK;
     };
@@ -1416,6 +1409,7 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
     AMS_TRY(ctx(&L));
     AMS_TRY(start_solve(h, L, f_dev, nrhs, 0x7fffffff, 0.0));
     const int cand_bps[] = {3, 4, 6};
+    auto local_pre = [&]() -> ams_status { return launch_local(h, ld, ResidIn{h->d_r, h->d_q, h->d_sc}, true); };
     {   // element layout: direction update + SpMV
         float best = 1e30f;
         int arg = T.bps_elem;
@@ -1423,7 +1417,10 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
             T.bps_elem = bps;
             AMS_TRY(ctx(&L));
             float ms = 0.f;
-            AMS_TRY(timed([&]() -> ams_status { launch_direction_spmv(h, L, h->d_p, h->d_p2); return AMS_OK; }, &ms));
+            AMS_TRY(timed_after(local_pre, [&]() -> ams_status {
+                launch_direction_spmv(h, L, h->d_p, h->d_p2);
+                return AMS_OK;
+            }, &ms));
             if (ms < best) {
                 best = ms;
                 arg = bps;
@@ -1495,7 +1492,7 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
             T.bps_sub = bps;
             AMS_TRY(ctx(&L));
             float ms = 0.f;
-            AMS_TRY(timed([&]() -> ams_status {
+            AMS_TRY(timed_after(local_pre, [&]() -> ams_status {
                 launch_prolong_update(L, h->prec, prolong_args(h, 2, h->d_p2, ld));
                 return AMS_OK;
             }, &ms));

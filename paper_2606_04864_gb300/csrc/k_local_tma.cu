@@ -552,8 +552,7 @@ struct BasisRow {
 // so every tile column is read from shared memory once.
 template <typename TP, int MM, bool C1>
 __global__ void __launch_bounds__(32, 8)
-k_local_tma1(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUtensorMap tmB,
-             const SubInfo* __restrict__ subs,
+k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict__ subs,
              const int64_t* __restrict__ tile_row0, const float* __restrict__ piv,
              const double* __restrict__ rin, const double* __restrict__ qin,
              const CgScalars* __restrict__ csc, float* __restrict__ zf, const TP* __restrict__ psi,
@@ -615,23 +614,19 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CU
         pol_dead = l2_policy_evict_first();
         pol_keep = l2mode == 2 ? l2_policy_evict_last() : l2_policy_evict_normal();
     }
-    // C1: a backward reload copies the transposed tile (row `lane` of M_K^T
-    // is column `lane` of M_K), so the backward step reads it by rows.
-    const CUtensorMap* map_reload = C1 ? &tmB : &tmF;
     auto issue = [&](int K, int slot, bool reload) {
         if (lane == 0) {
             const uint32_t bar = smem_u32(bars + slot);
             mbar_expect_tx(bar, tile_bytes);
             const bool keep = !reload && K < Rres && K >= Rres - l2keep;
             const uint64_t pol = keep ? pol_keep : pol_dead;
-            const CUtensorMap* map = reload ? map_reload : &tmF;
             for (int d = 0; d < c; ++d) {
                 const uint32_t dst = smem_u32(tiles + slot * slot_floats + d * 1024);
                 const int32_t y = (int32_t)(trow + ((int64_t)K * c + d) * 32);
                 if (l2mode > 0)
-                    tma_load_2d_hint(dst, map, 0, y, bar, pol);
+                    tma_load_2d_hint(dst, &tmF, 0, y, bar, pol);
                 else
-                    tma_load_2d(dst, map, 0, y, bar);
+                    tma_load_2d(dst, &tmF, 0, y, bar);
             }
         }
         pend |= 1u << slot;
@@ -819,19 +814,12 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CU
         __syncwarp();
         // x_K = L_KK^{-T} w: rows r > lane of column lane of M_K.  Column
         // `lane` splits exactly into au (rows r > lane, from L_KK^{-1}) and
-        // al (rows r <= lane, from L_{K,K-c}).  A reloaded C1 tile is M_K^T
-        // and gives the column as row `lane`.
+        // al (rows r <= lane, from L_{K,K-c}).  (Reloading the transposed
+        // tile instead, to read the column as a row, measured slower: the
+        // reloads of the forward tiles find part of them still in L2, those
+        // of a second array find nothing.)
         float2 au[16], al[16];
-        if (C1 && K < Rres) {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float4 m4 = *reinterpret_cast<const float4*>(Tm + rsw[j]);
-                au[2 * j] = lo2(m4);
-                au[2 * j + 1] = hi2(m4);
-            }
-        } else {
-            col_pairs(Tm, csw, au);
-        }
+        col_pairs(Tm, csw, au);
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             const float2 a2 = au[i];
@@ -955,7 +943,7 @@ static cudaError_t tma1(const LocalTmaArgs& a, const void* psi, void* zf, void* 
         if (e != cudaSuccess) return e;
         smem_set = smem;
     }
-    return launch_kernel(a.pdl, kern, dim3(a.nsub), dim3(32), smem, a.stream, *a.tmF, *a.tmB, a.subs, a.tile_row0,
+    return launch_kernel(a.pdl, kern, dim3(a.nsub), dim3(32), smem, a.stream, *a.tmF, a.subs, a.tile_row0,
                          a.piv,
                          a.in.r, a.in.q, a.in.sc, (float*)zf, (const TP*)psi, (float*)rc, a.cmax, a.nbmax, depth,
                          a.l2mode, a.l2keep, a.budget, a.st);
