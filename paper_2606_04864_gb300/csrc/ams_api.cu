@@ -1367,12 +1367,15 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
         return AMS_OK;
     };
     // Every candidate launch is timed right after a launch that streams other
-    // data through L2, as in a solve: the SpMV and the prolongation after a
-    // local solve, the local solve after an SpMV.  Back-to-back launches of
-    // one kernel find part of their own operands still in L2 and favour the
-    // wrong shapes (deep rings; three blocks per SM for the SpMV).  Each
-    // candidate: one warm pair, then the faster of two rounds of three (one
-    // round let a clock or L2 hiccup pick a slower shape).
+    // data through L2, as in a solve: the SpMV after a local solve, the local
+    // solve after an SpMV.  Back-to-back launches of one kernel find part of
+    // their own operands still in L2 and favour the wrong shapes (deep
+    // rings; three blocks per SM for the SpMV).  The prolongation is the
+    // exception: timed after the local and coarse solves it favours six
+    // blocks per SM, which take 61 us per launch in the solve against 44 us
+    // for the four that back-to-back timing picks.  Each candidate: one
+    // warm pair, then the faster of two rounds of three (one round let a
+    // clock or L2 hiccup pick a slower shape).
     cudaEvent_t ev[6] = {};
     struct Events {
         cudaEvent_t* e;
@@ -1410,6 +1413,7 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
     AMS_TRY(start_solve(h, L, f_dev, nrhs, 0x7fffffff, 0.0));
     const int cand_bps[] = {3, 4, 6};
     auto local_pre = [&]() -> ams_status { return launch_local(h, ld, ResidIn{h->d_r, h->d_q, h->d_sc}, true); };
+
     {   // element layout: direction update + SpMV
         float best = 1e30f;
         int arg = T.bps_elem;
@@ -1492,7 +1496,7 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
             T.bps_sub = bps;
             AMS_TRY(ctx(&L));
             float ms = 0.f;
-            AMS_TRY(timed_after(local_pre, [&]() -> ams_status {
+            AMS_TRY(timed_after([]() -> ams_status { return AMS_OK; }, [&]() -> ams_status {
                 launch_prolong_update(L, h->prec, prolong_args(h, 2, h->d_p2, ld));
                 return AMS_OK;
             }, &ms));
