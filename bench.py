@@ -178,8 +178,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    from workloads import make_config2
-    full = make_config2()
+    from workloads import make_channels2d_1024
+    full = make_channels2d_1024()
     cores = os.cpu_count()
     smp = OracleSample(full, crop=args.ref_crop)
     for _ in range(args.warmup):
@@ -212,7 +212,7 @@ def run_gpu(args):
     import torch.distributed as dist
 
     from paper_2606_04864_gb300 import AmsSolver
-    from workloads import make_config2
+    from workloads import make_channels2d_1024
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -229,8 +229,9 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    from workloads import make_config3, make_config5
-    w = {"cfg2": make_config2, "cfg3": make_config3, "cfg5": make_config5}[args.workload]()
+    from workloads import make_grf3d_128_rhs32, make_grf3d_96_adjoint
+    w = {"channels2d_1024": make_channels2d_1024, "grf3d_128_rhs32": make_grf3d_128_rhs32,
+         "grf3d_96": make_grf3d_96_adjoint}[args.workload]()
     f_dev = torch.as_tensor(w.rhs, device=dev)
     mixed = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp32_bf16",
                       device=True)
@@ -293,7 +294,7 @@ def run_gpu(args):
         v["share"] = v["ms_total"] / tot if tot > 0 else None
     dom = max(kern, key=lambda n: kern[n]["ms_total"])
     traffic, traffic_src = (None, None)
-    if args.workload == "cfg2" and dom in STEP_KERNELS:
+    if args.workload == "channels2d_1024" and dom in STEP_KERNELS:
         traffic, traffic_src = _profiled_traffic(STEP_KERNELS[dom])
     peak, peak_kind = _peaks()
     iter_bytes = sum(v["bytes"] for v in kern.values())
@@ -332,7 +333,7 @@ def run_gpu(args):
     e2e_s = slowest_rank(e2e_s, world, dev)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cfg2":
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "channels2d_1024":
         smp = OracleSample(w)
         est, detail = smp.step(int(its[0]))
         cpu = {"value": est, "unit": "s", "cores": os.cpu_count(), "kind": "oracle",
@@ -401,9 +402,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cfg2", choices=["cfg2", "cfg3", "cfg5"],
-                    help="cfg2 (default, the headline line): 1024^2 channels; cfg3: 128^3 with 32 "
-                         "right-hand sides; cfg5: 96^3 single right-hand side")
+    ap.add_argument("--workload", default="channels2d_1024",
+                    choices=["channels2d_1024", "grf3d_128_rhs32", "grf3d_96"],
+                    help="channels2d_1024 (default, the headline line): 1024^2 channelised Darcy; "
+                         "grf3d_128_rhs32: 128^3 lognormal with 32 right-hand sides; grf3d_96: 96^3 "
+                         "lognormal, one right-hand side")
     ap.add_argument("--launch-shape", default="",
                     help="fix the mixed solver's launch shapes instead of autotuning them: "
                          "bps_elem,bps_sub,depth,nr,l2mode,l2keep (as reported in config.launch_shape); for "

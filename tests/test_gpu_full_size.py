@@ -19,8 +19,8 @@ import scipy.linalg as la
 
 import oracle
 from oracle import OracleAMS, csr_to_scipy, index_maps, local_eigenpairs, local_matrices, pcg
-from workloads import (make_config2, make_config3, make_config4, make_config5, tpfa_csr,
-                       tpfa_values_from_logk, grf_logk, make_from_logk)
+from workloads import (grf_logk, make_batch48_uneven, make_channels2d_1024, make_from_logk,
+                       make_grf3d_96_adjoint, make_grf3d_128_rhs32, tpfa_csr, tpfa_values_from_logk)
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -50,13 +50,13 @@ def _check_sampled_eigs(s, w, A, subs, tol_lam=1e-10, tol_proj=1e-7):
 
 
 @pytest.fixture(scope="module")
-def cfg2():
-    w = make_config2()
+def channels2d():
+    w = make_channels2d_1024()
     return w, _A(w)
 
 
-def test_cfg2_index_maps_and_sampled_eigenpairs(cfg2):
-    w, A = cfg2
+def test_channels2d_index_maps_and_sampled_eigenpairs(channels2d):
+    w, A = channels2d
     s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp64")
     perm, sub_ptr = s.index_maps()
     p_o, ip_o, sp_o = index_maps(w.part, w.nparts)
@@ -70,8 +70,8 @@ def test_cfg2_index_maps_and_sampled_eigenpairs(cfg2):
     assert info["eig_max_residual"] <= 1e-11
 
 
-def test_cfg2_sampled_local_solves(cfg2):
-    w, A = cfg2
+def test_channels2d_sampled_local_solves(channels2d):
+    w, A = channels2d
     r = np.random.default_rng(7).standard_normal(w.n)
     perm, iperm, sub_ptr = index_maps(w.part, w.nparts)
     for prec, tol in [("fp64", 1e-11), ("fp32", 1e-4)]:
@@ -84,8 +84,8 @@ def test_cfg2_sampled_local_solves(cfg2):
             assert np.linalg.norm(z[dofs] - zi) <= tol * np.linalg.norm(zi), (prec, i)
 
 
-def test_cfg2_preconditioner_symmetric_positive(cfg2):
-    w, A = cfg2
+def test_channels2d_preconditioner_symmetric_positive(channels2d):
+    w, A = channels2d
     s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp64")
     rng = np.random.default_rng(8)
     r1, r2 = rng.standard_normal(w.n), rng.standard_normal(w.n)
@@ -95,8 +95,8 @@ def test_cfg2_preconditioner_symmetric_positive(cfg2):
     assert r1 @ z[0] > 0 and r2 @ z[1] > 0
 
 
-def test_cfg2_mixed_vs_fp64_full_size(cfg2):
-    w, A = cfg2
+def test_channels2d_mixed_vs_fp64_full_size(channels2d):
+    w, A = channels2d
     f = torch.as_tensor(w.rhs, device="cuda")
     s64 = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp64", device=True)
     smx = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp32_bf16", device=True)
@@ -112,8 +112,8 @@ def test_cfg2_mixed_vs_fp64_full_size(cfg2):
     assert r64[0] <= 1e-8 and rmx[0] <= 1e-8
 
 
-def test_cfg3_32_rhs_full_size():
-    w = make_config3()
+def test_grf3d_128_32_rhs_full_size():
+    w = make_grf3d_128_rhs32()
     A = _A(w)
     f = torch.as_tensor(w.rhs, device="cuda")
     smx = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp32_bf16", device=True)
@@ -130,7 +130,7 @@ def test_cfg3_32_rhs_full_size():
     _check_sampled_eigs(s64, w, A, [0, 1000, 2047, 4095])
 
 
-def _cfg5_loss_and_grad(w, solver, logk_np, d, obs, rtol):
+def _grf3d_loss_and_grad(w, solver, logk_np, d, obs, rtol):
     faces = w.extra["faces"]
     logk = torch.tensor(logk_np.reshape(-1), dtype=torch.float64, device="cuda", requires_grad=True)
     vals = tpfa_values_from_logk(logk, faces)
@@ -142,8 +142,8 @@ def _cfg5_loss_and_grad(w, solver, logk_np, d, obs, rtol):
     return float(loss), logk.grad.detach().cpu().numpy(), u.detach()
 
 
-def test_cfg5_adjoint_gradient_vs_central_differences():
-    w = make_config5()
+def test_grf3d_96_adjoint_gradient_vs_central_differences():
+    w = make_grf3d_96_adjoint()
     obs = w.extra["obs"]
     # data from the perturbed ("truth") field
     rp, ci, vt = tpfa_csr(w.extra["logk_truth"], w.extra["faces"])
@@ -152,7 +152,7 @@ def test_cfg5_adjoint_gradient_vs_central_differences():
     d = ut[obs]
     st.close()
     s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp64", device=True)
-    L0, g, u0 = _cfg5_loss_and_grad(w, s, w.logk, d, obs, rtol=1e-12)
+    L0, g, u0 = _grf3d_loss_and_grad(w, s, w.logk, d, obs, rtol=1e-12)
     rng = np.random.default_rng(55)
     h = 1e-6
     rel = []
@@ -173,16 +173,16 @@ def test_cfg5_adjoint_gradient_vs_central_differences():
     assert np.median(rel) <= 1e-5 and rel.max() <= 1e-4, rel
 
 
-def test_cfg5_gradient_vs_oracle_on_16cubed_copy():
-    full = make_config5()
+def test_grf3d_96_gradient_vs_oracle_on_16cubed_copy():
+    full = make_grf3d_96_adjoint()
     logk = grf_logk((16, 16, 16), sigma=6.0, std=2.0, seed=5)
-    w = make_from_logk("cfg5_16", logk, 8, 6)
+    w = make_from_logk("grf3d_16_copy", logk, 8, 6)
     A = _A(w)
     rng = np.random.default_rng(9)
     obs = np.sort(rng.choice(w.n, size=256, replace=False))
     d = np.zeros(len(obs))
     s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp64", device=True)
-    L, g, u = _cfg5_loss_and_grad(w, s, logk, d, obs, rtol=1e-13)
+    L, g, u = _grf3d_loss_and_grad(w, s, logk, d, obs, rtol=1e-13)
     # oracle: dense adjoint, chained through the same face formulas
     o = OracleAMS(A, w.part, w.nparts, w.m)
     uo = pcg(A, w.rhs[0], o.apply, rtol=1e-13).u
@@ -201,8 +201,8 @@ def test_cfg5_gradient_vs_oracle_on_16cubed_copy():
     assert np.linalg.norm(g - gl) <= 1e-8 * np.linalg.norm(gl)
 
 
-def test_cfg4_batched_48_systems():
-    ws = make_config4()
+def test_batched_48_uneven_systems():
+    ws = make_batch48_uneven()
     systems = [(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m) for w in ws]
     nrhs = 8
     b = AmsBatchedSolver(systems, precision="fp32_bf16", device=True)

@@ -12,7 +12,7 @@ import pytest
 import scipy.linalg as la
 
 from oracle import OracleAMS, csr_to_scipy, pcg
-from workloads import make_config1, make_small_2d, make_small_3d
+from workloads import make_grf2d_64, make_small_2d, make_small_3d
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -36,7 +36,7 @@ def _proj(Psi, s):
 
 
 CASES = {
-    "cfg1": lambda: make_config1(),
+    "grf2d_64": lambda: make_grf2d_64(),
     "2d_ragged": lambda: make_small_2d(side=45, bs=10, m=3, std=2.0, sigma=3.0, seed=31, ny=37),
     "3d_b8": lambda: make_small_3d(side=16, bs=8, m=6, std=2.5, sigma=3.0, seed=32),
     "3d_ragged": lambda: make_small_3d(side=13, bs=5, m=4, std=2.0, sigma=2.0, seed=33),

@@ -23,11 +23,11 @@ from .darcy import (  # noqa: F401
     tpfa_csr,
     tpfa_face_list,
     tpfa_values_from_logk,
-    make_config1,
-    make_config2,
-    make_config3,
-    make_config4,
-    make_config5,
+    make_grf2d_64,
+    make_channels2d_1024,
+    make_grf3d_128_rhs32,
+    make_batch48_uneven,
+    make_grf3d_96_adjoint,
     make_small_2d,
     make_small_3d,
     make_from_logk,

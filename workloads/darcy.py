@@ -303,13 +303,13 @@ def make_small_3d(side=8, bs=4, m=2, std=1.0, sigma=2.0, seed=0, nrhs=1,
                   seed)
 
 
-def make_config1():
+def make_grf2d_64():
     """2-D 64x64 GRF Darcy (sigma 4, log-std 2), 8x8 blocks, m=4, 1 RHS."""
     logk = grf_logk((64, 64), sigma=4.0, std=2.0, seed=1)
     return _build("darcy2d_64x64_grf_b8_m4", logk, 8, 4, "unit", 1, 1)
 
 
-def make_config2(side=1024):
+def make_channels2d_1024(side=1024):
     """2-D 1024x1024 channelised Darcy (200 channels, k=1e6), 32x32 blocks,
     m=8, 1 RHS."""
     logk = channel_field((side, side), nchannels=200, kmax=1e6, seed=2)
@@ -317,7 +317,7 @@ def make_config2(side=1024):
                   "unit", 1, 2)
 
 
-def make_config3(side=128, nrhs=32):
+def make_grf3d_128_rhs32(side=128, nrhs=32):
     """3-D 128^3 lognormal Darcy (log-std 3, sigma 6), 8^3 blocks, m=6,
     32 RHS iid N(0,1)."""
     logk = grf_logk((side, side, side), sigma=6.0, std=3.0, seed=3)
@@ -325,7 +325,7 @@ def make_config3(side=128, nrhs=32):
                   nrhs, 3)
 
 
-def make_config4(nsys2d=24, nsys3d=24, lo2=128, hi2=512, lo3=32, hi3=96,
+def make_batch48_uneven(nsys2d=24, nsys3d=24, lo2=128, hi2=512, lo3=32, hi3=96,
                  nrhs=8, seed=4) -> List[Workload]:
     """48 uneven systems: 2-D sides U[128,512] and 3-D sides U[32,96],
     log-std U[2,3], 8^d blocks (partial at the far edges), m U{4..8},
@@ -345,7 +345,7 @@ def make_config4(nsys2d=24, nsys3d=24, lo2=128, hi2=512, lo3=32, hi3=96,
     return out
 
 
-def make_config5(side=96, nobs=4096, seed=5):
+def make_grf3d_96_adjoint(side=96, nobs=4096, seed=5):
     """3-D 96^3 lognormal Darcy (log-std 2, sigma 6), f=1, 8^3 blocks, m=6.
 
     ``extra`` holds the observation cells (``obs``, drawn without
