@@ -42,6 +42,14 @@ Readings where the paper is silent (each is listed in the design notes):
   beta_k = z_{k+1}^T (r_{k+1} - r_k) / (z_k^T r_k).
 * Adjoint (not in the paper): lambda = A^{-1} g by the same PCG,
   dL/dA_ij = -lambda_i u_j on A's pattern, dL/df = lambda.
+* Multiplicative two-grid cycle (the two-grid algorithm stated with the
+  coarse space in Section 3.2: pre-smoothing, coarse-grid correction,
+  post-smoothing; the Analysis of Section 4 carries its smoother constant
+  C).  The paper names "a smoother S" without fixing it; this reading takes
+  the local solves, damped: S = omega sum_i R_i^T A_i^{-1} R_i, the same
+  smoother before and after the correction (so the cycle is symmetric),
+  omega given by the caller (the cycle is SPD when
+  0 < omega < 2 / lambda_max(sum_i R_i^T A_i^{-1} R_i A)).
 """
 
 from __future__ import annotations
@@ -247,6 +255,28 @@ class OracleAMS:
 
     def apply(self, r: np.ndarray) -> np.ndarray:
         return self.local_part(r) + self.coarse_part(r)
+
+    # One two-grid cycle for A x = r from x^0 = 0 (Section 3.2's two-grid
+    # algorithm): x^1 = S r; coarse residual R_0 (r - A x^1), solved with
+    # A_0 and added back through R_0^T; x^3 = x^2 + S (r - A x^2); with the
+    # damped local solves as S.
+    def apply_two_grid(self, r: np.ndarray, omega: float) -> np.ndarray:
+        x1 = omega * self.local_part(r)
+        x2 = x1 + self.coarse_part(r - self.A @ x1)
+        return x2 + omega * self.local_part(r - self.A @ x2)
+
+    def local_lambda_max(self) -> float:
+        """Largest eigenvalue of T = (sum_i R_i^T A_i^{-1} R_i) A.  The sum of
+        local solves is the inverse of the block-diagonal part D of A (its
+        entries inside subdomains), so lambda_max(T) is the largest
+        eigenvalue of the SPD pencil A x = lambda D x (Lanczos)."""
+        A = self.A.tocoo()
+        same = self.part[A.row] == self.part[A.col]
+        D = sp.csr_matrix((A.data[same], (A.row[same], A.col[same])), shape=A.shape)
+        Dinv = spla.LinearOperator(A.shape, matvec=self.local_part, dtype=np.float64)
+        lam = spla.eigsh(self.A, k=1, M=D, Minv=Dinv, which="LA", tol=1e-12,
+                         return_eigenvectors=False)
+        return float(lam[0])
 
     def dense_Minv(self) -> np.ndarray:
         return np.column_stack([self.apply(e) for e in np.eye(self.n)])

@@ -127,3 +127,33 @@ def test_mutation_adjoint_sign(monkeypatch):
 
     _patch(monkeypatch, "adjoint_gradient", bad)
     _expect_some_pin_fails([P.test_adjoint_matches_dense_and_closed_form_and_fd])
+
+
+_TWO_GRID_PINS = [P.test_two_grid_cycle_is_symmetric_positive_definite,
+                  P.test_two_grid_full_coarse_space_is_the_inverse,
+                  P.test_two_grid_without_coarse_space_is_the_symmetrised_smoother,
+                  P.test_two_grid_identity_of_the_abstract_theory]
+
+
+@pytest.mark.parametrize("mistake", ["no_post_smoothing", "coarse_on_r", "post_residual_sign",
+                                     "undamped_post_smoothing"])
+def test_mutation_two_grid_cycle(monkeypatch, mistake):
+    """A dropped post-smoothing step, a coarse correction of r instead of
+    the residual, a wrong sign in the post-smoothing residual, or damping
+    on one smoothing step only."""
+    def bad(self, r, omega):
+        x1 = omega * self.local_part(r)
+        if mistake == "coarse_on_r":
+            x2 = x1 + self.coarse_part(r)
+        else:
+            x2 = x1 + self.coarse_part(r - self.A @ x1)
+        if mistake == "no_post_smoothing":
+            return x2
+        if mistake == "post_residual_sign":
+            return x2 + omega * self.local_part(r + self.A @ x2)
+        if mistake == "undamped_post_smoothing":
+            return x2 + self.local_part(r - self.A @ x2)
+        raise AssertionError(mistake)
+
+    monkeypatch.setattr(O.OracleAMS, "apply_two_grid", bad)
+    _expect_some_pin_fails(_TWO_GRID_PINS)

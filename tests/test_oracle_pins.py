@@ -447,3 +447,114 @@ def test_adjoint_matches_dense_and_closed_form_and_fd():
         fd = (lp - lm) / (2 * h)
         an = dlogk @ v
         assert abs(fd - an) <= 1e-5 * max(abs(an), 1e-30)
+
+
+# ------------------------------------------------- multiplicative two-grid cycle
+
+def _dense(op, n):
+    return np.column_stack([op(e) for e in np.eye(n)])
+
+
+def _two_grid_case(m=3, seed=5):
+    w = make_small_2d(side=24, bs=6, m=m, std=2.0, sigma=3.0, seed=seed)
+    A = _A(w)
+    return w, A, OracleAMS(A, w.part, w.nparts, w.m)
+
+
+def test_two_grid_cycle_is_symmetric_positive_definite():
+    """Pre- and post-smoothing with the same symmetric smoother make the
+    cycle symmetric; with a convergent smoother (omega < 2/lambda_max(SA))
+    and an exact coarse solve, the spectrum of B A lies in (0, 1]."""
+    w, A, o = _two_grid_case()
+    lmax = o.local_lambda_max()
+    Ad = A.toarray()
+    Sd = _dense(o.local_part, o.n)
+    exact = la.eigvals(Sd @ Ad).real.max()
+    assert exact * (1 - 1e-6) <= lmax <= exact * (1 + 1e-12)
+    for omega in (0.5 / lmax, 1.0 / lmax, 1.9 / lmax):
+        B = _dense(lambda r: o.apply_two_grid(r, omega), o.n)
+        assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+        ev = la.eigvals(B @ Ad).real
+        assert ev.min() > 0 and ev.max() <= 1 + 1e-10
+
+
+def test_two_grid_full_coarse_space_is_the_inverse():
+    """Keeping every local mode makes the coarse correction exact: the
+    error after it is zero and post-smoothing keeps it zero, so B = A^{-1}
+    for any omega."""
+    w = make_small_2d(side=12, bs=4, m=16, std=2.0, seed=21)
+    A = _A(w)
+    o = OracleAMS(A, w.part, w.nparts, 16)
+    assert o.Nc == o.n
+    Ainv = la.inv(A.toarray())
+    for omega in (0.3, 0.7, 1.0):
+        B = _dense(lambda r: o.apply_two_grid(r, omega), o.n)
+        assert np.abs(B - Ainv).max() <= 1e-9 * np.abs(Ainv).max()
+
+
+def test_two_grid_without_coarse_space_is_the_symmetrised_smoother():
+    """With no coarse space the cycle is two smoothing steps,
+    B = 2 omega S - omega^2 S A S (S the sum of local solves)."""
+    w = make_small_2d(side=16, bs=4, m=2, std=2.0, seed=22)
+    A = _A(w)
+    o = OracleAMS(A, w.part, w.nparts, 0, coarse=False)
+    Sd = _dense(o.local_part, o.n)
+    Ad = A.toarray()
+    omega = 0.6
+    B = _dense(lambda r: o.apply_two_grid(r, omega), o.n)
+    ref = 2 * omega * Sd - omega ** 2 * Sd @ Ad @ Sd
+    assert np.abs(B - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def _rbar_and_error(o, A, omega):
+    Ad = A.toarray()
+    Sd = _dense(o.local_part, o.n)
+    Rbar = 2 * omega * Sd - omega ** 2 * Sd @ Ad @ Sd       # symmetrised smoother
+    B = _dense(lambda r: o.apply_two_grid(r, omega), o.n)
+    E = np.eye(o.n) - B @ Ad                                # error propagation
+    normE = la.eigvals(E).real.max()                        # E is A-self-adjoint, >= 0
+    return Ad, Rbar, normE
+
+
+def test_two_grid_identity_of_the_abstract_theory():
+    """The two-grid identity the Analysis (Section 4) builds on:
+    ||E||_A = 1 - 1/K with K = max_v min_{v_c} ||v - v_c||^2_{Rbar^{-1}} /
+    ||v||_A^2 over the coarse space, Rbar the symmetrised smoother.  K is
+    computed here from a generalised eigenproblem, independently of the
+    cycle."""
+    for m, seed in ((2, 5), (4, 6)):
+        w, A, o = _two_grid_case(m=m, seed=seed)
+        omega = 1.0 / o.local_lambda_max()
+        Ad, Rbar, normE = _rbar_and_error(o, A, omega)
+        W = la.inv(Rbar)
+        P = o.R0T.toarray()
+        proj = P @ la.solve(P.T @ W @ P, P.T @ W)          # W-orthogonal projection onto range(P)
+        Q = np.eye(o.n) - proj
+        K = la.eigh(Q.T @ W @ Q, Ad, eigvals_only=True).max()
+        assert abs(normE - (1 - 1 / K)) <= 1e-8
+
+
+def test_two_grid_bound_of_the_convergence_theorem():
+    """Section 4: ||E||_A <= 1 - mu_c / C, where mu_c = min_i lambda^(i)_{m_i+1}
+    (the first local eigenvalue left out of the coarse space) and C bounds
+    the symmetrised smoother against the weighting matrix,
+    ||v||^2_{Rbar^{-1}} <= C ||v||^2_S."""
+    w, A, o = _two_grid_case(m=3, seed=7)
+    omega = 1.0 / o.local_lambda_max()
+    Ad, Rbar, normE = _rbar_and_error(o, A, omega)
+    s = np.zeros(o.n)
+    for dofs in o.sub_dofs:
+        s[dofs] = local_matrices(A, dofs)[2]
+    d = 1 / np.sqrt(s)
+    C = la.eigh(d[:, None] * la.inv(Rbar) * d[None, :], eigvals_only=True).max()
+    mu_c = min(lam[Psi.shape[1]] for lam, Psi in zip(o.lams, o.Psis))
+    assert 0 < normE <= 1 - mu_c / C + 1e-12
+
+
+def test_two_grid_pcg_reaches_the_dense_solution():
+    w, A, o = _two_grid_case()
+    omega = 1.0 / o.local_lambda_max()
+    res = pcg(A, w.rhs[0], lambda r: o.apply_two_grid(r, omega), rtol=1e-10)
+    u = la.solve(A.toarray(), w.rhs[0], assume_a="pos")
+    assert res.converged
+    assert np.linalg.norm(res.u - u) <= 1e-8 * np.linalg.norm(u)
