@@ -442,6 +442,61 @@ void recurse(const Graph& g, const std::vector<int32_t>& ids, int32_t k, int32_t
     }
 }
 
+// Greedy k-way refinement of the final partition: each boundary vertex
+// moves to the neighbouring part it has the most edges into when that beats
+// the edges into its own part (or ties them and evens the sizes), as long as
+// the receiving part stays within maxsize and the giving part keeps a
+// vertex.  Passes repeat until one moves nothing.
+void kway_refine(const Graph& g, int32_t* part, int32_t k, int64_t maxsize, int passes) {
+    std::vector<int64_t> size(k, 0);
+    for (int32_t v = 0; v < g.n; ++v) ++size[part[v]];
+    std::vector<int32_t> nb_part;
+    std::vector<int64_t> nb_w;
+    for (int pass = 0; pass < passes; ++pass) {
+        int64_t moved = 0;
+        for (int32_t v = 0; v < g.n; ++v) {
+            const int32_t own = part[v];
+            nb_part.clear();
+            nb_w.clear();
+            int64_t in = 0;
+            for (int64_t e = g.xadj[v]; e < g.xadj[v + 1]; ++e) {
+                const int32_t q = part[g.adj[e]];
+                if (q == own) {
+                    in += g.ew[e];
+                    continue;
+                }
+                size_t j = 0;
+                while (j < nb_part.size() && nb_part[j] != q) ++j;
+                if (j == nb_part.size()) {
+                    nb_part.push_back(q);
+                    nb_w.push_back(0);
+                }
+                nb_w[j] += g.ew[e];
+            }
+            if (nb_part.empty() || size[own] <= 1) continue;
+            int32_t best = -1;
+            int64_t bw = 0;
+            for (size_t j = 0; j < nb_part.size(); ++j) {
+                const int32_t q = nb_part[j];
+                if (size[q] + 1 > maxsize) continue;
+                const bool better = nb_w[j] > in || (nb_w[j] == in && size[q] + 1 < size[own]);
+                if (!better) continue;
+                if (best < 0 || nb_w[j] > bw || (nb_w[j] == bw && (size[q] < size[best] ||
+                                                                   (size[q] == size[best] && q < best)))) {
+                    best = q;
+                    bw = nb_w[j];
+                }
+            }
+            if (best < 0) continue;
+            part[v] = best;
+            --size[own];
+            ++size[best];
+            ++moved;
+        }
+        if (moved == 0) break;
+    }
+}
+
 }  // namespace
 
 ams_status partition_graph(int64_t n, const int64_t* rowptr, const int32_t* colind, int32_t nparts,
@@ -517,6 +572,15 @@ ams_status partition_graph(int64_t n, const int64_t* rowptr, const int32_t* coli
     std::vector<int32_t> ids(n);
     for (int32_t i = 0; i < (int32_t)n; ++i) ids[i] = i;
     recurse(g, ids, nparts, 0, ub, rng, part);
+    if (nparts > 1) {
+        int64_t largest = 0;
+        {
+            std::vector<int64_t> size(nparts, 0);
+            for (int32_t v = 0; v < (int32_t)n; ++v) largest = std::max(largest, ++size[part[v]]);
+        }
+        const int64_t maxsize = std::max<int64_t>(largest, (int64_t)std::floor((1.0 + imbalance) * (double)n / nparts));
+        kway_refine(g, part, nparts, maxsize, 8);
+    }
     if (edge_cut) {
         int64_t cut = 0;
         for (int32_t v = 0; v < (int32_t)n; ++v)
