@@ -295,7 +295,8 @@ class AmsSolver(_Base):
 class AmsBatchedSolver(_Base):
     """Several independent systems solved together (``ams_setup_batched``).
 
-    ``systems`` is a sequence of (rowptr, colind, vals, part, nparts, m).
+    ``systems`` is a sequence of (rowptr, colind, vals, part, nparts, m);
+    ``part=None`` takes the built-in partition of that system's pattern.
     The C ABI lays the systems' n_s x nrhs column-major blocks end to end;
     :meth:`pack` and :meth:`unpack` convert from and to lists of per-system
     (nrhs, n_s) arrays.
@@ -310,12 +311,12 @@ class AmsBatchedSolver(_Base):
         self.sizes = []
         for k, (rowptr, colind, vals, part, nparts, m) in enumerate(systems):
             arrs = (conv(rowptr, np.int64), conv(colind, np.int32), conv(vals, np.float64),
-                    conv(part, np.int32))
+                    conv(part, np.int32) if part is not None else None)
             keep.append(arrs)
             n = int(arrs[0].shape[0] - 1)
             self.sizes.append(n)
-            descs[k] = ams_system_desc(n, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]), _ptr(arrs[3]),
-                                       int(nparts), int(m))
+            descs[k] = ams_system_desc(n, _ptr(arrs[0]), _ptr(arrs[1]), _ptr(arrs[2]),
+                                       _ptr(arrs[3]) if arrs[3] is not None else None, int(nparts), int(m))
         self.n = int(sum(self.sizes))
         self.nsys = len(systems)
         self.opts = make_options(precision, cg, maxit, self.device, coarse, autotune=autotune)

@@ -357,6 +357,15 @@ def test_built_in_partition_when_none_is_given():
     A = sp.csr_matrix((w.vals, w.colind, w.rowptr), shape=(w.n, w.n))
     assert rel[0] <= 1e-8
     assert np.linalg.norm(w.rhs[0] - A @ u) <= 1e-6 * np.linalg.norm(w.rhs[0])
+    # a batch whose second system comes without a partition
+    w2 = make_small_2d(side=40, bs=8, m=3, std=2.0, sigma=2.0, seed=48)
+    b = AmsBatchedSolver([(w.rowptr, w.colind, w.vals, w.part, w.nparts, 4),
+                          (w2.rowptr, w2.colind, w2.vals, None, 10, 3)], precision="fp32_bf16")
+    ub, itb, relb = b.solve(b.pack([w.rhs[:1], w2.rhs[:1]]), 1, rtol=1e-8)
+    u1, u2 = b.unpack(ub, 1)
+    A2 = sp.csr_matrix((w2.vals, w2.colind, w2.rowptr), shape=(w2.n, w2.n))
+    assert (relb <= 1e-8).all()
+    assert np.linalg.norm(w2.rhs[0] - A2 @ u2[0]) <= 1e-6 * np.linalg.norm(w2.rhs[0])
 
 
 def test_profile_and_time_kernel_report_every_slot():
