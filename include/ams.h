@@ -88,6 +88,13 @@ typedef struct {
     int32_t eig_maxit;           /* local eigensolver iteration cap; 0 = default 300 */
     double eig_tol;              /* local eigenpair residual target; 0 = default 1e-13 */
     int64_t spin_budget_cycles;  /* budget of any bounded device wait; 0 = default */
+    double eig_threshold;        /* > 0: adaptive coarse space, m_i = the local
+                                    eigenvalues below this threshold (at least
+                                    1, at most m, grown across a cluster), so
+                                    that lambda_{m_i+1} >= threshold wherever
+                                    the cap m does not bind (mu_c of Section 4
+                                    is then at least the threshold);
+                                    0 (default) = m_i = min(m, n_i) */
 } ams_options;
 
 /* Fill *opt with the defaults listed above. */

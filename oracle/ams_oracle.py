@@ -119,17 +119,24 @@ def local_matrices(A: sp.csr_matrix, dofs: np.ndarray):
 
 
 def local_eigenpairs(Ahat: np.ndarray, s: np.ndarray, m: int,
-                     tie_rtol: float = 1e-8, all_pairs: bool = False):
+                     tie_rtol: float = 1e-8, all_pairs: bool = False,
+                     threshold: Optional[float] = None):
     """Smallest eigenpairs of \\hat A_i psi = lambda S_i psi
     (Eq. algebraic-eigenproblem).
 
     Dense LAPACK generalized symmetric solver; eigenvectors come out
     S_i-orthonormal.  Returns ``(lam_all, Psi, m_i)`` with Psi of shape
     (n_i, m_i).  ``lam_all`` holds every computed eigenvalue (ascending).
+    With ``threshold`` the count is adaptive: the modes with eigenvalue
+    below it, at least one and at most m, so that lambda_{m_i+1} >= threshold
+    wherever the cap does not bind (mu_c of Section 4 is then at least the
+    threshold).
     """
     n_i = Ahat.shape[0]
     lam, V = la.eigh(Ahat, np.diag(s))
     m_i = min(m, n_i)
+    if threshold is not None and m_i > 0:
+        m_i = max(1, int(np.count_nonzero(lam[:m_i] < threshold)))
     while 0 < m_i < n_i and abs(lam[m_i] - lam[m_i - 1]) <= tie_rtol * max(abs(lam[m_i]), 1e-300):
         m_i += 1
     Psi = V[:, :m_i].copy()
@@ -208,6 +215,7 @@ class OracleAMS:
     coarse: bool = True
     tie_rtol: float = 1e-8
     basis_round: Optional[str] = None     # None, "fp32" or "bf16"
+    eig_threshold: Optional[float] = None  # adaptive m_i (see local_eigenpairs)
 
     def __post_init__(self):
         A = self.A
@@ -221,7 +229,8 @@ class OracleAMS:
             Ai, Ahat, s = local_matrices(A, dofs)
             self.local_chol.append(la.cho_factor(Ai, lower=True))
             if self.coarse and self.m > 0:
-                lam, Psi, mi = local_eigenpairs(Ahat, s, self.m, self.tie_rtol)
+                lam, Psi, mi = local_eigenpairs(Ahat, s, self.m, self.tie_rtol,
+                                                threshold=self.eig_threshold)
             else:
                 lam, Psi, mi = np.zeros(0), np.zeros((len(dofs), 0)), 0
             self.lams.append(lam)

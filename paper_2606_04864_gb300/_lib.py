@@ -38,6 +38,7 @@ class ams_options(C.Structure):
         ("eig_maxit", C.c_int32),
         ("eig_tol", C.c_double),
         ("spin_budget_cycles", C.c_int64),
+        ("eig_threshold", C.c_double),
     ]
 
 

@@ -576,7 +576,9 @@ static ams_status setup_eigen(ams_handle h, const int64_t* d_rowptr, const int32
     }
     h->info.eig_iterations = std::min(it, maxit);
     h->info.eig_max_residual = *std::max_element(res.begin(), res.end());
-    // kept modes per subdomain: m_i = min(m, n_i), grown across a cut cluster
+    // kept modes per subdomain: m_i = min(m, n_i), or with a threshold the
+    // eigenvalues below it among those (at least one), grown across a cut
+    // cluster
     int64_t psi_tot = 0;
     h->h_lam.clear();
     h->mmax = 0;
@@ -585,6 +587,11 @@ static ams_status setup_eigen(ams_handle h, const int64_t* d_rowptr, const int32
         const int mreq_s = h->sys[S.seg].m;
         int mi = std::min(mreq_s, S.n);
         const double* th = &theta[(size_t)s * P];
+        if (h->opt.eig_threshold > 0.0 && mi > 0) {
+            int below = 0;
+            while (below < mi && th[below] < h->opt.eig_threshold) ++below;
+            mi = std::max(1, below);
+        }
         while (mi > 0 && mi < S.p && mi < kMaxM &&
                std::fabs(th[mi] - th[mi - 1]) <= 1e-8 * std::max(std::fabs(th[mi]), 1e-300))
             ++mi;
@@ -906,6 +913,10 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     else ams_options_default(&h->opt);
     if (h->opt.precision < 0 || h->opt.precision > 2) {
         set_error("unknown precision mode");
+        return AMS_ERR_INVALID_ARG;
+    }
+    if (!(h->opt.eig_threshold >= 0.0) || !std::isfinite(h->opt.eig_threshold)) {
+        set_error("eig_threshold must be finite and >= 0");
         return AMS_ERR_INVALID_ARG;
     }
     if (h->opt.maxit <= 0) h->opt.maxit = 10000;
@@ -1613,6 +1624,7 @@ void ams_options_default(ams_options* opt) {
     opt->eig_maxit = 0;
     opt->eig_tol = 0.0;
     opt->spin_budget_cycles = 0;
+    opt->eig_threshold = 0.0;
 }
 
 const char* ams_status_string(ams_status s) {

@@ -368,6 +368,29 @@ def test_built_in_partition_when_none_is_given():
     assert np.linalg.norm(w2.rhs[0] - A2 @ u2[0]) <= 1e-6 * np.linalg.norm(w2.rhs[0])
 
 
+def test_threshold_coarse_space_matches_oracle():
+    """ams_options.eig_threshold: each subdomain keeps its local eigenvalues
+    below the threshold (at least one, at most m); the counts equal the
+    oracle's, subdomain by subdomain, and the FP64 solve matches the
+    oracle's PCG on that coarse space."""
+    w = make_small_2d(side=24, bs=6, m=8, std=2.0, sigma=3.0, seed=9)
+    A = csr_to_scipy(w.rowptr, w.colind, w.vals)
+    theta = 0.08
+    o = OracleAMS(A, w.part, w.nparts, 8, eig_threshold=theta)
+    near = np.concatenate([lam[:9] for lam in o.lams])
+    assert np.min(np.abs(near - theta)) > 1e-3 * theta      # no count decided within rounding
+    assert len(set(o.m_i)) > 1                              # the count does vary
+    s = _solver(w, precision="fp64", eig_threshold=theta)
+    mi, lam, psi = s.coarse_basis()
+    assert mi.tolist() == list(o.m_i)
+    ref = pcg(A, w.rhs[0], o.apply, rtol=1e-8)
+    u, its, rel = s.solve(w.rhs[0], rtol=1e-8)
+    assert abs(int(its[0]) - ref.iters) <= 2
+    assert np.linalg.norm(u - ref.u) <= 1e-10 * np.linalg.norm(ref.u)
+    with pytest.raises(AmsError):
+        _solver(w, precision="fp64", eig_threshold=-1.0)
+
+
 def test_profile_and_time_kernel_report_every_slot():
     """ams_profile_solve times every kernel slot of a real solve (one launch
     per slot and iteration, plus the first application), and ams_time_kernel

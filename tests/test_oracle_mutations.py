@@ -58,7 +58,7 @@ def test_mutation_weight_from_a_not_ahat(monkeypatch):
 def test_mutation_largest_instead_of_smallest_modes(monkeypatch):
     orig = O.local_eigenpairs
 
-    def bad(Ahat, s, m, tie_rtol=1e-8, all_pairs=False):
+    def bad(Ahat, s, m, tie_rtol=1e-8, all_pairs=False, threshold=None):
         lam, V = la.eigh(Ahat, np.diag(s))
         mi = min(m, Ahat.shape[0])
         return lam[::-1], V[:, ::-1][:, :mi].copy(), mi

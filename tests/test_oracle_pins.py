@@ -558,3 +558,50 @@ def test_two_grid_pcg_reaches_the_dense_solution():
     u = la.solve(A.toarray(), w.rhs[0], assume_a="pos")
     assert res.converged
     assert np.linalg.norm(res.u - u) <= 1e-8 * np.linalg.norm(u)
+
+
+# ------------------------------------------------ adaptive m_i by threshold
+
+def test_threshold_count_and_the_bound_it_buys():
+    """m_i = the local eigenvalues below the threshold (at least one, at most
+    m, grown across a cluster): every kept eigenvalue is below it except the
+    floor's single mode, the first left out is at or above it unless the cap
+    binds, so mu_c >= threshold; with the two-grid cycle the Section 4 bound
+    then gives ||E||_A <= 1 - threshold / C."""
+    w = make_small_2d(side=24, bs=6, m=8, std=2.0, sigma=3.0, seed=9)
+    A = _A(w)
+    theta = 0.08
+    o = OracleAMS(A, w.part, w.nparts, 8, eig_threshold=theta)
+    capped = 0
+    for dofs, lam, Psi in zip(o.sub_dofs, o.lams, o.Psis):
+        Ai, Ahat, s = local_matrices(A, dofs)
+        ref = la.eigh(Ahat, np.diag(s), eigvals_only=True)      # independent count
+        mi = Psi.shape[1]
+        below = int(np.count_nonzero(ref < theta))
+        assert mi == min(max(below, 1), 8) or (mi > min(max(below, 1), 8) and
+                                                abs(ref[mi - 1] - ref[mi - 2]) <= 1e-8 * abs(ref[mi - 1]))
+        if mi < 8:
+            assert ref[mi] >= theta
+        else:
+            capped += 1
+    assert capped < len(o.sub_dofs)
+    if capped == 0:
+        omega = 1.0 / o.local_lambda_max()
+        Ad, Rbar, normE = _rbar_and_error(o, A, omega)
+        sw = np.zeros(o.n)
+        for dofs in o.sub_dofs:
+            sw[dofs] = local_matrices(A, dofs)[2]
+        d = 1 / np.sqrt(sw)
+        C = la.eigh(d[:, None] * la.inv(Rbar) * d[None, :], eigvals_only=True).max()
+        assert normE <= 1 - theta / C + 1e-12
+
+
+def test_higher_threshold_keeps_more_modes_and_no_more_iterations():
+    w = make_small_2d(side=24, bs=6, m=8, std=2.0, sigma=3.0, seed=9)
+    A = _A(w)
+    prev_m, prev_it = -1, 10 ** 9
+    for theta in (0.02, 0.08, 0.3):
+        o = OracleAMS(A, w.part, w.nparts, 8, eig_threshold=theta)
+        res = pcg(A, w.rhs[0], o.apply, rtol=1e-10)
+        assert o.Nc >= prev_m and res.iters <= prev_it + 1
+        prev_m, prev_it = o.Nc, res.iters
