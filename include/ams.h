@@ -87,7 +87,10 @@ typedef struct {
     double eig_shift;            /* shift sigma of the local eigensolver; 0 = default 1e-2 */
     int32_t eig_maxit;           /* local eigensolver iteration cap; 0 = default 300 */
     double eig_tol;              /* local eigenpair residual target; 0 = default 1e-13 */
-    int64_t spin_budget_cycles;  /* budget of any bounded device wait; 0 = default */
+    int64_t spin_budget_cycles;  /* reserved: every bounded device wait (the
+                                    TMA staging's mbarrier waits) currently
+                                    polls at most 2^20 times, whatever this
+                                    field holds */
     double eig_threshold;        /* > 0: adaptive coarse space, m_i = the local
                                     eigenvalues below this threshold (at least
                                     1, at most m, grown across a cluster), so
