@@ -157,3 +157,61 @@ def test_mutation_two_grid_cycle(monkeypatch, mistake):
 
     monkeypatch.setattr(O.OracleAMS, "apply_two_grid", bad)
     _expect_some_pin_fails(_TWO_GRID_PINS)
+
+
+def test_mutation_coarse_matrix_without_a(monkeypatch):
+    """A_0 = R_0 R_0^T: the operator dropped from the Galerkin product."""
+    def bad(A, R0T):
+        return (R0T.T @ R0T).toarray()
+
+    _patch(monkeypatch, "coarse_matrix", bad)
+    _expect_some_pin_fails([P.test_coarse_matrix_spd_and_galerkin_brute_force,
+                            P.test_full_coarse_space_reproduces_inverse])
+
+
+def test_mutation_local_solve_with_a_perturbed_block(monkeypatch):
+    """The fine-level solves factor A_i with its diagonal scaled by 1.05."""
+    orig = O.local_matrices
+
+    def bad(A, dofs):
+        Ai, Ahat, s = orig(A, dofs)
+        Ai = Ai + 0.05 * np.diag(np.diag(Ai))
+        return Ai, Ahat, s
+
+    _patch(monkeypatch, "local_matrices", bad)
+    _expect_some_pin_fails([P.test_single_subdomain_converges_in_one_iteration,
+                            P.test_local_matrix_definitions_brute_force])
+
+
+@pytest.mark.parametrize("mistake", ["loose_threshold", "off_by_one"])
+def test_mutation_threshold_count(monkeypatch, mistake):
+    """The adaptive count taken against 1.5 times the threshold, or one mode
+    short (down to zero modes)."""
+    orig = O.local_eigenpairs
+
+    def bad(Ahat, s, m, tie_rtol=1e-8, all_pairs=False, threshold=None):
+        lam, Psi, mi = orig(Ahat, s, m, tie_rtol, all_pairs, None)
+        if threshold is None:
+            return lam, Psi, mi
+        cap = min(m, Ahat.shape[0])
+        if mistake == "loose_threshold":
+            k = max(1, int(np.count_nonzero(lam[:cap] <= threshold * 1.5)))
+        else:
+            k = int(np.count_nonzero(lam[:cap] < threshold)) - 1
+            k = max(k, 0)
+        Psi_all = orig(Ahat, s, max(k, 1), tie_rtol, all_pairs, None)[1]
+        return lam, Psi_all[:, :k], k
+
+    _patch(monkeypatch, "local_eigenpairs", bad)
+    _expect_some_pin_fails([P.test_threshold_count_and_the_bound_it_buys])
+
+
+def test_mutation_smoother_lambda_max_from_point_jacobi(monkeypatch):
+    """lambda_max taken for the point-Jacobi pencil (A, diag A) instead of
+    the block-diagonal one."""
+    def bad(self):
+        d = self.A.diagonal()
+        return float(la.eigh(self.A.toarray(), np.diag(d), eigvals_only=True).max())
+
+    monkeypatch.setattr(O.OracleAMS, "local_lambda_max", bad)
+    _expect_some_pin_fails([P.test_two_grid_cycle_is_symmetric_positive_definite])
