@@ -5,14 +5,17 @@
 // recursive bisection.  Each bisection coarsens the graph by heavy-edge
 // matching, splits the coarsest graph by region growing from several seeds,
 // and refines the split on every level on the way back with
-// Fiduccia-Mattheyses passes under a balance constraint.  Host code only;
-// the result depends on the seed alone (integer arithmetic, total orders).
+// Fiduccia-Mattheyses passes under a balance constraint.  Host code only,
+// large splits on threads of their own; the result depends on the seed
+// alone (integer arithmetic, total orders, per-split generators).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
 #include <memory>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "ams_internal.h"
@@ -425,20 +428,52 @@ void ensure_counts(const Graph& g, std::vector<uint8_t>& side, int32_t k0, int32
     }
 }
 
-void recurse(const Graph& g, const std::vector<int32_t>& ids, int32_t k, int32_t part0, double ub, Rng& rng,
-             int32_t* part) {
+// Splits run on their own threads down to subgraphs of kParallelMin
+// vertices, at most `threads` at a time.  Each split seeds its generator
+// from (seed, first part, parts), so the partition does not depend on the
+// thread schedule.
+struct RecurseCtx {
+    uint64_t seed;
+    double ub;
+    int32_t* part;
+    std::atomic<int> spare;     // threads that may still be started
+    std::atomic<bool> failed;   // a split on another thread threw
+};
+constexpr int32_t kParallelMin = 20000;
+
+void recurse(const Graph& g, const std::vector<int32_t>& ids, int32_t k, int32_t part0, RecurseCtx& C) {
     if (k == 1) {
-        for (int32_t i = 0; i < g.n; ++i) part[ids[i]] = part0;
+        for (int32_t i = 0; i < g.n; ++i) C.part[ids[i]] = part0;
         return;
     }
     const int32_t k0 = k / 2, k1 = k - k0;
-    std::vector<uint8_t> side = bisect(g, (double)k0 / k, ub, rng);
+    Rng rng{C.seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(part0 + 1)) ^ ((uint64_t)k << 40)};
+    std::vector<uint8_t> side = bisect(g, (double)k0 / k, C.ub, rng);
     ensure_counts(g, side, k0, k1);
-    for (int s = 0; s < 2; ++s) {
-        std::vector<int32_t> sub_ids;
-        Graph h = induced(g, side, s, sub_ids);
-        for (auto& v : sub_ids) v = ids[v];
-        recurse(h, sub_ids, s == 0 ? k0 : k1, s == 0 ? part0 : part0 + k0, ub, rng, part);
+    std::vector<int32_t> ids0, ids1;
+    Graph h0 = induced(g, side, 0, ids0);
+    Graph h1 = induced(g, side, 1, ids1);
+    for (auto& v : ids0) v = ids[v];
+    for (auto& v : ids1) v = ids[v];
+    side.clear();
+    side.shrink_to_fit();
+    std::thread t;
+    if (h0.n >= kParallelMin && k0 > 1 && C.spare.fetch_sub(1) > 0) {
+        t = std::thread([&]() {
+            try {
+                recurse(h0, ids0, k0, part0, C);
+            } catch (...) {
+                C.failed = true;
+            }
+        });
+    } else {
+        if (h0.n >= kParallelMin && k0 > 1) C.spare.fetch_add(1);
+        recurse(h0, ids0, k0, part0, C);
+    }
+    recurse(h1, ids1, k1, part0 + k0, C);
+    if (t.joinable()) {
+        t.join();
+        C.spare.fetch_add(1);
     }
 }
 
@@ -568,10 +603,21 @@ ams_status partition_graph(int64_t n, const int64_t* rowptr, const int32_t* coli
     // the bisections on the way down share that factor
     const int levels = (int)std::ceil(std::log2((double)nparts));
     const double ub = levels > 0 ? std::pow(1.0 + imbalance, 1.0 / levels) : 1.0 + imbalance;
-    Rng rng{seed};
     std::vector<int32_t> ids(n);
     for (int32_t i = 0; i < (int32_t)n; ++i) ids[i] = i;
-    recurse(g, ids, nparts, 0, ub, rng, part);
+    RecurseCtx ctx{seed, ub, part, {}, {}};
+    ctx.spare = (int)std::min(std::thread::hardware_concurrency(), 64u) - 1;
+    ctx.failed = false;
+    try {
+        recurse(g, ids, nparts, 0, ctx);
+    } catch (const std::exception& e) {   // thread start or allocation failure
+        set_error(std::string("partition: ") + e.what());
+        return AMS_ERR_OOM;
+    }
+    if (ctx.failed) {
+        set_error("partition: a split failed (allocation or thread start)");
+        return AMS_ERR_OOM;
+    }
     if (nparts > 1) {
         int64_t largest = 0;
         {
