@@ -98,6 +98,13 @@ typedef struct {
                                     the cap m does not bind (mu_c of Section 4
                                     is then at least the threshold);
                                     0 (default) = m_i = min(m, n_i) */
+    double two_grid_omega;       /* > 0: precondition with the multiplicative
+                                    two-grid cycle of Section 3.2 (smoother
+                                    omega sum_i R_i^T A_i^{-1} R_i before and
+                                    after the coarse correction; SPD for
+                                    0 < omega < 2 / lambda_max of the local
+                                    solves times A); 0 (default) = the
+                                    additive two-level preconditioner */
 } ams_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -39,6 +39,7 @@ class ams_options(C.Structure):
         ("eig_tol", C.c_double),
         ("spin_budget_cycles", C.c_int64),
         ("eig_threshold", C.c_double),
+        ("two_grid_omega", C.c_double),
     ]
 
 

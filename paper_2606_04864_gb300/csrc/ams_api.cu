@@ -155,6 +155,7 @@ struct ams_handle_s {
     double *d_x = nullptr, *d_r = nullptr, *d_p = nullptr, *d_q = nullptr, *d_z = nullptr;
     double* d_p2 = nullptr;             // second direction buffer (iterations alternate p and p2)
     void *d_zf = nullptr, *d_rc = nullptr, *d_yc = nullptr, *d_ec = nullptr;
+    double* d_tw = nullptr;     // two-grid cycle: residual of the current iterate
     double *d_stage_in = nullptr, *d_stage_out = nullptr, *d_stage_aux = nullptr;
     double* d_stage_dvals = nullptr;
     CgScalars* d_sc = nullptr;
@@ -915,6 +916,10 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
         set_error("unknown precision mode");
         return AMS_ERR_INVALID_ARG;
     }
+    if (!(h->opt.two_grid_omega >= 0.0) || !std::isfinite(h->opt.two_grid_omega)) {
+        set_error("two_grid_omega must be finite and >= 0");
+        return AMS_ERR_INVALID_ARG;
+    }
     if (!(h->opt.eig_threshold >= 0.0) || !std::isfinite(h->opt.eig_threshold)) {
         set_error("eig_threshold must be finite and >= 0");
         return AMS_ERR_INVALID_ARG;
@@ -1135,7 +1140,8 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
 static ams_status ensure_work(ams_handle h, int ld) {
     if (ld > h->ld_alloc) {
         for (void* p : {(void*)h->d_x, (void*)h->d_r, (void*)h->d_p, (void*)h->d_p2, (void*)h->d_q, (void*)h->d_z, h->d_zf, h->d_rc,
-                        h->d_yc, h->d_ec, (void*)h->d_stage_in, (void*)h->d_stage_out, (void*)h->d_stage_aux})
+                        h->d_yc, h->d_ec, (void*)h->d_stage_in, (void*)h->d_stage_out, (void*)h->d_stage_aux,
+                        (void*)h->d_tw})
             h->release(p);
         const size_t nv = (size_t)h->n_pad * ld;
         const size_t nc = (size_t)std::max<int64_t>(h->Nc, 1) * ld;
@@ -1152,6 +1158,8 @@ static ams_status ensure_work(ams_handle h, int ld) {
         AMS_TRY(h->alloc_t(&h->d_stage_in, (size_t)h->n_total * ld));
         AMS_TRY(h->alloc_t(&h->d_stage_out, (size_t)h->n_total * ld));
         AMS_TRY(h->alloc_t(&h->d_stage_aux, (size_t)h->n_total * ld));
+        h->d_tw = nullptr;
+        if (h->opt.two_grid_omega > 0.0) AMS_TRY(h->alloc_t(&h->d_tw, nv));
         h->ld_alloc = ld;
         h->ld_last = 0;
     }
@@ -1199,8 +1207,9 @@ static LocalTmaArgs local_tma_args(ams_handle h, int ld, const ResidIn& in, bool
                         h->use_pdl, h->tune[ld].depth, h->tune[ld].nr, h->tune[ld].l2mode, h->tune[ld].l2keep};
 }
 
-static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool with_state) {
-    const bool coarse = h->Nc > 0;
+static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool with_state,
+                               bool restrict_rc = true) {
+    const bool coarse = h->Nc > 0 && restrict_rc;
     if (h->use_tma) {
         LocalTmaArgs a = local_tma_args(h, ld, in, with_state);
         AMS_CUDA_TRY(launch_local_tma(a, h->prec, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
@@ -1238,12 +1247,58 @@ static ProlongArgs prolong_args(ams_handle h, int mode, const double* p, int ld)
                        p, h->d_z, std::max(1, h->mmax), h->flexible, mode};
 }
 
+// Multiplicative two-grid cycle z = B r' (Section 3.2's two-grid algorithm
+// from x^0 = 0; the smoother is omega times the local solves, before and
+// after the coarse-grid correction):
+//   x^1 = omega S r'                 local solves, scaled in place in z_f
+//   r_c = R_0 (r' - A x^1)           residual SpMV, restriction
+//   x^2 = x^1 + R_0^T A_0^{-1} r_c   coarse substitutions, prolongation (mode 0, into z)
+//   z   = x^2 + omega S (r' - A x^2) residual SpMV, local solves, combine in z_f
+// and the additive path's prolongation kernel, with the coarse term off,
+// applies z = z_f and the CG update of `mode` as in apply_precond.
+static ams_status apply_two_grid(ams_handle h, const LaunchCtx& L, int mode, const double* p) {
+    const bool with_state = mode != 0;
+    const double omega = h->opt.two_grid_omega;
+    const int64_t nv = h->n_pad * L.ld;
+    const ResidIn rin{h->d_r, mode == 2 ? h->d_q : nullptr, h->d_sc};
+    LaunchCtx L2 = L;
+    if (!with_state) L2.st = nullptr;
+    prof_begin(h, AMS_KERNEL_LOCAL);
+    AMS_TRY(launch_local(h, L.ld, rin, with_state, false));
+    launch_tg_scale(L2, h->prec, h->d_zf, omega, nv);
+    prof_end(h);
+    prof_begin(h, AMS_KERNEL_COARSE);
+    launch_tg_resid(L2, h->d_zf, h->prec == AMS_PREC_FP64, rin, h->d_tw);
+    launch_tg_restrict(L2, h->prec, h->d_psi, h->d_tw, h->d_rc, std::max(1, h->mmax));
+    h->launches += 4 + launch_coarse(h, L.ld, with_state);
+    prof_end(h);
+    prof_begin(h, AMS_KERNEL_PROLONG);
+    launch_prolong_update(L2, h->prec, prolong_args(h, 0, p, L.ld));   // z = x^2
+    launch_tg_resid(L2, h->d_z, 1, rin, h->d_tw);
+    prof_end(h);
+    prof_begin(h, AMS_KERNEL_LOCAL);
+    AMS_TRY(launch_local(h, L.ld, ResidIn{h->d_tw, nullptr, h->d_sc}, with_state, false));
+    launch_tg_combine(L2, h->prec, h->d_zf, h->d_z, omega, nv);
+    prof_end(h);
+    ProlongArgs a = prolong_args(h, mode, p, L.ld);
+    a.ec = nullptr;
+    a.yc = nullptr;
+    a.qmat = nullptr;
+    prof_begin(h, AMS_KERNEL_PROLONG);
+    launch_prolong_update(L2, h->prec, a);
+    prof_end(h);
+    h->launches += 5;   // prolongation, residual, local solves, combine, prolongation
+    AMS_CUDA_TRY(cudaGetLastError());
+    return AMS_OK;
+}
+
 // z = M^{-1} r' (internal layout).  mode 0: plain application (r' = r, no
 // dots); mode 1: first application of a solve (r' = r, rho = r.z); mode 2:
 // inside an iteration (r' = r - alpha q formed by the local solves and
 // stored by the prolongation together with x += alpha p, the dots and the
 // convergence test).  p is the direction of the current iteration.
 static ams_status apply_precond(ams_handle h, const LaunchCtx& L, int mode, const double* p) {
+    if (h->opt.two_grid_omega > 0.0 && h->Nc > 0) return apply_two_grid(h, L, mode, p);
     const bool coarse = h->Nc > 0;
     const bool with_state = mode != 0;
     prof_begin(h, AMS_KERNEL_LOCAL);
@@ -1625,6 +1680,7 @@ void ams_options_default(ams_options* opt) {
     opt->eig_tol = 0.0;
     opt->spin_budget_cycles = 0;
     opt->eig_threshold = 0.0;
+    opt->two_grid_omega = 0.0;
 }
 
 const char* ams_status_string(ams_status s) {

@@ -1,0 +1,169 @@
+// Kernels of the multiplicative two-grid cycle (the two-grid algorithm
+// stated with the coarse space in Section 3.2: pre-smoothing, coarse-grid
+// correction, post-smoothing), with the damped local solves
+// S = omega sum_i R_i^T A_i^{-1} R_i as the smoother before and after the
+// correction.  The local solves, the coarse substitutions and the
+// prolongation are the additive path's kernels; this file adds the pieces
+// the cycle needs in between:
+//   k_tg_resid    w = r' - A v   (r' = r - alpha q formed as the local
+//                                 solves form it; v the FP32/FP64 iterate)
+//   k_tg_scale    z_f <- omega z_f
+//   k_tg_restrict r_c = R_0 w    (restriction of a residual that is not
+//                                 the local solves' input)
+//   k_tg_combine  z_f <- x^2 + omega z_f
+#include <algorithm>
+#include <cstdint>
+
+#include "ams_internal.h"
+#include "kernels.cuh"
+#include "launch.h"
+
+namespace ams {
+
+template <typename T> __device__ __forceinline__ double tg_widen(T v);
+template <> __device__ __forceinline__ double tg_widen<float>(float v) { return f32_to_f64(v); }
+template <> __device__ __forceinline__ double tg_widen<double>(double v) { return v; }
+
+// w = r' - A v over the element layout of the SpMV (block ranges of
+// (row, rhs) elements, one system per block).
+template <int LD, typename TV>
+__global__ void __launch_bounds__(kRedThreads)
+k_tg_resid(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sell_col,
+           const double* __restrict__ sell_val, const TV* __restrict__ v, const double* __restrict__ r,
+           const double* __restrict__ q, RedLayout R, const CgScalars* __restrict__ sc,
+           const SolveState* st, double* __restrict__ w) {
+    pdl_wait();
+    if (st != nullptr && st->done) return;
+    const int rhs = threadIdx.x % LD;
+    double alpha = 0.0;
+    bool upd = false;
+    if (q != nullptr) {
+        const CgScalars c = sc[(int64_t)R.blk_seg[blockIdx.x] * LD + rhs];
+        upd = c.active != 0;
+        if (upd) alpha = c.rho / c.pq;
+    }
+    const int64_t lo = R.blk_lo[blockIdx.x], hi = R.blk_lo[blockIdx.x + 1];
+    for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) {
+        const int64_t row = e / LD;
+        const int64_t sl = row >> 5;
+        const int lane = (int)(row & 31);
+        const int64_t b0 = __ldg(sell_ptr + sl);
+        const int width = (int)((__ldg(sell_ptr + sl + 1) - b0) >> 5);
+        double acc = 0.0;
+        for (int j = 0; j < width; ++j) {
+            const int64_t o = b0 + 32 * j + lane;
+            acc = fma(__ldg(sell_val + o), tg_widen<TV>(v[(int64_t)__ldg(sell_col + o) * LD + rhs]), acc);
+        }
+        const double rv = upd ? fma(-alpha, q[e], r[e]) : r[e];
+        w[e] = rv - acc;
+    }
+}
+
+template <typename TF>
+__global__ void k_tg_scale(TF* __restrict__ zf, double omega, int64_t n, const SolveState* st) {
+    if (st != nullptr && st->done) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        zf[e] = (TF)(omega * tg_widen<TF>(zf[e]));
+}
+
+template <typename TF>
+__global__ void k_tg_combine(TF* __restrict__ zf, const double* __restrict__ x2, double omega, int64_t n,
+                             const SolveState* st) {
+    if (st != nullptr && st->done) return;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        zf[e] = (TF)fma(omega, tg_widen<TF>(zf[e]), x2[e]);
+}
+
+// r_c[(coff + k) ld + rhs] = sum over the subdomain's rows of
+// Psi_i[row][k] w[row, rhs]; one warp per (subdomain, rhs).
+template <typename TF, typename TP, int MM>
+__global__ void __launch_bounds__(256)
+k_tg_restrict(const SubInfo* __restrict__ subs, int nsub, const TP* __restrict__ psi,
+              const double* __restrict__ w, TF* __restrict__ rc, int ld, const SolveState* st) {
+    if (st != nullptr && st->done) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (gw >= (int64_t)nsub * ld) return;
+    const int sub = (int)(gw / ld), rhs = (int)(gw % ld);
+    const SubInfo S = subs[sub];
+    const int m = S.m;
+    if (m == 0) return;
+    double acc[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) acc[k] = 0.0;
+    for (int i = lane; i < S.n; i += 32) {
+        const double wv = w[(S.row0 + i) * ld + rhs];
+        const TP* pr = psi + S.psi_off + (int64_t)i * m;
+#pragma unroll
+        for (int k = 0; k < MM; ++k)
+            if (k < m) acc[k] = fma(to_d(pr[k]), wv, acc[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+        double a = acc[k];
+        for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+        if (lane == 0 && k < m) rc[(S.coff + k) * ld + rhs] = (TF)a;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <int LD, typename TV>
+static void resid_ld_t(const LaunchCtx& L, const TV* v, const ResidIn& in, double* w) {
+    launch_kernel(false, k_tg_resid<LD, TV>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream, L.sell_ptr,
+                  L.sell_col, L.sell_val, v, in.r, in.q, L.red, in.sc, (const SolveState*)L.st, w);
+}
+template <int LD>
+static void resid_ld(const LaunchCtx& L, const void* v, int v_kind, const ResidIn& in, double* w) {
+    if (v_kind == 0) resid_ld_t<LD, float>(L, (const float*)v, in, w);
+    else resid_ld_t<LD, double>(L, (const double*)v, in, w);
+}
+void launch_tg_resid(const LaunchCtx& L, const void* v, int v_is_fp64, const ResidIn& in, double* w) {
+    switch (L.ld) {
+        case 1: resid_ld<1>(L, v, v_is_fp64, in, w); break;
+        case 2: resid_ld<2>(L, v, v_is_fp64, in, w); break;
+        case 4: resid_ld<4>(L, v, v_is_fp64, in, w); break;
+        case 8: resid_ld<8>(L, v, v_is_fp64, in, w); break;
+        case 16: resid_ld<16>(L, v, v_is_fp64, in, w); break;
+        default: resid_ld<32>(L, v, v_is_fp64, in, w); break;
+    }
+}
+
+static unsigned tg_blocks(int64_t n) {
+    const int64_t b = (n + 255) / 256;
+    return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 16);
+}
+
+void launch_tg_scale(const LaunchCtx& L, int prec, void* zf, double omega, int64_t n) {
+    if (prec == AMS_PREC_FP64)
+        k_tg_scale<double><<<tg_blocks(n), 256, 0, L.stream>>>((double*)zf, omega, n, L.st);
+    else
+        k_tg_scale<float><<<tg_blocks(n), 256, 0, L.stream>>>((float*)zf, omega, n, L.st);
+}
+
+void launch_tg_combine(const LaunchCtx& L, int prec, void* zf, const double* x2, double omega, int64_t n) {
+    if (prec == AMS_PREC_FP64)
+        k_tg_combine<double><<<tg_blocks(n), 256, 0, L.stream>>>((double*)zf, x2, omega, n, L.st);
+    else
+        k_tg_combine<float><<<tg_blocks(n), 256, 0, L.stream>>>((float*)zf, x2, omega, n, L.st);
+}
+
+template <typename TF, typename TP>
+static void restrict_t(const LaunchCtx& L, const void* psi, const double* w, void* rc, int mmax) {
+    const int64_t warps = (int64_t)L.nsub * L.ld;
+    const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+    if (mmax > 8)
+        k_tg_restrict<TF, TP, kMaxM><<<blocks, 256, 0, L.stream>>>(L.subs, L.nsub, (const TP*)psi, w, (TF*)rc,
+                                                                   L.ld, L.st);
+    else
+        k_tg_restrict<TF, TP, 8><<<blocks, 256, 0, L.stream>>>(L.subs, L.nsub, (const TP*)psi, w, (TF*)rc, L.ld,
+                                                              L.st);
+}
+void launch_tg_restrict(const LaunchCtx& L, int prec, const void* psi, const double* w, void* rc, int mmax) {
+    if (prec == AMS_PREC_FP64) restrict_t<double, double>(L, psi, w, rc, mmax);
+    else if (prec == AMS_PREC_FP32) restrict_t<float, float>(L, psi, w, rc, mmax);
+    else restrict_t<float, __nv_bfloat16>(L, psi, w, rc, mmax);
+}
+
+}  // namespace ams

@@ -144,6 +144,13 @@ struct ProlongArgs {
     int mode;                // 0 apply only, 1 first application, 2 CG iteration
 };
 void launch_prolong_update(const LaunchCtx& L, int prec, const ProlongArgs& a);
+
+// multiplicative two-grid cycle (k_two_grid.cu); v_is_fp64: v holds doubles,
+// else the apply precision's floats
+void launch_tg_resid(const LaunchCtx& L, const void* v, int v_is_fp64, const ResidIn& in, double* w);
+void launch_tg_scale(const LaunchCtx& L, int prec, void* zf, double omega, int64_t n);
+void launch_tg_combine(const LaunchCtx& L, int prec, void* zf, const double* x2, double omega, int64_t n);
+void launch_tg_restrict(const LaunchCtx& L, int prec, const void* psi, const double* w, void* rc, int mmax);
 void launch_permute_in(cudaStream_t s, const double* f, int64_t n, int nrhs, int ld,
                        const int64_t* int_row, double* r, double* x);
 void launch_permute_out(cudaStream_t s, const double* x, int64_t n, int nrhs, int ld,

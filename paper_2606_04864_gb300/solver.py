@@ -63,7 +63,8 @@ def _ptr(a):
 
 
 def make_options(precision="fp32_bf16", cg="auto", maxit=10000, device=False, coarse=True,
-                 eig_shift=0.0, eig_maxit=0, eig_tol=0.0, autotune=True, eig_threshold=0.0) -> ams_options:
+                 eig_shift=0.0, eig_maxit=0, eig_tol=0.0, autotune=True, eig_threshold=0.0,
+                 two_grid_omega=0.0) -> ams_options:
     o = ams_options()
     lib().ams_options_default(C.byref(o))
     o.precision = _lib.PREC[precision] if isinstance(precision, str) else int(precision)
@@ -76,6 +77,7 @@ def make_options(precision="fp32_bf16", cg="auto", maxit=10000, device=False, co
     o.eig_tol = float(eig_tol)
     o.autotune = 1 if autotune else 0
     o.eig_threshold = float(eig_threshold)
+    o.two_grid_omega = float(two_grid_omega)
     return o
 
 
@@ -199,7 +201,7 @@ class AmsSolver(_Base):
 
     def __init__(self, rowptr, colind, vals, part, nparts: int, m: int, precision="fp32_bf16",
                  cg="auto", maxit=10000, device: bool = False, coarse=True, eig_shift=0.0,
-                 eig_maxit=0, eig_tol=0.0, autotune=True, eig_threshold=0.0):
+                 eig_maxit=0, eig_tol=0.0, autotune=True, eig_threshold=0.0, two_grid_omega=0.0):
         self.device = bool(device)
         conv = _as_dev if self.device else _as_host
         self._rowptr = conv(rowptr, np.int64)
@@ -211,7 +213,7 @@ class AmsSolver(_Base):
         self.nparts = int(nparts)
         self.nsys = 1
         self.opts = make_options(precision, cg, maxit, self.device, coarse, eig_shift, eig_maxit, eig_tol,
-                                 autotune, eig_threshold)
+                                 autotune, eig_threshold, two_grid_omega)
         h = C.c_void_p()
         st = lib().ams_setup(self.n, _ptr(self._rowptr), _ptr(self._colind), _ptr(self._vals),
                              _ptr(self._part) if self._part is not None else None, self.nparts, int(m),
