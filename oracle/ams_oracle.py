@@ -185,16 +185,25 @@ def coarse_matrix(A: sp.csr_matrix, R0T: sp.csr_matrix) -> np.ndarray:
 
 def round_basis(Psi: np.ndarray, mode: Optional[str]) -> np.ndarray:
     """Basis entries rounded to a storage precision (round to nearest, ties
-    to even).  Reading for the reduced-precision preconditioner: the coarse
-    matrix is formed in FP64 from the rounded basis, so the coarse correction
-    stays the exact Galerkin projection onto the stored space."""
+    to even), directly from FP64.  Reading for the reduced-precision
+    preconditioner: the coarse matrix is formed in FP64 from the rounded
+    basis, so the coarse correction stays the exact Galerkin projection onto
+    the stored space.
+
+    bfloat16 keeps 8 significant bits and the exponent range of binary32:
+    near |x| in [2^e-1, 2^e) its values are spaced 2^(e-8); below 2^-126
+    (subnormal) the spacing stays 2^-133; magnitudes that round to 2^128 or
+    beyond become infinite."""
     if mode is None:
         return Psi
     if mode == "fp32":
         return Psi.astype(np.float32).astype(np.float64)
     if mode == "bf16":
-        m, e = np.frexp(Psi)                  # Psi = m * 2^e, 0.5 <= |m| < 1
-        return np.ldexp(np.rint(m * 256.0), e - 8)
+        Psi = np.asarray(Psi, dtype=np.float64)
+        _, e = np.frexp(Psi)                  # Psi = m * 2^e, 0.5 <= |m| < 1
+        q = np.maximum(e, -125) - 8           # spacing 2^q of the bfloat16 values there
+        out = np.ldexp(np.rint(np.ldexp(Psi, -q)), q)
+        return np.where(np.abs(out) >= 2.0 ** 128, np.copysign(np.inf, Psi), out)
     raise ValueError(mode)
 
 

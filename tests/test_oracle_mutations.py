@@ -215,3 +215,36 @@ def test_mutation_smoother_lambda_max_from_point_jacobi(monkeypatch):
 
     monkeypatch.setattr(O.OracleAMS, "local_lambda_max", bad)
     _expect_some_pin_fails([P.test_two_grid_cycle_is_symmetric_positive_definite])
+
+
+def _bf16_pins():
+    return [P.test_bf16_rounding_hand_worked_values,
+            P.test_bf16_rounding_matches_integer_rounding_and_torch_on_binary32_inputs]
+
+
+@pytest.mark.parametrize("kind", ["seven_bits", "truncate", "half_away", "via_binary32", "no_subnormal"])
+def test_mutation_bf16_rounding(monkeypatch, kind):
+    """Plausible mistakes in the bfloat16 storage rounding: one bit short,
+    truncation, ties away from zero, double rounding through binary32, and
+    normal spacing carried below 2^-126."""
+    orig = O.round_basis
+
+    def bad(Psi, mode):
+        if mode != "bf16":
+            return orig(Psi, mode)
+        Psi = np.asarray(Psi, dtype=np.float64)
+        m, e = np.frexp(Psi)
+        if kind == "seven_bits":
+            return np.ldexp(np.rint(m * 128.0), e - 7)
+        if kind == "truncate":
+            return np.ldexp(np.trunc(m * 256.0), e - 8)
+        if kind == "half_away":
+            return np.ldexp(np.sign(m) * np.floor(np.abs(m) * 256.0 + 0.5), e - 8)
+        if kind == "via_binary32":
+            return orig(Psi.astype(np.float32).astype(np.float64), mode)
+        return np.ldexp(np.rint(m * 256.0), e - 8)        # no_subnormal
+
+    monkeypatch.setattr(O, "round_basis", bad)
+    import oracle.ams_oracle as OA
+    monkeypatch.setattr(OA, "round_basis", bad)
+    _expect_some_pin_fails(_bf16_pins())

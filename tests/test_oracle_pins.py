@@ -605,3 +605,81 @@ def test_higher_threshold_keeps_more_modes_and_no_more_iterations():
         res = pcg(A, w.rhs[0], o.apply, rtol=1e-10)
         assert o.Nc >= prev_m and res.iters <= prev_it + 1
         prev_m, prev_it = o.Nc, res.iters
+
+
+# ------------------------------------------------ reduced-precision basis storage
+# The mixed-precision parity tests compare the GPU with an oracle whose basis
+# is rounded the way the GPU stores it (round_basis), so the rounding itself
+# is pinned here against hand-worked values of the formats and two
+# independent converters.
+
+_BF16_CASES = [
+    # (input, bfloat16 value): 8 significant bits, round to nearest, ties to even
+    (1.0, 1.0),
+    (1.0 + 2.0 ** -9, 1.0),                              # below half a spacing (2^-7)
+    (1.0 + 2.0 ** -8, 1.0),                              # tie, 1.0 is even
+    (1.0 + 3 * 2.0 ** -9, 1.0 + 2.0 ** -7),              # above half
+    (1.0 + 3 * 2.0 ** -8, 1.0 + 2.0 ** -6),              # tie, 1+2^-7 is odd: up
+    (1.0 + 2.0 ** -8 + 2.0 ** -40, 1.0 + 2.0 ** -7),     # just above a tie: rounded from FP64 directly
+    (2.0 - 2.0 ** -9, 2.0),                              # carry into the exponent
+    (2.0 - 2.0 ** -8, 2.0),                              # tie, 2 - 2^-7 is odd: up to 2
+    (-(1.0 + 3 * 2.0 ** -9), -(1.0 + 2.0 ** -7)),        # sign symmetric
+    (0.3, 0.30078125),                                   # 0.3 = 1.2 * 2^-2 -> 154/128 * 2^-2
+    (-0.0, -0.0),
+    (0.0, 0.0),
+    (2.0 ** -130 + 2.0 ** -134, 2.0 ** -130),            # subnormal tie (8.5 spacings of 2^-133): even
+    (2.0 ** -130 + 3 * 2.0 ** -134, 5 * 2.0 ** -132),    # subnormal tie (9.5 spacings): up to 10
+    (2.0 ** -135, 0.0),                                  # a quarter spacing
+    (3 * 2.0 ** -135, 2.0 ** -133),                      # three quarters: the smallest subnormal
+    ((2 - 2.0 ** -7) * 2.0 ** 127, (2 - 2.0 ** -7) * 2.0 ** 127),   # largest finite value
+    ((2 - 2.0 ** -8) * 2.0 ** 127, np.inf),              # tie above it rounds to 2^128: overflow
+]
+
+
+def test_bf16_rounding_hand_worked_values():
+    from oracle.ams_oracle import round_basis
+    x = np.array([c[0] for c in _BF16_CASES])
+    want = np.array([c[1] for c in _BF16_CASES])
+    got = round_basis(x, "bf16")
+    assert np.array_equal(got, want), [(a, b, c) for a, b, c in zip(x, got, want) if b != c]
+    assert np.array_equal(np.signbit(got), np.signbit(want))
+
+
+def _bf16_rne_from_binary32_bits(x32: np.ndarray) -> np.ndarray:
+    """Textbook integer rounding of binary32 bit patterns to their upper 16
+    bits (add 0x7FFF plus the lowest kept bit, drop 16 bits); exact for
+    finite binary32 inputs, subnormals included."""
+    b = x32.view(np.uint32).astype(np.uint64)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) >> 16) << 16
+    return r.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_bf16_rounding_matches_integer_rounding_and_torch_on_binary32_inputs():
+    """On values that binary32 holds exactly, FP64 -> bfloat16 and
+    binary32 -> bfloat16 are the same rounding, so two independent
+    converters apply: the integer bit trick and torch's bfloat16 cast."""
+    import torch
+    from oracle.ams_oracle import round_basis
+    rng = np.random.default_rng(5)
+    parts = [rng.standard_normal(20000),
+             rng.uniform(-1, 1, 20000) * 2.0 ** rng.integers(-140, 120, 20000),   # wide exponents, subnormals
+             (1.0 + np.arange(512) * 2.0 ** -16) * rng.choice([-1.0, 1.0], 512)]  # every tie pattern near 1
+    x32 = np.concatenate(parts).astype(np.float32)
+    x32 = x32[np.isfinite(x32)]
+    x = x32.astype(np.float64)
+    got = round_basis(x, "bf16")
+    assert np.array_equal(got, _bf16_rne_from_binary32_bits(x32))
+    via_torch = torch.from_numpy(x32).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(got, via_torch)
+
+
+def test_fp32_rounding_matches_binary32():
+    from oracle.ams_oracle import round_basis
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal(1000) * 2.0 ** rng.integers(-160, 120, 1000)
+    got = round_basis(x, "fp32")
+    # binary32 keeps 24 significant bits: |x - fl(x)| <= 2^-24 |x| for normals
+    normal = np.abs(x) >= 2.0 ** -126
+    assert np.all(np.abs(got - x)[normal] <= 2.0 ** -24 * np.abs(x[normal]))
+    assert round_basis(np.array([1.0 + 2.0 ** -24]), "fp32")[0] == 1.0          # tie to even
+    assert round_basis(np.array([1.0 + 3 * 2.0 ** -24]), "fp32")[0] == 1.0 + 2.0 ** -22
