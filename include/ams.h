@@ -87,10 +87,16 @@ typedef struct {
     double eig_shift;            /* shift sigma of the local eigensolver; 0 = default 1e-2 */
     int32_t eig_maxit;           /* local eigensolver iteration cap; 0 = default 300 */
     double eig_tol;              /* local eigenpair residual target; 0 = default 1e-13 */
-    int64_t spin_budget_cycles;  /* reserved: every bounded device wait (the
-                                    TMA staging's mbarrier waits) currently
-                                    polls at most 2^20 times, whatever this
-                                    field holds */
+    int64_t spin_budget_cycles;  /* budget of every bounded device-side wait
+                                    (the local solves' mbarrier waits for
+                                    their factor-tile copies), in SM clock
+                                    cycles; 0 (default) = 2^30 (about half a
+                                    second).  A wait that runs out ends the
+                                    solve with AMS_ERR_DEVICE_TIMEOUT after
+                                    the block has waited (about a second at
+                                    most) for its own copies in flight; the
+                                    CUDA context stays usable.  Negative:
+                                    AMS_ERR_INVALID_ARG */
     double eig_threshold;        /* > 0: adaptive coarse space, m_i = the local
                                     eigenvalues below this threshold (at least
                                     1, at most m, grown across a cluster), so
@@ -104,7 +110,25 @@ typedef struct {
                                     after the coarse correction; SPD for
                                     0 < omega < 2 / lambda_max of the local
                                     solves times A); 0 (default) = the
-                                    additive two-level preconditioner */
+                                    additive two-level preconditioner.
+                                    With no coarse space (coarse = 0 or
+                                    every m_i = 0) the cycle is the
+                                    symmetrised smoother 2 omega S -
+                                    omega^2 S A S.  An omega at or above
+                                    2 / lambda_max makes the cycle
+                                    indefinite and CG may then stall or
+                                    report AMS_ERR_BREAKDOWN; setup does not
+                                    estimate lambda_max */
+    int32_t timeout_probe;       /* test hook, 0 (default) = off.  1: every
+                                    block of the local-solve kernels first
+                                    waits, within spin_budget_cycles, on a
+                                    barrier that nothing completes, so that
+                                    the timeout path (status, drain of the
+                                    copies in flight, clean exit) runs on
+                                    purpose; every solve then returns
+                                    AMS_ERR_DEVICE_TIMEOUT.  Applies to the
+                                    reduced-precision modes (the FP64 local
+                                    solves have no bounded waits) */
 } ams_options;
 
 /* Fill *opt with the defaults listed above. */

@@ -40,6 +40,7 @@ class ams_options(C.Structure):
         ("spin_budget_cycles", C.c_int64),
         ("eig_threshold", C.c_double),
         ("two_grid_omega", C.c_double),
+        ("timeout_probe", C.c_int32),
     ]
 
 

@@ -19,6 +19,12 @@ class AmsSolveFunction(torch.autograd.Function):
     def forward(ctx, vals, f, solver: AmsSolver, rtol: float, adjoint_rtol: float):
         if not solver.device:
             raise ValueError("AmsSolveFunction needs a solver built with device=True")
+        if vals.shape != (solver.nnz,):
+            raise ValueError(f"vals must hold the {solver.nnz} CSR values of the solver's pattern")
+        # the solve uses these values (device to device); the preconditioner
+        # built at setup is kept, so CG stays exact for the new matrix and
+        # converges fastest while it stays close to the setup matrix
+        solver.set_matrix_values(vals.detach())
         u, its, rel = solver.solve(f, rtol)
         ctx.solver = solver
         ctx.adjoint_rtol = adjoint_rtol
@@ -40,7 +46,9 @@ def ams_solve(vals: torch.Tensor, f: torch.Tensor, solver: AmsSolver, rtol: floa
               adjoint_rtol: float | None = None) -> torch.Tensor:
     """u = A(vals)^{-1} f, differentiable in ``vals`` and ``f``.
 
-    ``solver`` must have been set up (device=True) on the matrix whose CSR
-    values are ``vals``; the values tensor is the autograd leaf through
-    which dL/dA flows (its entries are not re-read by the forward)."""
+    ``solver`` must have been set up (device=True) on a matrix with the
+    CSR pattern of ``vals``.  Each call first loads ``vals`` into the
+    solver (``set_matrix_values``), so the forward solves with the matrix
+    these values define and the backward's adjoint solve and dL/dA use the
+    same matrix; the preconditioner stays the one built at setup."""
     return AmsSolveFunction.apply(vals, f, solver, rtol, rtol if adjoint_rtol is None else adjoint_rtol)

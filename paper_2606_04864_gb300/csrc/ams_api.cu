@@ -105,7 +105,7 @@ struct ams_handle_s {
     cudaStream_t stream = nullptr;      // internal non-blocking stream (all device work)
     cudaStream_t ustream = nullptr;     // caller's stream (ordering only)
     cudaEvent_t ev_enter = nullptr;
-    std::map<int, cudaGraphExec_t> iter_graph;   // one captured PCG iteration per ld
+    std::map<int, cudaGraphExec_t> loop_graph;   // device-resident iteration loop per ld
     KernelProfile* prof = nullptr;
     int prec = AMS_PREC_FP32_BF16;
     int flexible = 1;
@@ -194,7 +194,7 @@ struct ams_handle_s {
     }
     ~ams_handle_s() {
         if (stream) cudaStreamSynchronize(stream);
-        for (auto& g : iter_graph) cudaGraphExecDestroy(g.second);
+        for (auto& g : loop_graph) cudaGraphExecDestroy(g.second);
         for (auto& b : bufs)
             if (b.p) cudaFree(b.p);
         if (ev_enter) cudaEventDestroy(ev_enter);
@@ -920,6 +920,10 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
         set_error("two_grid_omega must be finite and >= 0");
         return AMS_ERR_INVALID_ARG;
     }
+    if (h->opt.spin_budget_cycles < 0 || h->opt.timeout_probe < 0 || h->opt.timeout_probe > 1) {
+        set_error("spin_budget_cycles must be >= 0 and timeout_probe 0 or 1");
+        return AMS_ERR_INVALID_ARG;
+    }
     if (!(h->opt.eig_threshold >= 0.0) || !std::isfinite(h->opt.eig_threshold)) {
         set_error("eig_threshold must be finite and >= 0");
         return AMS_ERR_INVALID_ARG;
@@ -1200,11 +1204,34 @@ static ams_status prof_flush(ams_handle h) {
     return AMS_OK;
 }
 
+// The device status word that kernels set when a bounded wait runs out
+// (SolveState::status): cleared before work outside a solve, read after.
+static ams_status clear_device_status(ams_handle h) {
+    AMS_CUDA_TRY(cudaMemsetAsync(&h->d_st->status, 0, sizeof(int32_t), h->stream));
+    return AMS_OK;
+}
+static ams_status device_status(ams_handle h) {
+    int32_t s = 0;
+    AMS_CUDA_TRY(cudaMemcpyAsync(&s, &h->d_st->status, sizeof(s), cudaMemcpyDeviceToHost, h->stream));
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (s == AMS_ERR_DEVICE_TIMEOUT) {
+        set_error("a bounded device-side wait ran out (spin_budget_cycles)");
+        return AMS_ERR_DEVICE_TIMEOUT;
+    }
+    return AMS_OK;
+}
+
+// Budget of every bounded device-side wait, in SM clock cycles.
+static int64_t spin_budget(ams_handle h) {
+    return h->opt.spin_budget_cycles > 0 ? h->opt.spin_budget_cycles : kDefaultSpinCycles;
+}
+
 // Fine-level local solves (+ restriction when the coarse space exists).
 static LocalTmaArgs local_tma_args(ams_handle h, int ld, const ResidIn& in, bool with_state) {
     return LocalTmaArgs{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, in, ld, h->cmax,
-                        std::max(1, h->mmax), h->nbmax, int64_t(1) << 20, with_state ? h->d_st : nullptr,
-                        h->use_pdl, h->tune[ld].depth, h->tune[ld].nr, h->tune[ld].l2mode, h->tune[ld].l2keep};
+                        std::max(1, h->mmax), h->nbmax, spin_budget(h), with_state ? h->d_st : nullptr,
+                        h->use_pdl, h->tune[ld].depth, h->tune[ld].nr, h->tune[ld].l2mode, h->tune[ld].l2keep,
+                        &h->d_st->status, h->opt.timeout_probe};
 }
 
 static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool with_state,
@@ -1267,11 +1294,14 @@ static ams_status apply_two_grid(ams_handle h, const LaunchCtx& L, int mode, con
     AMS_TRY(launch_local(h, L.ld, rin, with_state, false));
     launch_tg_scale(L2, h->prec, h->d_zf, omega, nv);
     prof_end(h);
-    prof_begin(h, AMS_KERNEL_COARSE);
-    launch_tg_resid(L2, h->d_zf, h->prec == AMS_PREC_FP64, rin, h->d_tw);
-    launch_tg_restrict(L2, h->prec, h->d_psi, h->d_tw, h->d_rc, std::max(1, h->mmax));
-    h->launches += 4 + launch_coarse(h, L.ld, with_state);
-    prof_end(h);
+    h->launches += 2;
+    if (h->Nc > 0) {   // without a coarse space x^2 = x^1
+        prof_begin(h, AMS_KERNEL_COARSE);
+        launch_tg_resid(L2, h->d_zf, h->prec == AMS_PREC_FP64, rin, h->d_tw);
+        launch_tg_restrict(L2, h->prec, h->d_psi, h->d_tw, h->d_rc, std::max(1, h->mmax));
+        h->launches += 2 + launch_coarse(h, L.ld, with_state);
+        prof_end(h);
+    }
     prof_begin(h, AMS_KERNEL_PROLONG);
     launch_prolong_update(L2, h->prec, prolong_args(h, 0, p, L.ld));   // z = x^2
     launch_tg_resid(L2, h->d_z, 1, rin, h->d_tw);
@@ -1298,7 +1328,7 @@ static ams_status apply_two_grid(ams_handle h, const LaunchCtx& L, int mode, con
 // stored by the prolongation together with x += alpha p, the dots and the
 // convergence test).  p is the direction of the current iteration.
 static ams_status apply_precond(ams_handle h, const LaunchCtx& L, int mode, const double* p) {
-    if (h->opt.two_grid_omega > 0.0 && h->Nc > 0) return apply_two_grid(h, L, mode, p);
+    if (h->opt.two_grid_omega > 0.0) return apply_two_grid(h, L, mode, p);
     const bool coarse = h->Nc > 0;
     const bool with_state = mode != 0;
     prof_begin(h, AMS_KERNEL_LOCAL);
@@ -1320,7 +1350,9 @@ static ams_status apply_precond(ams_handle h, const LaunchCtx& L, int mode, cons
 }
 
 static int launches_per_iteration(ams_handle h, int ld) {
-    return 4 + (h->Nc > 0 ? (fused_backward(ld) ? 1 : 2) : 0);
+    const int coarse = h->Nc > 0 ? (fused_backward(ld) ? 1 : 2) : 0;
+    if (h->opt.two_grid_omega > 0.0) return 9 + (h->Nc > 0 ? 2 + coarse : 0);
+    return 4 + coarse;
 }
 
 static void launch_direction_spmv(ams_handle h, const LaunchCtx& L, const double* p_old, double* p_new) {
@@ -1339,32 +1371,50 @@ static ams_status launch_iteration(ams_handle h, const LaunchCtx& L, int par) {
     return apply_precond(h, L, 2, p_new);
 }
 
-// Two CG iterations (the direction buffers swap roles once each) captured
-// as a CUDA graph; kernel arguments are fixed device pointers and every
-// scalar lives in device memory.
-static ams_status get_iter_graph(ams_handle h, const LaunchCtx& L, cudaGraphExec_t* out) {
-    auto it = h->iter_graph.find(L.ld);
-    if (it != h->iter_graph.end()) {
+// The whole iteration loop as one CUDA graph: a while node whose body is
+// two CG iterations (the direction buffers swap roles once each) and the
+// condition kernel, which stops the loop once the device solve state says
+// done (every (system, rhs) converged, the iteration cap, a breakdown or a
+// device timeout) or after `cap` bodies.  Kernel arguments are fixed device
+// pointers and every scalar lives in device memory, so one graph launch
+// runs the solve to the end with no host round trip.
+static ams_status get_loop_graph(ams_handle h, const LaunchCtx& L, cudaGraphExec_t* out) {
+    auto it = h->loop_graph.find(L.ld);
+    if (it != h->loop_graph.end()) {
         *out = it->second;
         return AMS_OK;
     }
-    const int64_t saved = h->launches;
     cudaGraph_t g = nullptr;
-    AMS_CUDA_TRY(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    AMS_CUDA_TRY(cudaGraphCreate(&g, 0));
+    struct GraphGuard {
+        cudaGraph_t g;
+        ~GraphGuard() {
+            if (g) cudaGraphDestroy(g);
+        }
+    } guard{g};
+    cudaGraphConditionalHandle cond;
+    AMS_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = cond;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    AMS_CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &p));
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    const int64_t saved = h->launches;
+    AMS_CUDA_TRY(cudaStreamBeginCaptureToGraph(h->stream, body, nullptr, nullptr, 0,
+                                               cudaStreamCaptureModeThreadLocal));
     ams_status st = launch_iteration(h, L, 0);
     if (st == AMS_OK) st = launch_iteration(h, L, 1);
-    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (st == AMS_OK) launch_loop_cond(h->stream, cond, h->d_st, h->opt.maxit / 2 + 2);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &body);
     h->launches = saved;
-    if (st != AMS_OK) {
-        if (g) cudaGraphDestroy(g);
-        return st;
-    }
+    if (st != AMS_OK) return st;
     AMS_CUDA_TRY(e);
     cudaGraphExec_t ex = nullptr;
-    e = cudaGraphInstantiate(&ex, g, 0);
-    cudaGraphDestroy(g);
-    AMS_CUDA_TRY(e);
-    h->iter_graph[L.ld] = ex;
+    AMS_CUDA_TRY(cudaGraphInstantiate(&ex, g, 0));
+    h->loop_graph[L.ld] = ex;
     *out = ex;
     return AMS_OK;
 }
@@ -1591,41 +1641,42 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
     }
     AMS_TRY(start_solve(h, L, f_dev, nrhs, h->opt.maxit, rtol * rtol));
     AMS_TRY(prof_flush(h));
-    cudaGraphExec_t graph = nullptr;
-    if (!h->prof) AMS_TRY(get_iter_graph(h, L, &graph));
-    // Launch iterations in chunks; between chunks read the device state and
-    // size the next chunk from the observed residual decay.  Iterations
-    // launched after convergence return at once (device-side done flag).
     SolveState st{};
-    int chunk = 8;
-    int it_prev = 0;
-    double w_prev = 1.0;
-    const double target = rtol * rtol;
-    while (true) {
-        // iterations run in pairs (one graph launch = two iterations)
-        for (int k = 0; k < (chunk + 1) / 2; ++k) {
-            if (graph) {
-                AMS_CUDA_TRY(cudaGraphLaunch(graph, h->stream));
-                h->launches += 2 * launches_per_iteration(h, ld);
-            } else {
+    if (!h->prof) {
+        // the whole loop on the device: one graph launch, one read at the end
+        cudaGraphExec_t graph = nullptr;
+        AMS_TRY(get_loop_graph(h, L, &graph));
+        AMS_CUDA_TRY(cudaGraphLaunch(graph, h->stream));
+        AMS_CUDA_TRY(cudaMemcpyAsync(&st, h->d_st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
+        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        h->launches += (int64_t)st.bodies * (2 * launches_per_iteration(h, ld) + 1);
+    } else {
+        // profiled solve: kernels launched one by one (events around each),
+        // the device state read between chunks of iterations, each chunk
+        // sized from the observed residual decay
+        int chunk = 8;
+        int it_prev = 0;
+        double w_prev = 1.0;
+        const double target = rtol * rtol;
+        while (true) {
+            for (int k = 0; k < (chunk + 1) / 2; ++k)
                 for (int par = 0; par < 2; ++par) {
                     AMS_TRY(launch_iteration(h, L, par));
                     AMS_TRY(prof_flush(h));
                 }
+            AMS_CUDA_TRY(cudaMemcpyAsync(&st, h->d_st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
+            AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+            if (st.done) break;
+            int next = 2 * chunk;
+            if (st.it > it_prev && st.worst > 0 && w_prev > 0 && st.worst < w_prev) {
+                const double rate = std::log(st.worst / w_prev) / (st.it - it_prev);   // < 0
+                const double need = std::log(target / st.worst) / rate;
+                next = (int)std::ceil(need);
             }
+            chunk = std::max(1, std::min(next, 64));
+            it_prev = st.it;
+            w_prev = st.worst;
         }
-        AMS_CUDA_TRY(cudaMemcpyAsync(&st, h->d_st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
-        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-        if (st.done) break;
-        int next = 2 * chunk;
-        if (st.it > it_prev && st.worst > 0 && w_prev > 0 && st.worst < w_prev) {
-            const double rate = std::log(st.worst / w_prev) / (st.it - it_prev);   // < 0
-            const double need = std::log(target / st.worst) / rate;
-            next = (int)std::ceil(need);
-        }
-        chunk = std::max(1, std::min(next, 64));
-        it_prev = st.it;
-        w_prev = st.worst;
     }
     // outputs
     if (h->nsys == 1) {
@@ -1648,6 +1699,10 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
             if (relres) relres[s * nrhs + k] = c.fnorm2 > 0 ? std::sqrt(c.rr / c.fnorm2) : 0.0;
             any_active = any_active || c.active;
         }
+    if (st.status == AMS_ERR_DEVICE_TIMEOUT) {
+        set_error("a bounded device-side wait ran out (spin_budget_cycles)");
+        return AMS_ERR_DEVICE_TIMEOUT;
+    }
     if (st.status == AMS_ERR_BREAKDOWN) {
         set_error("CG breakdown (p^T A p <= 0 or non-finite scalar)");
         return AMS_ERR_BREAKDOWN;
@@ -1681,6 +1736,7 @@ void ams_options_default(ams_options* opt) {
     opt->spin_budget_cycles = 0;
     opt->eig_threshold = 0.0;
     opt->two_grid_omega = 0.0;
+    opt->timeout_probe = 0;
 }
 
 const char* ams_status_string(ams_status s) {
@@ -1920,10 +1976,10 @@ ams_status ams_set_launch_shape(ams_handle h, int32_t nrhs, const int32_t* shape
     T.depth = depth;
     T.nr = nr;
     T.done = true;
-    auto g = h->iter_graph.find(ld);   // captured with the previous shapes
-    if (g != h->iter_graph.end()) {
+    auto g = h->loop_graph.find(ld);   // captured with the previous shapes
+    if (g != h->loop_graph.end()) {
         AMS_CUDA_TRY(cudaGraphExecDestroy(g->second));
-        h->iter_graph.erase(g);
+        h->loop_graph.erase(g);
     }
     return AMS_OK;
 }
@@ -2000,6 +2056,7 @@ ams_status ams_apply_preconditioner(ams_handle h, const double* r, int32_t nrhs,
     AMS_TRY(stage_in(h, r, nrhs, h->d_stage_in, &r_dev));
     launch_permute_in(h->stream, r_dev, h->n_total, nrhs, ld, h->d_int_row, h->d_r, nullptr);
     h->launches += 2;
+    AMS_TRY(clear_device_status(h));
     AMS_TRY(apply_precond(h, L, 0, nullptr));
     double* z_dev = h->opt.device_ptrs ? z : h->d_stage_out;
     launch_permute_out(h->stream, h->d_z, h->n_total, nrhs, ld, h->d_int_row, z_dev);
@@ -2007,7 +2064,7 @@ ams_status ams_apply_preconditioner(ams_handle h, const double* r, int32_t nrhs,
     if (!h->opt.device_ptrs)
         AMS_CUDA_TRY(cudaMemcpyAsync(z, z_dev, sizeof(double) * h->n_total * nrhs, cudaMemcpyDeviceToHost, h->stream));
     AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    return AMS_OK;
+    return device_status(h);
 }
 
 ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y) {

@@ -30,6 +30,7 @@ constexpr int kRedBlocksPerSM = 4;     // reduction-kernel grid: about this many
 constexpr int kMaxLd = 32;             // right-hand sides per solve call
 constexpr int kMaxM = 16;              // eigenvectors per subdomain (cap)
 constexpr int kCoarseChunk = 512;      // node-matrix columns per coarse item
+constexpr int64_t kDefaultSpinCycles = int64_t(1) << 30;   // bounded device waits: ~0.5 s at 2 GHz
 
 // ---- per-subdomain descriptor (device array) ------------------------------
 struct SubInfo {
@@ -104,7 +105,7 @@ struct SolveState {    // device-resident control block
     int32_t status;    // ams_status set by device-side checks
     int32_t nactive;
     int32_t maxit;     // iteration cap of the current solve
-    int32_t pad;
+    int32_t bodies;    // loop bodies (two iterations each) the device-resident loop has run
     double rtol2;      // squared relative residual target
     double worst;      // max over active (system, rhs) of ||r||^2 / ||f||^2
 };

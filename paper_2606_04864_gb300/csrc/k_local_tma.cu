@@ -52,12 +52,38 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: false when the budget runs out.
+// Bounded wait: false when `budget` SM clock cycles pass without the phase
+// of the given parity completing.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int64_t budget) {
-    for (int64_t i = 0; i < budget; ++i)
+    const long long t0 = clock64();
+    do {
         if (mbar_try_wait(bar, parity)) return true;
+    } while (clock64() - t0 < budget);
     return false;
 }
+// Budget of the exit drain (about a second): a copy in flight lands within
+// microseconds, but the block must not leave while one may still write its
+// shared memory.
+constexpr int64_t kDrainCycles = int64_t(1) << 31;
+// Exit path after a wait ran out: record the timeout, then wait for every
+// copy this thread saw issued and not yet completed (slots with their bit
+// in `pend`, at the parity they were issued with).
+__device__ __forceinline__ void drain_copies(const uint64_t* bars, int nbuf, uint32_t pend, uint32_t phase) {
+    for (int i = 0; i < nbuf; ++i)
+        if ((pend >> i) & 1u) mbar_wait(smem_u32(bars + i), (phase >> i) & 1u, kDrainCycles);
+}
+__device__ __forceinline__ void timeout_drain(const uint64_t* bars, int nbuf, uint32_t pend, uint32_t phase,
+                                              int32_t* err, SolveState* st, bool leader) {
+    if (leader) {
+        if (err != nullptr) atomicExch(err, (int)AMS_ERR_DEVICE_TIMEOUT);
+        if (st != nullptr) st->done = 1;
+    }
+    drain_copies(bars, nbuf, pend, phase);
+}
+// Shared-memory mbarrier slots of a ring of nbuf copies: one per slot plus
+// the probe barrier that nothing ever completes (timeout_probe), rounded up
+// to an even count so that what follows stays 16-byte aligned.
+__host__ __device__ __forceinline__ int ring_bar_slots(int nbuf) { return (nbuf + 2) & ~1; }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int32_t x, int32_t y,
                                             uint32_t bar) {
     asm volatile(
@@ -190,7 +216,8 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
             const SubInfo* __restrict__ subs, const int64_t* __restrict__ tile_row0,
             const float* __restrict__ piv, const double* __restrict__ rin, const double* __restrict__ qin,
             const CgScalars* __restrict__ csc, float* __restrict__ zf, const TP* __restrict__ psi,
-            float* __restrict__ rc, int ld, int cmax, int depth, int64_t budget, SolveState* st) {
+            float* __restrict__ rc, int ld, int cmax, int depth, int64_t budget, SolveState* st, int32_t* err,
+            int probe) {
     pdl_wait();
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -201,23 +228,28 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
     const int D = depth;
     const int nbuf = cmax + D + 1;
     float* tiles = (float*)base;                                        // nbuf * cmax * 1024
-    uint64_t* bars = (uint64_t*)(tiles + (size_t)nbuf * cmax * 1024);    // nbuf (padded to even)
+    uint64_t* bars = (uint64_t*)(tiles + (size_t)nbuf * cmax * 1024);    // ring_bar_slots(nbuf)
     // y/x ring and scratch: rows of lds = ld + 4 floats, so that the 32 lanes
     // storing their own rows hit distinct banks (a row stride of ld floats
     // put every lane on the same bank) while rows stay 16-byte aligned
     const int lds = local_tma_row_stride(ld);
-    float* ring = (float*)(bars + ((nbuf + 1) & ~1));                    // (cmax+1)*32*lds
+    float* ring = (float*)(bars + ring_bar_slots(nbuf));                 // (cmax+1)*32*lds
     float* tmp = ring + (size_t)(cmax + 1) * 32 * lds;                   // 32*lds
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rhs0 = warp * NR;
     const int m = S.m;
     const int64_t trow = tile_row0[blockIdx.x];      // first tensor row of this subdomain
     const uint32_t tile_bytes = 4096u * (uint32_t)c;
-    uint32_t phase = 0;                              // parity bit per slot
+    // Per slot: the parity of its next completion, and whether a copy was
+    // issued into it and not yet seen complete.  Both change only when a
+    // wait succeeds, so after a wait runs out the exit drain still waits
+    // for that slot's copy at the parity it was issued with.  Every thread
+    // keeps its own copy (issue and wait are called by all threads).
+    uint32_t phase = 0, pend = 0;
     bool ok = true;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < nbuf; ++i) mbar_init(smem_u32(bars + i), 1);
+        for (int i = 0; i <= nbuf; ++i) mbar_init(smem_u32(bars + i), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncthreads();
@@ -231,12 +263,17 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
                 tma_load_2d(smem_u32(tiles + ((size_t)slot * cmax + d) * 1024), map, 0,
                             (int32_t)(trow + ((int64_t)K * c + d) * 32), bar);
         }
+        pend |= 1u << (K % nbuf);
     };
     auto wait_slot = [&](int K) {
         const int slot = K % nbuf;
         const uint32_t par = (phase >> slot) & 1u;
-        if (!mbar_wait(smem_u32(bars + slot), par, budget)) ok = false;
+        if (!mbar_wait(smem_u32(bars + slot), par, budget)) {
+            ok = false;
+            return;
+        }
         phase ^= 1u << slot;
+        pend &= ~(1u << slot);
     };
     auto slot_tile = [&](int K, int d) -> const float* {
         return tiles + ((size_t)(K % nbuf) * cmax + d) * 1024;
@@ -346,6 +383,10 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
 
     // ---------------- forward ----------------
     for (int j = 0; j < D && j < nb; ++j) issue(&tmF, j);
+    if (probe) {   // timeout test hook: a bounded wait on a barrier nothing completes
+        if (!mbar_wait(smem_u32(bars + nbuf), 0u, budget)) ok = false;
+        ok = __syncthreads_and(ok);
+    }
 #pragma unroll 1
     for (int K0 = 0; K0 < nb && ok; K0 += PF) {
 #pragma unroll
@@ -426,14 +467,7 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
         for (int u = 0; u < PF; ++u)
             if (K0 - u >= 0 && ok) bwd_step(K0 - u, bw[u], bv[u]);
     }
-    if (!ok) {
-        // record the timeout and drain this block's copies in flight (bounded)
-        if (threadIdx.x == 0 && st != nullptr) {
-            atomicExch(&st->status, (int)AMS_ERR_DEVICE_TIMEOUT);
-            st->done = 1;
-        }
-        for (int i = 0; i < nbuf; ++i) mbar_wait(smem_u32(bars + i), (phase >> i) & 1u, budget);
-    }
+    if (!ok) timeout_drain(bars, nbuf, pend, phase, err, st, threadIdx.x == 0);
 }
 
 
@@ -557,7 +591,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
              const double* __restrict__ rin, const double* __restrict__ qin,
              const CgScalars* __restrict__ csc, float* __restrict__ zf, const TP* __restrict__ psi,
              float* __restrict__ rc, int cmax, int nbmax, int depth, int l2mode, int l2keep, int64_t budget,
-             SolveState* st) {
+             SolveState* st, int32_t* err, int probe) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_align1024(smem_raw);
     const SubInfo S = subs[blockIdx.x];
@@ -569,15 +603,17 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     // the backward one; rows below Rres are loaded twice.
     const int Rres = nb > nbuf ? nb - nbuf : 0;
     float* tiles = (float*)base;                                        // nbuf * cmax * 1024
-    uint64_t* bars = (uint64_t*)(tiles + (size_t)nbuf * cmax * 1024);    // nbuf (padded to even)
-    float* yv = (float*)(bars + ((nbuf + 1) & ~1));                      // nbmax * 32: y, then x
+    uint64_t* bars = (uint64_t*)(tiles + (size_t)nbuf * cmax * 1024);    // ring_bar_slots(nbuf)
+    float* yv = (float*)(bars + ring_bar_slots(nbuf));                   // nbmax * 32: y, then x
     float* tmp = yv + (size_t)nbmax * 32;                                // 32
     const int lane = threadIdx.x;
     const int jr = lane >> 2, er = lane & 3;
     const int64_t trow = tile_row0[blockIdx.x];
     const uint32_t tile_bytes = 4096u * (uint32_t)c;
     const int slot_floats = cmax * 1024;
-    uint32_t phase = 0, pend = 0;   // parity per slot; slots with a copy in flight
+    // parity of each slot's next completion, and the slots with a copy in
+    // flight; both change only when a wait succeeds (see k_local_tma)
+    uint32_t phase = 0, pend = 0;
     bool ok = true;
 
     // per-lane offsets and masks, fixed for the whole kernel
@@ -596,7 +632,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     const float2 neg1 = make_float2(-1.f, -1.f);
 
     if (lane == 0) {
-        for (int i = 0; i < nbuf; ++i) mbar_init(smem_u32(bars + i), 1);
+        for (int i = 0; i <= nbuf; ++i) mbar_init(smem_u32(bars + i), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     __syncwarp();
@@ -632,7 +668,10 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
         pend |= 1u << slot;
     };
     auto wait_slot = [&](int slot) {
-        if (!mbar_wait(smem_u32(bars + slot), (phase >> slot) & 1u, budget)) ok = false;
+        if (!mbar_wait(smem_u32(bars + slot), (phase >> slot) & 1u, budget)) {
+            ok = false;
+            return;
+        }
         phase ^= 1u << slot;
         pend &= ~(1u << slot);
     };
@@ -668,11 +707,17 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
 #pragma unroll
     for (int u = 0; u < PF; ++u) load_static(u, bp[u], bv[u]);
     pdl_wait();
-    if (st != nullptr && st->done) ok = false;
-    if (!ok) {
-        for (int i = 0; i < nbuf; ++i)
-            if ((pend >> i) & 1u) mbar_wait(smem_u32(bars + i), (phase >> i) & 1u, budget);
+    if (st != nullptr && st->done) {   // converged: leave once the first copies have landed
+        drain_copies(bars, nbuf, pend, phase);
         return;
+    }
+    if (probe) {   // timeout test hook: a bounded wait on a barrier nothing completes
+        if (!mbar_wait(smem_u32(bars + nbuf), 0u, budget)) ok = false;
+        ok = __all_sync(0xffffffffu, ok);
+        if (!ok) {
+            timeout_drain(bars, nbuf, pend, phase, err, st, lane == 0);
+            return;
+        }
     }
     // r' = r - alpha q when this subdomain's system is still iterating
     double alpha = 0.0;
@@ -847,15 +892,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
         for (int u = 0; u < PF; ++u)
             if (K0 - u >= 0 && ok) bwd_step(K0 - u, bv[u]);
     }
-    if (!ok) {
-        // record the timeout and drain the copies still in flight (bounded)
-        if (lane == 0 && st != nullptr) {
-            atomicExch(&st->status, (int)AMS_ERR_DEVICE_TIMEOUT);
-            st->done = 1;
-        }
-        for (int i = 0; i < nbuf; ++i)
-            if ((pend >> i) & 1u) mbar_wait(smem_u32(bars + i), (phase >> i) & 1u, budget);
-    }
+    if (!ok) timeout_drain(bars, nbuf, pend, phase, err, st, lane == 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -864,7 +901,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
 size_t local_tma_smem(int cmax, int ld, int depth) {
     const int nbuf = cmax + depth + 1;
     const int lds = local_tma_row_stride(ld);
-    return 1024 /* alignment slack */ + (size_t)nbuf * cmax * 4096 + (size_t)((nbuf + 1) & ~1) * 8 +
+    return 1024 /* alignment slack */ + (size_t)nbuf * cmax * 4096 + (size_t)ring_bar_slots(nbuf) * 8 +
            ((size_t)(cmax + 1) * 32 * lds + 32 * lds) * sizeof(float);
 }
 
@@ -893,7 +930,7 @@ static cudaError_t tma_nr(const LocalTmaArgs& a, const void* psi, void* zf, void
     }
     return launch_kernel(a.pdl, kern, dim3(a.nsub), dim3(warps * 32), smem, a.stream, *a.tmF, *a.tmB, a.subs,
                          a.tile_row0, a.piv, a.in.r, a.in.q, a.in.sc, (float*)zf, (const TP*)psi, (float*)rc, a.ld,
-                         a.cmax, depth, a.budget, a.st);
+                         a.cmax, depth, a.budget, a.st, a.err, a.probe);
 }
 
 template <typename TP>
@@ -920,7 +957,7 @@ static cudaError_t tma_tp(const LocalTmaArgs& a, const void* psi, void* zf, void
 
 size_t local_tma1_smem(int cmax, int nbmax, int depth) {
     const int nbuf = cmax + depth + 1;
-    return 1024 /* alignment slack */ + (size_t)nbuf * cmax * 4096 + (size_t)((nbuf + 1) & ~1) * 8 +
+    return 1024 /* alignment slack */ + (size_t)nbuf * cmax * 4096 + (size_t)ring_bar_slots(nbuf) * 8 +
            ((size_t)nbmax * 32 + 32) * sizeof(float);
 }
 
@@ -946,7 +983,7 @@ static cudaError_t tma1(const LocalTmaArgs& a, const void* psi, void* zf, void* 
     return launch_kernel(a.pdl, kern, dim3(a.nsub), dim3(32), smem, a.stream, *a.tmF, a.subs, a.tile_row0,
                          a.piv,
                          a.in.r, a.in.q, a.in.sc, (float*)zf, (const TP*)psi, (float*)rc, a.cmax, a.nbmax, depth,
-                         a.l2mode, a.l2keep, a.budget, a.st);
+                         a.l2mode, a.l2keep, a.budget, a.st, a.err, a.probe);
 }
 
 // The one-right-hand-side kernel keeps y for a whole subdomain in shared

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "ams_internal.h"
@@ -80,23 +81,62 @@ k_csr_spmv_dot_noalloc(int64_t n, const int64_t* __restrict__ rowptr, const int3
     }
 }
 
-// Device address of the scratch array, resolved once per device.
+// Identity of the current CUDA context (cuCtxGetId: unique for the life of
+// the process, so a context re-created after cudaDeviceReset gets a new
+// one), through the driver entry points the runtime exposes; 0 if the
+// driver does not provide it.
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext*);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long*);
+
+unsigned long long current_context_id() {
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (PfnCtxGetCurrent)fn;
+        fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PfnCtxGetId)fn;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current && get_id && get_current(&ctx) == CUDA_SUCCESS && ctx && get_id(ctx, &id) == CUDA_SUCCESS)
+        return id;
+    return 0;
+}
+
+// Device address of the scratch array, resolved once per device and
+// context: a device reset ends the context that held the old address, and
+// the first call in the new context resolves it again.
+struct ScratchAddr {
+    unsigned long long ctx = 0;
+    double* ptr = nullptr;
+};
 std::mutex g_na_mu;
-std::vector<double*> g_na_ptr;
+std::vector<ScratchAddr> g_na_ptr;
 
 ams_status noalloc_scratch(int dev, double** out) {
     std::lock_guard<std::mutex> lock(g_na_mu);
-    if ((int)g_na_ptr.size() <= dev) g_na_ptr.resize(dev + 1, nullptr);
-    if (!g_na_ptr[dev]) {
+    if ((int)g_na_ptr.size() <= dev) g_na_ptr.resize(dev + 1);
+    const unsigned long long ctx = current_context_id();
+    ScratchAddr& a = g_na_ptr[dev];
+    if (!a.ptr || a.ctx != ctx) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || p == nullptr) {
             set_error(std::string("cudaGetSymbolAddress(g_noalloc_scratch): ") + cudaGetErrorString(e));
             return AMS_ERR_CUDA;
         }
-        g_na_ptr[dev] = (double*)p;
+        a.ptr = (double*)p;
+        a.ctx = ctx;
     }
-    *out = g_na_ptr[dev];
+    *out = a.ptr;
     return AMS_OK;
 }
 

@@ -822,6 +822,18 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
     }
 }
 
+// End of one body of the device-resident loop: count it and set the while
+// node's condition.  The body cap bounds the loop even if no kernel ever
+// reported convergence or the iteration cap.
+__global__ void k_loop_cond(cudaGraphConditionalHandle h, SolveState* st, int cap) {
+    const int b = ++st->bodies;
+    cudaGraphSetConditional(h, (!st->done && b < cap) ? 1u : 0u);
+}
+
+void launch_loop_cond(cudaStream_t s, cudaGraphConditionalHandle h, SolveState* st, int cap) {
+    k_loop_cond<<<1, 1, 0, s>>>(h, st, cap);
+}
+
 // ||f||^2 per (system, rhs) and CG scalar initialisation
 template <int LD>
 __global__ void __launch_bounds__(kRedThreads)

@@ -93,6 +93,8 @@ struct LocalTmaArgs {
                              // tiles read for the last time, 2 as 1 plus evict-last on kept tiles
     int l2keep;              // block rows below the ring's resident ones whose forward load is
                              // kept (not marked evict-first): the backward sweep reloads them soonest
+    int32_t* err;            // status word set to AMS_ERR_DEVICE_TIMEOUT when a wait runs out (or NULL)
+    int probe;               // 1: every block first waits on a barrier nothing completes (timeout test)
 };
 
 struct CoarseLaunch {
@@ -151,6 +153,10 @@ void launch_tg_resid(const LaunchCtx& L, const void* v, int v_is_fp64, const Res
 void launch_tg_scale(const LaunchCtx& L, int prec, void* zf, double omega, int64_t n);
 void launch_tg_combine(const LaunchCtx& L, int prec, void* zf, const double* x2, double omega, int64_t n);
 void launch_tg_restrict(const LaunchCtx& L, int prec, const void* psi, const double* w, void* rc, int mmax);
+// Condition of the device-resident iteration loop (a while node of a CUDA
+// graph): continue while the solve is not done and fewer than `cap` bodies
+// have run.
+void launch_loop_cond(cudaStream_t s, cudaGraphConditionalHandle h, SolveState* st, int cap);
 void launch_permute_in(cudaStream_t s, const double* f, int64_t n, int nrhs, int ld,
                        const int64_t* int_row, double* r, double* x);
 void launch_permute_out(cudaStream_t s, const double* x, int64_t n, int nrhs, int ld,

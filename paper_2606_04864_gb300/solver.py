@@ -64,7 +64,7 @@ def _ptr(a):
 
 def make_options(precision="fp32_bf16", cg="auto", maxit=10000, device=False, coarse=True,
                  eig_shift=0.0, eig_maxit=0, eig_tol=0.0, autotune=True, eig_threshold=0.0,
-                 two_grid_omega=0.0) -> ams_options:
+                 two_grid_omega=0.0, spin_budget_cycles=0, timeout_probe=False) -> ams_options:
     o = ams_options()
     lib().ams_options_default(C.byref(o))
     o.precision = _lib.PREC[precision] if isinstance(precision, str) else int(precision)
@@ -78,6 +78,8 @@ def make_options(precision="fp32_bf16", cg="auto", maxit=10000, device=False, co
     o.autotune = 1 if autotune else 0
     o.eig_threshold = float(eig_threshold)
     o.two_grid_omega = float(two_grid_omega)
+    o.spin_budget_cycles = int(spin_budget_cycles)
+    o.timeout_probe = 1 if timeout_probe else 0
     return o
 
 
@@ -201,7 +203,8 @@ class AmsSolver(_Base):
 
     def __init__(self, rowptr, colind, vals, part, nparts: int, m: int, precision="fp32_bf16",
                  cg="auto", maxit=10000, device: bool = False, coarse=True, eig_shift=0.0,
-                 eig_maxit=0, eig_tol=0.0, autotune=True, eig_threshold=0.0, two_grid_omega=0.0):
+                 eig_maxit=0, eig_tol=0.0, autotune=True, eig_threshold=0.0, two_grid_omega=0.0,
+                 spin_budget_cycles=0, timeout_probe=False):
         self.device = bool(device)
         conv = _as_dev if self.device else _as_host
         self._rowptr = conv(rowptr, np.int64)
@@ -213,7 +216,7 @@ class AmsSolver(_Base):
         self.nparts = int(nparts)
         self.nsys = 1
         self.opts = make_options(precision, cg, maxit, self.device, coarse, eig_shift, eig_maxit, eig_tol,
-                                 autotune, eig_threshold, two_grid_omega)
+                                 autotune, eig_threshold, two_grid_omega, spin_budget_cycles, timeout_probe)
         h = C.c_void_p()
         st = lib().ams_setup(self.n, _ptr(self._rowptr), _ptr(self._colind), _ptr(self._vals),
                              _ptr(self._part) if self._part is not None else None, self.nparts, int(m),
@@ -343,6 +346,17 @@ class AmsBatchedSolver(_Base):
             out.append(flat[o:o + n * nrhs].reshape(nrhs, n))
             o += n * nrhs
         return out
+
+    def profile_solve(self, f_flat, nrhs: int, rtol: float = 1e-8):
+        """As :meth:`AmsSolver.profile_solve`, for f_flat in the ABI layout."""
+        fv = _as_dev(f_flat, np.float64) if self.device else _as_host(f_flat, np.float64)
+        ms = np.zeros(AMS_NUM_KERNELS, dtype=np.float64)
+        by = np.zeros(AMS_NUM_KERNELS, dtype=np.float64)
+        cnt = np.zeros(AMS_NUM_KERNELS, dtype=np.int64)
+        check(lib().ams_profile_solve(self._h, _ptr(fv), int(nrhs), float(rtol), _ptr(ms), _ptr(by), _ptr(cnt)),
+              "ams_profile_solve", allow=(4,))
+        return [{"name": KERNEL_NAMES[k], "ms": float(ms[k]), "count": int(cnt[k]), "bytes": float(by[k])}
+                for k in range(AMS_NUM_KERNELS)]
 
     def solve(self, f_flat, nrhs: int, rtol: float = 1e-8, allow_not_converged: bool = False):
         """f_flat in the ABI layout (see :meth:`pack`).  Returns (u_flat,

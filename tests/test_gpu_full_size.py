@@ -170,7 +170,7 @@ def test_grf3d_96_adjoint_gradient_vs_central_differences():
         an = g @ v
         rel.append(abs(fd - an) / max(abs(an), 1e-300))
     rel = np.array(rel)
-    assert np.median(rel) <= 1e-5 and rel.max() <= 1e-4, rel
+    assert rel.max() <= 1e-5, rel
 
 
 def test_grf3d_96_gradient_vs_oracle_on_16cubed_copy():

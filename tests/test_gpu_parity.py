@@ -413,3 +413,91 @@ def test_profile_and_time_kernel_report_every_slot():
     for k in range(AMS_NUM_KERNELS):
         ms, by = s.time_kernel(k, 3)
         assert ms > 0 and by > 0
+
+
+# ------------------------------------------------- many right-hand sides
+# 16 and 32 right-hand sides take the code paths the one-to-six-RHS cases do
+# not: local-solve warps whose right-hand-side group starts past 0 (several
+# warps per block), the separate backward coarse substitution and the
+# register-blocked coarse block products at 32 columns.
+
+MANY = {
+    "3d_b8": lambda nrhs: make_small_3d(side=16, bs=8, m=6, std=2.5, sigma=3.0, seed=32, nrhs=nrhs,
+                                        rhs_kind="normal"),
+    "2d_ragged": lambda nrhs: make_small_2d(side=45, bs=10, m=3, std=2.0, sigma=3.0, seed=31, ny=37,
+                                            nrhs=nrhs, rhs_kind="normal"),
+}
+
+
+@pytest.fixture(scope="module", params=[(c, k) for c in MANY for k in (16, 32)],
+                ids=lambda p: f"{p[0]}-{p[1]}rhs")
+def many(request):
+    name, nrhs = request.param
+    w = MANY[name](nrhs)
+    A = _A(w)
+    o = OracleAMS(A, w.part, w.nparts, w.m)
+    return name, nrhs, w, A, o
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5), ("fp32_bf16", 2e-5)])
+def test_many_rhs_apply_matches_oracle(many, prec, tol):
+    name, nrhs, w, A, o = many
+    rnd = {"fp64": None, "fp32": "fp32", "fp32_bf16": "bf16"}[prec]
+    orc = o if rnd is None else OracleAMS(A, w.part, w.nparts, w.m, basis_round=rnd)
+    s = _solver(w, precision=prec)
+    r = np.random.default_rng(7).standard_normal((nrhs, w.n))
+    z = s.apply_preconditioner(r)
+    for k in range(nrhs):
+        zr = orc.apply(r[k])
+        assert np.linalg.norm(z[k] - zr) <= tol * np.linalg.norm(zr), (prec, k)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_bf16"])
+def test_many_rhs_pcg_matches_oracle(many, prec):
+    """Every column: iterations within 2 of the oracle's PCG, solution within
+    1e-10 (FP64 path) or max(1e-6, 10 x the oracle's own rtol-1e-8 error
+    against its rtol-1e-13 solution) of the oracle."""
+    name, nrhs, w, A, o = many
+    s = _solver(w, precision=prec)
+    u, its, rel = s.solve(w.rhs, rtol=1e-8)
+    assert (rel <= 1e-8).all()
+    for k in range(nrhs):
+        ref = pcg(A, w.rhs[k], o.apply, rtol=1e-8)
+        assert abs(int(its[k]) - ref.iters) <= 2, (k, its[k], ref.iters)
+        err = np.linalg.norm(u[k] - ref.u) / np.linalg.norm(ref.u)
+        if prec == "fp64":
+            assert err <= 1e-10, (k, err)
+        else:
+            tight = pcg(A, w.rhs[k], o.apply, rtol=1e-13)
+            floor = np.linalg.norm(ref.u - tight.u) / np.linalg.norm(tight.u)
+            assert err <= max(1e-6, 10 * floor), (k, err, floor)
+
+
+def test_autograd_solves_with_the_values_it_is_given():
+    """ams_solve(vals, ...) loads vals into the solver before the forward:
+    after log k changes, u and the gradient are those of the new matrix
+    (the preconditioner is still the one built for the first matrix)."""
+    from oracle import adjoint_gradient
+    from paper_2606_04864_gb300.autograd import ams_solve
+    from workloads import grf_logk, tpfa_csr, tpfa_values_from_logk
+    w = make_small_3d(side=12, bs=4, m=4, std=2.0, sigma=2.0, seed=90)
+    faces = w.extra["faces"]
+    s = _solver(w, precision="fp64", device=True)
+    f = torch.as_tensor(w.rhs[0], device="cuda")
+    g_np = np.random.default_rng(91).standard_normal(w.n)
+    for step, logk_np in enumerate([w.logk, w.logk + 0.7 * grf_logk(w.shape, 2.0, 1.0, 92)]):
+        logk = torch.tensor(logk_np.reshape(-1), dtype=torch.float64, device="cuda", requires_grad=True)
+        vals = tpfa_values_from_logk(logk, faces)
+        vals.retain_grad()
+        u = ams_solve(vals, f, s, rtol=1e-12)
+        loss = torch.dot(u, torch.as_tensor(g_np, device="cuda"))
+        loss.backward()
+        rp, ci, vv = tpfa_csr(logk_np, faces)
+        A = csr_to_scipy(rp, ci, vv)
+        o = OracleAMS(A, w.part, w.nparts, w.m)
+        ref = pcg(A, w.rhs[0], o.apply, rtol=1e-13)
+        un = u.detach().cpu().numpy()
+        assert np.linalg.norm(un - ref.u) <= 1e-9 * np.linalg.norm(ref.u), step
+        lam_o, dv_o, _ = adjoint_gradient(A, ref.u, g_np, o.apply, rtol=1e-13)
+        dv = vals.grad.detach().cpu().numpy()
+        assert np.abs(dv - dv_o).max() <= 1e-8 * np.abs(dv_o).max(), step

@@ -58,8 +58,41 @@ def test_two_grid_pcg_matches_oracle(kind):
                   two_grid_omega=omega)
     um, itm, relm = m.solve(w.rhs[0], rtol=1e-8)
     assert np.linalg.norm(w.rhs[0] - A @ um) <= 1e-6 * np.linalg.norm(w.rhs[0])
+    # mixed path (flexible CG on the reduced-precision cycle): iterations
+    # within 2 of the oracle's flexible CG on the FP64 cycle, solution within
+    # max(1e-6, 10 x the oracle's own rtol-1e-8 error) of the oracle's
+    ref_f = pcg(A, w.rhs[0], lambda r: o.apply_two_grid(r, omega), rtol=1e-8, flexible=True)
+    tight = pcg(A, w.rhs[0], lambda r: o.apply_two_grid(r, omega), rtol=1e-13)
+    assert abs(int(itm[0]) - ref_f.iters) <= 2, (itm, ref_f.iters)
+    floor = np.linalg.norm(ref_f.u - tight.u) / np.linalg.norm(tight.u)
+    err = np.linalg.norm(um - ref_f.u) / np.linalg.norm(ref_f.u)
+    assert err <= max(1e-6, 10 * floor), (err, floor)
     add = pcg(A, w.rhs[0], o.apply, rtol=1e-8)
     assert ref.iters < add.iters
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 5e-5)])
+def test_two_grid_without_coarse_space_matches_oracle(prec, tol):
+    """With no coarse space the cycle is the symmetrised smoother
+    2 omega S - omega^2 S A S (not the plain local solves)."""
+    w = _case("2d")
+    A = csr_to_scipy(w.rowptr, w.colind, w.vals)
+    o = OracleAMS(A, w.part, w.nparts, w.m, coarse=False)
+    omega = 0.8 / o.local_lambda_max()
+    s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision=prec, coarse=False,
+                  two_grid_omega=omega)
+    r = np.random.default_rng(8).standard_normal((3, w.n))
+    z = s.apply_preconditioner(r)
+    for k in range(3):
+        zr = o.apply_two_grid(r[k], omega)
+        assert np.linalg.norm(z[k] - zr) <= tol * np.linalg.norm(zr), (prec, k)
+        zplain = o.local_part(r[k])
+        assert np.linalg.norm(z[k] - zplain) > 1e-3 * np.linalg.norm(zplain)
+    if prec == "fp64":
+        ref = pcg(A, w.rhs[0], lambda r: o.apply_two_grid(r, omega), rtol=1e-8)
+        u, its, _ = s.solve(w.rhs[0], rtol=1e-8)
+        assert abs(int(its[0]) - ref.iters) <= 2
+        assert np.linalg.norm(u - ref.u) <= 1e-10 * np.linalg.norm(ref.u)
 
 
 def test_two_grid_omega_is_validated():

@@ -2,15 +2,17 @@
 
 It is for callers that cannot allocate device memory when they need the
 product (for example while another library is capturing a CUDA graph).  It
-is compared with the handle-based SpMV on two calls in a row, since every
-call reuses the same fixed scratch array inside the library.  This file is
-collected last so that a failure here never hides the other tests.
+is compared with the handle-based SpMV and with the host product of SciPy
+on two calls in a row, since every call reuses the same fixed scratch
+array inside the library.  This file is collected last so that a failure
+here never hides the other tests.
 """
 
 import ctypes
 
 import numpy as np
 import pytest
+import scipy.sparse as sp
 
 from workloads import make_small_2d, make_small_3d
 
@@ -31,6 +33,7 @@ def _p(t):
 def test_noalloc_spmv_dot_matches_handle_spmv_twice(make):
     w = make()
     ref = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, 0, precision="fp64", coarse=False)
+    A = sp.csr_matrix((w.vals, w.colind, w.rowptr), shape=(w.n, w.n))
     dev = torch.device("cuda")
     rowptr = torch.as_tensor(w.rowptr, device=dev)
     colind = torch.as_tensor(w.colind, device=dev)
@@ -49,7 +52,9 @@ def test_noalloc_spmv_dot_matches_handle_spmv_twice(make):
         y_ref = ref.spmv(x_np)
         y_np = y.cpu().numpy()
         assert np.abs(y_np - y_ref).max() <= 1e-13 * np.abs(y_ref).max(), call
-        d_ref = float(x_np @ y_ref)
+        y_host = A @ x_np
+        assert np.abs(y_np - y_host).max() <= 1e-13 * np.abs(y_host).max(), call
+        d_ref = float(x_np @ y_host)
         assert abs(float(xy.item()) - d_ref) <= 1e-12 * abs(d_ref), call
 
 
