@@ -1,0 +1,119 @@
+"""The sharded solve phase on CPU ranks (gloo): contiguous subdomain ranges
+per rank, a halo exchange of p before each SpMV, all-reduces of the dots,
+an all-gather of r_c before the replicated coarse solve.  Its iterates
+equal the single-rank solve's (the oracle's PCG and flexible CG) to 1e-12
+at world sizes 2 and 4; the plan's ghost, send and receive lists are
+checked by brute force."""
+
+import os
+import sys
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+from workloads import make_small_2d, make_small_3d
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CASES = {
+    "2d": lambda: make_small_2d(side=40, bs=8, m=3, std=2.0, sigma=3.0, seed=61, ny=33),
+    "3d": lambda: make_small_3d(side=12, bs=4, m=4, std=2.0, sigma=2.0, seed=62),
+}
+
+
+def _plan(w, world):
+    from oracle import OracleAMS, csr_to_scipy
+    from paper_2606_04864_gb300.sharded import make_plan
+    o = OracleAMS(csr_to_scipy(w.rowptr, w.colind, w.vals), w.part, w.nparts, w.m)
+    return o, make_plan(w.rowptr, w.colind, w.vals, w.part, w.nparts, o.m_i, world)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 4, 7])
+@pytest.mark.parametrize("case", list(CASES))
+def test_plan_ranges_ghosts_and_exchange_lists(case, world):
+    w = CASES[case]()
+    o, plan = _plan(w, world)
+    n = w.n
+    assert (plan.perm == o.perm).all() and (plan.sub_ptr == o.sub_ptr).all()
+    iperm = np.empty(n, dtype=np.int64)
+    iperm[plan.perm] = np.arange(n)
+    sizes = [rp.n_owned for rp in plan.ranks]
+    assert sum(sizes) == n and plan.ranks[0].row_lo == 0 and plan.ranks[-1].row_hi == n
+    assert max(sizes) - min(sizes) <= 2 * max(np.diff(plan.sub_ptr))      # balanced to a subdomain
+    A = __import__("scipy.sparse", fromlist=["csr_matrix"]).csr_matrix((w.vals, w.colind, w.rowptr), shape=(n, n))
+    P = A[plan.perm][:, plan.perm].tocsr()                                  # internal order
+    for rp in plan.ranks:
+        blk = P[rp.row_lo:rp.row_hi]
+        cols = np.unique(blk.indices)
+        ghost = cols[(cols < rp.row_lo) | (cols >= rp.row_hi)]
+        assert np.array_equal(ghost, rp.ghost)
+        # the rank's rows of A in owned-then-ghost numbering reproduce the block
+        full = np.concatenate([np.arange(rp.row_lo, rp.row_hi), rp.ghost])
+        L = __import__("scipy.sparse", fromlist=["csr_matrix"]).csr_matrix(
+            (rp.vals, rp.colind, rp.rowptr), shape=(rp.n_owned, len(full)))
+        x = np.random.default_rng(rp.rank).standard_normal(n)
+        assert np.allclose(L @ x[full], blk @ x, rtol=0, atol=1e-14 * np.abs(blk @ x).max())
+        # receives are exactly the ghosts, each from its owner; sends mirror them
+        got = np.concatenate([rp.ghost[pos] for pos in rp.recv.values()]) if rp.recv else np.zeros(0, int)
+        assert np.array_equal(np.sort(got), rp.ghost)
+        for q, pos in rp.recv.items():
+            src = plan.ranks[q]
+            assert ((rp.ghost[pos] >= src.row_lo) & (rp.ghost[pos] < src.row_hi)).all()
+            assert np.array_equal(src.send[rp.rank] + src.row_lo, rp.ghost[pos])
+    # coarse blocks are contiguous and cover N_c in rank order
+    assert plan.ranks[0].coarse_lo == 0 and plan.ranks[-1].coarse_hi == o.Nc
+    for a, b in zip(plan.ranks[:-1], plan.ranks[1:]):
+        assert a.coarse_hi == b.coarse_lo and a.sub_hi == b.sub_lo
+
+
+def _worker(rank, world, port, case, flexible, out):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2606_04864_gb300.sharded import TorchComm, sharded_pcg
+        from tests.sharded_oracle_ops import OracleRankOps
+        w = CASES[case]()
+        o, plan = _plan(w, world)
+        rp = plan.ranks[rank]
+        f_owned = w.rhs[0][plan.perm[rp.row_lo:rp.row_hi]]
+        res = sharded_pcg(plan, rank, OracleRankOps(o, plan, rank), TorchComm(rp, world), f_owned,
+                          rtol=1e-10, flexible=flexible)
+        out[rank] = (np.asarray(res.x), res.iters, res.alphas, res.betas, res.collectives)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("flexible", [False, True])
+@pytest.mark.parametrize("world", [2, 4])
+@pytest.mark.parametrize("case", list(CASES))
+def test_sharded_iterates_equal_single_rank(case, world, flexible):
+    from oracle import OracleAMS, csr_to_scipy, pcg
+    w = CASES[case]()
+    A = csr_to_scipy(w.rowptr, w.colind, w.vals)
+    o = OracleAMS(A, w.part, w.nparts, w.m)
+    ref = pcg(A, w.rhs[0], o.apply, rtol=1e-10, flexible=flexible)
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = 20000 + (os.getpid() * 7 + world * 131 + (5 if flexible else 0) + len(case)) % 20000
+    procs = [ctx.Process(target=_worker, args=(r, world, port, case, flexible, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    x = np.concatenate([out[r][0] for r in range(world)])
+    u = np.empty(w.n)
+    u[o.perm] = x
+    assert all(out[r][1] == ref.iters for r in range(world))
+    assert np.linalg.norm(u - ref.u) <= 1e-12 * np.linalg.norm(ref.u)
+    for r in range(world):
+        assert np.allclose(out[r][2], ref.alphas, rtol=1e-12, atol=0)
+        assert np.allclose(out[r][3], ref.betas, rtol=1e-10, atol=1e-14)
+        c = out[r][4]
+        # per iteration: one halo exchange, two all-reduces, one all-gather
+        assert c["halo"] == ref.iters and c["allreduce"] == 2 + 2 * ref.iters
+        assert c["allgather"] == 1 + ref.iters
