@@ -118,7 +118,16 @@ typedef struct {
                                     2 / lambda_max makes the cycle
                                     indefinite and CG may then stall or
                                     report AMS_ERR_BREAKDOWN; setup does not
-                                    estimate lambda_max */
+                                    estimate lambda_max for a positive value.
+                                    Negative (between -2 and 0): omega =
+                                    -two_grid_omega / lambda_max, lambda_max
+                                    estimated at setup by power steps on the
+                                    local solves times A (a Rayleigh
+                                    quotient, which approaches lambda_max
+                                    from below; at most 300 steps, until it
+                                    moves by less than 1e-7 relative);
+                                    ams_get_info reports the omega and the
+                                    estimate */
     int32_t timeout_probe;       /* test hook, 0 (default) = off.  1: every
                                     block of the local-solve kernels first
                                     waits, within spin_budget_cycles, on a
@@ -298,6 +307,10 @@ typedef struct {
     int64_t basis_bytes;         /* bytes of the stored basis blocks */
     int32_t spmv_variant;        /* launch shape picked for the SpMV */
     int64_t kernel_launches;     /* CUDA kernels this handle has launched so far */
+    double two_grid_omega;       /* damping of the multiplicative cycle in use
+                                    (0: additive preconditioner) */
+    double local_lambda_max;     /* estimated lambda_max of the local solves
+                                    times A (two_grid_omega < 0 at setup), else 0 */
 } ams_info;
 
 ams_status ams_get_info(ams_handle h, ams_info* info);
@@ -308,7 +321,9 @@ ams_status ams_get_info(ams_handle h, ams_info* info);
  * shape[0]  blocks per SM of the element-layout grids (direction update, SpMV)
  * shape[1]  blocks per SM of the subdomain-layout grid (prolongation)
  * shape[2]  local-solve ring depth in band tiles; 0 = derived from the band width
- * shape[3]  right-hand sides per warp of the several-RHS local solve; 0 = default
+ * shape[3]  right-hand sides per warp of the several-RHS local solve (2, 4 or 8
+ *           below 8 right-hand sides; 8 or 16 from 8 on, where the tile
+ *           products run on the tensor cores); 0 = default
  * shape[4]  L2 priorities of the one-RHS local solve's factor-tile copies:
  *           0 none (default); 1 evict-first on copies that read a block row
  *           for the last time; 2 as 1, plus evict-last on the kept copies
@@ -323,7 +338,8 @@ ams_status ams_get_info(ams_handle h, ams_info* info);
  * between solves.  Errors: AMS_ERR_INVALID_ARG (NULL, nrhs out of range,
  * blocks per SM outside 1..8, depth outside 0..6, below 2 with TMA staging or
  * needing more than 200 KB of shared memory, right-hand sides per warp not
- * 0/2/4/8, above the rounded count or leaving more than 8 warps per block,
+ * 0 or one of the values above, above the rounded count or leaving more
+ * than 8 warps per block (4 from 8 right-hand sides on),
  * L2 mode outside 0..2, negative kept rows).
  */
 ams_status ams_get_launch_shape(ams_handle h, int32_t nrhs, int32_t* shape);

@@ -76,6 +76,8 @@ class ams_info(C.Structure):
         ("basis_bytes", C.c_int64),
         ("spmv_variant", C.c_int32),
         ("kernel_launches", C.c_int64),
+        ("two_grid_omega", C.c_double),
+        ("local_lambda_max", C.c_double),
     ]
 
 

@@ -14,6 +14,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cusolverDn.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "ams_internal.h"
 #include "kernels.cuh"
@@ -23,6 +24,19 @@ namespace ams {
 
 static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
+
+// NVTX range for the duration of a scope: every entry point marks its work
+// (ams_setup, ams_solve, ...), and the per-kernel profiling solve marks
+// each kernel slot, so profilers can select them by name.  Costs nothing
+// when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+static const char* const kSlotNames[AMS_NUM_KERNELS] = {"spmv_direction", "local_solve_restrict", "coarse_solve",
+                                                        "prolong_update"};
 
 static int pow2ceil(int v) {
     int p = 1;
@@ -901,6 +915,8 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
     return AMS_OK;
 }
 
+static ams_status estimate_two_grid_omega(ams_handle h);
+
 static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const ams_options* opt,
                              void* stream, ams_handle* out) {
     const double t0 = now_s();
@@ -916,8 +932,8 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
         set_error("unknown precision mode");
         return AMS_ERR_INVALID_ARG;
     }
-    if (!(h->opt.two_grid_omega >= 0.0) || !std::isfinite(h->opt.two_grid_omega)) {
-        set_error("two_grid_omega must be finite and >= 0");
+    if (!(h->opt.two_grid_omega > -2.0) || !std::isfinite(h->opt.two_grid_omega)) {
+        set_error("two_grid_omega must be finite and > -2 (negative: that multiple of 1/lambda_max, estimated)");
         return AMS_ERR_INVALID_ARG;
     }
     if (h->opt.spin_budget_cycles < 0 || h->opt.timeout_probe < 0 || h->opt.timeout_probe > 1) {
@@ -1133,6 +1149,8 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     I.coarse_inverse_bytes = (h->R_elems + h->Q_elems) * (int64_t)h->tf_bytes();
     I.basis_bytes = h->psi_elems * (int64_t)h->tp_bytes();
     I.spmv_variant = 0;
+    if (h->opt.two_grid_omega < 0.0) AMS_TRY(estimate_two_grid_omega(h.get()));
+    I.two_grid_omega = h->opt.two_grid_omega;
     I.setup_seconds = now_s() - t0;
     *out = h.release();
     return AMS_OK;
@@ -1163,7 +1181,9 @@ static ams_status ensure_work(ams_handle h, int ld) {
         AMS_TRY(h->alloc_t(&h->d_stage_out, (size_t)h->n_total * ld));
         AMS_TRY(h->alloc_t(&h->d_stage_aux, (size_t)h->n_total * ld));
         h->d_tw = nullptr;
-        if (h->opt.two_grid_omega > 0.0) AMS_TRY(h->alloc_t(&h->d_tw, nv));
+        // the cycle's residual buffer: an automatic omega (negative at setup)
+        // turns positive after its power steps, which already use this space
+        if (h->opt.two_grid_omega != 0.0) AMS_TRY(h->alloc_t(&h->d_tw, nv));
         h->ld_alloc = ld;
         h->ld_last = 0;
     }
@@ -1181,6 +1201,7 @@ static ams_status ensure_work(ams_handle h, int ld) {
 static void prof_begin(ams_handle h, int which) {
     KernelProfile* P = h->prof;
     if (!P) return;
+    nvtxRangePushA(kSlotNames[which]);
     cudaEventRecord(P->ev[2 * P->nev], h->stream);
     P->which[P->nev] = which;
 }
@@ -1189,6 +1210,7 @@ static void prof_end(ams_handle h) {
     if (!P) return;
     cudaEventRecord(P->ev[2 * P->nev + 1], h->stream);
     P->nev++;
+    nvtxRangePop();
 }
 static ams_status prof_flush(ams_handle h) {
     KernelProfile* P = h->prof;
@@ -1245,6 +1267,89 @@ static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool wit
                           with_state ? h->d_st : nullptr, h->use_pdl, h->tune[ld].depth};
         AMS_CUDA_TRY(launch_local_solve(la, h->prec, h->d_fac, h->d_psi, h->d_zf, coarse ? h->d_rc : nullptr));
     }
+    return AMS_OK;
+}
+
+// Damping of the multiplicative cycle from the local solves' spectrum:
+// omega = c / lambda_max(T), T = (sum_i R_i^T A_i^{-1} R_i) A, c = minus
+// the option's value.  lambda_max is estimated by power steps (Rayleigh
+// quotient of T in the A inner product, which rises towards lambda_max
+// from below) in the apply precision, per system, until the estimate moves
+// by less than 1e-7 relative between steps (at most kPowerSteps); the
+// handle takes the largest (the smallest omega).  The cycle is SPD for omega < 2 /
+// lambda_max, so c < 2 keeps it SPD up to the estimate's shortfall.
+constexpr int kPowerSteps = 300;
+
+static ams_status estimate_two_grid_omega(ams_handle h) {
+    const double c = -h->opt.two_grid_omega;
+    AMS_TRY(ensure_work(h, 1));
+    RedCache *rc = nullptr, *rcs = nullptr;
+    AMS_TRY(get_red(h, 1, &rc, &rcs));
+    LaunchCtx L = make_ctx(h, *rc, *rcs);
+    L.st = nullptr;
+    const int64_t nblk = h->n_pad / kRowAlign;
+    std::vector<int64_t> sys_blk0(h->nsys + 1);
+    std::vector<int32_t> blk_sys(nblk);
+    for (int s = 0; s < h->nsys; ++s) {
+        sys_blk0[s] = h->sys[s].row0 / kRowAlign;
+        sys_blk0[s + 1] = (h->sys[s].row0 + h->sys[s].npad) / kRowAlign;
+        for (int64_t b = sys_blk0[s]; b < sys_blk0[s + 1]; ++b) blk_sys[b] = s;
+    }
+    int64_t* d_sys_blk0 = nullptr;
+    int32_t* d_blk_sys = nullptr;
+    double *d_part = nullptr, *d_out = nullptr, *d_inv = nullptr;
+    AMS_TRY(upload(h, &d_sys_blk0, sys_blk0));
+    AMS_TRY(upload(h, &d_blk_sys, blk_sys));
+    AMS_TRY(h->alloc_t(&d_part, (size_t)3 * nblk));
+    AMS_TRY(h->alloc_t(&d_out, (size_t)3 * h->nsys));
+    AMS_TRY(h->alloc_t(&d_inv, (size_t)h->nsys));
+    // x_0: 1 + sin(i)/2 at every dof (caller order), zero on padding rows
+    std::vector<double> x0(h->n_total);
+    for (int64_t i = 0; i < h->n_total; ++i) x0[i] = 1.0 + 0.5 * std::sin((double)i);
+    AMS_CUDA_TRY(cudaMemcpyAsync(h->d_stage_in, x0.data(), sizeof(double) * h->n_total, cudaMemcpyHostToDevice,
+                                 h->stream));
+    AMS_CUDA_TRY(cudaMemsetAsync(h->d_r, 0, sizeof(double) * h->n_pad, h->stream));
+    for (int s = 0; s < h->nsys; ++s) {
+        const SystemHost& S = h->sys[s];
+        launch_permute_in(h->stream, h->d_stage_in + S.caller0, S.n, 1, 1, h->d_int_row + S.caller0, h->d_r, nullptr);
+    }
+    double* x = h->d_r;          // iterate, normalised each step (the next one is built in p)
+    double* y = h->d_q;
+    std::vector<double> out(3 * h->nsys);
+    auto estimate = [&]() {
+        double l = 0.0;
+        for (int s = 0; s < h->nsys; ++s)
+            if (out[3 * s] > 0.0) l = std::max(l, out[3 * s + 1] / out[3 * s]);
+        return l;
+    };
+    double lam = 0.0;
+    for (int step = 0; step < kPowerSteps; ++step) {
+        launch_spmv_dot(L, x, y, 0);                                              // y = A x
+        AMS_TRY(launch_local(h, 1, ResidIn{y, nullptr, h->d_sc}, false, false));  // z = S y
+        launch_power_step(h->stream, h->prec, x, y, h->d_zf, h->n_pad, d_sys_blk0, d_blk_sys, h->nsys, d_part,
+                          d_out, d_inv, h->d_p);
+        AMS_CUDA_TRY(cudaMemcpyAsync(x, h->d_p, sizeof(double) * h->n_pad, cudaMemcpyDeviceToDevice, h->stream));
+        AMS_CUDA_TRY(cudaMemcpyAsync(out.data(), d_out, sizeof(double) * out.size(), cudaMemcpyDeviceToHost,
+                                     h->stream));
+        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        const double next = estimate();
+        const bool settled = step >= 4 && std::fabs(next - lam) <= 1e-7 * next;
+        lam = next;
+        if (settled) break;
+    }
+    AMS_CUDA_TRY(cudaGetLastError());
+    for (void* p : {(void*)d_sys_blk0, (void*)d_blk_sys, (void*)d_part, (void*)d_out, (void*)d_inv}) h->release(p);
+    if (!(lam > 0.0) || !std::isfinite(lam)) {
+        set_error("two-grid damping: the power steps gave no positive eigenvalue estimate");
+        return AMS_ERR_BREAKDOWN;
+    }
+    h->info.local_lambda_max = lam;
+    h->opt.two_grid_omega = c / lam;
+    if (h->d_tw == nullptr) {
+        set_error("two-grid damping: the cycle's work vector is missing");
+        return AMS_ERR_CUDA;
+    }
+    h->ld_last = 0;   // the next solve starts from cleared work vectors
     return AMS_OK;
 }
 
@@ -1593,8 +1698,11 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
         const ResidIn in{h->d_r, h->d_q, h->d_sc};
         float best = 1e30f;
         int arg = 0;
-        for (int nr = 8; nr >= 2; nr /= 2) {
-            if (nr > ld || ld / nr > 8) continue;    // at most 8 warps per block
+        // tensor-core kernel from 8 right-hand sides on: 8 or 16 per warp,
+        // at most four warps; below that 2, 4 or 8 per warp, at most eight
+        const int hi = ld >= 8 ? 16 : 8, lo = ld >= 8 ? 8 : 2, maxw = ld >= 8 ? 4 : 8;
+        for (int nr = hi; nr >= lo; nr /= 2) {
+            if (nr > ld || ld / nr > maxw) continue;
             T.nr = nr;
             float ms = 0.f;
             AMS_TRY(timed_after(spmv, [&]() -> ams_status { return launch_local(h, ld, in, true); }, &ms));
@@ -1758,6 +1866,7 @@ const char* ams_last_error(void) { return g_last_error.c_str(); }
 ams_status ams_setup(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
                      const int32_t* part, int32_t nparts, int32_t m, const ams_options* opt, void* stream,
                      ams_handle* out) {
+    NvtxRange nvtx_range("ams_setup");
     g_last_error.clear();
     ams_system_desc d{n, rowptr, colind, vals, part, nparts, m};
     return setup_impl(1, &d, opt, stream, out);
@@ -1765,6 +1874,7 @@ ams_status ams_setup(int64_t n, const int64_t* rowptr, const int32_t* colind, co
 
 ams_status ams_setup_batched(int32_t nsys, const ams_system_desc* systems, const ams_options* opt, void* stream,
                              ams_handle* out) {
+    NvtxRange nvtx_range("ams_setup_batched");
     g_last_error.clear();
     return setup_impl(nsys, systems, opt, stream, out);
 }
@@ -1830,6 +1940,7 @@ static ams_status check_solve_args(ams_handle h, const void* a, const void* b, i
 
 ams_status ams_solve(ams_handle h, const double* f, int32_t nrhs, double rtol, double* u, int32_t* iters,
                      double* relres) {
+    NvtxRange nvtx_range("ams_solve");
     g_last_error.clear();
     AMS_TRY(check_solve_args(h, f, u, nrhs, rtol));
     AMS_TRY(ensure_work(h, pow2ceil(nrhs)));
@@ -1848,6 +1959,7 @@ ams_status ams_solve(ams_handle h, const double* f, int32_t nrhs, double rtol, d
 
 ams_status ams_solve_adjoint(ams_handle h, const double* g, int32_t nrhs, double rtol, const double* u,
                              double* lambda, double* dvals, int32_t* iters) {
+    NvtxRange nvtx_range("ams_solve_adjoint");
     g_last_error.clear();
     AMS_TRY(check_solve_args(h, g, lambda, nrhs, rtol));
     if (h->nsys != 1) {
@@ -1960,8 +2072,11 @@ ams_status ams_set_launch_shape(ams_handle h, int32_t nrhs, const int32_t* shape
             return AMS_ERR_INVALID_ARG;
         }
     }
-    if (nr != 0 && ((nr != 2 && nr != 4 && nr != 8) || nr > ld || ld / nr > 8)) {
-        set_error("right-hand sides per warp must be 0, or 2, 4 or 8 with at most 8 warps per block");
+    const bool nr_ok = ld >= 8 ? ((nr == 8 || nr == 16) && nr <= ld && ld / nr <= 4)
+                               : ((nr == 2 || nr == 4 || nr == 8) && nr <= ld && ld / nr <= 8);
+    if (nr != 0 && !nr_ok) {
+        set_error("right-hand sides per warp must be 0, or (below 8 right-hand sides) 2, 4 or 8 with at most "
+                  "8 warps per block, or (8 or more) 8 or 16 with at most 4 warps per block");
         return AMS_ERR_INVALID_ARG;
     }
     if (l2mode < 0 || l2mode > 2 || l2keep < 0) {
@@ -2041,6 +2156,7 @@ ams_status ams_get_coarse_matrix(ams_handle h, double* A0) {
 }
 
 ams_status ams_apply_preconditioner(ams_handle h, const double* r, int32_t nrhs, double* z) {
+    NvtxRange nvtx_range("ams_apply_preconditioner");
     g_last_error.clear();
     AMS_TRY(check_solve_args(h, r, z, nrhs, 1.0));
     if (h->nsys != 1) {
@@ -2068,6 +2184,7 @@ ams_status ams_apply_preconditioner(ams_handle h, const double* r, int32_t nrhs,
 }
 
 ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y) {
+    NvtxRange nvtx_range("ams_spmv");
     g_last_error.clear();
     AMS_TRY(check_solve_args(h, x, y, nrhs, 1.0));
     if (h->nsys != 1) {
@@ -2095,6 +2212,7 @@ ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y) {
 }
 
 ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* avg_ms, double* bytes) {
+    NvtxRange nvtx_range("ams_time_kernel");
     g_last_error.clear();
     if (!h || reps <= 0 || which < 0 || which >= AMS_NUM_KERNELS || h->ld_last == 0) {
         set_error("invalid arguments (a solve must run first)");
@@ -2157,6 +2275,7 @@ ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* av
 
 ams_status ams_profile_solve(ams_handle h, const double* f, int32_t nrhs, double rtol, double* ms,
                              double* bytes, int64_t* count) {
+    NvtxRange nvtx_range("ams_profile_solve");
     g_last_error.clear();
     AMS_TRY(check_solve_args(h, f, f, nrhs, rtol));
     AMS_TRY(ensure_work(h, pow2ceil(nrhs)));

@@ -15,6 +15,7 @@
 #include "ams_internal.h"
 #include "kernels.cuh"
 #include "launch.h"
+#include "mma_tf32.cuh"
 
 namespace ams {
 
@@ -496,6 +497,129 @@ k_coarse_gemm(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
         for (int ch = 0; ch < it.nchunks; ++ch) s += (A)__ldcg(partial + (int64_t)(it.slot0 + ch) * OUT + o);
         const int rr = o / LD, hh = o % LD;
         if (rr < it.nrows) out[(int64_t)(it.out0 + rr) * LD + hh] = (TF)s;
+    }
+    if (t == 0) cnt[it.tile_id] = 0;
+}
+
+// Many right-hand sides (LD >= 8) in the reduced-precision apply: the same
+// items as k_coarse_gemm, with the 32-row tile times the gathered input
+// computed by warp-level tensor-core MMAs (m16n8k8, TF32 head/tail split
+// of both operands, FP32 accumulation: FP32 accuracy).  Warp w owns the
+// 16 x 8 output fragment (rows 16 (w / (LD/8)) .., columns 8 (w % (LD/8)) ..);
+// stages of 64 columns of the tile (row-major, rows padded to 68 floats so
+// that the A-fragment loads are conflict-free) and of the gathered input
+// (rows padded to 8 mod 32 words for the B fragments) pass through shared
+// memory, the next stage loaded into registers while the current one is
+// multiplied.  Split-K chunks reduce as in k_coarse_gemm.
+template <int LD>
+__global__ void __launch_bounds__(LD * 8)
+k_coarse_mma(const CoarseItem* __restrict__ items, const float* __restrict__ mat, const int32_t* __restrict__ rng,
+             const int32_t* __restrict__ gat, const float* __restrict__ in, float* __restrict__ out,
+             float* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
+    pdl_wait();
+    if (st != nullptr && st->done) return;
+    pdl_trigger();
+    static_assert(LD == 8 || LD == 16 || LD == 32, "k_coarse_mma serves 8, 16 or 32 right-hand sides");
+    constexpr int NT = LD * 8;                               // threads: 2 x (LD / 8) warps
+    constexpr int KC = 64;                                   // columns per stage
+    constexpr int SA = KC + 4;
+    constexpr int SB = LD >= 16 ? LD + 8 : 24;
+    constexpr int OUT = 32 * LD;
+    constexpr int MV = 32 * KC / 4 / NT;                     // float4 tile pieces per thread
+    constexpr int XV = KC * LD / NT;                         // input values per thread (8)
+    __shared__ __align__(16) float sA[32][SA];
+    __shared__ __align__(16) float sB[KC][SB];
+    __shared__ int s_last;
+    const CoarseItem it = items[blockIdx.x];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int g = lane >> 2, tq = lane & 3;
+    const int nf = w % (LD / 8), mf = w / (LD / 8);
+    const float* M0 = mat + it.moff + (int64_t)it.row_in_node * it.ldm;
+    const int g0 = (it.gat_off < 0) ? rng[2 * it.rng_off] : 0;
+    const int32_t* G = gat + (it.gat_off < 0 ? 0 : it.gat_off);
+    float4 mreg[MV];
+    float xreg[XV];
+    auto load_stage = [&](int kb) {
+        const int kn = min(KC, it.k1 - kb);
+#pragma unroll
+        for (int u = 0; u < MV; ++u) {
+            const int i = t + NT * u;
+            const int r = i / (KC / 4), c4 = i % (KC / 4);
+            mreg[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r < it.nrows && 4 * c4 < kn)
+                mreg[u] = *reinterpret_cast<const float4*>(M0 + (int64_t)r * it.ldm + kb + 4 * c4);
+        }
+#pragma unroll
+        for (int u = 0; u < XV; ++u) {
+            const int i = t + NT * u;
+            const int kk = i / LD, hh = i % LD;
+            xreg[u] = 0.f;
+            if (kk < kn) {
+                const int k = kb + kk;
+                const int gi = (it.gat_off < 0) ? g0 + k : __ldg(G + k);
+                xreg[u] = in[(int64_t)gi * LD + hh];
+            }
+        }
+    };
+    auto store_stage = [&]() {
+#pragma unroll
+        for (int u = 0; u < MV; ++u) {
+            const int i = t + NT * u;
+            *reinterpret_cast<float4*>(&sA[i / (KC / 4)][4 * (i % (KC / 4))]) = mreg[u];
+        }
+#pragma unroll
+        for (int u = 0; u < XV; ++u) {
+            const int i = t + NT * u;
+            sB[i / LD][i % LD] = xreg[u];
+        }
+    };
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    load_stage(it.k0);
+    for (int kb = it.k0; kb < it.k1; kb += KC) {
+        __syncthreads();                     // the previous stage is no longer read
+        store_stage();
+        __syncthreads();
+        if (kb + KC < it.k1) load_stage(kb + KC);
+#pragma unroll
+        for (int ks = 0; ks < KC / 8; ++ks) {
+            const int r0 = 16 * mf + g, k0 = 8 * ks + tq;
+            uint32_t ah[4], al[4], b0h, b0l, b1h, b1l;
+            split_tf32(sA[r0][k0], ah[0], al[0]);
+            split_tf32(sA[r0 + 8][k0], ah[1], al[1]);
+            split_tf32(sA[r0][k0 + 4], ah[2], al[2]);
+            split_tf32(sA[r0 + 8][k0 + 4], ah[3], al[3]);
+            split_tf32(sB[k0][8 * nf + g], b0h, b0l);
+            split_tf32(sB[k0 + 4][8 * nf + g], b1h, b1l);
+            mma_tf32(acc, al, b0h, b1h);
+            mma_tf32(acc, ah, b0l, b1l);
+            mma_tf32(acc, ah, b0h, b1h);
+        }
+    }
+    // accumulator i: row 16 mf + g + 8 (i >> 1), column 8 nf + 2 tq + (i & 1)
+    if (it.nchunks == 1) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int rr = 16 * mf + g + 8 * (i >> 1);
+            if (rr < it.nrows) out[(int64_t)(it.out0 + rr) * LD + 8 * nf + 2 * tq + (i & 1)] = acc[i];
+        }
+        return;
+    }
+    float* P = partial + (int64_t)(it.slot0 + it.chunk) * OUT;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) P[(16 * mf + g + 8 * (i >> 1)) * LD + 8 * nf + 2 * tq + (i & 1)] = acc[i];
+    __syncthreads();
+    if (t == 0) {
+        __threadfence();
+        s_last = (atomicAdd(cnt + it.tile_id, 1) == it.nchunks - 1);
+        if (s_last) __threadfence();
+    }
+    __syncthreads();
+    if (!s_last) return;
+    for (int o = t; o < OUT; o += NT) {
+        float sum = 0.f;
+        for (int ch = 0; ch < it.nchunks; ++ch) sum += __ldcg(partial + (int64_t)(it.slot0 + ch) * OUT + o);
+        const int rr = o / LD, hh = o % LD;
+        if (rr < it.nrows) out[(int64_t)(it.out0 + rr) * LD + hh] = sum;
     }
     if (t == 0) cnt[it.tile_id] = 0;
 }
@@ -1022,9 +1146,14 @@ static void coarse_ld(const CoarseLaunch& c, const void* in, void* out) {
         launch_kernel(c.pdl, k_coarse_rows<TF, (LD <= 4 ? LD : 4)>, dim3(c.nitems), dim3(256), 0, c.stream, c.items,
                       (const TF*)c.mat, c.rng, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt, c.st);
     else
-        launch_kernel(c.pdl, k_coarse_gemm<TF, (LD >= 8 ? LD : 8)>, dim3(c.nitems), dim3(256), 0, c.stream,
-                      c.items, (const TF*)c.mat, c.rng, c.gat, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt,
-                      c.st);
+        if constexpr (sizeof(TF) == 4)   // reduced-precision apply: tile products on the tensor cores
+            launch_kernel(c.pdl, k_coarse_mma<(LD >= 8 ? LD : 8)>, dim3(c.nitems), dim3((LD >= 8 ? LD : 8) * 8), 0,
+                          c.stream, c.items, (const float*)c.mat, c.rng, c.gat, (const float*)in, (float*)out,
+                          (float*)c.partial, c.cnt, c.st);
+        else
+            launch_kernel(c.pdl, k_coarse_gemm<TF, (LD >= 8 ? LD : 8)>, dim3(c.nitems), dim3(256), 0, c.stream,
+                          c.items, (const TF*)c.mat, c.rng, c.gat, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt,
+                          c.st);
 }
 template <typename TF>
 static void coarse_tf(const CoarseLaunch& c, int ld, const void* in, void* out) {

@@ -20,6 +20,11 @@
 
 namespace ams {
 
+static unsigned tg_blocks_pw(int64_t n) {
+    const int64_t b = (n + 255) / 256;
+    return (unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
 template <typename T> __device__ __forceinline__ double tg_widen(T v);
 template <> __device__ __forceinline__ double tg_widen<float>(float v) { return f32_to_f64(v); }
 template <> __device__ __forceinline__ double tg_widen<double>(double v) { return v; }
@@ -103,6 +108,79 @@ k_tg_restrict(const SubInfo* __restrict__ subs, int nsub, const TP* __restrict__
         double a = acc[k];
         for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
         if (lane == 0 && k < m) rc[(S.coff + k) * ld + rhs] = (TF)a;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Damping of the cycle: power steps on T = (sum_i R_i^T A_i^{-1} R_i) A.
+// T is self-adjoint in the A inner product, so with y = A x and z = S y the
+// Rayleigh quotient (y . z) / (x . y) rises towards lambda_max(T) per
+// system.  Partials cover kRowAlign rows each (one system per block, since
+// systems are padded to that many rows) and are summed in block order.
+// ---------------------------------------------------------------------------
+template <typename TZ>
+__global__ void __launch_bounds__(256)
+k_pw_partials(const double* __restrict__ x, const double* __restrict__ y, const TZ* __restrict__ z, int64_t nrows,
+              double* __restrict__ part) {
+    __shared__ double s[3][256];
+    const int64_t lo = blockIdx.x * (int64_t)kRowAlign;
+    const int64_t hi = lo + kRowAlign < nrows ? lo + kRowAlign : nrows;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += 256) {
+        const double yi = y[i], zi = tg_widen<TZ>(z[i]);
+        a = fma(x[i], yi, a);
+        b = fma(yi, zi, b);
+        c = fma(zi, zi, c);
+    }
+    s[0][threadIdx.x] = a;
+    s[1][threadIdx.x] = b;
+    s[2][threadIdx.x] = c;
+    __syncthreads();
+    for (int h = 128; h >= 1; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int k = 0; k < 3; ++k) s[k][threadIdx.x] += s[k][threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) part[3 * (int64_t)blockIdx.x + threadIdx.x] = s[threadIdx.x][0];
+}
+
+// Per system: sums of its blocks' partials (x.y, y.z, z.z) and 1/||z||.
+__global__ void k_pw_finish(const double* __restrict__ part, const int64_t* __restrict__ sys_blk0, int nsys,
+                            double* __restrict__ out, double* __restrict__ inv_norm) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nsys) return;
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int64_t k = sys_blk0[s]; k < sys_blk0[s + 1]; ++k) {
+        a += part[3 * k];
+        b += part[3 * k + 1];
+        c += part[3 * k + 2];
+    }
+    out[3 * s] = a;
+    out[3 * s + 1] = b;
+    out[3 * s + 2] = c;
+    inv_norm[s] = c > 0.0 ? 1.0 / sqrt(c) : 0.0;
+}
+
+// x = z / ||z|| (per system)
+template <typename TZ>
+__global__ void k_pw_normalize(const TZ* __restrict__ z, const int32_t* __restrict__ blk_sys,
+                               const double* __restrict__ inv_norm, int64_t nrows, double* __restrict__ x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nrows; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = tg_widen<TZ>(z[i]) * inv_norm[blk_sys[i / kRowAlign]];
+}
+
+void launch_power_step(cudaStream_t s, int prec, const double* x, const double* y, const void* z, int64_t nrows,
+                       const int64_t* sys_blk0, const int32_t* blk_sys, int nsys, double* part, double* out,
+                       double* inv_norm, double* x_next) {
+    const unsigned nblk = (unsigned)((nrows + kRowAlign - 1) / kRowAlign);
+    if (prec == AMS_PREC_FP64) {
+        k_pw_partials<double><<<nblk, 256, 0, s>>>(x, y, (const double*)z, nrows, part);
+        k_pw_finish<<<(nsys + 127) / 128, 128, 0, s>>>(part, sys_blk0, nsys, out, inv_norm);
+        k_pw_normalize<double><<<tg_blocks_pw(nrows), 256, 0, s>>>((const double*)z, blk_sys, inv_norm, nrows, x_next);
+    } else {
+        k_pw_partials<float><<<nblk, 256, 0, s>>>(x, y, (const float*)z, nrows, part);
+        k_pw_finish<<<(nsys + 127) / 128, 128, 0, s>>>(part, sys_blk0, nsys, out, inv_norm);
+        k_pw_normalize<float><<<tg_blocks_pw(nrows), 256, 0, s>>>((const float*)z, blk_sys, inv_norm, nrows, x_next);
     }
 }
 

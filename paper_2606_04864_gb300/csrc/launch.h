@@ -121,6 +121,9 @@ cudaError_t launch_local_solve(const LocalSolveArgs& a, int prec, const void* fa
                                void* zf, void* rc);
 void launch_coarse_gemm(const CoarseLaunch& c, int prec, int ld, const void* in, void* out);
 cudaError_t launch_local_tma(const LocalTmaArgs& a, int prec, const void* psi, void* zf, void* rc);
+// 8 to 32 right-hand sides: tile products as tensor-core MMAs (k_local_mma.cu)
+cudaError_t launch_local_mma(const LocalTmaArgs& a, int prec, const void* psi, void* zf, void* rc);
+size_t local_mma_smem(int cmax, int ld, int depth);
 size_t local_tma_smem(int cmax, int ld, int depth);
 // Shared memory the TMA local-solve launch for `a` needs at ring depth `depth`.
 size_t local_tma_launch_smem(const LocalTmaArgs& a, int depth);
@@ -153,6 +156,13 @@ void launch_tg_resid(const LaunchCtx& L, const void* v, int v_is_fp64, const Res
 void launch_tg_scale(const LaunchCtx& L, int prec, void* zf, double omega, int64_t n);
 void launch_tg_combine(const LaunchCtx& L, int prec, void* zf, const double* x2, double omega, int64_t n);
 void launch_tg_restrict(const LaunchCtx& L, int prec, const void* psi, const double* w, void* rc, int mmax);
+// One power step for the cycle's damping: per system the sums x.y, y.z and
+// z.z into out[3 s ..] (y = A x, z = the local solves of y in the apply
+// precision), and x_next = z / ||z||.  sys_blk0: first kRowAlign-row block
+// of each system (nsys + 1 entries); blk_sys: system of each block.
+void launch_power_step(cudaStream_t s, int prec, const double* x, const double* y, const void* z, int64_t nrows,
+                       const int64_t* sys_blk0, const int32_t* blk_sys, int nsys, double* part, double* out,
+                       double* inv_norm, double* x_next);
 // Condition of the device-resident iteration loop (a while node of a CUDA
 // graph): continue while the solve is not done and fewer than `cap` bodies
 // have run.

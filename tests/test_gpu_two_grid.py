@@ -98,6 +98,37 @@ def test_two_grid_without_coarse_space_matches_oracle(prec, tol):
 def test_two_grid_omega_is_validated():
     from paper_2606_04864_gb300._lib import AmsError
     w = _case("2d")
-    for bad in (-0.5, float("nan"), float("inf")):
+    for bad in (-2.0, float("nan"), float("inf")):
         with pytest.raises(AmsError):
             AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, two_grid_omega=bad)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_bf16"])
+def test_two_grid_damping_from_power_steps(prec):
+    """two_grid_omega = -c: setup estimates lambda_max of the local solves
+    times A by power steps (from below) and takes omega = c / lambda_max;
+    the estimate agrees with the oracle's Lanczos value, and the solve with
+    that omega matches the oracle's cycle with the same omega."""
+    w = _case("3d")
+    A = csr_to_scipy(w.rowptr, w.colind, w.vals)
+    o = OracleAMS(A, w.part, w.nparts, w.m, basis_round=ROUND[prec])
+    lam = o.local_lambda_max()
+    s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision=prec, two_grid_omega=-1.0)
+    info = s.info()
+    est = info["local_lambda_max"]
+    assert 0.99 * lam <= est <= lam * (1 + (1e-6 if prec == "fp64" else 1e-4)), (est, lam)
+    assert info["two_grid_omega"] == pytest.approx(1.0 / est, rel=1e-15)
+    omega = info["two_grid_omega"]
+    ref = pcg(A, w.rhs[0], lambda r: o.apply_two_grid(r, omega), rtol=1e-8, flexible=(prec != "fp64"))
+    u, its, rel = s.solve(w.rhs[0], rtol=1e-8)
+    assert abs(int(its[0]) - ref.iters) <= 2, (its, ref.iters)
+    err = np.linalg.norm(u - ref.u) / np.linalg.norm(ref.u)
+    if prec == "fp64":
+        assert err <= 1e-10, err
+    else:
+        tight = pcg(A, w.rhs[0], lambda r: o.apply_two_grid(r, omega), rtol=1e-13)
+        floor = np.linalg.norm(ref.u - tight.u) / np.linalg.norm(tight.u)
+        assert err <= max(1e-6, 10 * floor), (err, floor)
+    from paper_2606_04864_gb300._lib import AmsError
+    with pytest.raises(AmsError):
+        AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision=prec, two_grid_omega=-2.5)
