@@ -200,6 +200,24 @@ def slot_bytes(systems, nrhs, prec="mixed"):
     }
 
 
+def slot_fp64_flops(systems, nrhs):
+    """FP64 floating-point operations per launch of each slot (an FMA counts
+    two): the SpMV and its fused dot and direction update, the residual
+    update the local solves form, and the prolongation's CG update and
+    dots.  The preconditioner itself runs in FP32/TF32."""
+    n = sum(w.n for w, _ in systems)
+    nnz = sum(w.nnz for w, _ in systems)
+    nv = n * nrhs
+    return {"spmv_direction": 2 * nnz * nrhs + 2 * nv + 2 * nv,   # q = A p, p = z + beta p_old, p.q
+            "local_solve_restrict": 2 * nv,                         # r' = r - alpha q
+            "coarse_solve": 0,
+            "prolong_update": 10 * nv}                              # r, x updates; r.z, r.r, z.q
+
+
+# FP64 peak (no measured figure exists for it): the nominal GB300 rate
+FP64_PEAK_TFLOPS = 1.25
+
+
 def default_m_i(w):
     """m_i = min(m, n_i) per subdomain of a regular block partition."""
     from workloads import block_partition
@@ -427,6 +445,12 @@ def _second_workload(name, torch, stream):
                                                       "setup_s": round(s.info()["setup_seconds"], 3)}
         s.close()
     out["mixed_speedup_vs_fp64"] = out["fp64"]["time_s"] / out["mixed"]["time_s"]
+    s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp32_bf16", device=True,
+                  two_grid_omega=-1.0)
+    s.solve(f, rtol=1e-8)
+    ms, (u, its, rel) = _timed(lambda: s.solve(f, rtol=1e-8), 3, stream, torch)
+    out["two_grid_cycle"] = {"time_s": ms / 1e3, "iters": int(its.max()), "omega": s.info()["two_grid_omega"]}
+    s.close()
     return out
 
 
@@ -543,14 +567,20 @@ def run_gpu(args):
         else:
             sysm = [(w, mixed.coarse_basis()[0])]
         alg = slot_bytes(sysm, nrhs, "mixed") if sysm is not None else None
+        f64 = slot_fp64_flops(sysm, nrhs) if sysm is not None else None
+        peak_hbm, _ = _peaks()
         for pk in prof:
             if not pk["count"] or alg is None:
                 continue
             avg = pk["ms"] / pk["count"]
             a = alg[pk["name"]]
+            gbs = a / (avg * 1e-3) / 1e9 if avg > 0 else None
+            tf = f64[pk["name"]] / (avg * 1e-3) / 1e12 if avg > 0 else None
             kern[pk["name"]] = {"ms_total": pk["ms"], "launches": pk["count"], "ms": avg,
-                                "alg_bytes": a, "stored_bytes": pk["bytes"],
-                                "gbs": a / (avg * 1e-3) / 1e9 if avg > 0 else None}
+                                "alg_bytes": a, "stored_bytes": pk["bytes"], "gbs": gbs,
+                                "fp64_flops": f64[pk["name"]], "fp64_tflops": tf,
+                                "hbm_frac": gbs / peak_hbm if gbs else None,
+                                "fp64_frac": tf / FP64_PEAK_TFLOPS if tf else None}
         tot = sum(v["ms_total"] for v in kern.values())
         for v in kern.values():
             v["share"] = v["ms_total"] / tot if tot > 0 else None
@@ -562,12 +592,17 @@ def run_gpu(args):
                 traffic, traffic_src, traffic_wl = t, src, wl
                 break
         peak, peak_kind = _peaks()
+        kd = kern[dom]
+        alu = (kd["fp64_frac"] or 0.0) > (kd["hbm_frac"] or 0.0)   # the binding roof
         roof = {
-            "bound": "hbm", "kernel": dom,
-            "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
-            "frac": kern[dom]["gbs"] / peak, "traffic": traffic,
+            "bound": "alu" if alu else "hbm", "kernel": dom,
+            "achieved": kd["fp64_tflops"] if alu else kd["gbs"], "peak": FP64_PEAK_TFLOPS if alu else peak,
+            "unit": "TFLOP/s (FP64)" if alu else "GB/s",
+            "frac": kd["fp64_frac"] if alu else kd["hbm_frac"], "traffic": traffic,
+            "hbm_frac": kd["hbm_frac"], "fp64_frac": kd["fp64_frac"],
             "traffic_source": traffic_src,
-            "peak_source": f"{peak_kind} hbm_gbs (copy burst)",
+            "peak_source": ("nominal GB300 FP64 1.25 TFLOP/s (about two FP64 FMAs per clock per SM at 2.07 GHz; "
+                            "no measured FP64 peak)") if alu else f"{peak_kind} hbm_gbs (copy burst)",
             "timing": "CUDA events around every launch inside one profiled solve",
             "algorithmic_bytes_per_launch": kern[dom]["alg_bytes"],
             "stored_bytes_per_launch": kern[dom]["stored_bytes"],
@@ -584,6 +619,19 @@ def run_gpu(args):
     rel_mixed_vs_fp64 = float(torch.linalg.norm(u - u64) / torch.linalg.norm(u64))
     info64 = fp64.info()
     fp64.close()
+
+    # multiplicative two-grid cycle (omega = 1 / lambda_max, estimated at setup)
+    two_grid = None
+    if not batched and not args.no_two_grid:
+        tg = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp32_bf16", device=True,
+                       two_grid_omega=-1.0)
+        solve(tg, f_dev)
+        mtg, (utg, itg, _) = _timed(lambda: solve(tg, f_dev), nfp, stream, torch)
+        ti = tg.info()
+        two_grid = {"time_s": mtg / 1e3, "iters": int(np.max(itg)), "omega": ti["two_grid_omega"],
+                    "lambda_max_estimate": ti["local_lambda_max"], "setup_s": round(ti["setup_seconds"], 3),
+                    "u_rel_diff_vs_additive": float(torch.linalg.norm(utg - u) / torch.linalg.norm(u))}
+        tg.close()
 
     # end to end through the public API with host buffers (pinned), copies timed
     host = build("fp32_bf16", False)
@@ -627,6 +675,8 @@ def run_gpu(args):
                   "launch_shape": {**shape, "source": "--launch-shape" if args.launch_shape else "autotuned"}}
         if adjoint is not None:
             config["adjoint"] = adjoint
+        if two_grid is not None:
+            config["two_grid_cycle"] = two_grid
         if kern:
             it_ms = sum(v["ms"] for v in kern.values())
             config["iteration_ms"] = it_ms
@@ -634,7 +684,10 @@ def run_gpu(args):
             config["kernels"] = {k: {"ms_per_launch": round(v["ms"], 5), "launches": v["launches"],
                                      "share": round(v["share"], 4), "alg_bytes": int(v["alg_bytes"]),
                                      "stored_bytes": int(v["stored_bytes"]),
-                                     "gbs": round(v["gbs"], 1) if v["gbs"] else None}
+                                     "gbs": round(v["gbs"], 1) if v["gbs"] else None,
+                                     "hbm_frac": round(v["hbm_frac"], 3) if v["hbm_frac"] else None,
+                                     "fp64_tflops": round(v["fp64_tflops"], 3) if v["fp64_tflops"] else None,
+                                     "fp64_frac": round(v["fp64_frac"], 3) if v["fp64_frac"] else None}
                                  for k, v in kern.items()}
         if second is not None:
             config["channels2d_1024"] = second
@@ -676,6 +729,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-second", action="store_true", help="skip the second (1024^2) workload")
+    ap.add_argument("--no-two-grid", action="store_true", help="skip the multiplicative two-grid cycle")
     ap.add_argument("--workload", default="grf3d_128_rhs32", choices=list(WORKLOADS),
                     help="grf3d_128_rhs32 (default, the headline line): 128^3 lognormal with 32 right-hand "
                          "sides; channels2d_1024: 1024^2 channelised Darcy; grf3d_96: 96^3 lognormal, one "

@@ -112,6 +112,36 @@ def test_channels2d_mixed_vs_fp64_full_size(channels2d):
     assert r64[0] <= 1e-8 and rmx[0] <= 1e-8
 
 
+def test_channels2d_against_the_oracles_full_size_solve(channels2d):
+    """Against the oracle's own solve of the full-size system
+    (tests/golden/channels2d_1024_oracle.json, written from oracle/ alone by
+    tests/golden/make_channels2d_1024_oracle.py): iterations within 2; at
+    4096 seeded entries the FP64 path within 1e-10 of the oracle's rtol-1e-8
+    solution and the mixed path within max(1e-6, 10 x floor), the floor
+    being the oracle's own rtol-1e-8 error against its rtol-1e-13 solution;
+    both within 1e-6 + floor of the tight solution."""
+    import json
+    import os
+    w, A = channels2d
+    with open(os.path.join(os.path.dirname(__file__), "golden", "channels2d_1024_oracle.json")) as fh:
+        fx = json.load(fh)
+    assert fx["n"] == w.n and fx["nnz"] == w.nnz
+    idx = np.asarray(fx["sample_idx"])
+    u8, u13 = np.asarray(fx["u_1e-8"]), np.asarray(fx["u_1e-13"])
+    floor = fx["floor_rtol_1e-8_vs_1e-13"]
+    f = torch.as_tensor(w.rhs, device="cuda")
+    for prec in ("fp64", "fp32_bf16"):
+        s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision=prec, device=True)
+        u, its, rel = s.solve(f, rtol=1e-8)
+        assert abs(int(its[0]) - fx["rtol_1e-08"]["iters"]) <= 2, (prec, its, fx["rtol_1e-08"]["iters"])
+        us = u.cpu().numpy()[0][idx]
+        err8 = np.linalg.norm(us - u8) / np.linalg.norm(u8)
+        err13 = np.linalg.norm(us - u13) / np.linalg.norm(u13)
+        assert err8 <= (1e-10 if prec == "fp64" else max(1e-6, 10 * floor)), (prec, err8, floor)
+        assert err13 <= 1e-6 + 2 * floor, (prec, err13, floor)
+        s.close()
+
+
 def test_grf3d_128_32_rhs_full_size():
     w = make_grf3d_128_rhs32()
     A = _A(w)
