@@ -51,8 +51,10 @@ METRIC = "PCG time-to-solution at rtol 1e-8 (s), iters, HBM GB/s; mixed vs FP64"
 WORKLOADS = ("grf3d_128_rhs32", "channels2d_1024", "grf3d_96", "batch48_uneven")
 
 # Kernel behind each timed solve slot, for the ncu traffic lookup.
-SLOT_KERNELS = {"local_solve_restrict": ("k_local_tma1", "k_local_tma"), "spmv_direction": ("k_spmv_dot",),
-                "coarse_solve": ("k_coarse_gemm", "k_coarse_rows"), "prolong_update": ("k_prolong_update",)}
+SLOT_KERNELS = {"local_solve_restrict": ("k_local_mma", "k_local_tma1", "k_local_tma"),
+                "spmv_direction": ("k_spmv_dot",),
+                "coarse_solve": ("k_coarse_mma", "k_coarse_gemm", "k_coarse_rows"),
+                "prolong_update": ("k_prolong_update",)}
 
 
 def _make(name):
@@ -585,11 +587,11 @@ def run_gpu(args):
         for v in kern.values():
             v["share"] = v["ms_total"] / tot if tot > 0 else None
         dom = max(kern, key=lambda k: kern[k]["ms_total"])
-        traffic, traffic_src, traffic_wl = None, None, None
+        traffic, traffic_src, traffic_wl, traffic_kernel = None, None, None, None
         for kname in SLOT_KERNELS.get(dom, ()):
             t, src, wl = _profiled_traffic(kname)
             if t is not None and (wl is None or wl == args.workload):
-                traffic, traffic_src, traffic_wl = t, src, wl
+                traffic, traffic_src, traffic_wl, traffic_kernel = t, src, wl, kname
                 break
         peak, peak_kind = _peaks()
         kd = kern[dom]
@@ -600,7 +602,7 @@ def run_gpu(args):
             "unit": "TFLOP/s (FP64)" if alu else "GB/s",
             "frac": kd["fp64_frac"] if alu else kd["hbm_frac"], "traffic": traffic,
             "hbm_frac": kd["hbm_frac"], "fp64_frac": kd["fp64_frac"],
-            "traffic_source": traffic_src,
+            "traffic_source": traffic_src, "traffic_kernel": traffic_kernel,
             "peak_source": ("nominal GB300 FP64 1.25 TFLOP/s (about two FP64 FMAs per clock per SM at 2.07 GHz; "
                             "no measured FP64 peak)") if alu else f"{peak_kind} hbm_gbs (copy burst)",
             "timing": "CUDA events around every launch inside one profiled solve",
@@ -721,6 +723,38 @@ def run_gpu(args):
     return 0
 
 
+def run_kernel_timing(args):
+    """--kernel-timing: a smaller copy of the 3-D lognormal workload (side^3
+    cells, same generator, 8^3 blocks, m = 6, nrhs N(0,1) right-hand sides;
+    with --workload channels2d_1024 the 1024^2 channel workload itself)
+    solved once on fixed default launch shapes, then every kernel slot
+    launched directly (ams_time_kernel, outside any graph) a few times.  The
+    small case for per-kernel ncu captures (-k <kernel> -s <n> -c <n>),
+    which do not see kernels inside the solve's conditional graph."""
+    import torch
+
+    from paper_2606_04864_gb300 import AmsSolver
+    from workloads import grf_logk, make_from_logk
+    torch.cuda.set_device(0)
+    if args.workload == "channels2d_1024":   # the one-right-hand-side workload itself
+        w = _make("channels2d_1024")
+    else:
+        logk = grf_logk((args.side,) * 3, sigma=6.0, std=3.0, seed=3)
+        w = make_from_logk(f"grf3d_{args.side}_rhs{args.nrhs}", logk, 8, 6, rhs_kind="normal", nrhs=args.nrhs,
+                           seed=3)
+    s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision="fp32_bf16", device=True,
+                  autotune=False)
+    u, its, rel = s.solve(torch.as_tensor(w.rhs, device="cuda"), rtol=1e-8)
+    out = {"workload": w.name, "n": w.n, "nrhs": w.nrhs, "iters": int(its.max()), "launch_shape": s.launch_shape(w.nrhs),
+           "slots": {}}
+    from paper_2606_04864_gb300._lib import KERNEL_NAMES
+    for k, name in enumerate(KERNEL_NAMES):
+        ms = [s.time_kernel(k, 3)[0] for _ in range(2)]
+        out["slots"][name] = {"ms_per_launch": min(ms)}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -739,7 +773,14 @@ def main():
                          "bps_elem,bps_sub,depth,nr,l2mode,l2keep (as reported in config.launch_shape); for "
                          "profiling one configuration under ncu, where autotuning timings are "
                          "distorted by the replays")
+    ap.add_argument("--kernel-timing", action="store_true",
+                    help="small 3-D case for per-kernel ncu captures: solve once, then launch every kernel slot "
+                         "directly (see run_kernel_timing)")
+    ap.add_argument("--side", type=int, default=96, help="--kernel-timing: cells per side")
+    ap.add_argument("--nrhs", type=int, default=32, help="--kernel-timing: right-hand sides")
     args = ap.parse_args()
+    if args.kernel_timing:
+        return run_kernel_timing(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

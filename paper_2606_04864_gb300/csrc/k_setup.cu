@@ -265,21 +265,36 @@ k_eig_rr(const SubInfo* __restrict__ subs, int P, const int64_t* __restrict__ ro
     double* ev = Rm + P * P;        // P
     ahat_mult(Sb, P, rowptr, colind, vals, ahat_diag, Y, AY);
     __syncthreads();
-    // Gram matrices (upper triangles)
-    for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
-        const int a = t / p, b = t % p;
-        if (b < a) continue;
-        double g = 0.0, h = 0.0;
-        for (int i = 0; i < Sb.n; ++i) {
-            const int64_t r = Sb.row0 + i;
-            const double ya = Y[r * P + a];
-            g += S[r] * ya * Y[r * P + b];
-            h += ya * AY[r * P + b];
+    // Gram matrices (upper triangles): one warp per pair (a, b), lanes over
+    // the subdomain's rows, partial sums combined by a fixed shuffle tree
+    {
+        const int wid = threadIdx.x >> 5, wl = threadIdx.x & 31, nw = blockDim.x >> 5;
+        const int npairs = p * (p + 1) / 2;
+        for (int pr = wid; pr < npairs; pr += nw) {
+            int a = 0, rem = pr;
+            while (rem >= p - a) {
+                rem -= p - a;
+                ++a;
+            }
+            const int b = a + rem;
+            double g = 0.0, h = 0.0;
+            for (int i = wl; i < Sb.n; i += 32) {
+                const int64_t r = Sb.row0 + i;
+                const double ya = Y[r * P + a];
+                g += S[r] * ya * Y[r * P + b];
+                h += ya * AY[r * P + b];
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                g += __shfl_xor_sync(0xffffffffu, g, off);
+                h += __shfl_xor_sync(0xffffffffu, h, off);
+            }
+            if (wl == 0) {
+                G[a * P + b] = g;
+                G[b * P + a] = g;
+                H[a * P + b] = h;
+                H[b * P + a] = h;
+            }
         }
-        G[a * P + b] = g;
-        G[b * P + a] = g;
-        H[a * P + b] = h;
-        H[b * P + a] = h;
     }
     __syncthreads();
     if (threadIdx.x >= 32) return;
