@@ -514,6 +514,15 @@ def run_gpu(args):
         def solve(s, f):
             return s.solve(f, rtol=1e-8)
 
+    # one-time process costs (CUDA context, module loading, solver library
+    # initialisation) on a tiny system first, so the setups below time only
+    # their own work
+    from workloads import make_small_2d
+    t_first = time.perf_counter()
+    tiny = make_small_2d(side=16, bs=8, m=2)
+    AmsSolver(tiny.rowptr, tiny.colind, tiny.vals, tiny.part, tiny.nparts, tiny.m, precision="fp32_bf16",
+              device=True).close()
+    first_call_s = time.perf_counter() - t_first
     t_setup0 = time.perf_counter()
     mixed = build("fp32_bf16", True)
     setup_wall = time.perf_counter() - t_setup0
@@ -640,11 +649,17 @@ def run_gpu(args):
     f_pin = torch.empty(rhs_host.shape, dtype=torch.float64).pin_memory()
     f_pin.copy_(torch.as_tensor(rhs_host))
     f_np = f_pin.numpy()
-    solve(host, f_np)
+    u_np_pin = None
+    if not batched:   # the solution goes straight into pinned host memory
+        u_np_pin = torch.empty((nrhs, n_total), dtype=torch.float64).pin_memory().numpy()
+        solve_host = lambda s_, f_: s_.solve(f_, rtol=1e-8, out=u_np_pin)   # noqa: E731
+    else:
+        solve_host = solve
+    solve_host(host, f_np)
     barrier()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        uh, itsh, _ = solve(host, f_np)
+        uh, itsh, _ = solve_host(host, f_np)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
     host.close()
@@ -668,6 +683,7 @@ def run_gpu(args):
                   "iters": int(np.max(its)), "relres": float(np.max(rel)), "true_relres": true_rel,
                   "ncoarse": info["ncoarse"], "setup_s": round(info["setup_seconds"], 3),
                   "setup_wall_s": round(setup_wall, 3),
+                  "first_call_s": round(first_call_s, 3),
                   "eig_s": round(info["eig_seconds"], 3), "eig_iterations": info["eig_iterations"],
                   "l2": "working set > 129 MB L2 (no flush needed)",
                   "fp64": {"time_s": ms64 / 1e3, "iters": int(np.max(its64)),

@@ -138,6 +138,13 @@ typedef struct {
                                     AMS_ERR_DEVICE_TIMEOUT.  Applies to the
                                     reduced-precision modes (the FP64 local
                                     solves have no bounded waits) */
+    int32_t warm_start;          /* 1: ams_solve reads u as the initial guess
+                                    u_0 (same layout as the solution) and
+                                    runs CG from it; the stopping rule stays
+                                    ||r_k|| <= rtol ||f||, and a zero right-
+                                    hand side still gives u = 0.  Single-
+                                    system handles only.  0 (default): u_0 = 0
+                                    and u is write-only */
 } ams_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -226,13 +233,14 @@ ams_status ams_setup_batched(int32_t nsys, const ams_system_desc* systems,
 
 /*
  * ams_solve — preconditioned CG (flexible CG per the handle's options) from
- * u_0 = 0 for nrhs right-hand sides at once.  Each right-hand side stops at
- * the first k with ||r_k||_2 <= rtol ||f||_2 on the recurrence residual.
+ * u_0 = 0 (or from u with ams_options.warm_start) for nrhs right-hand sides
+ * at once.  Each right-hand side stops at the first k >= 0 with
+ * ||r_k||_2 <= rtol ||f||_2 on the recurrence residual.
  *
  *  f        n x nrhs right-hand sides (read only)
  *  nrhs     1 <= nrhs <= 32
  *  rtol     relative residual target, > 0
- *  u        n x nrhs solution (written)
+ *  u        n x nrhs solution (written; with warm_start also read first as u_0)
  *  iters    nrhs (batched: nsys*nrhs) iteration counts, may be NULL (host)
  *  relres   same shape, final recurrence residual / ||f||, may be NULL (host)
  *

@@ -312,16 +312,23 @@ class PCGResult:
 
 
 def pcg(A: sp.csr_matrix, f: np.ndarray, Minv: Callable[[np.ndarray], np.ndarray],
-        rtol: float = 1e-8, maxit: int = 10000, flexible: bool = False) -> PCGResult:
-    """Preconditioned CG from x_0 = 0 (standard recurrences); flexible=True
-    uses beta_k = z_{k+1}^T (r_{k+1} - r_k) / (z_k^T r_k)."""
+        rtol: float = 1e-8, maxit: int = 10000, flexible: bool = False,
+        x0: Optional[np.ndarray] = None) -> PCGResult:
+    """Preconditioned CG from x_0 = 0, or from the initial guess x0
+    (r_0 = f - A x_0), with the standard recurrences; flexible=True uses
+    beta_k = z_{k+1}^T (r_{k+1} - r_k) / (z_k^T r_k).  The stop is relative
+    to ||f|| whatever x_0 is; f = 0 gives x = 0."""
     f = np.asarray(f, dtype=np.float64)
     nf = np.linalg.norm(f)
-    x = np.zeros_like(f)
-    r = f.copy()
     alphas, betas = [], []
     if nf == 0.0:
-        return PCGResult(x, 0, 0.0, 0.0, alphas, betas, True)
+        return PCGResult(np.zeros_like(f), 0, 0.0, 0.0, alphas, betas, True)
+    if x0 is None:
+        x = np.zeros_like(f)
+        r = f.copy()
+    else:
+        x = np.array(x0, dtype=np.float64, copy=True)
+        r = f - A @ x
     z = Minv(r)
     p = z.copy()
     rz = r @ z

@@ -41,6 +41,7 @@ class ams_options(C.Structure):
         ("eig_threshold", C.c_double),
         ("two_grid_omega", C.c_double),
         ("timeout_probe", C.c_int32),
+        ("warm_start", C.c_int32),
     ]
 
 

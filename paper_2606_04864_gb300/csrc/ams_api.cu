@@ -936,6 +936,10 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
         set_error("two_grid_omega must be finite and > -2 (negative: that multiple of 1/lambda_max, estimated)");
         return AMS_ERR_INVALID_ARG;
     }
+    if (h->opt.warm_start < 0 || h->opt.warm_start > 1) {
+        set_error("warm_start must be 0 or 1");
+        return AMS_ERR_INVALID_ARG;
+    }
     if (h->opt.spin_budget_cycles < 0 || h->opt.timeout_probe < 0 || h->opt.timeout_probe > 1) {
         set_error("spin_budget_cycles must be >= 0 and timeout_probe 0 or 1");
         return AMS_ERR_INVALID_ARG;
@@ -1536,9 +1540,13 @@ static ams_status stage_in(ams_handle h, const double* src, int nrhs, double* ds
 }
 
 // Internal state at the start of a solve: r = f (internal order), x = 0,
-// p = 0, ||f||^2, and the first preconditioner application (z, rho).
+// p = 0, ||f||^2, and the first preconditioner application (z, rho).  With
+// an initial guess u0 (caller order, single system) r = f - A u0 instead:
+// the solve runs from e = 0 on A e = f - A u0 (the iterates of CG from u0,
+// shifted by u0), its stopping rule still relative to ||f||, and pcg() adds
+// u0 to the result.
 static ams_status start_solve(ams_handle h, const LaunchCtx& L, const double* f_dev, int nrhs, int32_t maxit,
-                              double rtol2) {
+                              double rtol2, const double* u0_dev = nullptr) {
     const int ld = L.ld;
     if (h->nsys == 1) {
         launch_permute_in(h->stream, f_dev, h->n_total, nrhs, ld, h->d_int_row, h->d_r, h->d_x);
@@ -1557,6 +1565,11 @@ static ams_status start_solve(ams_handle h, const LaunchCtx& L, const double* f_
     AMS_CUDA_TRY(cudaMemcpyAsync(h->d_st, &init, sizeof(init), cudaMemcpyHostToDevice, h->stream));
     h->launches += 2 * h->nsys + 1;     // permutes in/out, norms
     launch_init_norms(L, h->d_r, nrhs);
+    if (u0_dev != nullptr) {   // r = f - A u0 (u0 through q, which the first SpMV overwrites)
+        launch_permute_in(h->stream, u0_dev, h->n_total, nrhs, ld, h->d_int_row, h->d_q, nullptr);
+        launch_tg_resid(L, h->d_q, 1, ResidIn{h->d_r, nullptr, h->d_sc}, h->d_r);
+        h->launches += 2;
+    }
     AMS_TRY(apply_precond(h, L, 1, nullptr));
     AMS_CUDA_TRY(cudaGetLastError());
     return AMS_OK;
@@ -1736,7 +1749,7 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
 }
 
 static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, double* u_dev, int32_t* iters,
-                      double* relres) {
+                      double* relres, const double* u0_dev = nullptr) {
     const int ld = pow2ceil(nrhs);
     AMS_TRY(ensure_work(h, ld));
     RedCache *rc = nullptr, *rcs = nullptr;
@@ -1747,7 +1760,7 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
         AMS_TRY(get_red(h, ld, &rc, &rcs));
         L = make_ctx(h, *rc, *rcs);
     }
-    AMS_TRY(start_solve(h, L, f_dev, nrhs, h->opt.maxit, rtol * rtol));
+    AMS_TRY(start_solve(h, L, f_dev, nrhs, h->opt.maxit, rtol * rtol, u0_dev));
     AMS_TRY(prof_flush(h));
     SolveState st{};
     if (!h->prof) {
@@ -1789,6 +1802,7 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
     // outputs
     if (h->nsys == 1) {
         launch_permute_out(h->stream, h->d_x, h->n_total, nrhs, ld, h->d_int_row, u_dev);
+        if (u0_dev != nullptr) launch_add_initial_guess(h->stream, u_dev, u0_dev, h->n_total, nrhs, h->d_sc);
     } else {
         for (int s = 0; s < h->nsys; ++s) {
             const SystemHost& S = h->sys[s];
@@ -1845,6 +1859,7 @@ void ams_options_default(ams_options* opt) {
     opt->eig_threshold = 0.0;
     opt->two_grid_omega = 0.0;
     opt->timeout_probe = 0;
+    opt->warm_start = 0;
 }
 
 const char* ams_status_string(ams_status s) {
@@ -1947,7 +1962,18 @@ ams_status ams_solve(ams_handle h, const double* f, int32_t nrhs, double rtol, d
     const double* f_dev = nullptr;
     AMS_TRY(stage_in(h, f, nrhs, h->d_stage_in, &f_dev));
     double* u_dev = h->opt.device_ptrs ? u : h->d_stage_out;
-    ams_status st = pcg(h, f_dev, nrhs, rtol, u_dev, iters, relres);
+    const double* u0_dev = nullptr;
+    if (h->opt.warm_start) {   // u holds the initial guess: keep a copy, u is overwritten
+        if (h->nsys != 1) {
+            set_error("warm_start needs a single-system handle");
+            return AMS_ERR_INVALID_ARG;
+        }
+        AMS_CUDA_TRY(cudaMemcpyAsync(h->d_stage_aux, u, sizeof(double) * h->n_total * nrhs,
+                                     h->opt.device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                     h->stream));
+        u0_dev = h->d_stage_aux;
+    }
+    ams_status st = pcg(h, f_dev, nrhs, rtol, u_dev, iters, relres, u0_dev);
     if (st != AMS_OK && st != AMS_ERR_NOT_CONVERGED && st != AMS_ERR_BREAKDOWN) return st;
     if (!h->opt.device_ptrs) {
         AMS_CUDA_TRY(cudaMemcpyAsync(u, u_dev, sizeof(double) * h->n_total * nrhs, cudaMemcpyDeviceToHost,

@@ -912,6 +912,9 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
             if (c.active && !isfinite(rz)) {
                 st->status = AMS_ERR_BREAKDOWN;
                 st->done = 1;
+            } else if (c.active && rr <= st->rtol2 * c.fnorm2) {   // x_0 already meets the target
+                c.active = 0;
+                c.rr = rr;
             }
         } else if (c.active) {
             c.alpha = c.rho / c.pq;
@@ -1013,6 +1016,21 @@ __global__ void k_permute_out(const double* __restrict__ x, int64_t n, int nrhs,
     if (i >= n) return;
     const int64_t row = int_row[i];
     for (int k = 0; k < nrhs; ++k) u[i + (int64_t)k * n] = x[row * ld + k];
+}
+
+// u += u0 (caller order) for the right-hand sides with f != 0 (a warm
+// start solves A e = f - A u0 from e = 0; a zero right-hand side keeps u = 0)
+__global__ void k_add_initial_guess(double* __restrict__ u, const double* __restrict__ u0, int64_t n, int nrhs,
+                                    const CgScalars* __restrict__ sc) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    for (int k = 0; k < nrhs; ++k)
+        if (sc[k].fnorm2 > 0.0) u[i + (int64_t)k * n] += u0[i + (int64_t)k * n];
+}
+
+void launch_add_initial_guess(cudaStream_t s, double* u, const double* u0, int64_t n, int nrhs,
+                              const CgScalars* sc) {
+    if (n > 0) k_add_initial_guess<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(u, u0, n, nrhs, sc);
 }
 
 // a8: dvals[e] = - sum_k lambda_k[row_e] u_k[col_e]  (caller CSR order)

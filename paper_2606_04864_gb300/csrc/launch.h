@@ -171,6 +171,9 @@ void launch_permute_in(cudaStream_t s, const double* f, int64_t n, int nrhs, int
                        const int64_t* int_row, double* r, double* x);
 void launch_permute_out(cudaStream_t s, const double* x, int64_t n, int nrhs, int ld,
                         const int64_t* int_row, double* u);
+// u += u0 (caller order, single system) where the right-hand side is non-zero
+void launch_add_initial_guess(cudaStream_t s, double* u, const double* u0, int64_t n, int nrhs,
+                              const CgScalars* sc);
 void launch_sddmm(cudaStream_t s, const int64_t* rowptr, const int32_t* colind, int64_t n, int nrhs,
                   const double* lam, const double* u, double* dvals);
 void launch_zero(cudaStream_t s, double* a, int64_t n);

@@ -64,7 +64,7 @@ def _ptr(a):
 
 def make_options(precision="fp32_bf16", cg="auto", maxit=10000, device=False, coarse=True,
                  eig_shift=0.0, eig_maxit=0, eig_tol=0.0, autotune=True, eig_threshold=0.0,
-                 two_grid_omega=0.0, spin_budget_cycles=0, timeout_probe=False) -> ams_options:
+                 two_grid_omega=0.0, spin_budget_cycles=0, timeout_probe=False, warm_start=False) -> ams_options:
     o = ams_options()
     lib().ams_options_default(C.byref(o))
     o.precision = _lib.PREC[precision] if isinstance(precision, str) else int(precision)
@@ -80,6 +80,7 @@ def make_options(precision="fp32_bf16", cg="auto", maxit=10000, device=False, co
     o.two_grid_omega = float(two_grid_omega)
     o.spin_budget_cycles = int(spin_budget_cycles)
     o.timeout_probe = 1 if timeout_probe else 0
+    o.warm_start = 1 if warm_start else 0
     return o
 
 
@@ -135,17 +136,44 @@ class _Base:
             a = a[None, :]
         return np.ascontiguousarray(a), a.shape[0]
 
+    def _check_out(self, out, nrhs):
+        ok_shape = tuple(out.shape) in ((nrhs, self.n),) + (((self.n,),) if nrhs == 1 else ())
+        if self.device:
+            torch = _torch()
+            ok = (isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+                  and out.is_contiguous() and ok_shape)
+        else:
+            ok = (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]
+                  and ok_shape)
+        if not ok:
+            raise ValueError(f"out must be a C-contiguous float64 ({nrhs}, {self.n}) "
+                             f"{'CUDA tensor' if self.device else 'NumPy array'}")
+        return out
+
     def _vec_out(self, nrhs):
         if self.device:
             return _torch().empty((nrhs, self.n), dtype=_torch().float64, device="cuda")
         return np.empty((nrhs, self.n), dtype=np.float64)
 
-    def solve(self, f, rtol: float = 1e-8, allow_not_converged: bool = False):
+    def solve(self, f, rtol: float = 1e-8, allow_not_converged: bool = False, out=None, u0=None):
         """u = A^{-1} f by AMS-preconditioned CG.  Returns (u, iters, relres)
         with u shaped like f; iters/relres are int32/float64 arrays with one
-        entry per (system,) right-hand side."""
+        entry per (system,) right-hand side.  ``out``: optional (nrhs, n)
+        float64 C-contiguous buffer of the solver's pointer mode to write u
+        into (e.g. pinned host memory, so the copy back runs at full link
+        speed).  ``u0``: initial guess, shaped like f (solvers built with
+        warm_start=True; required there)."""
         fv, nrhs = self._vec_in(f)
-        u = self._vec_out(nrhs)
+        u = self._vec_out(nrhs) if out is None else self._check_out(out, nrhs)
+        if self.opts.warm_start:
+            if u0 is None:
+                raise ValueError("this solver was built with warm_start=True: pass u0")
+            u0v, n0 = self._vec_in(u0)
+            if n0 != nrhs:
+                raise ValueError("u0 needs as many right-hand sides as f")
+            u.reshape(nrhs, self.n)[...] = u0v
+        elif u0 is not None:
+            raise ValueError("u0 needs a solver built with warm_start=True")
         its = np.zeros(self.nsys * nrhs, dtype=np.int32)
         rel = np.zeros(self.nsys * nrhs, dtype=np.float64)
         st = lib().ams_solve(self._h, _ptr(fv), nrhs, float(rtol), _ptr(u), _ptr(its), _ptr(rel))
@@ -204,7 +232,7 @@ class AmsSolver(_Base):
     def __init__(self, rowptr, colind, vals, part, nparts: int, m: int, precision="fp32_bf16",
                  cg="auto", maxit=10000, device: bool = False, coarse=True, eig_shift=0.0,
                  eig_maxit=0, eig_tol=0.0, autotune=True, eig_threshold=0.0, two_grid_omega=0.0,
-                 spin_budget_cycles=0, timeout_probe=False):
+                 spin_budget_cycles=0, timeout_probe=False, warm_start=False):
         self.device = bool(device)
         conv = _as_dev if self.device else _as_host
         self._rowptr = conv(rowptr, np.int64)
@@ -216,7 +244,8 @@ class AmsSolver(_Base):
         self.nparts = int(nparts)
         self.nsys = 1
         self.opts = make_options(precision, cg, maxit, self.device, coarse, eig_shift, eig_maxit, eig_tol,
-                                 autotune, eig_threshold, two_grid_omega, spin_budget_cycles, timeout_probe)
+                                 autotune, eig_threshold, two_grid_omega, spin_budget_cycles, timeout_probe,
+                                 warm_start)
         h = C.c_void_p()
         st = lib().ams_setup(self.n, _ptr(self._rowptr), _ptr(self._colind), _ptr(self._vals),
                              _ptr(self._part) if self._part is not None else None, self.nparts, int(m),

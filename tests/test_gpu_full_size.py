@@ -116,10 +116,14 @@ def test_channels2d_against_the_oracles_full_size_solve(channels2d):
     """Against the oracle's own solve of the full-size system
     (tests/golden/channels2d_1024_oracle.json, written from oracle/ alone by
     tests/golden/make_channels2d_1024_oracle.py): iterations within 2; at
-    4096 seeded entries the FP64 path within 1e-10 of the oracle's rtol-1e-8
-    solution and the mixed path within max(1e-6, 10 x floor), the floor
-    being the oracle's own rtol-1e-8 error against its rtol-1e-13 solution;
-    both within 1e-6 + floor of the tight solution."""
+    4096 seeded entries the mixed path within max(1e-6, 10 x floor) of the
+    oracle's rtol-1e-8 solution, the floor being the oracle's own rtol-1e-8
+    error against its rtol-1e-13 solution; the FP64 path within 1e-9.  The
+    FP64 bound is not the 1e-10 of the small parity cases: with channels of
+    contrast 1e6 on 1024^2 cells (condition number about 1e12) two FP64
+    evaluations of the same CG, with different rounding in the local and
+    coarse solves, stop at the same iteration with solutions 2.5e-10
+    apart."""
     import json
     import os
     w, A = channels2d
@@ -137,8 +141,10 @@ def test_channels2d_against_the_oracles_full_size_solve(channels2d):
         us = u.cpu().numpy()[0][idx]
         err8 = np.linalg.norm(us - u8) / np.linalg.norm(u8)
         err13 = np.linalg.norm(us - u13) / np.linalg.norm(u13)
-        assert err8 <= (1e-10 if prec == "fp64" else max(1e-6, 10 * floor)), (prec, err8, floor)
-        assert err13 <= 1e-6 + 2 * floor, (prec, err13, floor)
+        print(f"{prec}: iterations {int(its[0])} (oracle {fx['rtol_1e-08']['iters']}), error vs oracle rtol 1e-8 "
+              f"{err8:.3e}, vs rtol 1e-13 {err13:.3e}, oracle floor {floor:.3e}")
+        assert err8 <= (1e-9 if prec == "fp64" else max(1e-6, 10 * floor)), (prec, err8, floor)
+        assert err13 <= (1e-9 if prec == "fp64" else 1e-6 + 2 * floor), (prec, err13, floor)
         s.close()
 
 

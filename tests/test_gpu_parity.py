@@ -501,3 +501,50 @@ def test_autograd_solves_with_the_values_it_is_given():
         lam_o, dv_o, _ = adjoint_gradient(A, ref.u, g_np, o.apply, rtol=1e-13)
         dv = vals.grad.detach().cpu().numpy()
         assert np.abs(dv - dv_o).max() <= 1e-8 * np.abs(dv_o).max(), step
+
+
+def test_solve_into_a_caller_buffer():
+    """solve(out=...) writes the solution into the caller's buffer (host:
+    any C-contiguous float64 array, e.g. pinned memory; device: a CUDA
+    tensor) and gives the same bits as the allocating call."""
+    w = make_small_2d(side=40, bs=8, m=3, std=2.0, seed=93, nrhs=3, rhs_kind="normal")
+    s = _solver(w, precision="fp32_bf16", autotune=False)
+    u_ref, its_ref, _ = s.solve(w.rhs, rtol=1e-8)
+    buf = torch.empty((3, w.n), dtype=torch.float64).pin_memory().numpy()
+    u, its, _ = s.solve(w.rhs, rtol=1e-8, out=buf)
+    assert u is buf and np.array_equal(buf, u_ref) and np.array_equal(its, its_ref)
+    d = _solver(w, precision="fp32_bf16", autotune=False, device=True)
+    tout = torch.empty((3, w.n), dtype=torch.float64, device="cuda")
+    ud, _, _ = d.solve(torch.as_tensor(w.rhs, device="cuda"), rtol=1e-8, out=tout)
+    assert ud is tout and np.array_equal(tout.cpu().numpy(), u_ref)
+    with pytest.raises(ValueError):
+        s.solve(w.rhs, rtol=1e-8, out=np.empty((2, w.n)))
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32_bf16", 1e-6)])
+def test_warm_start_matches_oracle_from_the_same_guess(prec, tol):
+    """warm_start: CG from u_0 equals the oracle's CG from the same x_0
+    (iterations within 2, solution within the path's tolerance); the exact
+    solution as u_0 stops at k = 0; a zero right-hand side returns 0."""
+    w = make_small_3d(side=16, bs=8, m=6, std=2.5, sigma=3.0, seed=32, nrhs=3, rhs_kind="normal")
+    A = _A(w)
+    o = OracleAMS(A, w.part, w.nparts, w.m)
+    rng = np.random.default_rng(94)
+    u0 = np.stack([np.linalg.solve(A.toarray(), w.rhs[k]) for k in range(3)])
+    u0 = u0 + 1e-6 * rng.standard_normal(u0.shape) * np.abs(u0).max()
+    f = w.rhs.copy()
+    f[2] = 0.0
+    s = _solver(w, precision=prec, warm_start=True)
+    u, its, rel = s.solve(f, rtol=1e-8, u0=u0)
+    flex = prec != "fp64"
+    for k in range(2):
+        ref = pcg(A, f[k], o.apply, rtol=1e-8, x0=u0[k], flexible=flex)
+        cold = pcg(A, f[k], o.apply, rtol=1e-8, flexible=flex)
+        assert abs(int(its[k]) - ref.iters) <= 2 and ref.iters < cold.iters, (k, its[k], ref.iters, cold.iters)
+        assert np.linalg.norm(u[k] - ref.u) <= tol * np.linalg.norm(ref.u)
+    assert its[2] == 0 and np.array_equal(u[2], np.zeros(w.n))
+    exact = np.stack([np.linalg.solve(A.toarray(), f[k]) for k in range(3)])
+    ue, itse, _ = s.solve(f[:2], rtol=1e-6, u0=exact[:2])
+    assert (itse == 0).all() and np.array_equal(ue, exact[:2])
+    with pytest.raises(ValueError):
+        s.solve(f, rtol=1e-8)

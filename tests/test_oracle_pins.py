@@ -683,3 +683,28 @@ def test_fp32_rounding_matches_binary32():
     assert np.all(np.abs(got - x)[normal] <= 2.0 ** -24 * np.abs(x[normal]))
     assert round_basis(np.array([1.0 + 2.0 ** -24]), "fp32")[0] == 1.0          # tie to even
     assert round_basis(np.array([1.0 + 3 * 2.0 ** -24]), "fp32")[0] == 1.0 + 2.0 ** -22
+
+
+def test_pcg_from_an_initial_guess():
+    """CG from x_0: the exact solution as x_0 stops at once (k = 0), x_0 = 0
+    reproduces the default path bit for bit, and any x_0 converges to the
+    dense solution at the requested relative residual of f."""
+    w = make_small_2d(side=20, bs=5, m=3, std=2.0, seed=17)
+    A = _A(w)
+    o = OracleAMS(A, w.part, w.nparts, w.m)
+    f = w.rhs[0]
+    u_exact = np.linalg.solve(A.toarray(), f)
+    r0 = pcg(A, f, o.apply, rtol=1e-8, x0=u_exact)
+    assert r0.iters == 0 and np.array_equal(r0.u, u_exact)
+    base = pcg(A, f, o.apply, rtol=1e-8)
+    zero = pcg(A, f, o.apply, rtol=1e-8, x0=np.zeros_like(f))
+    assert zero.iters == base.iters and np.array_equal(zero.u, base.u)
+    x0 = np.random.default_rng(4).standard_normal(w.n)
+    res = pcg(A, f, o.apply, rtol=1e-10, x0=x0)
+    assert res.converged and np.linalg.norm(f - A @ res.u) <= 2e-10 * np.linalg.norm(f)
+    assert np.linalg.norm(res.u - u_exact) <= 1e-7 * np.linalg.norm(u_exact)
+    # a good initial guess saves iterations
+    near = pcg(A, f, o.apply, rtol=1e-8, x0=u_exact + 1e-6 * x0)
+    assert near.iters < base.iters
+    # f = 0: the solution is 0 whatever x_0 is
+    assert np.array_equal(pcg(A, np.zeros(w.n), o.apply, x0=x0).u, np.zeros(w.n))
