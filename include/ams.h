@@ -51,7 +51,7 @@ typedef enum {
     AMS_OK = 0,
     AMS_ERR_INVALID_ARG = 1,     /* bad size, pointer, CSR, partition or option */
     AMS_ERR_NOT_SPD = 2,         /* non-positive pivot in a local or coarse Cholesky */
-    AMS_ERR_BREAKDOWN = 3,       /* p^T A p <= 0 or a non-finite scalar in CG */
+    AMS_ERR_BREAKDOWN = 3,       /* p^T A p <= 0, r^T M^{-1} r <= 0 or a non-finite scalar in CG */
     AMS_ERR_NOT_CONVERGED = 4,   /* maxit reached; outputs hold the last iterate */
     AMS_ERR_DEVICE_TIMEOUT = 5,  /* a bounded device-side wait ran out */
     AMS_ERR_CUDA = 6,            /* a CUDA runtime or cuSOLVER call failed */
@@ -116,9 +116,10 @@ typedef struct {
                                     symmetrised smoother 2 omega S -
                                     omega^2 S A S.  An omega at or above
                                     2 / lambda_max makes the cycle
-                                    indefinite and CG may then stall or
-                                    report AMS_ERR_BREAKDOWN; setup does not
-                                    estimate lambda_max for a positive value.
+                                    indefinite: the solve then reports
+                                    AMS_ERR_BREAKDOWN once r^T z <= 0 (or
+                                    stalls); setup does not estimate
+                                    lambda_max for a positive value.
                                     Negative (between -2 and 0): omega =
                                     -two_grid_omega / lambda_max, lambda_max
                                     estimated at setup by power steps on the
@@ -246,7 +247,9 @@ ams_status ams_setup_batched(int32_t nsys, const ams_system_desc* systems,
  *
  * iters and relres are always host pointers.  Returns AMS_ERR_NOT_CONVERGED
  * when maxit is reached (u, iters, relres hold the last iterate) and
- * AMS_ERR_BREAKDOWN when p^T A p <= 0 or a scalar is not finite.
+ * AMS_ERR_BREAKDOWN when p^T A p <= 0, r^T z <= 0 (the preconditioner is not
+ * SPD, e.g. a two-grid omega at or above 2 / lambda_max) or a scalar is not
+ * finite.
  */
 ams_status ams_solve(ams_handle h, const double* f, int32_t nrhs, double rtol,
                      double* u, int32_t* iters, double* relres);

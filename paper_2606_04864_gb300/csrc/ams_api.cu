@@ -141,6 +141,8 @@ struct ams_handle_s {
     int64_t *d_sell_ptr = nullptr;
     int32_t* d_sell_col = nullptr;
     double* d_sell_val = nullptr;
+    float* d_sell_val32 = nullptr;      // the values in FP32, for the two-grid cycle's residuals (mixed path)
+    int64_t sell_elems = 0;             // stored SELL entries (padding included)
     int64_t* d_crowptr = nullptr;       // caller CSR (single system) for dL/dA
     int32_t* d_ccolind = nullptr;
     int64_t* d_sell_pos = nullptr;      // caller CSR entry -> SELL slot (single system)
@@ -371,6 +373,7 @@ static LaunchCtx make_ctx(ams_handle h, const RedCache& rc, const RedCache& rcs)
     L.sell_ptr = h->d_sell_ptr;
     L.sell_col = h->d_sell_col;
     L.sell_val = h->d_sell_val;
+    L.sell_val32 = h->d_sell_val32;
     L.sub_of_row = h->d_sub_of_row;
     L.subs = h->d_subs;
     L.pdl = h->use_pdl;
@@ -1097,6 +1100,12 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     AMS_TRY(upload(H, &h->d_sell_ptr, sell_ptr));
     AMS_TRY(upload(H, &h->d_sell_col, sell_col));
     AMS_TRY(upload(H, &h->d_sell_val, sell_val));
+    h->sell_elems = (int64_t)sell_val.size();
+    if (h->opt.two_grid_omega != 0.0 && h->prec != AMS_PREC_FP64) {
+        // the cycle's internal residuals belong to the reduced-precision apply
+        AMS_TRY(h->alloc_t(&h->d_sell_val32, sell_val.size()));
+        launch_round_to_f32(h->stream, h->d_sell_val, (int64_t)sell_val.size(), h->d_sell_val32);
+    }
     int64_t* d_irp = nullptr;
     int32_t* d_icol = nullptr;
     double* d_ival = nullptr;
@@ -2040,6 +2049,8 @@ ams_status ams_set_matrix_values(ams_handle h, const double* vals) {
         dv = tmp;
     }
     launch_scatter_vals(h->stream, dv, h->d_sell_pos, h->nnz_total, h->d_sell_val);
+    if (h->d_sell_val32 != nullptr)
+        launch_round_to_f32(h->stream, h->d_sell_val, h->sell_elems, h->d_sell_val32);
     h->launches += 1;
     AMS_CUDA_TRY(cudaGetLastError());
     AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));

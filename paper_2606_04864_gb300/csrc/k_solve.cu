@@ -915,6 +915,9 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
             } else if (c.active && rr <= st->rtol2 * c.fnorm2) {   // x_0 already meets the target
                 c.active = 0;
                 c.rr = rr;
+            } else if (c.active && !(rz > 0.0)) {   // r^T M^{-1} r <= 0: the preconditioner is not SPD
+                st->status = AMS_ERR_BREAKDOWN;
+                st->done = 1;
             }
         } else if (c.active) {
             c.alpha = c.rho / c.pq;
@@ -926,6 +929,12 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
             } else if (rr <= st->rtol2 * c.fnorm2) {
                 c.active = 0;
                 c.beta = 0.0;
+            } else if (!flexible && !(rz > 0.0)) {
+                // r^T M^{-1} r <= 0 in exact-arithmetic PCG: M is not SPD (the
+                // flexible variant, whose M^{-1} is applied in FP32, is only
+                // checked on its first residual, in mode 1)
+                st->status = AMS_ERR_BREAKDOWN;
+                st->done = 1;
             } else {
                 c.beta = flexible ? -zq / c.pq : rz / c.rho;
             }

@@ -30,11 +30,14 @@ template <> __device__ __forceinline__ double tg_widen<float>(float v) { return 
 template <> __device__ __forceinline__ double tg_widen<double>(double v) { return v; }
 
 // w = r' - A v over the element layout of the SpMV (block ranges of
-// (row, rhs) elements, one system per block).
-template <int LD, typename TV>
+// (row, rhs) elements, one system per block).  TA: the matrix values and
+// the accumulation, FP64, or FP32 inside the reduced-precision apply (the
+// cycle's residual is part of the preconditioner application; r' keeps
+// the FP64 formation of the local solves' input).
+template <int LD, typename TV, typename TA>
 __global__ void __launch_bounds__(kRedThreads)
 k_tg_resid(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sell_col,
-           const double* __restrict__ sell_val, const TV* __restrict__ v, const double* __restrict__ r,
+           const TA* __restrict__ sell_val, const TV* __restrict__ v, const double* __restrict__ r,
            const double* __restrict__ q, RedLayout R, const CgScalars* __restrict__ sc,
            const SolveState* st, double* __restrict__ w) {
     pdl_wait();
@@ -54,29 +57,34 @@ k_tg_resid(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
         const int lane = (int)(row & 31);
         const int64_t b0 = __ldg(sell_ptr + sl);
         const int width = (int)((__ldg(sell_ptr + sl + 1) - b0) >> 5);
-        double acc = 0.0;
+        TA acc = TA(0);
         for (int j = 0; j < width; ++j) {
             const int64_t o = b0 + 32 * j + lane;
-            acc = fma(__ldg(sell_val + o), tg_widen<TV>(v[(int64_t)__ldg(sell_col + o) * LD + rhs]), acc);
+            const TV vj = v[(int64_t)__ldg(sell_col + o) * LD + rhs];
+            if constexpr (sizeof(TA) == 8) acc = fma(__ldg(sell_val + o), tg_widen<TV>(vj), acc);
+            else acc = fmaf(__ldg(sell_val + o), (float)vj, acc);
         }
         const double rv = upd ? fma(-alpha, q[e], r[e]) : r[e];
-        w[e] = rv - acc;
+        w[e] = rv - tg_widen<TA>(acc);
     }
 }
 
 template <typename TF>
 __global__ void k_tg_scale(TF* __restrict__ zf, double omega, int64_t n, const SolveState* st) {
     if (st != nullptr && st->done) return;
+    // in the apply precision (FP32 for the reduced-precision modes)
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        zf[e] = (TF)(omega * tg_widen<TF>(zf[e]));
+        zf[e] = (TF)omega * zf[e];
 }
 
 template <typename TF>
 __global__ void k_tg_combine(TF* __restrict__ zf, const double* __restrict__ x2, double omega, int64_t n,
                              const SolveState* st) {
     if (st != nullptr && st->done) return;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-        zf[e] = (TF)fma(omega, tg_widen<TF>(zf[e]), x2[e]);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (sizeof(TF) == 8) zf[e] = fma(omega, zf[e], x2[e]);
+        else zf[e] = fmaf((float)omega, zf[e], __double2float_rn(x2[e]));   // apply precision
+    }
 }
 
 // r_c[(coff + k) ld + rhs] = sum over the subdomain's rows of
@@ -108,6 +116,44 @@ k_tg_restrict(const SubInfo* __restrict__ subs, int nsub, const TP* __restrict__
         double a = acc[k];
         for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
         if (lane == 0 && k < m) rc[(S.coff + k) * ld + rhs] = (TF)a;
+    }
+}
+
+// r_c = R_0 w for 8 or more right-hand sides: one block per subdomain,
+// thread (rhs, row group) reads whole rows of w (all right-hand sides of a
+// row are contiguous, so the reads coalesce) and accumulates the m_i mode
+// sums of its rows in the apply precision; the row groups are summed in a
+// fixed order in shared memory.
+template <typename TF, typename TP, int MM, int LD>
+__global__ void __launch_bounds__(256)
+k_tg_restrict_rows(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, const double* __restrict__ w,
+                   TF* __restrict__ rc, const SolveState* st) {
+    if (st != nullptr && st->done) return;
+    constexpr int RG = 256 / LD;                     // row groups
+    using A = typename Acc<TF>::type;
+    __shared__ A part[RG][MM][LD];
+    const SubInfo S = subs[blockIdx.x];
+    const int m = S.m;
+    if (m == 0) return;
+    const int rhs = threadIdx.x % LD, rg = threadIdx.x / LD;
+    A acc[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) acc[k] = A(0);
+    for (int i = rg; i < S.n; i += RG) {
+        const A wv = (A)w[(S.row0 + i) * LD + rhs];
+        const TP* pr = psi + S.psi_off + (int64_t)i * m;
+#pragma unroll
+        for (int k = 0; k < MM; ++k)
+            if (k < m) acc[k] += (A)to_d(pr[k]) * wv;
+    }
+#pragma unroll
+    for (int k = 0; k < MM; ++k) part[rg][k][rhs] = acc[k];
+    __syncthreads();
+    for (int o = threadIdx.x; o < m * LD; o += 256) {
+        const int k = o / LD, h = o % LD;
+        A sum = A(0);
+        for (int g = 0; g < RG; ++g) sum += part[g][k][h];
+        rc[(S.coff + k) * LD + h] = (TF)sum;
     }
 }
 
@@ -189,8 +235,12 @@ void launch_power_step(cudaStream_t s, int prec, const double* x, const double* 
 // ---------------------------------------------------------------------------
 template <int LD, typename TV>
 static void resid_ld_t(const LaunchCtx& L, const TV* v, const ResidIn& in, double* w) {
-    launch_kernel(false, k_tg_resid<LD, TV>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream, L.sell_ptr,
-                  L.sell_col, L.sell_val, v, in.r, in.q, L.red, in.sc, (const SolveState*)L.st, w);
+    if (L.sell_val32 != nullptr)
+        launch_kernel(false, k_tg_resid<LD, TV, float>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream,
+                      L.sell_ptr, L.sell_col, L.sell_val32, v, in.r, in.q, L.red, in.sc, (const SolveState*)L.st, w);
+    else
+        launch_kernel(false, k_tg_resid<LD, TV, double>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream,
+                      L.sell_ptr, L.sell_col, L.sell_val, v, in.r, in.q, L.red, in.sc, (const SolveState*)L.st, w);
 }
 template <int LD>
 static void resid_ld(const LaunchCtx& L, const void* v, int v_kind, const ResidIn& in, double* w) {
@@ -213,6 +263,15 @@ static unsigned tg_blocks(int64_t n) {
     return (unsigned)std::min<int64_t>(std::max<int64_t>(b, 1), 152 * 16);
 }
 
+__global__ void k_round_to_f32(const double* __restrict__ a, int64_t n, float* __restrict__ b) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        b[e] = __double2float_rn(a[e]);
+}
+
+void launch_round_to_f32(cudaStream_t s, const double* a, int64_t n, float* b) {
+    if (n > 0) k_round_to_f32<<<tg_blocks(n), 256, 0, s>>>(a, n, b);
+}
+
 void launch_tg_scale(const LaunchCtx& L, int prec, void* zf, double omega, int64_t n) {
     if (prec == AMS_PREC_FP64)
         k_tg_scale<double><<<tg_blocks(n), 256, 0, L.stream>>>((double*)zf, omega, n, L.st);
@@ -227,8 +286,20 @@ void launch_tg_combine(const LaunchCtx& L, int prec, void* zf, const double* x2,
         k_tg_combine<float><<<tg_blocks(n), 256, 0, L.stream>>>((float*)zf, x2, omega, n, L.st);
 }
 
+template <typename TF, typename TP, int MM>
+static bool restrict_rows(const LaunchCtx& L, const void* psi, const double* w, void* rc) {
+    switch (L.ld) {
+        case 8: k_tg_restrict_rows<TF, TP, MM, 8><<<L.nsub, 256, 0, L.stream>>>(L.subs, (const TP*)psi, w, (TF*)rc, L.st); return true;
+        case 16: k_tg_restrict_rows<TF, TP, MM, 16><<<L.nsub, 256, 0, L.stream>>>(L.subs, (const TP*)psi, w, (TF*)rc, L.st); return true;
+        case 32: k_tg_restrict_rows<TF, TP, MM, 32><<<L.nsub, 256, 0, L.stream>>>(L.subs, (const TP*)psi, w, (TF*)rc, L.st); return true;
+        default: return false;
+    }
+}
+
 template <typename TF, typename TP>
 static void restrict_t(const LaunchCtx& L, const void* psi, const double* w, void* rc, int mmax) {
+    if (L.nsub > 0 && (mmax > 8 ? restrict_rows<TF, TP, kMaxM>(L, psi, w, rc) : restrict_rows<TF, TP, 8>(L, psi, w, rc)))
+        return;
     const int64_t warps = (int64_t)L.nsub * L.ld;
     const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
     if (mmax > 8)

@@ -44,6 +44,7 @@ struct LaunchCtx {
     const int64_t* sell_ptr;
     const int32_t* sell_col;
     const double* sell_val;
+    const float* sell_val32;   // FP32 copy of the values for the two-grid cycle's residuals, or NULL
     const int32_t* sub_of_row;
     const SubInfo* subs;
 };
@@ -154,6 +155,8 @@ void launch_prolong_update(const LaunchCtx& L, int prec, const ProlongArgs& a);
 // else the apply precision's floats
 void launch_tg_resid(const LaunchCtx& L, const void* v, int v_is_fp64, const ResidIn& in, double* w);
 void launch_tg_scale(const LaunchCtx& L, int prec, void* zf, double omega, int64_t n);
+// b = a rounded to FP32 (round to nearest even)
+void launch_round_to_f32(cudaStream_t s, const double* a, int64_t n, float* b);
 void launch_tg_combine(const LaunchCtx& L, int prec, void* zf, const double* x2, double omega, int64_t n);
 void launch_tg_restrict(const LaunchCtx& L, int prec, const void* psi, const double* w, void* rc, int mmax);
 // One power step for the cycle's damping: per system the sums x.y, y.z and

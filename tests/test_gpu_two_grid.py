@@ -132,3 +132,21 @@ def test_two_grid_damping_from_power_steps(prec):
     from paper_2606_04864_gb300._lib import AmsError
     with pytest.raises(AmsError):
         AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision=prec, two_grid_omega=-2.5)
+
+
+def test_oversized_omega_is_reported_as_breakdown():
+    """omega = 10 / lambda_max makes the cycle indefinite (r^T B r < 0 for
+    the first residual already, checked on the oracle's cycle): the solve
+    stops with AMS_ERR_BREAKDOWN instead of iterating on."""
+    from paper_2606_04864_gb300._lib import AmsError
+    w = _case("3d")
+    A = csr_to_scipy(w.rowptr, w.colind, w.vals)
+    o = OracleAMS(A, w.part, w.nparts, w.m)
+    omega = 10.0 / o.local_lambda_max()
+    assert w.rhs[0] @ o.apply_two_grid(w.rhs[0], omega) < 0
+    for prec in ("fp64", "fp32_bf16"):
+        s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision=prec, two_grid_omega=omega,
+                      maxit=500)
+        with pytest.raises(AmsError) as e:
+            s.solve(w.rhs[0], rtol=1e-8)
+        assert e.value.status == 3, prec
