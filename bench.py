@@ -685,6 +685,11 @@ def run_gpu(args):
                   "setup_wall_s": round(setup_wall, 3),
                   "first_call_s": round(first_call_s, 3),
                   "eig_s": round(info["eig_seconds"], 3), "eig_iterations": info["eig_iterations"],
+                  "coarse_s": round(info["coarse_seconds"], 3),
+                  "coarse_factor": {"s": round(info["coarse_factor_seconds"], 3),
+                                    "gflop": round(info["coarse_factor_gflop"], 1),
+                                    "gflop_per_s": round(info["coarse_factor_gflop"] /
+                                                         max(info["coarse_factor_seconds"], 1e-9), 1)},
                   "l2": "working set > 129 MB L2 (no flush needed)",
                   "fp64": {"time_s": ms64 / 1e3, "iters": int(np.max(its64)),
                            "setup_s": round(info64["setup_seconds"], 3)},

@@ -322,6 +322,10 @@ typedef struct {
                                     (0: additive preconditioner) */
     double local_lambda_max;     /* estimated lambda_max of the local solves
                                     times A (two_grid_omega < 0 at setup), else 0 */
+    double coarse_factor_seconds;/* of coarse_seconds: Cholesky factor of A_0
+                                    and its inverse */
+    double coarse_factor_gflop;  /* FP64 work of those on the kept tiles (2 flops
+                                    per multiply-add) */
 } ams_info;
 
 ams_status ams_get_info(ams_handle h, ams_info* info);
@@ -382,6 +386,16 @@ ams_status ams_get_coarse_basis(ams_handle h, int32_t* m_i, double* lambda,
  * the rounded basis.  Single-system handles only.
  */
 ams_status ams_get_coarse_matrix(ams_handle h, double* A0);
+
+/*
+ * The inverse L_c^{-1} of the Cholesky factor of A_0 (A_0 = L_c L_c^T in
+ * the nested-dissection order of the coarse dofs that the coarse solve
+ * uses; Section 3.1 defines A_0, the order is this library's), as a dense
+ * N_c x N_c row-major host array (lower triangular), and nd_paper[p], the
+ * paper-order index (as in ams_get_coarse_matrix) of ND position p.
+ * Either output may be NULL.  Single-system handles with N_c <= 4096 only.
+ */
+ams_status ams_get_coarse_factor_inverse(ams_handle h, int64_t* nd_paper, double* Linv);
 
 /*
  * One application z = M^{-1} r of the two-level preconditioner (n x nrhs,

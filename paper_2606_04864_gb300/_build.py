@@ -64,7 +64,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
                     raise RuntimeError(f"nvcc failed on {os.path.basename(src)}")
     if jobs or not os.path.exists(LIB) or force:
         libdir = _cuda_lib_dir(nvcc)
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-L", libdir, "-lcusolver", "-lcudart", "-ldl",
+        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-L", libdir, "-lcudart", "-ldl",
                "-Xlinker", "-rpath", "-Xlinker", libdir]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:

@@ -79,6 +79,8 @@ class ams_info(C.Structure):
         ("kernel_launches", C.c_int64),
         ("two_grid_omega", C.c_double),
         ("local_lambda_max", C.c_double),
+        ("coarse_factor_seconds", C.c_double),
+        ("coarse_factor_gflop", C.c_double),
     ]
 
 
@@ -105,6 +107,7 @@ SIGNATURES = {
     "ams_set_launch_shape": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p]),
     "ams_get_coarse_basis": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ams_get_coarse_matrix": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ams_get_coarse_factor_inverse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "ams_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ams_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ams_time_kernel": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),

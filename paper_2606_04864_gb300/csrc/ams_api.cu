@@ -13,7 +13,6 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
-#include <cusolverDn.h>
 #include <nvtx3/nvToolsExt.h>
 
 #include "ams_internal.h"
@@ -49,15 +48,6 @@ static int64_t round_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
     do {                                       \
         ams_status _s = (expr);                \
         if (_s != AMS_OK) return _s;           \
-    } while (0)
-
-#define AMS_SOLVER_TRY(expr)                                                          \
-    do {                                                                              \
-        cusolverStatus_t _c = (expr);                                                 \
-        if (_c != CUSOLVER_STATUS_SUCCESS) {                                          \
-            set_error(std::string(#expr) + ": cuSOLVER status " + std::to_string((int)_c)); \
-            return AMS_ERR_CUDA;                                                      \
-        }                                                                             \
     } while (0)
 
 // device allocation owned by a handle
@@ -98,6 +88,7 @@ struct SystemHost {
     std::vector<int64_t> perm, sub_ptr;
     std::vector<NDNode> nodes;
     std::vector<double> A0_nd;  // dense A_0 in ND order (small systems only)
+    std::vector<double> Linv_nd;  // L_c^{-1} in ND order, column-major (small systems only)
     std::vector<int64_t> nd_pos_of_sub;  // coarse position (relative) of mode 0 of each subdomain
 };
 
@@ -708,15 +699,6 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
     AMS_TRY(upload(h, &d_nbr, nbr));
     const int mm = std::max(1, h->mmax);
 
-    cusolverDnHandle_t sol = nullptr;
-    AMS_SOLVER_TRY(cusolverDnCreate(&sol));
-    std::unique_ptr<cusolverDnContext, decltype(&cusolverDnDestroy)> sol_guard(sol, cusolverDnDestroy);
-    AMS_SOLVER_TRY(cusolverDnSetStream(sol, h->stream));
-    cusolverDnParams_t params = nullptr;
-    AMS_SOLVER_TRY(cusolverDnCreateParams(&params));
-    std::unique_ptr<cusolverDnParams, decltype(&cusolverDnDestroyParams)> par_guard(params,
-                                                                                    cusolverDnDestroyParams);
-
     // node matrices and GEMM items (all systems)
     struct NodeMat { int64_t off; int64_t K; };
     std::vector<CoarseItem> fwd, bwd;
@@ -858,32 +840,38 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
             AMS_CUDA_TRY(cudaMemcpyAsync(S.A0_nd.data(), d_A, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost,
                                          h->stream));
         }
-        size_t wdev = 0, whost = 0, wdev2 = 0, whost2 = 0;
-        AMS_SOLVER_TRY(cusolverDnXpotrf_bufferSize(sol, params, CUBLAS_FILL_MODE_LOWER, nc, CUDA_R_64F, d_A, nc,
-                                                   CUDA_R_64F, &wdev, &whost));
-        AMS_SOLVER_TRY(cusolverDnXtrtri_bufferSize(sol, CUBLAS_FILL_MODE_LOWER, CUBLAS_DIAG_NON_UNIT, nc,
-                                                   CUDA_R_64F, d_A, nc, &wdev2, &whost2));
-        void* d_work = nullptr;
-        int* d_info = nullptr;
-        AMS_TRY(h->alloc(&d_work, std::max(wdev, wdev2)));
-        AMS_TRY(h->alloc((void**)&d_info, sizeof(int)));
-        std::vector<char> hwork(std::max<size_t>(1, std::max(whost, whost2)));
-        AMS_SOLVER_TRY(cusolverDnXpotrf(sol, params, CUBLAS_FILL_MODE_LOWER, nc, CUDA_R_64F, d_A, nc, CUDA_R_64F,
-                                        d_work, wdev, hwork.data(), whost, d_info));
-        int info = 0;
-        AMS_CUDA_TRY(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        // Cholesky factor of A_0 and its inverse on the tiles that the
+        // nested-dissection order keeps (k_coarse_factor.cu)
+        const double tf0 = now_s();
+        CoarseTilePlan plan;
+        build_coarse_tile_plan(S.nodes, nc, plan);
+        double *d_X = nullptr, *d_invd = nullptr;
+        int32_t *d_trsm = nullptr, *d_upd = nullptr, *d_inv = nullptr;
+        unsigned long long* d_bad = nullptr;
+        AMS_TRY(h->alloc_t(&d_X, (size_t)nc * nc));
+        AMS_CUDA_TRY(cudaMemsetAsync(d_X, 0, sizeof(double) * nc * nc, h->stream));
+        AMS_TRY(h->alloc_t(&d_invd, coarse_tile_invd_elems(plan.T)));
+        AMS_TRY(upload(h, &d_trsm, plan.trsm));
+        AMS_TRY(upload(h, &d_upd, plan.upd));
+        AMS_TRY(upload(h, &d_inv, plan.inv));
+        AMS_TRY(h->alloc_t(&d_bad, 1));
+        AMS_CUDA_TRY(cudaMemsetAsync(d_bad, 0xff, sizeof(unsigned long long), h->stream));
+        launch_coarse_tile_factor(h->stream, plan, d_trsm, reinterpret_cast<const int2*>(d_upd),
+                                  reinterpret_cast<const int2*>(d_inv), d_A, d_X, d_invd, d_bad);
+        AMS_CUDA_TRY(cudaGetLastError());
+        unsigned long long bad = 0;
+        AMS_CUDA_TRY(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->stream));
         AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-        if (info != 0) {
-            set_error("coarse matrix A_0 is not SPD (Cholesky pivot " + std::to_string(info) + ")");
+        if (bad != ~0ull) {
+            set_error("coarse matrix A_0 is not SPD (Cholesky pivot at coarse row " + std::to_string(bad) + ")");
             return AMS_ERR_NOT_SPD;
         }
-        AMS_SOLVER_TRY(cusolverDnXtrtri(sol, CUBLAS_FILL_MODE_LOWER, CUBLAS_DIAG_NON_UNIT, nc, CUDA_R_64F, d_A, nc,
-                                        d_work, wdev2, hwork.data(), whost2, d_info));
-        AMS_CUDA_TRY(cudaMemcpyAsync(&info, d_info, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-        if (info != 0) {
-            set_error("coarse triangular inverse failed");
-            return AMS_ERR_NOT_SPD;
+        h->info.coarse_factor_gflop += 2e-9 * plan.fma;
+        h->info.coarse_factor_seconds += now_s() - tf0;
+        if (nc <= 4096) {
+            S.Linv_nd.resize((size_t)nc * nc);
+            AMS_CUDA_TRY(cudaMemcpyAsync(S.Linv_nd.data(), d_X, sizeof(double) * nc * nc, cudaMemcpyDeviceToHost,
+                                         h->stream));
         }
         // system-relative gather ranges for the extraction
         std::vector<int32_t> rel = rng;
@@ -903,13 +891,14 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
         AMS_TRY(upload(h, &d_df, df));
         AMS_TRY(upload(h, &d_db, db));
         const bool f64 = h->prec == AMS_PREC_FP64;
-        launch_extract_chunks(h->stream, (int)(df.size() / 8), d_df, d_rel, d_A, nc,
+        launch_extract_chunks(h->stream, (int)(df.size() / 8), d_df, d_rel, d_X, nc,
                               f64 ? (double*)h->d_Rmat : nullptr, f64 ? nullptr : (float*)h->d_Rmat);
-        launch_extract_chunks(h->stream, (int)(db.size() / 8), d_db, d_rel, d_A, nc,
+        launch_extract_chunks(h->stream, (int)(db.size() / 8), d_db, d_rel, d_X, nc,
                               f64 ? (double*)h->d_Qmat : nullptr, f64 ? nullptr : (float*)h->d_Qmat);
         AMS_CUDA_TRY(cudaGetLastError());
         AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-        for (void* p : {(void*)d_A, d_work, (void*)d_info, (void*)d_rel, (void*)d_desc, (void*)d_df, (void*)d_db})
+        for (void* p : {(void*)d_A, (void*)d_X, (void*)d_invd, (void*)d_trsm, (void*)d_upd, (void*)d_inv,
+                        (void*)d_bad, (void*)d_rel, (void*)d_desc, (void*)d_df, (void*)d_db})
             h->release(p);
     }
     h->release(d_nbr_ptr);
@@ -2189,6 +2178,30 @@ ams_status ams_get_coarse_matrix(ams_handle h, double* A0) {
     }
     for (int64_t i = 0; i < S.nc; ++i)
         for (int64_t j = 0; j < S.nc; ++j) A0[paper_of_nd[i] * S.nc + paper_of_nd[j]] = S.A0_nd[i * S.nc + j];
+    return AMS_OK;
+}
+
+ams_status ams_get_coarse_factor_inverse(ams_handle h, int64_t* nd_paper, double* Linv) {
+    if (!h || h->nsys != 1) {
+        set_error("single-system handle required");
+        return AMS_ERR_INVALID_ARG;
+    }
+    const SystemHost& S = h->sys[0];
+    if (S.nc > 0 && S.Linv_nd.empty()) {
+        set_error("coarse factor inverse not retained (N_c > 4096)");
+        return AMS_ERR_INVALID_ARG;
+    }
+    if (nd_paper) {
+        int64_t pos = 0;
+        for (int32_t a = 0; a < S.nparts; ++a) {
+            const int m = h->h_subs[S.sub0 + a].m;
+            for (int k = 0; k < m; ++k) nd_paper[S.nd_pos_of_sub[a] + k] = pos + k;
+            pos += m;
+        }
+    }
+    if (Linv)
+        for (int64_t i = 0; i < S.nc; ++i)
+            for (int64_t j = 0; j < S.nc; ++j) Linv[i * S.nc + j] = S.Linv_nd[i + j * S.nc];
     return AMS_OK;
 }
 

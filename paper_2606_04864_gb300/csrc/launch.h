@@ -221,6 +221,31 @@ void launch_galerkin(cudaStream_t s, int nsub, const SubInfo* subs, const int64_
                      int mmax, double* Ac, int64_t ldA, int64_t coff0, int sub0);
 void launch_extract_chunks(cudaStream_t s, int nchunks, const int64_t* desc, const int32_t* rng,
                            const double* Linv, int64_t ldL, double* out64, float* out32);
+// Tile Cholesky factor of A_0 and its inverse (k_coarse_factor.cu).  The
+// plan lists, per step, the kept 64 x 64 tiles of the nested-dissection
+// pattern: row tiles of the TRSM of column k, (i, j) pairs of its update,
+// (i, c | last << 31) pairs of row step k of the inversion.
+struct CoarseTilePlan {
+    int64_t nc = 0;
+    int T = 0;                         // tiles per side
+    int64_t kept_tiles = 0;            // kept tiles of the lower triangle
+    double fma = 0.0;                  // tile multiply-adds of factor + inverse
+    std::vector<int32_t> trsm;         // row tiles, by step
+    std::vector<int64_t> trsm_ptr;     // T + 1
+    std::vector<int32_t> upd;          // (i, j) pairs, by step
+    std::vector<int64_t> upd_ptr;      // T + 1, in pairs
+    std::vector<int32_t> inv;          // (i, c | last << 31) pairs, by step
+    std::vector<int64_t> inv_ptr;      // T + 1, in pairs
+};
+void build_coarse_tile_plan(const std::vector<NDNode>& nodes, int64_t nc, CoarseTilePlan& P);
+size_t coarse_tile_invd_elems(int T);
+// A (N_c x N_c, column-major, lower triangle read) becomes L (lower
+// triangle); X must be zero on entry and becomes L^{-1} (lower triangle);
+// *bad (initially ~0) receives the first coarse row whose pivot is not
+// positive.
+void launch_coarse_tile_factor(cudaStream_t s, const CoarseTilePlan& P, const int32_t* d_trsm, const int2* d_upd,
+                               const int2* d_inv, double* d_A, double* d_X, double* d_invd,
+                               unsigned long long* d_bad);
 void launch_band_pack_work(cudaStream_t s, int nwork, const SubInfo* subs, const int64_t* band_off,
                            const int2* work, const double* band, const int64_t* out_off, double* out64,
                            float* out32);

@@ -314,6 +314,16 @@ class AmsSolver(_Base):
         check(lib().ams_get_coarse_matrix(self._h, _ptr(A0)), "ams_get_coarse_matrix")
         return A0
 
+    def coarse_factor_inverse(self):
+        """(L_c^{-1} in the coarse solve's nested-dissection order, nd_paper):
+        ``nd_paper[p]`` is the paper-order coarse index of ND position p."""
+        nc = int(self.info()["ncoarse"])
+        Linv = np.empty((nc, nc), dtype=np.float64)
+        order = np.empty(nc, dtype=np.int64)
+        check(lib().ams_get_coarse_factor_inverse(self._h, _ptr(order), _ptr(Linv)),
+              "ams_get_coarse_factor_inverse")
+        return Linv, order
+
     def apply_preconditioner(self, r):
         rv, nrhs = self._vec_in(r)
         z = self._vec_out(nrhs)

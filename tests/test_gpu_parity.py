@@ -88,6 +88,40 @@ def test_coarse_matrix_matches_oracle(case):
     assert np.abs(np.abs(A0) - np.abs(o.A0)).max() <= 1e-9 * np.abs(o.A0).max()
 
 
+FACTOR_CASES = {
+    # several 64-row tiles, deep nested-dissection trees, tiles straddling
+    # tree nodes, a ragged last tile
+    "2d_2400": lambda: make_small_2d(side=160, bs=8, m=6, std=2.0, sigma=3.0, seed=41),
+    "3d_4000": lambda: make_small_3d(side=40, bs=4, m=4, std=2.0, sigma=2.0, seed=42),
+    "2d_ragged_b10_m11": lambda: make_small_2d(side=111, bs=10, m=11, std=2.0, sigma=3.0, seed=43, ny=111),
+}
+
+
+@pytest.mark.parametrize("name", list(FACTOR_CASES))
+def test_coarse_factor_inverse_matches_dense_cholesky(name):
+    """The tile Cholesky factor of A_0 and its inverse, computed only on the
+    tiles that the nested-dissection order keeps, against LAPACK's dense
+    Cholesky of the same A_0 and a dense triangular inverse."""
+    w = FACTOR_CASES[name]()
+    s = _solver(w, precision="fp64")
+    A0 = s.coarse_matrix()
+    X, order = s.coarse_factor_inverse()
+    nc = len(order)
+    assert nc == A0.shape[0] and nc > 1000
+    assert (np.sort(order) == np.arange(nc)).all()
+    A0nd = A0[np.ix_(order, order)]
+    L = np.linalg.cholesky(A0nd)
+    Xref = la.solve_triangular(L, np.eye(nc), lower=True)
+    assert not np.triu(X, 1).any()
+    err = np.abs(X - Xref).max() / np.abs(Xref).max()
+    ident = np.abs(X @ A0nd @ X.T - np.eye(nc)).max()
+    print(f"{name}: N_c={nc} max|X-Xref|/max|Xref|={err:.2e} max|X A0 X^T - I|={ident:.2e}")
+    assert err <= 1e-11
+    assert ident <= 1e-11
+    info = s.info()
+    assert 0.0 < info["coarse_factor_gflop"] < 2 * nc ** 3 / 3 * 1e-9
+
+
 def test_spmv_matches_scipy(case):
     name, w, A, o = case
     s = _solver(w, precision="fp64")
