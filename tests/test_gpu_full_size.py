@@ -6,7 +6,8 @@ hold at any size.
   and local solves against the oracle, symmetry/positivity of M^{-1}, mixed
   vs FP64 solutions and iteration counts, true residuals.
 * 128^3 lognormal system with 32 right-hand sides: every column converges,
-  mixed vs FP64, sampled eigenpairs.
+  mixed vs FP64, sampled eigenpairs; one preconditioner application against
+  the oracle's at 1024 seeded rows of all 32 columns.
 * 96^3 differentiable solve: adjoint gradient dL/dlog k against central
   differences (h = 1e-6) on 32 random directions, and against the oracle's
   dense adjoint gradient on a 16^3 copy.
@@ -164,6 +165,36 @@ def test_grf3d_128_32_rhs_full_size():
     for k in range(0, 32, 7):
         assert np.linalg.norm(w.rhs[k] - A @ un[k]) <= 1e-6 * np.linalg.norm(w.rhs[k])
     _check_sampled_eigs(s64, w, A, [0, 1000, 2047, 4095])
+
+
+def test_grf3d_128_apply_against_the_oracle_full_size():
+    """One application z = M^{-1} r of the preconditioner on the full-size
+    128^3 system with 32 right-hand sides (the launch configuration the bench
+    times: 16 right-hand sides per warp in the local solves, the coarse block
+    products at 32 columns) against the oracle's application at 1024 seeded
+    rows of every column (tests/golden/grf3d_128_apply_oracle.json, written
+    from oracle/ alone by tests/golden/make_grf3d_128_apply_oracle.py): the
+    FP64 path with the FP64 basis, the mixed path with the oracle's basis
+    rounded to bfloat16."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "grf3d_128_apply_oracle.json")
+    with open(path) as fh:
+        fx = json.load(fh)
+    w = make_grf3d_128_rhs32()
+    assert fx["n"] == w.n and fx["nnz"] == w.nnz
+    rows = np.asarray(fx["sample_idx"])
+    r = np.random.default_rng(fx["rhs_seed"]).standard_normal((32, w.n))
+    rt = torch.as_tensor(r, device="cuda")
+    for prec, key, tol in (("fp64", "fp64", 1e-10), ("fp32_bf16", "bf16_basis", 2e-5)):
+        s = AmsSolver(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m, precision=prec, device=True)
+        assert int(s.info()["ncoarse"]) == fx[key]["ncoarse"]
+        z = s.apply_preconditioner(rt).cpu().numpy()[:, rows]
+        ref = np.asarray(fx[key]["z"])
+        err = np.abs(z - ref).max() / np.abs(ref).max()
+        print(f"{prec}: max |z - z_oracle| / max |z_oracle| = {err:.3e} at {ref.size} sampled entries")
+        assert err <= tol, (prec, err)
+        s.close()
 
 
 def _grf3d_loss_and_grad(w, solver, logk_np, d, obs, rtol):
