@@ -5,7 +5,7 @@
 //   k_spmv_dot        q = A p and p.q                          (SELL-32 SpMV)
 //   k_local_solve     z_f = sum_i R_i^T A_i^{-1} R_i r'  and  r_c = R_0 r',
 //   (k_local_tma*)    r' = r - alpha q formed on the fly       (alpha = rho/pq)
-//   k_coarse_rows     y = L_c^{-1} r_c                        (A_0 = L_c L_c^T)
+//   k_coarse_*        y = L_c^{-1} r_c  (k_coarse.cu)          (A_0 = L_c L_c^T)
 //   k_prolong_update  e_c = L_c^{-T} y, z = z_f + R_0^T e_c, r = r',
 //                     x += alpha p, r.z, r.r, z.q, convergence test, beta
 #include <cstdint>
@@ -369,384 +369,6 @@ __global__ void k_local_solve(const SubInfo* __restrict__ subs, const TF* __rest
         bwd_step(K, wb[0]);
         if (K - 1 >= 0) bwd_step(K - 1, wb[1]);
     }
-}
-
-// ===========================================================================
-// a5: coarse solve by blocks of L_c^{-1} (nested-dissection layout).
-// Each item multiplies a <=32-row tile of one node matrix by a gathered
-// chunk of the input; several chunks of one tile are summed in chunk order
-// by the last item to finish (deterministic split-K).
-// ===========================================================================
-template <typename TF, int LD>
-__global__ void __launch_bounds__(256)
-k_coarse_gemm(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
-              const int32_t* __restrict__ rng, const int32_t* __restrict__ gat, const TF* __restrict__ in,
-              TF* __restrict__ out, TF* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
-    // Many right-hand sides (LD >= 8): thread (h = t % LD, row group t / LD)
-    // accumulates RPT consecutive rows of the 32-row tile for right-hand side
-    // h.  Per stage of KC columns the tile (transposed, so one aligned load
-    // gives a thread its RPT rows at one column) and the gathered input go
-    // through shared memory; the next stage's global loads are issued into
-    // registers before the current stage is computed.
-    pdl_wait();
-    if (st != nullptr && st->done) return;
-    pdl_trigger();
-    using A = typename Acc<TF>::type;
-    using V4 = typename std::conditional<sizeof(TF) == 4, float4, double4>::type;
-    static_assert(LD >= 8 && LD <= 32, "k_coarse_gemm serves 8 to 32 right-hand sides");
-    constexpr int KC = 64;                                   // columns per stage
-    constexpr int OUT = 32 * LD;                             // outputs of a tile
-    constexpr int NRG = 256 / LD;                            // row groups
-    constexpr int RPT = 32 / NRG;                            // rows per thread (1, 2 or 4)
-    constexpr int TP = 32 + 4;                               // padded transposed row
-    constexpr int MV = 32 * KC / 4 / 256;                    // 4-column tile pieces per thread (2)
-    constexpr int XV = KC * LD / 256;                        // input values per thread
-    __shared__ __align__(32) TF sMT[KC][TP];
-    __shared__ TF sX[KC][LD];
-    __shared__ int s_last;
-    const CoarseItem it = items[blockIdx.x];
-    const int t = threadIdx.x;
-    const int h = t % LD, r0 = (t / LD) * RPT;
-    const TF* M0 = mat + it.moff + (int64_t)it.row_in_node * it.ldm;
-    const int g0 = (it.gat_off < 0) ? rng[2 * it.rng_off] : 0;
-    const int32_t* G = gat + (it.gat_off < 0 ? 0 : it.gat_off);
-    V4 mreg[MV];
-    TF xreg[XV];
-    auto load_stage = [&](int kb) {
-        const int kn = min(KC, it.k1 - kb);
-#pragma unroll
-        for (int u = 0; u < MV; ++u) {
-            const int i = t + 256 * u;
-            const int r = i / (KC / 4), c4 = i % (KC / 4);
-            mreg[u] = V4{};
-            if (r < it.nrows && 4 * c4 < kn)
-                mreg[u] = *reinterpret_cast<const V4*>(M0 + (int64_t)r * it.ldm + kb + 4 * c4);
-        }
-#pragma unroll
-        for (int u = 0; u < XV; ++u) {
-            const int i = t + 256 * u;
-            const int kk = i / LD, hh = i % LD;
-            xreg[u] = TF(0);
-            if (kk < kn) {
-                const int k = kb + kk;
-                const int g = (it.gat_off < 0) ? g0 + k : __ldg(G + k);
-                xreg[u] = in[(int64_t)g * LD + hh];
-            }
-        }
-    };
-    auto store_stage = [&]() {
-#pragma unroll
-        for (int u = 0; u < MV; ++u) {
-            const int i = t + 256 * u;
-            const int r = i / (KC / 4), c4 = i % (KC / 4);
-            sMT[4 * c4 + 0][r] = mreg[u].x;
-            sMT[4 * c4 + 1][r] = mreg[u].y;
-            sMT[4 * c4 + 2][r] = mreg[u].z;
-            sMT[4 * c4 + 3][r] = mreg[u].w;
-        }
-#pragma unroll
-        for (int u = 0; u < XV; ++u) {
-            const int i = t + 256 * u;
-            sX[i / LD][i % LD] = xreg[u];
-        }
-    };
-    A acc[RPT];
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) acc[i] = A(0);
-    load_stage(it.k0);
-    for (int kb = it.k0; kb < it.k1; kb += KC) {
-        __syncthreads();                     // the previous stage is no longer read
-        store_stage();
-        __syncthreads();
-        if (kb + KC < it.k1) load_stage(kb + KC);
-#pragma unroll 8
-        for (int kk = 0; kk < KC; ++kk) {
-            const A x = (A)sX[kk][h];
-            if (RPT == 4) {
-                const V4 m = *reinterpret_cast<const V4*>(&sMT[kk][r0]);
-                acc[0] += (A)m.x * x;
-                acc[RPT > 1 ? 1 : 0] += (A)m.y * x;
-                acc[RPT > 2 ? 2 : 0] += (A)m.z * x;
-                acc[RPT > 3 ? 3 : 0] += (A)m.w * x;
-            } else {
-#pragma unroll
-                for (int i = 0; i < RPT; ++i) acc[i] += (A)sMT[kk][r0 + i] * x;
-            }
-        }
-    }
-    if (it.nchunks == 1) {
-#pragma unroll
-        for (int i = 0; i < RPT; ++i)
-            if (r0 + i < it.nrows) out[(int64_t)(it.out0 + r0 + i) * LD + h] = (TF)acc[i];
-        return;
-    }
-    TF* P = partial + (int64_t)(it.slot0 + it.chunk) * OUT;
-#pragma unroll
-    for (int i = 0; i < RPT; ++i) P[(r0 + i) * LD + h] = (TF)acc[i];
-
-    __syncthreads();
-    if (t == 0) {
-        __threadfence();
-        s_last = (atomicAdd(cnt + it.tile_id, 1) == it.nchunks - 1);
-        if (s_last) __threadfence();
-    }
-    __syncthreads();
-    if (!s_last) return;
-    for (int o = t; o < OUT; o += 256) {
-        A s = A(0);
-        for (int ch = 0; ch < it.nchunks; ++ch) s += (A)__ldcg(partial + (int64_t)(it.slot0 + ch) * OUT + o);
-        const int rr = o / LD, hh = o % LD;
-        if (rr < it.nrows) out[(int64_t)(it.out0 + rr) * LD + hh] = (TF)s;
-    }
-    if (t == 0) cnt[it.tile_id] = 0;
-}
-
-// Many right-hand sides (LD >= 8) in the reduced-precision apply: the same
-// items as k_coarse_gemm, with the 32-row tile times the gathered input
-// computed by warp-level tensor-core MMAs (m16n8k8, TF32 head/tail split
-// of both operands, FP32 accumulation: FP32 accuracy).  Warp w owns the
-// 16 x 8 output fragment (rows 16 (w / (LD/8)) .., columns 8 (w % (LD/8)) ..);
-// stages of 64 columns of the tile (row-major, rows padded to 68 floats so
-// that the A-fragment loads are conflict-free) and of the gathered input
-// (rows padded to 8 mod 32 words for the B fragments) pass through shared
-// memory, the next stage loaded into registers while the current one is
-// multiplied.  Split-K chunks reduce as in k_coarse_gemm.
-template <int LD>
-__global__ void __launch_bounds__(LD * 8)
-k_coarse_mma(const CoarseItem* __restrict__ items, const float* __restrict__ mat, const int32_t* __restrict__ rng,
-             const int32_t* __restrict__ gat, const float* __restrict__ in, float* __restrict__ out,
-             float* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
-    pdl_wait();
-    if (st != nullptr && st->done) return;
-    pdl_trigger();
-    static_assert(LD == 8 || LD == 16 || LD == 32, "k_coarse_mma serves 8, 16 or 32 right-hand sides");
-    constexpr int NT = LD * 8;                               // threads: 2 x (LD / 8) warps
-    constexpr int KC = 64;                                   // columns per stage
-    constexpr int SA = KC + 4;
-    constexpr int SB = LD >= 16 ? LD + 8 : 24;
-    constexpr int OUT = 32 * LD;
-    constexpr int MV = 32 * KC / 4 / NT;                     // float4 tile pieces per thread
-    constexpr int XV = KC * LD / NT;                         // input values per thread (8)
-    __shared__ __align__(16) float sA[32][SA];
-    __shared__ __align__(16) float sB[KC][SB];
-    __shared__ int s_last;
-    const CoarseItem it = items[blockIdx.x];
-    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int g = lane >> 2, tq = lane & 3;
-    const int nf = w % (LD / 8), mf = w / (LD / 8);
-    const float* M0 = mat + it.moff + (int64_t)it.row_in_node * it.ldm;
-    const int g0 = (it.gat_off < 0) ? rng[2 * it.rng_off] : 0;
-    const int32_t* G = gat + (it.gat_off < 0 ? 0 : it.gat_off);
-    float4 mreg[MV];
-    float xreg[XV];
-    auto load_stage = [&](int kb) {
-        const int kn = min(KC, it.k1 - kb);
-#pragma unroll
-        for (int u = 0; u < MV; ++u) {
-            const int i = t + NT * u;
-            const int r = i / (KC / 4), c4 = i % (KC / 4);
-            mreg[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (r < it.nrows && 4 * c4 < kn)
-                mreg[u] = *reinterpret_cast<const float4*>(M0 + (int64_t)r * it.ldm + kb + 4 * c4);
-        }
-#pragma unroll
-        for (int u = 0; u < XV; ++u) {
-            const int i = t + NT * u;
-            const int kk = i / LD, hh = i % LD;
-            xreg[u] = 0.f;
-            if (kk < kn) {
-                const int k = kb + kk;
-                const int gi = (it.gat_off < 0) ? g0 + k : __ldg(G + k);
-                xreg[u] = in[(int64_t)gi * LD + hh];
-            }
-        }
-    };
-    auto store_stage = [&]() {
-#pragma unroll
-        for (int u = 0; u < MV; ++u) {
-            const int i = t + NT * u;
-            *reinterpret_cast<float4*>(&sA[i / (KC / 4)][4 * (i % (KC / 4))]) = mreg[u];
-        }
-#pragma unroll
-        for (int u = 0; u < XV; ++u) {
-            const int i = t + NT * u;
-            sB[i / LD][i % LD] = xreg[u];
-        }
-    };
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    load_stage(it.k0);
-    for (int kb = it.k0; kb < it.k1; kb += KC) {
-        __syncthreads();                     // the previous stage is no longer read
-        store_stage();
-        __syncthreads();
-        if (kb + KC < it.k1) load_stage(kb + KC);
-#pragma unroll
-        for (int ks = 0; ks < KC / 8; ++ks) {
-            const int r0 = 16 * mf + g, k0 = 8 * ks + tq;
-            uint32_t ah[4], al[4], b0h, b0l, b1h, b1l;
-            split_tf32(sA[r0][k0], ah[0], al[0]);
-            split_tf32(sA[r0 + 8][k0], ah[1], al[1]);
-            split_tf32(sA[r0][k0 + 4], ah[2], al[2]);
-            split_tf32(sA[r0 + 8][k0 + 4], ah[3], al[3]);
-            split_tf32(sB[k0][8 * nf + g], b0h, b0l);
-            split_tf32(sB[k0 + 4][8 * nf + g], b1h, b1l);
-            mma_tf32(acc, al, b0h, b1h);
-            mma_tf32(acc, ah, b0l, b1l);
-            mma_tf32(acc, ah, b0h, b1h);
-        }
-    }
-    // accumulator i: row 16 mf + g + 8 (i >> 1), column 8 nf + 2 tq + (i & 1)
-    if (it.nchunks == 1) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int rr = 16 * mf + g + 8 * (i >> 1);
-            if (rr < it.nrows) out[(int64_t)(it.out0 + rr) * LD + 8 * nf + 2 * tq + (i & 1)] = acc[i];
-        }
-        return;
-    }
-    float* P = partial + (int64_t)(it.slot0 + it.chunk) * OUT;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) P[(16 * mf + g + 8 * (i >> 1)) * LD + 8 * nf + 2 * tq + (i & 1)] = acc[i];
-    __syncthreads();
-    if (t == 0) {
-        __threadfence();
-        s_last = (atomicAdd(cnt + it.tile_id, 1) == it.nchunks - 1);
-        if (s_last) __threadfence();
-    }
-    __syncthreads();
-    if (!s_last) return;
-    for (int o = t; o < OUT; o += NT) {
-        float sum = 0.f;
-        for (int ch = 0; ch < it.nchunks; ++ch) sum += __ldcg(partial + (int64_t)(it.slot0 + ch) * OUT + o);
-        const int rr = o / LD, hh = o % LD;
-        if (rr < it.nrows) out[(int64_t)(it.out0 + rr) * LD + hh] = sum;
-    }
-    if (t == 0) cnt[it.tile_id] = 0;
-}
-
-// Few right-hand sides (LD <= 4): each warp streams whole rows of the node
-// matrix with coalesced 16-byte loads (lane j covers columns 4j..4j+3 of
-// every 128-column group) against the gathered input chunk held in shared
-// memory; no per-stage barriers.  Node-matrix rows are padded with zeros to
-// a multiple of 4 columns, so every row starts 16-byte aligned.
-template <typename TF, int LD>
-__global__ void __launch_bounds__(256)
-k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
-              const int32_t* __restrict__ rng, const TF* __restrict__ in, TF* __restrict__ out,
-              TF* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
-    using A = typename Acc<TF>::type;
-    using V4 = typename std::conditional<sizeof(TF) == 4, float4, double4>::type;
-    constexpr int OUT = 32 * LD;
-    constexpr int MAXR = 64;                  // gather ranges staged in shared memory
-    __shared__ __align__(16) TF sx[(kCoarseChunk + 4) * LD];
-    __shared__ A sres[OUT];
-    __shared__ int srng[2 * MAXR];
-    __shared__ int s_last;
-    const CoarseItem it = items[blockIdx.x];
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int kn = it.k1 - it.k0;
-    const int kn4 = (kn + 3) & ~3;
-    const int nr = min(it.nrng, MAXR);
-    const TF* M0 = mat + it.moff + (int64_t)it.row_in_node * it.ldm + it.k0;
-    const bool rv[4] = {warp < it.nrows, warp + 8 < it.nrows, warp + 16 < it.nrows, warp + 24 < it.nrows};
-    // warp w owns rows w, w+8, w+16, w+24 of the tile; lane takes 4 columns
-    // per step.  The first two steps of the (setup-data) tile are loaded
-    // before the input gather so both memory trips overlap.
-    auto load_cols = [&](int c4, V4 (&mv)[4]) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-            if (rv[i] && 4 * c4 < kn4) mv[i] = *reinterpret_cast<const V4*>(M0 + (int64_t)(warp + 8 * i) * it.ldm + 4 * c4);
-    };
-    V4 pre0[4], pre1[4];
-    load_cols(lane, pre0);
-    load_cols(lane + 32, pre1);
-    for (int i = t; i < 2 * nr; i += 256) srng[i] = rng[2 * it.rng_off + i];
-    pdl_wait();
-    if (st != nullptr && st->done) return;
-    pdl_trigger();
-    __syncthreads();
-    for (int kk = t; kk < kn4; kk += 256) {
-        TF v[LD];
-#pragma unroll
-        for (int h = 0; h < LD; ++h) v[h] = TF(0);
-        if (kk < kn) {
-            int k = it.k0 + kk, g = 0;
-            for (int j = 0; j < it.nrng; ++j) {
-                const int s0 = j < MAXR ? srng[2 * j] : rng[2 * (it.rng_off + j)];
-                const int len = j < MAXR ? srng[2 * j + 1] : rng[2 * (it.rng_off + j) + 1];
-                if (k < len) { g = s0 + k; break; }
-                k -= len;
-            }
-#pragma unroll
-            for (int h = 0; h < LD; ++h) v[h] = in[(int64_t)g * LD + h];
-        }
-#pragma unroll
-        for (int h = 0; h < LD; ++h) sx[kk * LD + h] = v[h];
-    }
-    __syncthreads();
-    A acc[4][LD];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int h = 0; h < LD; ++h) acc[i][h] = A(0);
-    auto step = [&](int c4, const V4 (&mv)[4]) {
-        if (4 * c4 >= kn4) return;
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            A xv[LD];
-#pragma unroll
-            for (int h = 0; h < LD; ++h) xv[h] = (A)sx[(4 * c4 + e) * LD + h];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                if (rv[i]) {
-                    const A m = (A)(e == 0 ? mv[i].x : e == 1 ? mv[i].y : e == 2 ? mv[i].z : mv[i].w);
-#pragma unroll
-                    for (int h = 0; h < LD; ++h) acc[i][h] += m * xv[h];
-                }
-            }
-        }
-    };
-    step(lane, pre0);
-    step(lane + 32, pre1);
-#pragma unroll 2
-    for (int c4 = lane + 64; 4 * c4 < kn4; c4 += 32) {
-        V4 mv[4];
-        load_cols(c4, mv);
-        step(c4, mv);
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int h = 0; h < LD; ++h) {
-            A v = acc[i][h];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) sres[(warp + 8 * i) * LD + h] = v;
-        }
-    __syncthreads();
-    if (it.nchunks == 1) {
-        for (int o = t; o < OUT; o += 256) {
-            const int r = o / LD;
-            if (r < it.nrows) out[(int64_t)(it.out0 + r) * LD + (o % LD)] = (TF)sres[o];
-        }
-        return;
-    }
-    TF* P = partial + (int64_t)(it.slot0 + it.chunk) * OUT;
-    for (int o = t; o < OUT; o += 256) P[o] = (TF)sres[o];
-    __syncthreads();
-    if (t == 0) {
-        __threadfence();
-        s_last = (atomicAdd(cnt + it.tile_id, 1) == it.nchunks - 1);
-        if (s_last) __threadfence();
-    }
-    __syncthreads();
-    if (!s_last) return;
-    for (int o = t; o < OUT; o += 256) {
-        A v = A(0);
-        for (int ch = 0; ch < it.nchunks; ++ch) v += (A)__ldcg(partial + (int64_t)(it.slot0 + ch) * OUT + o);
-        const int r = o / LD;
-        if (r < it.nrows) out[(int64_t)(it.out0 + r) * LD + (o % LD)] = (TF)v;
-    }
-    if (t == 0) cnt[it.tile_id] = 0;
 }
 
 // ===========================================================================
@@ -1164,38 +786,6 @@ cudaError_t launch_local_solve(const LocalSolveArgs& a, int prec, const void* fa
     if (prec == AMS_PREC_FP64) return local_tp<double, double>(a, fac, psi, zf, rc);
     if (prec == AMS_PREC_FP32) return local_tp<float, float>(a, fac, psi, zf, rc);
     return local_tp<float, __nv_bfloat16>(a, fac, psi, zf, rc);
-}
-
-template <typename TF, int LD>
-static void coarse_ld(const CoarseLaunch& c, const void* in, void* out) {
-    if (c.nitems == 0) return;
-    if (LD <= 4)
-        launch_kernel(c.pdl, k_coarse_rows<TF, (LD <= 4 ? LD : 4)>, dim3(c.nitems), dim3(256), 0, c.stream, c.items,
-                      (const TF*)c.mat, c.rng, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt, c.st);
-    else
-        if constexpr (sizeof(TF) == 4)   // reduced-precision apply: tile products on the tensor cores
-            launch_kernel(c.pdl, k_coarse_mma<(LD >= 8 ? LD : 8)>, dim3(c.nitems), dim3((LD >= 8 ? LD : 8) * 8), 0,
-                          c.stream, c.items, (const float*)c.mat, c.rng, c.gat, (const float*)in, (float*)out,
-                          (float*)c.partial, c.cnt, c.st);
-        else
-            launch_kernel(c.pdl, k_coarse_gemm<TF, (LD >= 8 ? LD : 8)>, dim3(c.nitems), dim3(256), 0, c.stream,
-                          c.items, (const TF*)c.mat, c.rng, c.gat, (const TF*)in, (TF*)out, (TF*)c.partial, c.cnt,
-                          c.st);
-}
-template <typename TF>
-static void coarse_tf(const CoarseLaunch& c, int ld, const void* in, void* out) {
-    switch (ld) {
-        case 1: coarse_ld<TF, 1>(c, in, out); break;
-        case 2: coarse_ld<TF, 2>(c, in, out); break;
-        case 4: coarse_ld<TF, 4>(c, in, out); break;
-        case 8: coarse_ld<TF, 8>(c, in, out); break;
-        case 16: coarse_ld<TF, 16>(c, in, out); break;
-        default: coarse_ld<TF, 32>(c, in, out); break;
-    }
-}
-void launch_coarse_gemm(const CoarseLaunch& c, int prec, int ld, const void* in, void* out) {
-    if (prec == AMS_PREC_FP64) coarse_tf<double>(c, ld, in, out);
-    else coarse_tf<float>(c, ld, in, out);
 }
 
 template <typename TF, typename TP, int LD>
