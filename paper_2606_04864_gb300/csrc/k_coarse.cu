@@ -148,9 +148,11 @@ k_coarse_gemm(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
 // Many right-hand sides (LD >= 8) in the reduced-precision apply: the same
 // items as k_coarse_gemm, with the 32-row tile times the gathered input
 // computed by warp-level tensor-core MMAs (m16n8k8, TF32 head/tail split
-// of both operands, FP32 accumulation: FP32 accuracy).  Warp w owns the
-// 16 x 8 output fragment (rows 16 (w / (LD/8)) .., columns 8 (w % (LD/8)) ..).
-// Stages of 64 columns of the tile (row-major, rows padded to 68 floats so
+// of both operands, FP32 accumulation: FP32 accuracy).  Every warp computes
+// the whole 32 x LD output tile over its own k-steps of each stage (warp w
+// takes k-steps w, w + NW, ..; NW = LD/4 warps), so each staged element is
+// split into its TF32 head and tail exactly once; the warps' partial tiles
+// are summed in warp order through shared memory at the end.  Stages of 64 columns of the tile (row-major, rows padded to 68 floats so
 // that the A-fragment loads are conflict-free) and of the gathered input
 // (rows padded to 8 mod 32 words for the B fragments) stream through a ring
 // of kCoarseStages shared-memory slots with 16-byte cp.async copies (zero
@@ -163,7 +165,7 @@ constexpr size_t coarse_mma_smem() {
     return (size_t)kCoarseStages * (32 * 68 + 64 * (LD >= 16 ? LD + 8 : 24)) * sizeof(float);
 }
 template <int LD>
-__global__ void __launch_bounds__(LD * 8)
+__global__ void __launch_bounds__(LD * 8, 4)
 k_coarse_mma(const CoarseItem* __restrict__ items, const float* __restrict__ mat, const int32_t* __restrict__ rng,
              const int32_t* __restrict__ gat, const float* __restrict__ in, float* __restrict__ out,
              float* __restrict__ partial, int32_t* __restrict__ cnt, const SolveState* st) {
@@ -171,7 +173,9 @@ k_coarse_mma(const CoarseItem* __restrict__ items, const float* __restrict__ mat
     if (st != nullptr && st->done) return;
     pdl_trigger();
     static_assert(LD == 8 || LD == 16 || LD == 32, "k_coarse_mma serves 8, 16 or 32 right-hand sides");
-    constexpr int NT = LD * 8;                               // threads: 2 x (LD / 8) warps
+    constexpr int NT = LD * 8;                               // threads
+    constexpr int NW = NT / 32;                              // warps (k-step groups)
+    constexpr int NFR = LD / 8;                              // 8-column fragments per warp
     constexpr int KC = 64;                                   // columns per stage
     constexpr int NS = kCoarseStages;
     constexpr int SA = KC + 4;
@@ -185,7 +189,6 @@ k_coarse_mma(const CoarseItem* __restrict__ items, const float* __restrict__ mat
     const CoarseItem it = items[blockIdx.x];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int g = lane >> 2, tq = lane & 3;
-    const int nf = w % (LD / 8), mf = w / (LD / 8);
     const float* M0 = mat + it.moff + (int64_t)it.row_in_node * it.ldm;
     const bool contiguous = it.gat_off < 0;
     const int g0 = contiguous ? rng[2 * it.rng_off] : 0;
@@ -228,7 +231,13 @@ k_coarse_mma(const CoarseItem* __restrict__ items, const float* __restrict__ mat
         cp_async_commit();
     }
     load_idx(NS - 1);
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    float acc[2][NFR][4];                                    // [row fragment][column fragment]
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < NFR; ++b)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[a][b][i] = 0.f;
     for (int s = 0; s < nst; ++s) {
         cp_async_wait_n(NS - 2);             // stage s has landed for this thread ...
         __syncthreads();                     // ... and for all; slot (s - 1) % NS is free
@@ -238,33 +247,62 @@ k_coarse_mma(const CoarseItem* __restrict__ items, const float* __restrict__ mat
         const float* sA = s_ring + (s % NS) * STAGE;
         const float* sB = sA + 32 * SA;
 #pragma unroll
-        for (int ks = 0; ks < KC / 8; ++ks) {
-            const int r0 = 16 * mf + g, k0 = 8 * ks + tq;
-            uint32_t ah[4], al[4], b0h, b0l, b1h, b1l;
-            split_tf32(sA[r0 * SA + k0], ah[0], al[0]);
-            split_tf32(sA[(r0 + 8) * SA + k0], ah[1], al[1]);
-            split_tf32(sA[r0 * SA + k0 + 4], ah[2], al[2]);
-            split_tf32(sA[(r0 + 8) * SA + k0 + 4], ah[3], al[3]);
-            split_tf32(sB[k0 * SB + 8 * nf + g], b0h, b0l);
-            split_tf32(sB[(k0 + 4) * SB + 8 * nf + g], b1h, b1l);
-            mma_tf32(acc, al, b0h, b1h);
-            mma_tf32(acc, ah, b0l, b1l);
-            mma_tf32(acc, ah, b0h, b1h);
+        for (int ks = w; ks < KC / 8; ks += NW) {
+            const int k0 = 8 * ks + tq;
+            uint32_t ah[2][4], al[2][4];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int r0 = 16 * a + g;
+                split_tf32(sA[r0 * SA + k0], ah[a][0], al[a][0]);
+                split_tf32(sA[(r0 + 8) * SA + k0], ah[a][1], al[a][1]);
+                split_tf32(sA[r0 * SA + k0 + 4], ah[a][2], al[a][2]);
+                split_tf32(sA[(r0 + 8) * SA + k0 + 4], ah[a][3], al[a][3]);
+            }
+#pragma unroll
+            for (int b = 0; b < NFR; ++b) {
+                uint32_t b0h, b0l, b1h, b1l;
+                split_tf32(sB[k0 * SB + 8 * b + g], b0h, b0l);
+                split_tf32(sB[(k0 + 4) * SB + 8 * b + g], b1h, b1l);
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    mma_tf32(acc[a][b], al[a], b0h, b1h);
+                    mma_tf32(acc[a][b], ah[a], b0l, b1l);
+                    mma_tf32(acc[a][b], ah[a], b0h, b1h);
+                }
+            }
         }
     }
     cp_async_wait_all();
-    // accumulator i: row 16 mf + g + 8 (i >> 1), column 8 nf + 2 tq + (i & 1)
+    // sum the warps' partial tiles in warp order (the ring is free now)
+    __syncthreads();
+    float* red = s_ring;                                     // NW x 32 x LD
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < NFR; ++b)
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                red[(w * 32 + 16 * a + g + 8 * (i >> 1)) * LD + 8 * b + 2 * tq + (i & 1)] = acc[a][b][i];
+    __syncthreads();
+    float res[OUT / NT];                                     // outputs o = t + NT u
+#pragma unroll
+    for (int u = 0; u < OUT / NT; ++u) {
+        float v = red[t + NT * u];
+#pragma unroll
+        for (int ww = 1; ww < NW; ++ww) v += red[ww * OUT + t + NT * u];
+        res[u] = v;
+    }
     if (it.nchunks == 1) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int rr = 16 * mf + g + 8 * (i >> 1);
-            if (rr < it.nrows) out[(int64_t)(it.out0 + rr) * LD + 8 * nf + 2 * tq + (i & 1)] = acc[i];
+        for (int u = 0; u < OUT / NT; ++u) {
+            const int o = t + NT * u, rr = o / LD;
+            if (rr < it.nrows) out[(int64_t)(it.out0 + rr) * LD + o % LD] = res[u];
         }
         return;
     }
     float* P = partial + (int64_t)(it.slot0 + it.chunk) * OUT;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) P[(16 * mf + g + 8 * (i >> 1)) * LD + 8 * nf + 2 * tq + (i & 1)] = acc[i];
+    for (int u = 0; u < OUT / NT; ++u) P[t + NT * u] = res[u];
     __syncthreads();
     if (t == 0) {
         __threadfence();

@@ -297,8 +297,8 @@ k_eig_rr(const SubInfo* __restrict__ subs, int P, const int64_t* __restrict__ ro
         }
     }
     __syncthreads();
-    if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
     // symmetrise H (Y^T \hat A Y is symmetric up to rounding)
     for (int a = 0; a < p; ++a) {
         if (lane < p && lane > a) {
@@ -369,58 +369,101 @@ k_eig_rr(const SubInfo* __restrict__ subs, int P, const int64_t* __restrict__ ro
         W[a * P + b] = (a == b) ? 1.0 : 0.0;
     }
     __syncwarp();
-    // cyclic Jacobi on C (in G), rotations accumulated in W
-    for (int sweep = 0; sweep < 30; ++sweep) {
-        double off = 0.0, dia = 0.0;
-        for (int t = lane; t < p * p; t += 32) {
-            const int a = t / p, b = t % p;
-            const double v = G[a * P + b];
-            if (a != b) off += v * v; else dia += v * v;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            off += __shfl_xor_sync(0xffffffffu, off, o);
-            dia += __shfl_xor_sync(0xffffffffu, dia, o);
-        }
-        if (off <= 1e-34 * dia || off == 0.0) break;
-        for (int i = 0; i < p - 1; ++i) {
-            for (int j = i + 1; j < p; ++j) {
-                const double aij = G[i * P + j];
-                if (aij == 0.0) continue;
-                const double aii = G[i * P + i], ajj = G[j * P + j];
-                const double tau = (ajj - aii) / (2.0 * aij);
-                const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-                const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = tt * cs;
-                __syncwarp();
-                double gki = 0, gkj = 0, wki = 0, wkj = 0;
-                if (lane < p) {
-                    gki = G[lane * P + i];
-                    gkj = G[lane * P + j];
-                    wki = W[lane * P + i];
-                    wkj = W[lane * P + j];
+    }   // tid < 32
+    __syncthreads();
+    // Jacobi on C (in G), rotations accumulated in W.  Each round applies
+    // pp/2 disjoint rotations at once (round-robin pairing of the pp = p
+    // rounded up to even indices; the pad index, when p is odd, pairs with
+    // nothing): first the columns of G and W (G J, W J), then the rows of G
+    // (J^T G J), every thread of the block taking (pair, row) items.
+    {
+        const int pp = p + (p & 1), half = pp / 2;
+        double* cs = H;            // H is free until the sort: per-pair cosines,
+        double* sn = H + P;        // sines
+        int* pij = reinterpret_cast<int*>(H + 2 * P);   // and (i, j), 2 ints per pair
+        __shared__ double red_off[8], red_dia[8];
+        for (int sweep = 0; sweep < 30; ++sweep) {
+            double off = 0.0, dia = 0.0;
+            for (int t = tid; t < p * p; t += blockDim.x) {
+                const int a = t / p, b = t % p;
+                const double v = G[a * P + b];
+                if (a != b) off += v * v; else dia += v * v;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                off += __shfl_xor_sync(0xffffffffu, off, o);
+                dia += __shfl_xor_sync(0xffffffffu, dia, o);
+            }
+            if (lane == 0) {
+                red_off[tid >> 5] = off;
+                red_dia[tid >> 5] = dia;
+            }
+            __syncthreads();
+            off = 0.0;
+            dia = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {   // same order in every thread
+                off += red_off[w];
+                dia += red_dia[w];
+            }
+            __syncthreads();
+            if (off <= 1e-34 * dia || off == 0.0) break;
+            for (int r = 0; r < pp - 1; ++r) {
+                if (tid < half) {
+                    // round r: (pp-1, r) and ((r + k) mod (pp-1), (r - k) mod (pp-1)), k = 1 .. half-1
+                    int a = tid == 0 ? pp - 1 : (r + tid) % (pp - 1);
+                    int b = tid == 0 ? r : (r - tid + (pp - 1)) % (pp - 1);
+                    const int i = min(a, b), j = max(a, b);
+                    double c = 1.0, sg = 0.0;
+                    if (j < p) {
+                        const double aij = G[i * P + j];
+                        if (aij != 0.0) {
+                            const double aii = G[i * P + i], ajj = G[j * P + j];
+                            const double tau = (ajj - aii) / (2.0 * aij);
+                            const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                            c = 1.0 / sqrt(1.0 + tt * tt);
+                            sg = tt * c;
+                        }
+                    }
+                    cs[tid] = c;
+                    sn[tid] = sg;
+                    pij[2 * tid] = i;
+                    pij[2 * tid + 1] = j;
                 }
-                __syncwarp();
-                if (lane < p) {
-                    G[lane * P + i] = cs * gki - sn * gkj;
-                    G[lane * P + j] = sn * gki + cs * gkj;
-                    W[lane * P + i] = cs * wki - sn * wkj;
-                    W[lane * P + j] = sn * wki + cs * wkj;
+                __syncthreads();
+                for (int e = tid; e < half * p; e += blockDim.x) {   // columns: G J and W J
+                    const int k = e / p, row = e % p;
+                    const int i = pij[2 * k], j = pij[2 * k + 1];
+                    if (j >= p || sn[k] == 0.0) continue;
+                    const double c = cs[k], sg = sn[k];
+                    const double gi = G[row * P + i], gj = G[row * P + j];
+                    G[row * P + i] = c * gi - sg * gj;
+                    G[row * P + j] = sg * gi + c * gj;
+                    const double wi = W[row * P + i], wj = W[row * P + j];
+                    W[row * P + i] = c * wi - sg * wj;
+                    W[row * P + j] = sg * wi + c * wj;
                 }
-                __syncwarp();
-                if (lane < p) {
-                    const double gik = G[i * P + lane], gjk = G[j * P + lane];
-                    __syncwarp(0xffffffffu >> (32 - p));
-                    G[i * P + lane] = cs * gik - sn * gjk;
-                    G[j * P + lane] = sn * gik + cs * gjk;
+                __syncthreads();
+                for (int e = tid; e < half * p; e += blockDim.x) {   // rows: J^T (G J)
+                    const int k = e / p, col = e % p;
+                    const int i = pij[2 * k], j = pij[2 * k + 1];
+                    if (j >= p || sn[k] == 0.0) continue;
+                    const double c = cs[k], sg = sn[k];
+                    const double gi = G[i * P + col], gj = G[j * P + col];
+                    G[i * P + col] = c * gi - sg * gj;
+                    G[j * P + col] = sg * gi + c * gj;
                 }
-                __syncwarp();
-                if (lane == 0) {
-                    G[i * P + j] = 0.0;
-                    G[j * P + i] = 0.0;
+                __syncthreads();
+                if (tid < half) {
+                    const int i = pij[2 * tid], j = pij[2 * tid + 1];
+                    if (j < p && sn[tid] != 0.0) {
+                        G[i * P + j] = 0.0;
+                        G[j * P + i] = 0.0;
+                    }
                 }
-                __syncwarp();
+                __syncthreads();
             }
         }
     }
+    if (tid >= 32) return;
     // sort eigenvalues ascending (selection sort of column order)
     if (lane == 0) {
         int ord[32];
