@@ -120,6 +120,10 @@ struct ams_handle_s {
     int32_t N = 0;
     int64_t Nc = 0;
     int cmax = 1, mmax = 0, nbmax = 1;
+    // subdomains grouped by band width (several-RHS local solve: one launch
+    // per group; empty when every subdomain has the same width)
+    std::vector<int> cls_c, cls_n;
+    int32_t* d_cls_order = nullptr;
     int num_sms = 1;                    // SMs of the handle's device
     bool use_pdl = false;               // solve-loop kernels overlap their prologue with the previous kernel
     std::vector<SubInfo> h_subs;
@@ -551,11 +555,14 @@ static ams_status setup_eigen(ams_handle h, const int64_t* d_rowptr, const int32
     const int ncheck = std::min(P, mreq + 1);
     for (it = 1; it <= maxit; ++it) {
         AMS_CUDA_TRY(launch_local_solve(la, AMS_PREC_FP64, d_efac, nullptr, d_Y, nullptr));
+        // Rayleigh-Ritz on the iterations whose residuals are checked; on the
+        // others only the S-orthonormalisation (the span is the same)
+        const bool check = it % 4 == 0 || it == maxit;
         launch_eig_rr(h->stream, h->N, d_esubs, P, d_rowptr, d_colind, d_vals, d_S, d_ahat, d_Y, d_AY, d_T,
-                      d_theta, d_status);
+                      d_theta, d_status, check ? 0 : 1);
         launch_eig_update(h->stream, h->n_pad, P, h->d_sub_of_row, d_esubs, d_Y, d_T, d_X);
         AMS_CUDA_TRY(cudaGetLastError());
-        if (it % 4 == 0 || it == maxit) {
+        if (check) {
             launch_eig_resid(h->stream, h->N, d_esubs, P, d_rowptr, d_colind, d_vals, d_S, d_ahat, d_X, d_theta,
                              ncheck, d_res);
             AMS_CUDA_TRY(cudaMemcpyAsync(res.data(), d_res, sizeof(double) * h->N, cudaMemcpyDeviceToHost,
@@ -567,7 +574,7 @@ static ams_status setup_eigen(ams_handle h, const int64_t* d_rowptr, const int32
     }
     // final exact S-orthonormalisation: Rayleigh-Ritz on span(X) itself
     launch_eig_rr(h->stream, h->N, d_esubs, P, d_rowptr, d_colind, d_vals, d_S, d_ahat, d_X, d_AY, d_T,
-                  d_theta, d_status);
+                  d_theta, d_status, 0);
     launch_eig_update(h->stream, h->n_pad, P, h->d_sub_of_row, d_esubs, d_X, d_T, d_Y);
     std::swap(d_X, d_Y);
     launch_eig_resid(h->stream, h->N, d_esubs, P, d_rowptr, d_colind, d_vals, d_S, d_ahat, d_X, d_theta,
@@ -1043,6 +1050,23 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
         }
     }
     irp[h->n_pad] = rp;
+    {
+        std::vector<int32_t> order;
+        for (int c = 1; c <= h->cmax; ++c) {
+            int cnt = 0;
+            for (int32_t i = 0; i < h->N; ++i)
+                if (h->h_subs[i].c == c) {
+                    order.push_back(i);
+                    ++cnt;
+                }
+            if (cnt > 0) {
+                h->cls_c.push_back(c);
+                h->cls_n.push_back(cnt);
+            }
+        }
+        if (h->cls_c.size() > 1) AMS_TRY(upload(h.get(), &h->d_cls_order, order));
+        else h->cls_c.clear(), h->cls_n.clear();
+    }
     // shared-memory staging limits of the local solve
     {
         const size_t lim = 227 * 1024;
@@ -1252,10 +1276,21 @@ static int64_t spin_budget(ams_handle h) {
 
 // Fine-level local solves (+ restriction when the coarse space exists).
 static LocalTmaArgs local_tma_args(ams_handle h, int ld, const ResidIn& in, bool with_state) {
-    return LocalTmaArgs{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, in, ld, h->cmax,
-                        std::max(1, h->mmax), h->nbmax, spin_budget(h), with_state ? h->d_st : nullptr,
-                        h->use_pdl, h->tune[ld].depth, h->tune[ld].nr, h->tune[ld].l2mode, h->tune[ld].l2keep,
-                        &h->d_st->status, h->opt.timeout_probe};
+    LocalTmaArgs a{h->stream, h->N, h->d_subs, &h->tmF, &h->tmB, h->d_trow0, h->d_piv, in, ld, h->cmax,
+                   std::max(1, h->mmax), h->nbmax, spin_budget(h), with_state ? h->d_st : nullptr,
+                   h->use_pdl, h->tune[ld].depth, h->tune[ld].nr, h->tune[ld].l2mode, h->tune[ld].l2keep,
+                   &h->d_st->status, h->opt.timeout_probe};
+    a.nclass = (int)h->cls_c.size();
+    a.class_c = h->cls_c.data();
+    a.class_n = h->cls_n.data();
+    a.order = h->d_cls_order;
+    return a;
+}
+
+// Launches of one local-solve pass beyond the first: the several-RHS
+// kernel launches once per band-width group.
+static int local_extra_launches(ams_handle h, int ld) {
+    return (h->use_tma && ld >= 8 && h->cls_c.size() > 1) ? (int)h->cls_c.size() - 1 : 0;
 }
 
 static ams_status launch_local(ams_handle h, int ld, const ResidIn& in, bool with_state,
@@ -1401,7 +1436,7 @@ static ams_status apply_two_grid(ams_handle h, const LaunchCtx& L, int mode, con
     AMS_TRY(launch_local(h, L.ld, rin, with_state, false));
     launch_tg_scale(L2, h->prec, h->d_zf, omega, nv);
     prof_end(h);
-    h->launches += 2;
+    h->launches += 2 + local_extra_launches(h, L.ld);
     if (h->Nc > 0) {   // without a coarse space x^2 = x^1
         prof_begin(h, AMS_KERNEL_COARSE);
         launch_tg_resid(L2, h->d_zf, h->prec == AMS_PREC_FP64, rin, h->d_tw);
@@ -1424,7 +1459,7 @@ static ams_status apply_two_grid(ams_handle h, const LaunchCtx& L, int mode, con
     prof_begin(h, AMS_KERNEL_PROLONG);
     launch_prolong_update(L2, h->prec, a);
     prof_end(h);
-    h->launches += 5;   // prolongation, residual, local solves, combine, prolongation
+    h->launches += 5 + local_extra_launches(h, L.ld);   // prolongation, residual, local solves, combine, prolongation
     AMS_CUDA_TRY(cudaGetLastError());
     return AMS_OK;
 }
@@ -1441,7 +1476,7 @@ static ams_status apply_precond(ams_handle h, const LaunchCtx& L, int mode, cons
     prof_begin(h, AMS_KERNEL_LOCAL);
     AMS_TRY(launch_local(h, L.ld, ResidIn{h->d_r, mode == 2 ? h->d_q : nullptr, h->d_sc}, with_state));
     prof_end(h);
-    h->launches += 2;
+    h->launches += 2 + local_extra_launches(h, L.ld);
     if (coarse) {
         prof_begin(h, AMS_KERNEL_COARSE);
         h->launches += launch_coarse(h, L.ld, with_state);
@@ -1458,8 +1493,9 @@ static ams_status apply_precond(ams_handle h, const LaunchCtx& L, int mode, cons
 
 static int launches_per_iteration(ams_handle h, int ld) {
     const int coarse = h->Nc > 0 ? (fused_backward(ld) ? 1 : 2) : 0;
-    if (h->opt.two_grid_omega > 0.0) return 9 + (h->Nc > 0 ? 2 + coarse : 0);
-    return 4 + coarse;
+    const int extra = local_extra_launches(h, ld);
+    if (h->opt.two_grid_omega > 0.0) return 9 + 2 * extra + (h->Nc > 0 ? 2 + coarse : 0);
+    return 4 + extra + coarse;
 }
 
 static void launch_direction_spmv(ams_handle h, const LaunchCtx& L, const double* p_old, double* p_new) {

@@ -124,13 +124,14 @@ k_local_mma(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict__
             const int64_t* __restrict__ tile_row0, const float* __restrict__ piv, const double* __restrict__ rin,
             const double* __restrict__ qin, const CgScalars* __restrict__ csc, float* __restrict__ zf,
             const TP* __restrict__ psi, float* __restrict__ rc, int ld, int cmax, int depth, int64_t budget,
-            SolveState* st, int32_t* err, int probe) {
+            SolveState* st, int32_t* err, int probe, const int32_t* __restrict__ order) {
     static_assert(MM == 8 || MM == 16, "basis blocks of up to 8 or 16 modes");
     pdl_wait();
     if (st != nullptr && st->done) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_align1024(smem_raw);
-    const SubInfo S = subs[blockIdx.x];
+    const int sid = order != nullptr ? order[blockIdx.x] : (int)blockIdx.x;
+    const SubInfo S = subs[sid];
     const int c = S.c, nb = S.nb, n = S.n, m = S.m;
     const int D = depth;
     const int nbuf = cmax + D + 1;
@@ -142,7 +143,7 @@ k_local_mma(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict__
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, t = lane & 3;
     const int cb = warp * 8 * NF;
-    const int64_t trow = tile_row0[blockIdx.x];
+    const int64_t trow = tile_row0[sid];
     const uint32_t tile_bytes = 4096u * (uint32_t)c;
     uint32_t phase = 0, pend = 0;    // as in k_local_tma: change only when a wait succeeds
     bool ok = true;
@@ -459,21 +460,35 @@ static int local_mma_depth(int cmax, int ld) {
     return d;
 }
 
+// One launch over all subdomains, or (a.nclass > 1) one per band-width
+// group with the ring sized for that width: narrow subdomains then take
+// less shared memory and more of their blocks share an SM.
 template <typename TP, int NF, int MM>
 static cudaError_t mma_nf(const LocalTmaArgs& a, const void* psi, void* zf, void* rc) {
     const int warps = a.ld / (8 * NF);
-    const int depth = a.depth > 0 ? a.depth : local_mma_depth(a.cmax, a.ld);
-    const size_t smem = local_mma_smem(a.cmax, a.ld, depth);
     auto kern = k_local_mma<TP, NF, MM>;
     static size_t smem_set = 0;
-    if (smem > smem_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto launch = [&](int nsub, int cmax, const int32_t* order) -> cudaError_t {
+        const int depth = a.depth > 0 ? a.depth : local_mma_depth(cmax, a.ld);
+        const size_t smem = local_mma_smem(cmax, a.ld, depth);
+        if (smem > smem_set) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            smem_set = smem;
+        }
+        return launch_kernel(a.pdl, kern, dim3(nsub), dim3(warps * 32), smem, a.stream, *a.tmF, a.subs,
+                             a.tile_row0, a.piv, a.in.r, a.in.q, a.in.sc, (float*)zf, (const TP*)psi, (float*)rc,
+                             a.ld, cmax, depth, a.budget, a.st, a.err, a.probe, order);
+    };
+    if (a.nclass <= 1 || a.order == nullptr) return launch(a.nsub, a.cmax, nullptr);
+    const int32_t* ord = a.order;
+    for (int k = 0; k < a.nclass; ++k) {
+        if (a.class_n[k] == 0) continue;
+        const cudaError_t e = launch(a.class_n[k], a.class_c[k], ord);
         if (e != cudaSuccess) return e;
-        smem_set = smem;
+        ord += a.class_n[k];
     }
-    return launch_kernel(a.pdl, kern, dim3(a.nsub), dim3(warps * 32), smem, a.stream, *a.tmF, a.subs, a.tile_row0,
-                         a.piv, a.in.r, a.in.q, a.in.sc, (float*)zf, (const TP*)psi, (float*)rc, a.ld, a.cmax, depth,
-                         a.budget, a.st, a.err, a.probe);
+    return cudaSuccess;
 }
 
 // Right-hand sides per warp: 8 or 16 (a.nr; 0 = 8), at most four warps per

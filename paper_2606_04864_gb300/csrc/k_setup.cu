@@ -247,13 +247,16 @@ __device__ inline void ahat_mult(const SubInfo& Sb, int P, const int64_t* rowptr
 // Rayleigh-Ritz on span(Y) for the pencil (\hat A, S):
 //   G = Y^T S Y = R^T R,  C = R^{-T} (Y^T \hat A Y) R^{-1} = W Theta W^T,
 //   T = R^{-1} W  (new basis X = Y T is S-orthonormal, Ritz values Theta).
-// One thread block per subdomain; the p x p work is done by warp 0.
+// orth_only = 1: only the S-orthonormalisation T = R^{-1} (same span; no
+// Ritz values), for the subspace iterations between convergence checks.
+// One thread block per subdomain; the small dense work is done by warp 0,
+// the Jacobi rotations by the whole block.
 __global__ void __launch_bounds__(256)
 k_eig_rr(const SubInfo* __restrict__ subs, int P, const int64_t* __restrict__ rowptr,
          const int32_t* __restrict__ colind, const double* __restrict__ vals,
          const double* __restrict__ S, const double* __restrict__ ahat_diag,
          const double* __restrict__ Y, double* __restrict__ AY, double* __restrict__ Tout,
-         double* __restrict__ theta, int32_t* status) {
+         double* __restrict__ theta, int32_t* status, int orth_only) {
     const SubInfo Sb = subs[blockIdx.x];
     const int p = Sb.p;
     if (p == 0) return;
@@ -263,7 +266,7 @@ k_eig_rr(const SubInfo* __restrict__ subs, int P, const int64_t* __restrict__ ro
     double* W = H + P * P;          // P*P
     double* Rm = W + P * P;         // P*P (R, then R^{-1})
     double* ev = Rm + P * P;        // P
-    ahat_mult(Sb, P, rowptr, colind, vals, ahat_diag, Y, AY);
+    if (!orth_only) ahat_mult(Sb, P, rowptr, colind, vals, ahat_diag, Y, AY);
     __syncthreads();
     // Gram matrices (upper triangles): one warp per pair (a, b), lanes over
     // the subdomain's rows, partial sums combined by a fixed shuffle tree
@@ -282,7 +285,7 @@ k_eig_rr(const SubInfo* __restrict__ subs, int P, const int64_t* __restrict__ ro
                 const int64_t r = Sb.row0 + i;
                 const double ya = Y[r * P + a];
                 g += S[r] * ya * Y[r * P + b];
-                h += ya * AY[r * P + b];
+                if (!orth_only) h += ya * AY[r * P + b];
             }
             for (int off = 16; off > 0; off >>= 1) {
                 g += __shfl_xor_sync(0xffffffffu, g, off);
@@ -344,6 +347,17 @@ k_eig_rr(const SubInfo* __restrict__ subs, int P, const int64_t* __restrict__ ro
     __syncwarp();
     for (int t = lane; t < p * p; t += 32) Rm[t / p * P + t % p] = W[t / p * P + t % p];
     __syncwarp();
+    if (orth_only) {   // T = R^{-1}  (P x P, zero beyond p)
+        double* T = Tout + (int64_t)blockIdx.x * P * P;
+        for (int t = lane; t < P * P; t += 32) {
+            const int a = t / P, b = t % P;
+            T[t] = (a < p && b < p && a <= b) ? Rm[a * P + b] : 0.0;
+        }
+    }
+    }   // tid < 32
+    __syncthreads();
+    if (orth_only) return;
+    if (tid < 32) {
     // C = R^{-T} H R^{-1}: first HR = H R^{-1} into W, then C into G
     for (int t = lane; t < p * p; t += 32) {
         const int a = t / p, b = t % p;
@@ -699,10 +713,11 @@ void launch_eig_init(cudaStream_t s, int nsub, const SubInfo* subs, int P, doubl
 }
 void launch_eig_rr(cudaStream_t s, int nsub, const SubInfo* subs, int P, const int64_t* rowptr,
                    const int32_t* colind, const double* vals, const double* S, const double* ahat_diag,
-                   const double* Y, double* AY, double* T, double* theta, int32_t* status) {
+                   const double* Y, double* AY, double* T, double* theta, int32_t* status, int orth_only) {
     const size_t smem = (size_t)(4 * P * P + P) * sizeof(double);
     cudaFuncSetAttribute(k_eig_rr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_eig_rr<<<nsub, 256, smem, s>>>(subs, P, rowptr, colind, vals, S, ahat_diag, Y, AY, T, theta, status);
+    k_eig_rr<<<nsub, 256, smem, s>>>(subs, P, rowptr, colind, vals, S, ahat_diag, Y, AY, T, theta, status,
+                                     orth_only);
 }
 void launch_eig_update(cudaStream_t s, int64_t nrows_pad, int P, const int32_t* sub_of_row,
                        const SubInfo* subs, const double* Y, const double* T, double* X) {

@@ -96,6 +96,12 @@ struct LocalTmaArgs {
                              // kept (not marked evict-first): the backward sweep reloads them soonest
     int32_t* err;            // status word set to AMS_ERR_DEVICE_TIMEOUT when a wait runs out (or NULL)
     int probe;               // 1: every block first waits on a barrier nothing completes (timeout test)
+    // several-RHS kernel: subdomains grouped by band width, one launch per
+    // group sized for its own width (nclass <= 1: one launch over all)
+    int nclass = 0;
+    const int* class_c = nullptr;        // host: band tiles of each group
+    const int* class_n = nullptr;        // host: subdomains of each group
+    const int32_t* order = nullptr;      // device: subdomain ids, group after group
 };
 
 struct CoarseLaunch {
@@ -202,7 +208,8 @@ void launch_band_cholesky(const BandArgs& a, double* band, int32_t* status);
 void launch_eig_init(cudaStream_t s, int nsub, const SubInfo* subs, int P, double* X);
 void launch_eig_rr(cudaStream_t s, int nsub, const SubInfo* subs, int P, const int64_t* rowptr,
                    const int32_t* colind, const double* vals, const double* S, const double* ahat_diag,
-                   const double* Y, double* AY, double* T, double* theta, int32_t* status);
+                   const double* Y, double* AY, double* T, double* theta, int32_t* status,
+                   int orth_only);
 void launch_eig_update(cudaStream_t s, int64_t nrows_pad, int P, const int32_t* sub_of_row,
                        const SubInfo* subs, const double* Y, const double* T, double* X);
 void launch_eig_resid(cudaStream_t s, int nsub, const SubInfo* subs, int P, const int64_t* rowptr,
