@@ -122,7 +122,7 @@ struct ams_handle_s {
     int cmax = 1, mmax = 0, nbmax = 1;
     // subdomains grouped by band width (several-RHS local solve: one launch
     // per group; empty when every subdomain has the same width)
-    std::vector<int> cls_c, cls_n;
+    std::vector<int> cls_c, cls_n, cls_nb;
     int32_t* d_cls_order = nullptr;
     int num_sms = 1;                    // SMs of the handle's device
     bool use_pdl = false;               // solve-loop kernels overlap their prologue with the previous kernel
@@ -1053,19 +1053,21 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     {
         std::vector<int32_t> order;
         for (int c = 1; c <= h->cmax; ++c) {
-            int cnt = 0;
+            int cnt = 0, nbm = 1;
             for (int32_t i = 0; i < h->N; ++i)
                 if (h->h_subs[i].c == c) {
                     order.push_back(i);
                     ++cnt;
+                    nbm = std::max(nbm, (int)h->h_subs[i].nb);
                 }
             if (cnt > 0) {
                 h->cls_c.push_back(c);
                 h->cls_n.push_back(cnt);
+                h->cls_nb.push_back(nbm);
             }
         }
         if (h->cls_c.size() > 1) AMS_TRY(upload(h.get(), &h->d_cls_order, order));
-        else h->cls_c.clear(), h->cls_n.clear();
+        else h->cls_c.clear(), h->cls_n.clear(), h->cls_nb.clear();
     }
     // shared-memory staging limits of the local solve
     {
@@ -1283,6 +1285,7 @@ static LocalTmaArgs local_tma_args(ams_handle h, int ld, const ResidIn& in, bool
     a.nclass = (int)h->cls_c.size();
     a.class_c = h->cls_c.data();
     a.class_n = h->cls_n.data();
+    a.class_nb = h->cls_nb.data();
     a.order = h->d_cls_order;
     return a;
 }

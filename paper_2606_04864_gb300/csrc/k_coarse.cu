@@ -273,23 +273,28 @@ k_coarse_mma(const CoarseItem* __restrict__ items, const float* __restrict__ mat
         }
     }
     cp_async_wait_all();
-    // sum the warps' partial tiles in warp order (the ring is free now)
+    // sum the warps' partial tiles in warp order (the ring is free now);
+    // rows padded to LD + 8 floats: the 8-byte stores of a warp fill the
+    // 32 banks twice, the minimum for 256 bytes
+    constexpr int SR = LD + 8;
     __syncthreads();
-    float* red = s_ring;                                     // NW x 32 x LD
+    float* red = s_ring;                                     // NW x 32 x SR
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < NFR; ++b)
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-                red[(w * 32 + 16 * a + g + 8 * (i >> 1)) * LD + 8 * b + 2 * tq + (i & 1)] = acc[a][b][i];
+            for (int h = 0; h < 2; ++h)
+                *reinterpret_cast<float2*>(red + (w * 32 + 16 * a + g + 8 * h) * SR + 8 * b + 2 * tq) =
+                    make_float2(acc[a][b][2 * h], acc[a][b][2 * h + 1]);
     __syncthreads();
     float res[OUT / NT];                                     // outputs o = t + NT u
 #pragma unroll
     for (int u = 0; u < OUT / NT; ++u) {
-        float v = red[t + NT * u];
+        const int o = t + NT * u, ro = (o / LD) * SR + o % LD;
+        float v = red[ro];
 #pragma unroll
-        for (int ww = 1; ww < NW; ++ww) v += red[ww * OUT + t + NT * u];
+        for (int ww = 1; ww < NW; ++ww) v += red[ww * 32 * SR + ro];
         res[u] = v;
     }
     if (it.nchunks == 1) {

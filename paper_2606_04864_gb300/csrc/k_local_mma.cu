@@ -27,6 +27,7 @@
 // of nbuf = cmax + depth + 1 slots with bounded mbarrier waits.  The
 // backward sweep reads the same tiles transposed.  Warp w of a block owns
 // columns [8 NF w, 8 NF (w+1)) of the subdomain's right-hand sides.
+#include <algorithm>
 #include <cstdint>
 
 #include <cuda.h>
@@ -468,8 +469,9 @@ static cudaError_t mma_nf(const LocalTmaArgs& a, const void* psi, void* zf, void
     const int warps = a.ld / (8 * NF);
     auto kern = k_local_mma<TP, NF, MM>;
     static size_t smem_set = 0;
-    auto launch = [&](int nsub, int cmax, const int32_t* order) -> cudaError_t {
-        const int depth = a.depth > 0 ? a.depth : local_mma_depth(cmax, a.ld);
+    auto launch = [&](int nsub, int cmax, int nbmax, const int32_t* order) -> cudaError_t {
+        // no deeper than the group's block rows: the rest of the ring would stay unused
+        const int depth = std::max(1, std::min(a.depth > 0 ? a.depth : local_mma_depth(cmax, a.ld), nbmax));
         const size_t smem = local_mma_smem(cmax, a.ld, depth);
         if (smem > smem_set) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -480,11 +482,11 @@ static cudaError_t mma_nf(const LocalTmaArgs& a, const void* psi, void* zf, void
                              a.tile_row0, a.piv, a.in.r, a.in.q, a.in.sc, (float*)zf, (const TP*)psi, (float*)rc,
                              a.ld, cmax, depth, a.budget, a.st, a.err, a.probe, order);
     };
-    if (a.nclass <= 1 || a.order == nullptr) return launch(a.nsub, a.cmax, nullptr);
+    if (a.nclass <= 1 || a.order == nullptr) return launch(a.nsub, a.cmax, a.nbmax, nullptr);
     const int32_t* ord = a.order;
     for (int k = 0; k < a.nclass; ++k) {
         if (a.class_n[k] == 0) continue;
-        const cudaError_t e = launch(a.class_n[k], a.class_c[k], ord);
+        const cudaError_t e = launch(a.class_n[k], a.class_c[k], a.class_nb[k], ord);
         if (e != cudaSuccess) return e;
         ord += a.class_n[k];
     }

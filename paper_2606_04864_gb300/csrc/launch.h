@@ -101,6 +101,7 @@ struct LocalTmaArgs {
     int nclass = 0;
     const int* class_c = nullptr;        // host: band tiles of each group
     const int* class_n = nullptr;        // host: subdomains of each group
+    const int* class_nb = nullptr;       // host: most block rows of a subdomain in each group
     const int32_t* order = nullptr;      // device: subdomain ids, group after group
 };
 

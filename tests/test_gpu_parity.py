@@ -227,6 +227,32 @@ def test_batched_uneven_systems_match_oracle():
                 assert np.linalg.norm(us[i][k] - ref.u) <= tol * np.linalg.norm(ref.u)
 
 
+@pytest.mark.parametrize("nrhs", [8, 16])
+def test_batched_mixed_band_widths_many_rhs(nrhs):
+    """Systems whose subdomains have different band widths (8x8 2-D blocks:
+    one 32-row band tile; 8^3 3-D blocks: two) with 8 and 16 right-hand
+    sides, where the tensor-core local solve launches once per band-width
+    group over an index list: iterations and solutions against the oracle."""
+    ws = [make_small_2d(side=40, bs=8, m=4, std=2.0, seed=53),
+          make_small_3d(side=16, bs=8, m=6, std=2.5, seed=54),
+          make_small_2d(side=24, bs=8, m=5, std=2.0, seed=55, ny=41)]
+    systems = [(w.rowptr, w.colind, w.vals, w.part, w.nparts, w.m) for w in ws]
+    rhs = [np.random.default_rng(70 + i).standard_normal((nrhs, w.n)) for i, w in enumerate(ws)]
+    refs = []
+    for i, w in enumerate(ws):
+        A = _A(w)
+        o = OracleAMS(A, w.part, w.nparts, w.m, basis_round="bf16")
+        refs.append([pcg(A, rhs[i][k], o.apply, rtol=1e-8) for k in range(nrhs)])
+    b = AmsBatchedSolver(systems, precision="fp32_bf16")
+    assert b.info()["max_band_tiles"] == 2
+    u, its, rel = b.solve(b.pack(rhs), nrhs, rtol=1e-8)
+    us = b.unpack(u, nrhs)
+    for i, w in enumerate(ws):
+        for k in range(nrhs):
+            assert abs(int(its[i, k]) - refs[i][k].iters) <= 2, (i, k, its[i, k], refs[i][k].iters)
+            assert np.linalg.norm(us[i][k] - refs[i][k].u) <= 1e-6 * np.linalg.norm(refs[i][k].u)
+
+
 # ------------------------------------------------------------- edge cases
 
 def test_isolated_dofs_and_tiny_subdomains():
