@@ -649,12 +649,12 @@ def run_gpu(args):
     f_pin = torch.empty(rhs_host.shape, dtype=torch.float64).pin_memory()
     f_pin.copy_(torch.as_tensor(rhs_host))
     f_np = f_pin.numpy()
-    u_np_pin = None
-    if not batched:   # the solution goes straight into pinned host memory
-        u_np_pin = torch.empty((nrhs, n_total), dtype=torch.float64).pin_memory().numpy()
+    # the solution goes straight into pinned host memory
+    u_np_pin = torch.empty(tuple(f_pin.shape), dtype=torch.float64).pin_memory().numpy()
+    if not batched:
         solve_host = lambda s_, f_: s_.solve(f_, rtol=1e-8, out=u_np_pin)   # noqa: E731
     else:
-        solve_host = solve
+        solve_host = lambda s_, f_: s_.solve(f_, nrhs, rtol=1e-8, out=u_np_pin)   # noqa: E731
     solve_host(host, f_np)
     barrier()
     t0 = time.perf_counter()

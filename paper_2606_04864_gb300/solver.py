@@ -397,11 +397,24 @@ class AmsBatchedSolver(_Base):
         return [{"name": KERNEL_NAMES[k], "ms": float(ms[k]), "count": int(cnt[k]), "bytes": float(by[k])}
                 for k in range(AMS_NUM_KERNELS)]
 
-    def solve(self, f_flat, nrhs: int, rtol: float = 1e-8, allow_not_converged: bool = False):
+    def solve(self, f_flat, nrhs: int, rtol: float = 1e-8, allow_not_converged: bool = False, out=None):
         """f_flat in the ABI layout (see :meth:`pack`).  Returns (u_flat,
-        iters[nsys, nrhs], relres[nsys, nrhs])."""
+        iters[nsys, nrhs], relres[nsys, nrhs]).  ``out``: optional float64
+        C-contiguous buffer shaped like f_flat, of the solver's pointer mode,
+        to write u into (e.g. pinned host memory)."""
         fv = _as_dev(f_flat, np.float64) if self.device else _as_host(f_flat, np.float64)
-        u = (_torch().empty_like(fv) if self.device else np.empty_like(fv))
+        if out is None:
+            u = (_torch().empty_like(fv) if self.device else np.empty_like(fv))
+        else:
+            torch = _torch() if self.device else None
+            ok = (tuple(out.shape) == tuple(fv.shape) and
+                  ((isinstance(out, torch.Tensor) and out.is_cuda and out.dtype == torch.float64
+                    and out.is_contiguous()) if self.device else
+                   (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags["C_CONTIGUOUS"])))
+            if not ok:
+                raise ValueError("out must be a C-contiguous float64 buffer shaped like f_flat, "
+                                 + ("a CUDA tensor" if self.device else "a host array"))
+            u = out
         its = np.zeros(self.nsys * nrhs, dtype=np.int32)
         rel = np.zeros(self.nsys * nrhs, dtype=np.float64)
         st = lib().ams_solve(self._h, _ptr(fv), int(nrhs), float(rtol), _ptr(u), _ptr(its), _ptr(rel))

@@ -246,6 +246,9 @@ def test_batched_mixed_band_widths_many_rhs(nrhs):
     b = AmsBatchedSolver(systems, precision="fp32_bf16")
     assert b.info()["max_band_tiles"] == 2
     u, its, rel = b.solve(b.pack(rhs), nrhs, rtol=1e-8)
+    buf = np.empty_like(u)
+    u2, _, _ = b.solve(b.pack(rhs), nrhs, rtol=1e-8, out=buf)   # into a caller buffer: the same solve
+    assert u2 is buf and np.array_equal(buf, u)
     us = b.unpack(u, nrhs)
     for i, w in enumerate(ws):
         for k in range(nrhs):
