@@ -469,6 +469,19 @@ ams_status ams_profile_solve(ams_handle h, const double* f, int32_t nrhs,
 ams_status ams_check_conversions(const double* x, int64_t n, int64_t* narrow_bad, int64_t* widen_bad);
 
 /*
+ * Checking build (libams_debug.so, compiled with -DAMS_DEBUG): the solve
+ * kernels check the indices they gather through (matrix columns, coarse
+ * gather lists, subdomain row ranges, the caller-order permutation); a
+ * failed check records its site and skips the access, and the call that
+ * launched it returns AMS_ERR_CUDA naming the site (ams_last_error).  This
+ * entry point launches a kernel that fails one check on purpose, site 99,
+ * without touching memory, and returns the recorded site in *site: 99 in
+ * the checking build, 0 in the release build (checks compiled out).  Not a
+ * method step (no section of the paper): a test hook of the library.
+ */
+ams_status ams_debug_selftest(int32_t* site);
+
+/*
  * ams_csr_spmv_dot_noalloc — y = A x and *xy = x^T y for a CSR matrix, with
  * no handle and no device allocation.  The paper has no counterpart: this
  * is a service for callers that cannot allocate device memory at the

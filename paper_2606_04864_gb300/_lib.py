@@ -12,7 +12,9 @@ import os
 import threading
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libams.so")
+# AMS_LIBRARY=debug selects the checking build (device-side index checks;
+# see _build.py), anything else the release build
+LIB_PATH = os.path.join(_PKG, "libams_debug.so" if os.environ.get("AMS_LIBRARY") == "debug" else "libams.so")
 
 AMS_OK = 0
 STATUS_NAMES = {
@@ -108,6 +110,7 @@ SIGNATURES = {
     "ams_get_coarse_basis": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ams_get_coarse_matrix": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ams_get_coarse_factor_inverse": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ams_debug_selftest": (C.c_int, [C.c_void_p]),
     "ams_apply_preconditioner": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ams_spmv": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p]),
     "ams_time_kernel": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.POINTER(C.c_double),
@@ -130,8 +133,8 @@ def lib() -> C.CDLL:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
                 raise RuntimeError(
-                    f"libams.so not found at {LIB_PATH}; build it with "
-                    "`python -c 'import __graft_entry__ as g; g.build()'`")
+                    f"{os.path.basename(LIB_PATH)} not found at {LIB_PATH}; build it with "
+                    "`python -m paper_2606_04864_gb300._build` (add --debug for the checking build)")
             L = C.CDLL(LIB_PATH)
             for name, (res, args) in SIGNATURES.items():
                 fn = getattr(L, name)

@@ -915,6 +915,8 @@ static ams_status setup_coarse(ams_handle h, const std::vector<SysInput>& inputs
 }
 
 static ams_status estimate_two_grid_omega(ams_handle h);
+static void debug_bounds(ams_handle h);
+static ams_status debug_check(ams_handle h, ams_status st);
 
 static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const ams_options* opt,
                              void* stream, ams_handle* out) {
@@ -1177,7 +1179,9 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     I.coarse_inverse_bytes = (h->R_elems + h->Q_elems) * (int64_t)h->tf_bytes();
     I.basis_bytes = h->psi_elems * (int64_t)h->tp_bytes();
     I.spmv_variant = 0;
+    debug_bounds(h.get());
     if (h->opt.two_grid_omega < 0.0) AMS_TRY(estimate_two_grid_omega(h.get()));
+    AMS_TRY(debug_check(h.get(), AMS_OK));
     I.two_grid_omega = h->opt.two_grid_omega;
     I.setup_seconds = now_s() - t0;
     *out = h.release();
@@ -1189,6 +1193,11 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
 // ---------------------------------------------------------------------------
 static ams_status ensure_work(ams_handle h, int ld) {
     if (ld > h->ld_alloc) {
+        // the cached iteration-loop graphs hold the old buffers' addresses
+        // in their kernel nodes: drop them before the buffers go
+        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        for (auto& g : h->loop_graph) cudaGraphExecDestroy(g.second);
+        h->loop_graph.clear();
         for (void* p : {(void*)h->d_x, (void*)h->d_r, (void*)h->d_p, (void*)h->d_p2, (void*)h->d_q, (void*)h->d_z, h->d_zf, h->d_rc,
                         h->d_yc, h->d_ec, (void*)h->d_stage_in, (void*)h->d_stage_out, (void*)h->d_stage_aux,
                         (void*)h->d_tw})
@@ -1873,6 +1882,37 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
     return AMS_OK;
 }
 
+// Checking build (-DAMS_DEBUG): point the device-side index checks at this
+// handle's sizes, and after a call turn a recorded failure into an error.
+// Release build: both do nothing.
+static void debug_bounds(ams_handle h) {
+#ifdef AMS_DEBUG
+    debug_set_bounds_solve(h->n_pad, h->Nc);
+    debug_set_bounds_coarse(h->n_pad, h->Nc);
+    debug_set_bounds_local_mma(h->n_pad, h->Nc);
+    debug_set_bounds_local_tma(h->n_pad, h->Nc);
+#else
+    (void)h;
+#endif
+}
+
+static ams_status debug_check(ams_handle h, ams_status st) {
+#ifdef AMS_DEBUG
+    cudaStreamSynchronize(h->stream);
+    int32_t site = 0;
+    for (int32_t v : {debug_take_site_solve(), debug_take_site_coarse(), debug_take_site_local_mma(),
+                      debug_take_site_local_tma()})
+        if (site == 0 && v != 0) site = v;
+    if (site != 0) {
+        set_error("AMS_DEBUG: a device-side index check failed (site " + std::to_string(site) + ")");
+        return AMS_ERR_CUDA;
+    }
+#else
+    (void)h;
+#endif
+    return st;
+}
+
 }  // namespace ams
 
 // ===========================================================================
@@ -1969,6 +2009,7 @@ static double kernel_bytes(ams_handle h, int which, int ld) {
 // Order the handle's internal stream after work already queued on the
 // caller's stream (the caller's inputs may be produced there).
 static ams_status enter(ams_handle h) {
+    debug_bounds(h);
     AMS_CUDA_TRY(cudaEventRecord(h->ev_enter, h->ustream));
     AMS_CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ev_enter, 0));
     return AMS_OK;
@@ -2017,7 +2058,7 @@ ams_status ams_solve(ams_handle h, const double* f, int32_t nrhs, double rtol, d
                                      h->stream));
         AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
     }
-    return st;
+    return debug_check(h, st);
 }
 
 ams_status ams_solve_adjoint(ams_handle h, const double* g, int32_t nrhs, double rtol, const double* u,
@@ -2059,7 +2100,7 @@ ams_status ams_solve_adjoint(ams_handle h, const double* g, int32_t nrhs, double
         AMS_CUDA_TRY(cudaMemcpyAsync(lambda, lam_dev, sizeof(double) * h->n_total * nrhs, cudaMemcpyDeviceToHost,
                                      h->stream));
     AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    return st;
+    return debug_check(h, st);
 }
 
 ams_status ams_set_matrix_values(ams_handle h, const double* vals) {
@@ -2244,6 +2285,19 @@ ams_status ams_get_coarse_factor_inverse(ams_handle h, int64_t* nd_paper, double
     return AMS_OK;
 }
 
+ams_status ams_debug_selftest(int32_t* site) {
+    g_last_error.clear();
+    if (!site) {
+        set_error("site pointer required");
+        return AMS_ERR_INVALID_ARG;
+    }
+    launch_debug_selftest(0);
+    AMS_CUDA_TRY(cudaGetLastError());
+    AMS_CUDA_TRY(cudaDeviceSynchronize());
+    *site = debug_take_site_solve();
+    return AMS_OK;
+}
+
 ams_status ams_apply_preconditioner(ams_handle h, const double* r, int32_t nrhs, double* z) {
     NvtxRange nvtx_range("ams_apply_preconditioner");
     g_last_error.clear();
@@ -2269,7 +2323,7 @@ ams_status ams_apply_preconditioner(ams_handle h, const double* r, int32_t nrhs,
     if (!h->opt.device_ptrs)
         AMS_CUDA_TRY(cudaMemcpyAsync(z, z_dev, sizeof(double) * h->n_total * nrhs, cudaMemcpyDeviceToHost, h->stream));
     AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    return device_status(h);
+    return debug_check(h, device_status(h));
 }
 
 ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y) {
@@ -2297,7 +2351,7 @@ ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y) {
     if (!h->opt.device_ptrs)
         AMS_CUDA_TRY(cudaMemcpyAsync(y, y_dev, sizeof(double) * h->n_total * nrhs, cudaMemcpyDeviceToHost, h->stream));
     AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    return AMS_OK;
+    return debug_check(h, AMS_OK);
 }
 
 ams_status ams_time_kernel(ams_handle h, int32_t which, int32_t reps, double* avg_ms, double* bytes) {

@@ -74,7 +74,7 @@ k_coarse_gemm(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
             if (kk < kn) {
                 const int k = kb + kk;
                 const int g = (it.gat_off < 0) ? g0 + k : __ldg(G + k);
-                xreg[u] = in[(int64_t)g * LD + hh];
+                if (AMS_COARSE_OK(g, 3)) xreg[u] = in[(int64_t)g * LD + hh];
             }
         }
     };
@@ -201,6 +201,7 @@ k_coarse_mma(const CoarseItem* __restrict__ items, const float* __restrict__ mat
         for (int u = 0; u < XV; ++u) {
             const int k = kb + (t + NT * u) / (LD / 4);
             gi[u] = (s < nst && k < it.k1) ? (contiguous ? g0 + k : __ldg(G + k)) : -1;
+            if (gi[u] >= 0 && !AMS_COARSE_OK(gi[u], 3)) gi[u] = -1;
         }
     };
     auto issue = [&](int s) {
@@ -378,8 +379,9 @@ k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
                 if (k < len) { g = s0 + k; break; }
                 k -= len;
             }
+            if (AMS_COARSE_OK(g, 3))
 #pragma unroll
-            for (int h = 0; h < LD; ++h) v[h] = in[(int64_t)g * LD + h];
+                for (int h = 0; h < LD; ++h) v[h] = in[(int64_t)g * LD + h];
         }
 #pragma unroll
         for (int h = 0; h < LD; ++h) sx[kk * LD + h] = v[h];
@@ -449,6 +451,8 @@ k_coarse_rows(const CoarseItem* __restrict__ items, const TF* __restrict__ mat,
     }
     if (t == 0) cnt[it.tile_id] = 0;
 }
+
+AMS_DEBUG_TU_HOOKS(coarse)
 
 // ---------------------------------------------------------------------------
 // launcher

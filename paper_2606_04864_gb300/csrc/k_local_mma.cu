@@ -133,6 +133,7 @@ k_local_mma(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict__
     unsigned char* base = smem_align1024(smem_raw);
     const int sid = order != nullptr ? order[blockIdx.x] : (int)blockIdx.x;
     const SubInfo S = subs[sid];
+    if (!AMS_ROW_OK(S.row0, 4) || !AMS_ROW_OK(S.row0 + S.n - 1, 4)) return;
     const int c = S.c, nb = S.nb, n = S.n, m = S.m;
     const int D = depth;
     const int nbuf = cmax + D + 1;
@@ -306,12 +307,27 @@ k_local_mma(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict__
         // t = r'_K - sum_d L_{K,K-c+d} y_{K-c+d}
         float acc[2][NF][4];
         zero_acc<NF>(acc);
-        for (int d = 0; d < c; ++d) {
-            const int src = K - c + d;
-            if (src < 0) continue;
-            const float* Y = ring + (size_t)(src % (c + 1)) * 32 * SY;
-            if (d == 0) tile_mma<1, false, NF>(slot_tile(K, 0), Y, SY, cb, g, t, acc);
-            else tile_mma<0, false, NF>(slot_tile(K, d), Y, SY, cb, g, t, acc);
+        if (c == 2 && K >= 2) {
+            // both band tiles present: separate accumulators, so that the two
+            // tiles' MMA chains are independent and interleave
+            float acc1[2][NF][4];
+            zero_acc<NF>(acc1);
+            tile_mma<1, false, NF>(slot_tile(K, 0), ring + (size_t)((K - 2) % 3) * 32 * SY, SY, cb, g, t, acc);
+            tile_mma<0, false, NF>(slot_tile(K, 1), ring + (size_t)((K - 1) % 3) * 32 * SY, SY, cb, g, t, acc1);
+#pragma unroll
+            for (int mf = 0; mf < 2; ++mf)
+#pragma unroll
+                for (int nf = 0; nf < NF; ++nf)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[mf][nf][i] += acc1[mf][nf][i];
+        } else {
+            for (int d = 0; d < c; ++d) {
+                const int src = K - c + d;
+                if (src < 0) continue;
+                const float* Y = ring + (size_t)(src % (c + 1)) * 32 * SY;
+                if (d == 0) tile_mma<1, false, NF>(slot_tile(K, 0), Y, SY, cb, g, t, acc);
+                else tile_mma<0, false, NF>(slot_tile(K, d), Y, SY, cb, g, t, acc);
+            }
         }
 #pragma unroll
         for (int mf = 0; mf < 2; ++mf)
@@ -399,13 +415,27 @@ k_local_mma(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict__
         // w = y_K - sum_d L_{K+d,K}^T x_{K+d}
         float acc[2][NF][4];
         zero_acc<NF>(acc);
-        for (int d = 1; d <= c; ++d) {
-            const int src = K + d;
-            if (src >= nb) break;
-            const float* X = ring + (size_t)(src % (c + 1)) * 32 * SY;
-            // L_{K+d,K}: dense tile c-d of block row K+d, or (d == c) the upper part of M_{K+c}
-            if (d < c) tile_mma<0, true, NF>(slot_tile(src, c - d), X, SY, cb, g, t, acc);
-            else tile_mma<1, true, NF>(slot_tile(src, 0), X, SY, cb, g, t, acc);
+        if (c == 2 && K + 2 < nb) {
+            // both transposed band tiles present: independent accumulators (as forward)
+            float acc1[2][NF][4];
+            zero_acc<NF>(acc1);
+            tile_mma<0, true, NF>(slot_tile(K + 1, 1), ring + (size_t)((K + 1) % 3) * 32 * SY, SY, cb, g, t, acc);
+            tile_mma<1, true, NF>(slot_tile(K + 2, 0), ring + (size_t)((K + 2) % 3) * 32 * SY, SY, cb, g, t, acc1);
+#pragma unroll
+            for (int mf = 0; mf < 2; ++mf)
+#pragma unroll
+                for (int nf = 0; nf < NF; ++nf)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) acc[mf][nf][i] += acc1[mf][nf][i];
+        } else {
+            for (int d = 1; d <= c; ++d) {
+                const int src = K + d;
+                if (src >= nb) break;
+                const float* X = ring + (size_t)(src % (c + 1)) * 32 * SY;
+                // L_{K+d,K}: dense tile c-d of block row K+d, or (d == c) the upper part of M_{K+c}
+                if (d < c) tile_mma<0, true, NF>(slot_tile(src, c - d), X, SY, cb, g, t, acc);
+                else tile_mma<1, true, NF>(slot_tile(src, 0), X, SY, cb, g, t, acc);
+            }
         }
 #pragma unroll
         for (int mf = 0; mf < 2; ++mf)
@@ -512,5 +542,7 @@ cudaError_t launch_local_mma(const LocalTmaArgs& a, int prec, const void* psi, v
     if (prec == AMS_PREC_FP32) return mma_tp<float>(a, psi, zf, rc);
     return mma_tp<__nv_bfloat16>(a, psi, zf, rc);
 }
+
+AMS_DEBUG_TU_HOOKS(local_mma)
 
 }  // namespace ams

@@ -131,6 +131,7 @@ k_local_tma(const __grid_constant__ CUtensorMap tmF, const __grid_constant__ CUt
     // 1024-byte aligned tile ring, then mbarriers, y/x ring, scratch
     unsigned char* base = smem_align1024(smem_raw);
     const SubInfo S = subs[blockIdx.x];
+    if (!AMS_ROW_OK(S.row0, 5) || !AMS_ROW_OK(S.row0 + S.n - 1, 5)) return;
     const int c = S.c, nb = S.nb, n = S.n;
     const int D = depth;
     const int nbuf = cmax + D + 1;
@@ -502,6 +503,7 @@ k_local_tma1(const __grid_constant__ CUtensorMap tmF, const SubInfo* __restrict_
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = smem_align1024(smem_raw);
     const SubInfo S = subs[blockIdx.x];
+    if (!AMS_ROW_OK(S.row0, 5) || !AMS_ROW_OK(S.row0 + S.n - 1, 5)) return;
     const int c = C1 ? 1 : S.c;
     const int nb = S.nb, n = S.n, m = S.m;
     const int D = depth;
@@ -942,5 +944,7 @@ cudaError_t make_tile_map(void* base, int64_t rows, CUtensorMap* out) {
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
+
+AMS_DEBUG_TU_HOOKS(local_tma)
 
 }  // namespace ams

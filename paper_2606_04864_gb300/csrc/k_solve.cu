@@ -70,7 +70,7 @@ k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
 #pragma unroll
         for (int j = 0; j < JU; ++j) {
             xv[j] = 0.0;
-            if (j < w) xv[j] = __ldg(p + (int64_t)col[j] * LD + rhs);
+            if (j < w && AMS_ROW_OK(col[j], 1)) xv[j] = __ldg(p + (int64_t)col[j] * LD + rhs);
         }
         double acc = 0.0;
 #pragma unroll
@@ -78,7 +78,8 @@ k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
             if (j < w) acc = fma(val[j], xv[j], acc);
         for (int j = JU; j < w; ++j) {
             const int64_t o = b0 + 32 * j + lane;
-            acc = fma(__ldg(sell_val + o), __ldg(p + (int64_t)__ldg(sell_col + o) * LD + rhs), acc);
+            const int cj = __ldg(sell_col + o);
+            if (AMS_ROW_OK(cj, 1)) acc = fma(__ldg(sell_val + o), __ldg(p + (int64_t)cj * LD + rhs), acc);
         }
         q[e] = acc;
         if (with_dot) dot[0] = fma(__ldg(p + e), acc, dot[0]);
@@ -462,8 +463,13 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
                 const int j0 = 4 * c4;
                 AT yv[4];
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    yv[e] = (j0 + e < cr.K) ? (AT)yc[(int64_t)__ldg(G + j0 + e) * LD + rhs] : AT(0);
+                for (int e = 0; e < 4; ++e) {
+                    yv[e] = AT(0);
+                    if (j0 + e < cr.K) {
+                        const int gi = __ldg(G + j0 + e);
+                        if (AMS_COARSE_OK(gi, 2)) yv[e] = (AT)yc[(int64_t)gi * LD + rhs];
+                    }
+                }
 #pragma unroll
                 for (int k = 0; k < MM; ++k) {
                     if (k < m) {
@@ -635,6 +641,7 @@ __global__ void k_permute_in(const double* __restrict__ f, int64_t n, int nrhs, 
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t row = int_row[i];
+    if (!AMS_ROW_OK(row, 6)) return;
     for (int k = 0; k < ld; ++k) {
         r[row * ld + k] = k < nrhs ? f[i + (int64_t)k * n] : 0.0;
         if (x != nullptr) x[row * ld + k] = 0.0;
@@ -646,6 +653,7 @@ __global__ void k_permute_out(const double* __restrict__ x, int64_t n, int nrhs,
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t row = int_row[i];
+    if (!AMS_ROW_OK(row, 6)) return;
     for (int k = 0; k < nrhs; ++k) u[i + (int64_t)k * n] = x[row * ld + k];
 }
 
@@ -831,5 +839,13 @@ void launch_scatter_vals(cudaStream_t s, const double* vals, const int64_t* pos,
 void launch_zero(cudaStream_t s, double* a, int64_t n) {
     if (n > 0) k_zero<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, n);
 }
+
+// ---------------------------------------------------------------------------
+// checking-build hooks and self-test (see kernels.cuh)
+// ---------------------------------------------------------------------------
+AMS_DEBUG_TU_HOOKS(solve)
+
+__global__ void k_debug_selftest() { (void)AMS_ROW_OK(-1, 99); }
+void launch_debug_selftest(cudaStream_t s) { k_debug_selftest<<<1, 1, 0, s>>>(); }
 
 }  // namespace ams

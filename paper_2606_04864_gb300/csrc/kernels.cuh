@@ -57,6 +57,55 @@ template <> __device__ __forceinline__ float from_d<float>(double v) { return (f
 template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
 
 // ---------------------------------------------------------------------------
+// Checking build (-DAMS_DEBUG): index checks on the gathers of the solve
+// kernels.  A failed check records its site number in this translation
+// unit's error word (the first one wins) and the access is skipped (the
+// value read as 0, or the subdomain left out); the host API reads the words
+// after each call and returns AMS_ERR_CUDA naming the site.  Nothing traps.
+// The bounds (internal rows, coarse rows) are per process: one handle at a
+// time in the checking build.  In the release build the checks compile to
+// `true` and the hooks do nothing.
+// Sites: 1 SpMV column, 2 prolongation gather of y, 3 coarse-product
+// gather, 4 several-RHS local solve rows, 5 one/few-RHS local solve rows,
+// 6 caller-order permutation, 99 the self-test.
+// ---------------------------------------------------------------------------
+struct DebugBounds {
+    int64_t n_rows;     // internal rows of all systems (padded)
+    int64_t n_coarse;   // coarse rows of all systems
+};
+#ifdef AMS_DEBUG
+static __constant__ DebugBounds c_dbg_bounds;
+static __device__ int32_t g_dbg_site;
+__device__ __forceinline__ bool dbg_index_ok(int64_t i, int64_t hi, int site) {
+    if (i >= 0 && i < hi) return true;
+    atomicCAS(&g_dbg_site, 0, site);
+    return false;
+}
+#define AMS_ROW_OK(i, site) ::ams::dbg_index_ok((int64_t)(i), ::ams::c_dbg_bounds.n_rows, (site))
+#define AMS_COARSE_OK(i, site) ::ams::dbg_index_ok((int64_t)(i), ::ams::c_dbg_bounds.n_coarse, (site))
+#define AMS_DEBUG_TU_HOOKS(tu)                                                            \
+    void debug_set_bounds_##tu(int64_t n_rows, int64_t n_coarse) {                        \
+        const DebugBounds b{n_rows, n_coarse};                                            \
+        cudaMemcpyToSymbol(c_dbg_bounds, &b, sizeof(b));                                  \
+    }                                                                                     \
+    int32_t debug_take_site_##tu() {                                                      \
+        int32_t v = 0;                                                                    \
+        if (cudaMemcpyFromSymbol(&v, g_dbg_site, sizeof(v)) != cudaSuccess) return -1;    \
+        if (v != 0) {                                                                     \
+            const int32_t z = 0;                                                          \
+            cudaMemcpyToSymbol(g_dbg_site, &z, sizeof(z));                                \
+        }                                                                                 \
+        return v;                                                                         \
+    }
+#else
+#define AMS_ROW_OK(i, site) true
+#define AMS_COARSE_OK(i, site) true
+#define AMS_DEBUG_TU_HOOKS(tu)                                                            \
+    void debug_set_bounds_##tu(int64_t, int64_t) {}                                       \
+    int32_t debug_take_site_##tu() { return 0; }
+#endif
+
+// ---------------------------------------------------------------------------
 // Programmatic dependent launch.  Kernels of the solve loop are launched so
 // that they may start while the previous kernel on the stream drains: work
 // that reads only setup data (matrix, factor tiles, basis) runs first, then

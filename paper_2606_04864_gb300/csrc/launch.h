@@ -229,6 +229,20 @@ void launch_galerkin(cudaStream_t s, int nsub, const SubInfo* subs, const int64_
                      int mmax, double* Ac, int64_t ldA, int64_t coff0, int sub0);
 void launch_extract_chunks(cudaStream_t s, int nchunks, const int64_t* desc, const int32_t* rng,
                            const double* Linv, int64_t ldL, double* out64, float* out32);
+// Checking-build hooks of the translation units with index checks (no-ops
+// in the release build; see kernels.cuh).
+void debug_set_bounds_solve(int64_t n_rows, int64_t n_coarse);
+void debug_set_bounds_coarse(int64_t n_rows, int64_t n_coarse);
+void debug_set_bounds_local_mma(int64_t n_rows, int64_t n_coarse);
+void debug_set_bounds_local_tma(int64_t n_rows, int64_t n_coarse);
+int32_t debug_take_site_solve();
+int32_t debug_take_site_coarse();
+int32_t debug_take_site_local_mma();
+int32_t debug_take_site_local_tma();
+// launches a kernel that fails one check on purpose (site 99) without any
+// memory access; the site then reads back from debug_take_site_solve()
+void launch_debug_selftest(cudaStream_t s);
+
 // Tile Cholesky factor of A_0 and its inverse (k_coarse_factor.cu).  The
 // plan lists, per step, the kept 64 x 64 tiles of the nested-dissection
 // pattern: row tiles of the TRSM of column k, (i, j) pairs of its update,

@@ -256,6 +256,29 @@ def test_batched_mixed_band_widths_many_rhs(nrhs):
             assert np.linalg.norm(us[i][k] - refs[i][k].u) <= 1e-6 * np.linalg.norm(refs[i][k].u)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_bf16"])
+def test_fewer_rhs_after_more_replays_no_stale_buffers(prec):
+    """A solve with fewer right-hand sides after one with more: the larger
+    solve grows the work buffers, and the iteration-loop graph of the smaller
+    count, captured before, must not replay on the freed ones.  The same
+    solve before and after (with an apply and an SpMV between) is bit-equal,
+    and matches the oracle."""
+    w = make_small_2d(side=45, bs=10, m=3, std=2.0, sigma=3.0, seed=31, ny=37)
+    A = _A(w)
+    f = np.random.default_rng(6).standard_normal((32, w.n))
+    s = _solver(w, precision=prec)
+    u1, i1, _ = s.solve(f[:1], rtol=1e-8)
+    u32, i32, _ = s.solve(f, rtol=1e-8)
+    s.apply_preconditioner(f[:4])
+    s.spmv(f[:2])
+    u1b, i1b, _ = s.solve(f[:1], rtol=1e-8)
+    assert np.array_equal(np.asarray(u1), np.asarray(u1b)) and int(i1[0]) == int(i1b[0])
+    ref = pcg(A, f[0], OracleAMS(A, w.part, w.nparts, w.m).apply, rtol=1e-8)
+    tol = 1e-10 if prec == "fp64" else 1e-6
+    assert np.linalg.norm(np.atleast_2d(u1b)[0] - ref.u) <= tol * np.linalg.norm(ref.u)
+    assert np.linalg.norm(np.asarray(u32)[0] - ref.u) <= tol * np.linalg.norm(ref.u)
+
+
 # ------------------------------------------------------------- edge cases
 
 def test_isolated_dofs_and_tiny_subdomains():

@@ -37,6 +37,16 @@ def test_every_declared_symbol_is_exported(built_lib):
     assert not missing, missing
 
 
+def test_checking_build_exports_the_same_boundary(built_lib):
+    """The AMS_DEBUG variant (device-side index checks) builds from the same
+    sources and exports every declared symbol, ams_debug_selftest included."""
+    from paper_2606_04864_gb300._build import build
+    dbg = ctypes.CDLL(build(debug=True))
+    missing = [n for n in _declared_functions() if not hasattr(dbg, n)]
+    assert not missing, missing
+    assert hasattr(built_lib, "ams_debug_selftest") and hasattr(dbg, "ams_debug_selftest")
+
+
 def test_python_binding_covers_every_symbol():
     from paper_2606_04864_gb300._lib import SIGNATURES
     assert sorted(SIGNATURES) == _declared_functions()
