@@ -203,8 +203,15 @@ struct ams_handle_s {
                 b.p = nullptr;
             }
     }
+    // pinned host mirrors of the solve state and the per-(system, rhs) CG
+    // scalars, read back at the end of a solve without a blocking copy
+    SolveState* h_st = nullptr;
+    CgScalars* h_sc = nullptr;
+    int64_t pending_lpi = 0;   // launches per loop body of the solve in flight (0: counted already)
     ~ams_handle_s() {
         if (stream) cudaStreamSynchronize(stream);
+        if (h_st) cudaFreeHost(h_st);
+        if (h_sc) cudaFreeHost(h_sc);
         for (auto& g : loop_graph) cudaGraphExecDestroy(g.second);
         for (auto& b : bufs)
             if (b.p) cudaFree(b.p);
@@ -1164,6 +1171,8 @@ static ams_status setup_impl(int32_t nsys, const ams_system_desc* systems, const
     AMS_TRY(h->alloc_t(&h->d_st, 1));
     AMS_CUDA_TRY(cudaMemsetAsync(h->d_st, 0, sizeof(SolveState), h->stream));
     AMS_TRY(h->alloc_t(&h->d_sc, (size_t)h->nsys * kMaxLd));
+    AMS_CUDA_TRY(cudaMallocHost((void**)&h->h_st, sizeof(SolveState)));
+    AMS_CUDA_TRY(cudaMallocHost((void**)&h->h_sc, sizeof(CgScalars) * (size_t)h->nsys * kMaxLd));
     AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
     // info
     ams_info& I = h->info;
@@ -1794,8 +1803,12 @@ static ams_status autotune(ams_handle h, const double* f_dev, int nrhs, int ld) 
     return AMS_OK;
 }
 
-static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, double* u_dev, int32_t* iters,
-                      double* relres, const double* u0_dev = nullptr) {
+// The solve up to its outputs, enqueued on the handle's stream: the loop,
+// the solution in caller order into u_dev, and the solve state and CG
+// scalars into the pinned host mirrors.  The caller enqueues its own copies
+// behind it, synchronises once and calls pcg_finish.
+static ams_status pcg_launch(ams_handle h, const double* f_dev, int nrhs, double rtol, double* u_dev,
+                             const double* u0_dev = nullptr) {
     const int ld = pow2ceil(nrhs);
     AMS_TRY(ensure_work(h, ld));
     RedCache *rc = nullptr, *rcs = nullptr;
@@ -1814,10 +1827,9 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
         cudaGraphExec_t graph = nullptr;
         AMS_TRY(get_loop_graph(h, L, &graph));
         AMS_CUDA_TRY(cudaGraphLaunch(graph, h->stream));
-        AMS_CUDA_TRY(cudaMemcpyAsync(&st, h->d_st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
-        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-        h->launches += (int64_t)st.bodies * (2 * launches_per_iteration(h, ld) + 1);
+        h->pending_lpi = 2 * launches_per_iteration(h, ld) + 1;   // counted per body in pcg_finish
     } else {
+        h->pending_lpi = 0;
         // profiled solve: kernels launched one by one (events around each),
         // the device state read between chunks of iterations, each chunk
         // sized from the observed residual decay
@@ -1855,10 +1867,20 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
             launch_permute_out(h->stream, h->d_x, S.n, nrhs, ld, h->d_int_row + S.caller0, u_dev + S.caller0 * nrhs);
         }
     }
-    std::vector<CgScalars> sc((size_t)h->nsys * ld);
-    AMS_CUDA_TRY(cudaMemcpyAsync(sc.data(), h->d_sc, sizeof(CgScalars) * sc.size(), cudaMemcpyDeviceToHost,
-                                 h->stream));
-    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    AMS_CUDA_TRY(cudaMemcpyAsync(h->h_st, h->d_st, sizeof(SolveState), cudaMemcpyDeviceToHost, h->stream));
+    AMS_CUDA_TRY(cudaMemcpyAsync(h->h_sc, h->d_sc, sizeof(CgScalars) * (size_t)h->nsys * ld,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    return AMS_OK;
+}
+
+// After the stream has been synchronised: launch count, iterations,
+// relative residuals and the status of the solve pcg_launch enqueued.
+static ams_status pcg_finish(ams_handle h, int nrhs, int32_t* iters, double* relres) {
+    const int ld = pow2ceil(nrhs);
+    const SolveState st = *h->h_st;
+    h->launches += (int64_t)st.bodies * h->pending_lpi;
+    h->pending_lpi = 0;
+    const CgScalars* sc = h->h_sc;
     bool any_active = false;
     for (int s = 0; s < h->nsys; ++s)
         for (int k = 0; k < nrhs; ++k) {
@@ -1880,6 +1902,13 @@ static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, 
         return AMS_ERR_NOT_CONVERGED;
     }
     return AMS_OK;
+}
+
+static ams_status pcg(ams_handle h, const double* f_dev, int nrhs, double rtol, double* u_dev, int32_t* iters,
+                      double* relres, const double* u0_dev = nullptr) {
+    AMS_TRY(pcg_launch(h, f_dev, nrhs, rtol, u_dev, u0_dev));
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return pcg_finish(h, nrhs, iters, relres);
 }
 
 // Checking build (-DAMS_DEBUG): point the device-side index checks at this
@@ -2051,13 +2080,12 @@ ams_status ams_solve(ams_handle h, const double* f, int32_t nrhs, double rtol, d
                                      h->stream));
         u0_dev = h->d_stage_aux;
     }
-    ams_status st = pcg(h, f_dev, nrhs, rtol, u_dev, iters, relres, u0_dev);
-    if (st != AMS_OK && st != AMS_ERR_NOT_CONVERGED && st != AMS_ERR_BREAKDOWN) return st;
-    if (!h->opt.device_ptrs) {
+    AMS_TRY(pcg_launch(h, f_dev, nrhs, rtol, u_dev, u0_dev));
+    if (!h->opt.device_ptrs)   // the solution goes back behind the solve: one wait for both
         AMS_CUDA_TRY(cudaMemcpyAsync(u, u_dev, sizeof(double) * h->n_total * nrhs, cudaMemcpyDeviceToHost,
                                      h->stream));
-        AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    }
+    AMS_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const ams_status st = pcg_finish(h, nrhs, iters, relres);
     return debug_check(h, st);
 }
 
