@@ -496,7 +496,7 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
         const bool vec = (m == MM) && ((reinterpret_cast<uintptr_t>(psi + S.psi_off) & 15) == 0);
         const int64_t ne = (int64_t)S.n * LD;
         const int64_t g0 = S.row0 * LD;
-#pragma unroll 2
+#pragma unroll 4
         for (int64_t le = threadIdx.x; le < ne; le += kRedThreads) {
             const int64_t e = g0 + le;
             AT acc = (AT)zf[e];
