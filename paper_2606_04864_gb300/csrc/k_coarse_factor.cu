@@ -140,17 +140,27 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_potrf(double* __restrict__ A,
         else v = (r == c) ? 1.0 : 0.0;
         S[r][c] = v;
     }
+    __shared__ double s_rs;         // reciprocal of the current pivot
+    __shared__ double s_inv[TB];    // reciprocal pivots, for the inverse
     __syncthreads();
     for (int j = 0; j < TB; ++j) {
-        double d = S[j][j];
-        __syncthreads();
-        if (!(d > 0.0)) {
-            if (tid == 0) atomicMin(bad, (unsigned long long)((int64_t)t * TB + j));
-            d = 1.0;
+        // one thread takes the pivot's square root and reciprocal (FP64
+        // square root and division are long sequences on this GPU's narrow
+        // FP64 pipe: not once per thread)
+        if (tid == 0) {
+            double d = S[j][j];
+            if (!(d > 0.0)) {
+                atomicMin(bad, (unsigned long long)((int64_t)t * TB + j));
+                d = 1.0;
+            }
+            const double sq = sqrt(d);
+            S[j][j] = sq;
+            s_rs = 1.0 / sq;
+            s_inv[j] = s_rs;
         }
-        const double sq = sqrt(d), rs = 1.0 / sq;
+        __syncthreads();
+        const double rs = s_rs;
         for (int r = j + 1 + tid; r < TB; r += TTHREADS) S[r][j] *= rs;
-        if (tid == 0) S[j][j] = sq;
         __syncthreads();
         for (int e = tid; e < TB * TB; e += TTHREADS) {
             const int r = e >> 6, c = e & 63;
@@ -161,7 +171,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_potrf(double* __restrict__ A,
     // inverse of the lower-triangular S, column c by four lanes of one warp
     {
         const int c = tid >> 2, q = tid & 3;
-        if (q == 0) Li[c][c] = 1.0 / S[c][c];
+        if (q == 0) Li[c][c] = s_inv[c];
         __syncwarp();
         for (int r = 1; r < TB; ++r) {
             double s = 0.0;
@@ -169,7 +179,7 @@ __global__ void __launch_bounds__(TTHREADS) k_tile_potrf(double* __restrict__ A,
                 for (int l = c + q; l < r; l += 4) s = fma(S[r][l], Li[l][c], s);
             s += __shfl_xor_sync(0xffffffffu, s, 1);
             s += __shfl_xor_sync(0xffffffffu, s, 2);
-            if (r > c && q == 0) Li[r][c] = -s / S[r][r];
+            if (r > c && q == 0) Li[r][c] = -s * s_inv[r];
             __syncwarp();
         }
         for (int r = q; r < c; r += 4) Li[r][c] = 0.0;

@@ -323,15 +323,23 @@ k_eig_rr(const SubInfo* __restrict__ subs, int P, const int64_t* __restrict__ ro
             Rm[j * P + j] = sqrt(d);
         }
         __syncwarp();
+        // one reciprocal per pivot, taken by lane 0 and broadcast (an FP64
+        // division per lane would occupy the narrow FP64 pipe 31 times over)
+        double rpiv = 0.0;
+        if (lane == 0) rpiv = 1.0 / Rm[j * P + j];
+        rpiv = __shfl_sync(0xffffffffu, rpiv, 0);
         if (lane > j && lane < p) {
             double v = G[j * P + lane];
             for (int k = 0; k < j; ++k) v -= Rm[k * P + j] * Rm[k * P + lane];
-            Rm[j * P + lane] = v / Rm[j * P + j];
+            Rm[j * P + lane] = v * rpiv;
         }
         if (lane < j) Rm[j * P + lane] = 0.0;   // lower part zero
         __syncwarp();
     }
-    // R^{-1} (upper) by columns: lane = column
+    // R^{-1} (upper) by columns: lane = column; reciprocal pivots first
+    // (one division per lane), then multiplications only
+    if (lane < p) ev[lane] = 1.0 / Rm[lane * P + lane];
+    __syncwarp();
     if (lane < p) {
         const int c = lane;
         double col[32];
@@ -339,7 +347,7 @@ k_eig_rr(const SubInfo* __restrict__ subs, int P, const int64_t* __restrict__ ro
         for (int i = c; i >= 0; --i) {
             double v = (i == c) ? 1.0 : 0.0;
             for (int k = i + 1; k <= c; ++k) v -= Rm[i * P + k] * col[k];
-            col[i] = v / Rm[i * P + i];
+            col[i] = v * ev[i];
         }
         __syncwarp(0xffffffffu >> (32 - p));
         for (int i = 0; i < p; ++i) W[i * P + c] = col[i];       // W temporarily holds R^{-1}
