@@ -189,15 +189,16 @@ def slot_bytes(systems, nrhs, prec="mixed"):
     fused = nrhs <= 4
     nv = n * nrhs
     return {
-        # z, p_old in; p, q out; A (values, columns, row pointers)
-        "spmv_direction": 12 * nnz + 4 * (n + len(systems)) + 32 * nv,
+        # z, p_old, x in; p, q, x out (x += alpha p_old of the previous
+        # iteration rides on the direction update); A (values, columns, row pointers)
+        "spmv_direction": 12 * nnz + 4 * (n + len(systems)) + 48 * nv,
         # factor once; r, q in; z_f, r_c out; basis rows
         "local_solve_restrict": bF * lnz + 16 * nv + bF * nv + bP * psi + bF * nc * nrhs,
         # forward sweep (and the backward one when separate): factor, r_c in, y out
         "coarse_solve": (bF * cnz + 2 * bF * nc * nrhs) * (1 if fused else 2),
-        # (backward sweep when fused) e_c in, z_f, basis; r, q, x, p in; r, x, z out
+        # (backward sweep when fused) e_c in, z_f, basis; r, q in; r, z out
         "prolong_update": (bF * cnz + bF * nc * nrhs if fused else 0) + bF * nc * nrhs + bF * nv + bP * psi
-        + 56 * nv,
+        + 32 * nv,
         "_nnz_local_factor_nd": lnz, "_nnz_coarse_factor_nd": cnz,
     }
 
@@ -206,14 +207,15 @@ def slot_fp64_flops(systems, nrhs):
     """FP64 floating-point operations per launch of each slot (an FMA counts
     two): the SpMV and its fused dot and direction update, the residual
     update the local solves form, and the prolongation's CG update and
-    dots.  The preconditioner itself runs in FP32/TF32."""
+    dots, with the x update on the direction update of the next iteration.
+    The preconditioner itself runs in FP32/TF32."""
     n = sum(w.n for w, _ in systems)
     nnz = sum(w.nnz for w, _ in systems)
     nv = n * nrhs
-    return {"spmv_direction": 2 * nnz * nrhs + 2 * nv + 2 * nv,   # q = A p, p = z + beta p_old, p.q
-            "local_solve_restrict": 2 * nv,                         # r' = r - alpha q
+    return {"spmv_direction": 2 * nnz * nrhs + 6 * nv,   # q = A p, p = z + beta p_old, x += alpha p_old, p.q
+            "local_solve_restrict": 2 * nv,               # r' = r - alpha q
             "coarse_solve": 0,
-            "prolong_update": 10 * nv}                              # r, x updates; r.z, r.r, z.q
+            "prolong_update": 8 * nv}                     # r update; r.z, r.r, z.q
 
 
 # FP64 peak (no measured figure exists for it): the nominal GB300 rate

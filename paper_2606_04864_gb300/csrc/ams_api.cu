@@ -1520,7 +1520,7 @@ static int launches_per_iteration(ams_handle h, int ld) {
 }
 
 static void launch_direction_spmv(ams_handle h, const LaunchCtx& L, const double* p_old, double* p_new) {
-    launch_dir_update(L, h->d_z, p_old, p_new);
+    launch_dir_update(L, h->d_z, p_old, p_new, h->d_x);
     launch_spmv_dot(L, p_new, h->d_q, 1);
 }
 
@@ -1857,6 +1857,9 @@ static ams_status pcg_launch(ams_handle h, const double* f_dev, int nrhs, double
             w_prev = st.worst;
         }
     }
+    // the last iteration's x += alpha p (no direction update followed it)
+    launch_x_flush(L, h->d_p, h->d_p2, h->d_x);
+    h->launches += 1;
     // outputs
     if (h->nsys == 1) {
         launch_permute_out(h->stream, h->d_x, h->n_total, nrhs, ld, h->d_int_row, u_dev);

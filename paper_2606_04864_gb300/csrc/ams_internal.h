@@ -97,6 +97,8 @@ struct CgScalars {
     double alpha, beta;
     int32_t active;    // 1 while not converged
     int32_t iters;     // completed iterations
+    int32_t xpend;     // x += alpha p of the last iteration still to apply (the
+                       // next direction update, or the flush after the loop)
 };
 
 struct SolveState {    // device-resident control block
@@ -106,6 +108,8 @@ struct SolveState {    // device-resident control block
     int32_t nactive;
     int32_t maxit;     // iteration cap of the current solve
     int32_t bodies;    // loop bodies (two iterations each) the device-resident loop has run
+    int32_t xdone_it;  // value of `it` when a direction update last ran (it applied the
+                       // pending x updates of iteration it - 1)
     double rtol2;      // squared relative residual target
     double worst;      // max over active (system, rhs) of ||r||^2 / ||f||^2
 };

@@ -105,14 +105,39 @@ k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
 template <int LD>
 __global__ void __launch_bounds__(kRedThreads)
 k_dir_update(const double* __restrict__ z, const double* __restrict__ p_old, double* __restrict__ p_new,
-             RedLayout R, const CgScalars* sc, const SolveState* st) {
+             double* __restrict__ x, RedLayout R, const CgScalars* sc, SolveState* st) {
     pdl_wait();
     if (st->done) return;
     pdl_trigger();
-    const double beta = sc[R.blk_seg[blockIdx.x] * LD + threadIdx.x % LD].beta;
+    if (blockIdx.x == 0 && threadIdx.x == 0) st->xdone_it = st->it;
+    const CgScalars& c = sc[R.blk_seg[blockIdx.x] * LD + threadIdx.x % LD];
+    const double beta = c.beta, alpha = c.alpha;
+    const bool xupd = c.xpend != 0;
     const int64_t lo = R.blk_lo[blockIdx.x], hi = R.blk_lo[blockIdx.x + 1];
 #pragma unroll 4
-    for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) p_new[e] = fma(beta, p_old[e], z[e]);
+    for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) {
+        const double po = p_old[e];
+        p_new[e] = fma(beta, po, z[e]);
+        if (xupd) x[e] = fma(alpha, po, x[e]);   // the previous iteration's x += alpha p
+    }
+}
+
+// After the loop: the last iteration's x += alpha p, unless a direction
+// update ran after it (a breakdown found by the next SpMV ends the loop
+// after that update).  Its direction is the one that iteration computed:
+// iteration k writes p2 when k is even, p when it is odd.
+template <int LD>
+__global__ void __launch_bounds__(kRedThreads)
+k_x_flush(const double* __restrict__ p, const double* __restrict__ p2, double* __restrict__ x, RedLayout R,
+          const CgScalars* sc, const SolveState* st) {
+    const int it = st->it;
+    if (it == 0 || st->xdone_it == it) return;
+    const CgScalars& c = sc[R.blk_seg[blockIdx.x] * LD + threadIdx.x % LD];
+    if (!c.xpend) return;
+    const double alpha = c.alpha;
+    const double* pl = ((it - 1) % 2 == 0) ? p2 : p;
+    const int64_t lo = R.blk_lo[blockIdx.x], hi = R.blk_lo[blockIdx.x + 1];
+    for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) x[e] = fma(alpha, pl[e], x[e]);
 }
 
 // ===========================================================================
@@ -512,10 +537,9 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
             if (mode != 0) {
                 double rv = r[e];
                 const double qv = (upd || (flexible && mode == 2)) ? q[e] : 0.0;
-                if (upd) {
+                if (upd) {   // x += alpha p follows in the next direction update (xpend)
                     rv = fma(-alpha, qv, rv);
                     r[e] = rv;
-                    x[e] = fma(alpha, p[e], x[e]);
                 }
                 v[0] = fma(rv, zv, v[0]);
                 v[1] = fma(rv, rv, v[1]);
@@ -549,6 +573,7 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
             }
         } else if (c.active) {
             c.alpha = c.rho / c.pq;
+            c.xpend = 1;   // x += alpha p of this iteration: next direction update or the flush
             c.rr = rr;
             c.iters = it + 1;
             if (!isfinite(rr) || !isfinite(rz)) {
@@ -568,6 +593,8 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
             }
             c.zq = zq;
             c.rho = rz;
+        } else {
+            c.xpend = 0;   // inactive this iteration: its update (if any) was applied
         }
     }
     if (mode != 2) return;
@@ -620,6 +647,7 @@ k_init_norms(const double* __restrict__ r, RedLayout R, CgScalars* sc, SolveStat
         c.alpha = 0.0;
         c.beta = 0.0;
         c.iters = 0;
+        c.xpend = 0;
         c.active = (threadIdx.x < nrhs && c.fnorm2 > 0.0) ? 1 : 0;
     }
     if (!last_system(R, nseg)) return;
@@ -628,6 +656,7 @@ k_init_norms(const double* __restrict__ r, RedLayout R, CgScalars* sc, SolveStat
         for (int i = 0; i < nseg * LD; ++i) nact += sc[i].active;
         st->nactive = nact;
         st->it = 0;
+        st->xdone_it = 0;
         st->status = 0;
         st->worst = 1.0;
         st->done = (nact == 0);
@@ -721,12 +750,20 @@ void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_do
 }
 
 template <int LD>
-static void dir_ld(const LaunchCtx& L, const double* z, const double* p_old, double* p_new) {
+static void dir_ld(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* x) {
     launch_kernel(L.pdl, k_dir_update<LD>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream, z, p_old, p_new,
-                  L.red, (const CgScalars*)L.sc, (const SolveState*)L.st);
+                  x, L.red, (const CgScalars*)L.sc, L.st);
 }
-void launch_dir_update(const LaunchCtx& L, const double* z, const double* p_old, double* p_new) {
-    AMS_DISPATCH_LD(L.ld, dir_ld, L, z, p_old, p_new);
+void launch_dir_update(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* x) {
+    AMS_DISPATCH_LD(L.ld, dir_ld, L, z, p_old, p_new, x);
+}
+template <int LD>
+static void flush_ld(const LaunchCtx& L, const double* p, const double* p2, double* x) {
+    k_x_flush<LD><<<(unsigned)L.nblk, kRedThreads, 0, L.stream>>>(p, p2, x, L.red, (const CgScalars*)L.sc,
+                                                               (const SolveState*)L.st);
+}
+void launch_x_flush(const LaunchCtx& L, const double* p, const double* p2, double* x) {
+    AMS_DISPATCH_LD(L.ld, flush_ld, L, p, p2, x);
 }
 
 template <int LD>

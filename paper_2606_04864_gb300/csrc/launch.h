@@ -121,7 +121,11 @@ struct CoarseLaunch {
 // q = A p, and p.q per (system, rhs) when with_dot
 void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_dot);
 // p_new = z + beta p_old (per system and right-hand side)
-void launch_dir_update(const LaunchCtx& L, const double* z, const double* p_old, double* p_new);
+// p_new = z + beta p_old, and the previous iteration's x += alpha p_old
+// where that is still pending
+void launch_dir_update(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* x);
+// after the loop: the last iteration's pending x += alpha p
+void launch_x_flush(const LaunchCtx& L, const double* p, const double* p2, double* x);
 void launch_init_norms(const LaunchCtx& L, const double* r, int nrhs);
 size_t local_solve_smem(int cmax, int ld, size_t tf_bytes, int depth);
 int local_solve_depth(int cmax, int ld, size_t tf_bytes);
