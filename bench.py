@@ -189,16 +189,16 @@ def slot_bytes(systems, nrhs, prec="mixed"):
     fused = nrhs <= 4
     nv = n * nrhs
     return {
-        # z, p_old, x in; p, q, x out (x += alpha p_old of the previous
-        # iteration rides on the direction update); A (values, columns, row pointers)
-        "spmv_direction": 12 * nnz + 4 * (n + len(systems)) + 48 * nv,
+        # z (apply precision), p_old, x in; p, q, x out (x += alpha p_old of the
+        # previous iteration rides on the direction update); A (values, columns, row pointers)
+        "spmv_direction": 12 * nnz + 4 * (n + len(systems)) + (40 + bF) * nv,
         # factor once; r, q in; z_f, r_c out; basis rows
         "local_solve_restrict": bF * lnz + 16 * nv + bF * nv + bP * psi + bF * nc * nrhs,
         # forward sweep (and the backward one when separate): factor, r_c in, y out
         "coarse_solve": (bF * cnz + 2 * bF * nc * nrhs) * (1 if fused else 2),
-        # (backward sweep when fused) e_c in, z_f, basis; r, q in; r, z out
+        # (backward sweep when fused) e_c in, z_f, basis; r, q in; r out, z out (apply precision)
         "prolong_update": (bF * cnz + bF * nc * nrhs if fused else 0) + bF * nc * nrhs + bF * nv + bP * psi
-        + 32 * nv,
+        + (24 + bF) * nv,
         "_nnz_local_factor_nd": lnz, "_nnz_coarse_factor_nd": cnz,
     }
 

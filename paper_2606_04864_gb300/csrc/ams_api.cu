@@ -1467,7 +1467,7 @@ static ams_status apply_two_grid(ams_handle h, const LaunchCtx& L, int mode, con
     }
     prof_begin(h, AMS_KERNEL_PROLONG);
     launch_prolong_update(L2, h->prec, prolong_args(h, 0, p, L.ld));   // z = x^2
-    launch_tg_resid(L2, h->d_z, 1, rin, h->d_tw);
+    launch_tg_resid(L2, h->d_z, h->prec == AMS_PREC_FP64, rin, h->d_tw);   // z in the apply precision
     prof_end(h);
     prof_begin(h, AMS_KERNEL_LOCAL);
     AMS_TRY(launch_local(h, L.ld, ResidIn{h->d_tw, nullptr, h->d_sc}, with_state, false));
@@ -1520,7 +1520,7 @@ static int launches_per_iteration(ams_handle h, int ld) {
 }
 
 static void launch_direction_spmv(ams_handle h, const LaunchCtx& L, const double* p_old, double* p_new) {
-    launch_dir_update(L, h->d_z, p_old, p_new, h->d_x);
+    launch_dir_update(L, h->prec, h->d_z, p_old, p_new, h->d_x);
     launch_spmv_dot(L, p_new, h->d_q, 1);
 }
 
@@ -2020,8 +2020,8 @@ static double kernel_bytes(ams_handle h, int which, int ld) {
     const double n = (double)h->n_total, nl = n * ld;
     const double tf = (double)h->tf_bytes(), tp = (double)h->tp_bytes();
     switch (which) {
-        case AMS_KERNEL_SPMV:    // vals + cols, z and p_old in, p and q out, slice pointers
-            return 12.0 * (double)h->nnz_total + 32.0 * nl + 8.0 * (double)h->n_pad / 32;
+        case AMS_KERNEL_SPMV:    // vals + cols, z (apply precision), p_old, x in, p, q, x out, slice pointers
+            return 12.0 * (double)h->nnz_total + (tf + 40.0) * nl + 8.0 * (double)h->n_pad / 32;
         case AMS_KERNEL_LOCAL: {
             // factor once (tiles + pivots, or the packed factor), r and q in,
             // z_f out, basis rows, r_c out
@@ -2031,9 +2031,9 @@ static double kernel_bytes(ams_handle h, int which, int ld) {
         case AMS_KERNEL_COARSE:     // forward blocks, r_c in, y out (+ the backward pass when separate)
             return (double)h->R_elems * tf + 2.0 * (double)h->Nc * ld * tf +
                    (fused_backward(ld) ? 0.0 : (double)h->Q_elems * tf + 2.0 * (double)h->Nc * ld * tf);
-        case AMS_KERNEL_PROLONG:    // (backward blocks, y) or e_c; z_f, basis; r, q, x, p in; r, x, z out
+        case AMS_KERNEL_PROLONG:    // (backward blocks, y) or e_c; z_f, basis; r, q in; r out, z out (apply precision)
             return (fused_backward(ld) ? (double)h->Q_elems * tf : 0.0) + (double)h->Nc * ld * tf + tf * nl +
-                   (double)h->psi_elems * tp + 56.0 * nl;
+                   (double)h->psi_elems * tp + (24.0 + tf) * nl;
     }
     return 0.0;
 }
@@ -2349,7 +2349,11 @@ ams_status ams_apply_preconditioner(ams_handle h, const double* r, int32_t nrhs,
     AMS_TRY(clear_device_status(h));
     AMS_TRY(apply_precond(h, L, 0, nullptr));
     double* z_dev = h->opt.device_ptrs ? z : h->d_stage_out;
-    launch_permute_out(h->stream, h->d_z, h->n_total, nrhs, ld, h->d_int_row, z_dev);
+    if (h->prec == AMS_PREC_FP64)
+        launch_permute_out(h->stream, h->d_z, h->n_total, nrhs, ld, h->d_int_row, z_dev);
+    else   // z is stored in the apply precision
+        launch_permute_out_f32(h->stream, reinterpret_cast<const float*>(h->d_z), h->n_total, nrhs, ld,
+                               h->d_int_row, z_dev);
     AMS_CUDA_TRY(cudaGetLastError());
     if (!h->opt.device_ptrs)
         AMS_CUDA_TRY(cudaMemcpyAsync(z, z_dev, sizeof(double) * h->n_total * nrhs, cudaMemcpyDeviceToHost, h->stream));

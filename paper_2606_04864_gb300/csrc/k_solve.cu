@@ -102,9 +102,9 @@ k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
 
 // a7: p_new = z + beta p_old per (system, rhs); p_old and p_new are
 // different buffers (successive iterations alternate them)
-template <int LD>
+template <int LD, typename ZT>
 __global__ void __launch_bounds__(kRedThreads)
-k_dir_update(const double* __restrict__ z, const double* __restrict__ p_old, double* __restrict__ p_new,
+k_dir_update(const ZT* __restrict__ z, const double* __restrict__ p_old, double* __restrict__ p_new,
              double* __restrict__ x, RedLayout R, const CgScalars* sc, SolveState* st) {
     pdl_wait();
     if (st->done) return;
@@ -117,7 +117,7 @@ k_dir_update(const double* __restrict__ z, const double* __restrict__ p_old, dou
 #pragma unroll 4
     for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) {
         const double po = p_old[e];
-        p_new[e] = fma(beta, po, z[e]);
+        p_new[e] = fma(beta, po, widen(z[e]));
         if (xupd) x[e] = fma(alpha, po, x[e]);   // the previous iteration's x += alpha p
     }
 }
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(kRedThreads)
 k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, const TF* __restrict__ ec,
                  const TF* __restrict__ yc, const TF* __restrict__ qmat, const CoarseRef* __restrict__ cref, const int32_t* __restrict__ gat,
                  const TF* __restrict__ zf, double* __restrict__ r, const double* __restrict__ q,
-                 double* __restrict__ x, const double* __restrict__ p, double* __restrict__ z, RedLayout R,
+                 double* __restrict__ x, const double* __restrict__ p, TF* __restrict__ z, RedLayout R,
                  CgScalars* sc, SolveState* st, int nseg, int flexible, int mode) {
     using AT = typename Acc<TF>::type;
     using V4 = typename std::conditional<sizeof(TF) == 4, float4, double4>::type;
@@ -532,8 +532,9 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
 #pragma unroll
                 for (int k = 0; k < MM; ++k) pe += (AT)to_d(pv[k]) * s_ec[k * LD + rhs];
             }
-            const double zv = widen(acc + pe);   // z in the apply precision, stored as FP64
-            z[e] = zv;
+            const AT zs = acc + pe;              // z in the apply precision, stored so
+            const double zv = widen(zs);         // (FP32 widens exactly: the iterates do not change)
+            z[e] = zs;
             if (mode != 0) {
                 double rv = r[e];
                 const double qv = (upd || (flexible && mode == 2)) ? q[e] : 0.0;
@@ -677,13 +678,14 @@ __global__ void k_permute_in(const double* __restrict__ f, int64_t n, int nrhs, 
     }
 }
 
-__global__ void k_permute_out(const double* __restrict__ x, int64_t n, int nrhs, int ld,
+template <typename XT>
+__global__ void k_permute_out(const XT* __restrict__ x, int64_t n, int nrhs, int ld,
                               const int64_t* __restrict__ int_row, double* __restrict__ u) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t row = int_row[i];
     if (!AMS_ROW_OK(row, 6)) return;
-    for (int k = 0; k < nrhs; ++k) u[i + (int64_t)k * n] = x[row * ld + k];
+    for (int k = 0; k < nrhs; ++k) u[i + (int64_t)k * n] = widen(x[row * ld + k]);
 }
 
 // u += u0 (caller order) for the right-hand sides with f != 0 (a warm
@@ -750,12 +752,16 @@ void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_do
 }
 
 template <int LD>
-static void dir_ld(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* x) {
-    launch_kernel(L.pdl, k_dir_update<LD>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream, z, p_old, p_new,
-                  x, L.red, (const CgScalars*)L.sc, L.st);
+static void dir_ld(const LaunchCtx& L, int prec, const void* z, const double* p_old, double* p_new, double* x) {
+    if (prec == AMS_PREC_FP64)
+        launch_kernel(L.pdl, k_dir_update<LD, double>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream,
+                      (const double*)z, p_old, p_new, x, L.red, (const CgScalars*)L.sc, L.st);
+    else
+        launch_kernel(L.pdl, k_dir_update<LD, float>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream,
+                      (const float*)z, p_old, p_new, x, L.red, (const CgScalars*)L.sc, L.st);
 }
-void launch_dir_update(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* x) {
-    AMS_DISPATCH_LD(L.ld, dir_ld, L, z, p_old, p_new, x);
+void launch_dir_update(const LaunchCtx& L, int prec, const void* z, const double* p_old, double* p_new, double* x) {
+    AMS_DISPATCH_LD(L.ld, dir_ld, L, prec, z, p_old, p_new, x);
 }
 template <int LD>
 static void flush_ld(const LaunchCtx& L, const double* p, const double* p2, double* x) {
@@ -838,7 +844,8 @@ static void prolong_ld(const LaunchCtx& L, const ProlongArgs& a) {
     if (L.nsub == 0) return;
     auto kern = a.mmax > 8 ? k_prolong_update<TF, TP, LD, kMaxM> : k_prolong_update<TF, TP, LD, 8>;
     launch_kernel(L.pdl, kern, dim3((unsigned)L.nblk_sub), dim3(kRedThreads), 0, L.stream, L.subs, (const TP*)a.psi,
-                  (const TF*)a.ec, (const TF*)a.yc, (const TF*)a.qmat, a.cref, a.gat, (const TF*)a.zf, a.r, a.q, a.x, a.p, a.z,
+                  (const TF*)a.ec, (const TF*)a.yc, (const TF*)a.qmat, a.cref, a.gat, (const TF*)a.zf, a.r, a.q, a.x, a.p,
+                  (TF*)a.z,
                   L.red_sub, L.sc, L.st, L.nseg, a.flexible, a.mode);
 }
 template <typename TF, typename TP>
@@ -864,7 +871,11 @@ void launch_permute_in(cudaStream_t s, const double* f, int64_t n, int nrhs, int
 }
 void launch_permute_out(cudaStream_t s, const double* x, int64_t n, int nrhs, int ld,
                         const int64_t* int_row, double* u) {
-    k_permute_out<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, nrhs, ld, int_row, u);
+    k_permute_out<double><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, nrhs, ld, int_row, u);
+}
+void launch_permute_out_f32(cudaStream_t s, const float* x, int64_t n, int nrhs, int ld,
+                            const int64_t* int_row, double* u) {
+    k_permute_out<float><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, nrhs, ld, int_row, u);
 }
 void launch_sddmm(cudaStream_t s, const int64_t* rowptr, const int32_t* colind, int64_t n, int nrhs,
                   const double* lam, const double* u, double* dvals) {

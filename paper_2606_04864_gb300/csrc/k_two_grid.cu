@@ -78,12 +78,12 @@ __global__ void k_tg_scale(TF* __restrict__ zf, double omega, int64_t n, const S
 }
 
 template <typename TF>
-__global__ void k_tg_combine(TF* __restrict__ zf, const double* __restrict__ x2, double omega, int64_t n,
+__global__ void k_tg_combine(TF* __restrict__ zf, const TF* __restrict__ x2, double omega, int64_t n,
                              const SolveState* st) {
     if (st != nullptr && st->done) return;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         if constexpr (sizeof(TF) == 8) zf[e] = fma(omega, zf[e], x2[e]);
-        else zf[e] = fmaf((float)omega, zf[e], __double2float_rn(x2[e]));   // apply precision
+        else zf[e] = fmaf((float)omega, zf[e], x2[e]);   // apply precision (x2 = z, stored in it)
     }
 }
 
@@ -279,11 +279,11 @@ void launch_tg_scale(const LaunchCtx& L, int prec, void* zf, double omega, int64
         k_tg_scale<float><<<tg_blocks(n), 256, 0, L.stream>>>((float*)zf, omega, n, L.st);
 }
 
-void launch_tg_combine(const LaunchCtx& L, int prec, void* zf, const double* x2, double omega, int64_t n) {
+void launch_tg_combine(const LaunchCtx& L, int prec, void* zf, const void* x2, double omega, int64_t n) {
     if (prec == AMS_PREC_FP64)
-        k_tg_combine<double><<<tg_blocks(n), 256, 0, L.stream>>>((double*)zf, x2, omega, n, L.st);
+        k_tg_combine<double><<<tg_blocks(n), 256, 0, L.stream>>>((double*)zf, (const double*)x2, omega, n, L.st);
     else
-        k_tg_combine<float><<<tg_blocks(n), 256, 0, L.stream>>>((float*)zf, x2, omega, n, L.st);
+        k_tg_combine<float><<<tg_blocks(n), 256, 0, L.stream>>>((float*)zf, (const float*)x2, omega, n, L.st);
 }
 
 template <typename TF, typename TP, int MM>

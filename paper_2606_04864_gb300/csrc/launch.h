@@ -123,7 +123,7 @@ void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_do
 // p_new = z + beta p_old (per system and right-hand side)
 // p_new = z + beta p_old, and the previous iteration's x += alpha p_old
 // where that is still pending
-void launch_dir_update(const LaunchCtx& L, const double* z, const double* p_old, double* p_new, double* x);
+void launch_dir_update(const LaunchCtx& L, int prec, const void* z, const double* p_old, double* p_new, double* x);
 // after the loop: the last iteration's pending x += alpha p
 void launch_x_flush(const LaunchCtx& L, const double* p, const double* p2, double* x);
 void launch_init_norms(const LaunchCtx& L, const double* r, int nrhs);
@@ -155,7 +155,7 @@ struct ProlongArgs {
     const double* q;
     double* x;
     const double* p;
-    double* z;
+    void* z;                 // z in the apply precision (FP32 values are exact in FP64)
     int mmax;
     int flexible;
     int mode;                // 0 apply only, 1 first application, 2 CG iteration
@@ -168,7 +168,7 @@ void launch_tg_resid(const LaunchCtx& L, const void* v, int v_is_fp64, const Res
 void launch_tg_scale(const LaunchCtx& L, int prec, void* zf, double omega, int64_t n);
 // b = a rounded to FP32 (round to nearest even)
 void launch_round_to_f32(cudaStream_t s, const double* a, int64_t n, float* b);
-void launch_tg_combine(const LaunchCtx& L, int prec, void* zf, const double* x2, double omega, int64_t n);
+void launch_tg_combine(const LaunchCtx& L, int prec, void* zf, const void* x2, double omega, int64_t n);
 void launch_tg_restrict(const LaunchCtx& L, int prec, const void* psi, const double* w, void* rc, int mmax);
 // One power step for the cycle's damping: per system the sums x.y, y.z and
 // z.z into out[3 s ..] (y = A x, z = the local solves of y in the apply
@@ -185,6 +185,9 @@ void launch_permute_in(cudaStream_t s, const double* f, int64_t n, int nrhs, int
                        const int64_t* int_row, double* r, double* x);
 void launch_permute_out(cudaStream_t s, const double* x, int64_t n, int nrhs, int ld,
                         const int64_t* int_row, double* u);
+// the same from FP32 values (z in the reduced-precision modes), widened exactly
+void launch_permute_out_f32(cudaStream_t s, const float* x, int64_t n, int nrhs, int ld,
+                            const int64_t* int_row, double* u);
 // u += u0 (caller order, single system) where the right-hand side is non-zero
 void launch_add_initial_guess(cudaStream_t s, double* u, const double* u0, int64_t n, int nrhs,
                               const CgScalars* sc);
