@@ -112,7 +112,7 @@ k_dir_update(const ZT* __restrict__ z, const double* __restrict__ p_old, double*
     if (blockIdx.x == 0 && threadIdx.x == 0) st->xdone_it = st->it;
     const CgScalars& c = sc[R.blk_seg[blockIdx.x] * LD + threadIdx.x % LD];
     const double beta = c.beta, alpha = c.alpha;
-    const bool xupd = c.xpend != 0;
+    const bool xupd = x != nullptr && c.xpend != 0;   // x == NULL: the prolongation updates x
     const int64_t lo = R.blk_lo[blockIdx.x], hi = R.blk_lo[blockIdx.x + 1];
 #pragma unroll 4
     for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) {
@@ -538,9 +538,12 @@ k_prolong_update(const SubInfo* __restrict__ subs, const TP* __restrict__ psi, c
             if (mode != 0) {
                 double rv = r[e];
                 const double qv = (upd || (flexible && mode == 2)) ? q[e] : 0.0;
-                if (upd) {   // x += alpha p follows in the next direction update (xpend)
+                if (upd) {
                     rv = fma(-alpha, qv, rv);
                     r[e] = rv;
+                    // x += alpha p here, or (x == NULL, from 8 right-hand
+                    // sides) in the next direction update, marked by xpend
+                    if (x != nullptr) x[e] = fma(alpha, p[e], x[e]);
                 }
                 v[0] = fma(rv, zv, v[0]);
                 v[1] = fma(rv, rv, v[1]);
