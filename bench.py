@@ -236,24 +236,57 @@ def _psi_entries(w, m_i):
     return ni * np.asarray(m_i)
 
 
+def kernel_text(path: str, kernel: str):
+    """The definition of the `__global__` function `kernel` in `path`: from
+    its name to the brace closing its body (None if not found)."""
+    text = open(path, errors="replace").read()
+    pos = 0
+    while True:
+        i = text.find(kernel + "(", pos)
+        if i < 0:
+            return None
+        head = text[max(0, i - 400):i]
+        g = head.rfind("__global__")
+        if g >= 0 and ";" not in head[g:] and "}" not in head[g:]:
+            break
+        pos = i + 1
+    j = text.find("{", i)
+    depth = 0
+    for k in range(j, len(text)):
+        if text[k] == "{":
+            depth += 1
+        elif text[k] == "}":
+            depth -= 1
+            if depth == 0:
+                return text[i:k + 1]
+    return None
+
+
+def kernel_hash(path: str, kernel: str):
+    """First 16 hex digits of the SHA-256 of the kernel's definition text."""
+    import hashlib
+    t = kernel_text(path, kernel)
+    return None if t is None else hashlib.sha256(t.encode()).hexdigest()[:16]
+
+
 def _profiled_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` and the summary's workload from a
     committed ncu summary under profiles/, or None when no summary matches
-    the kernel's current source (the counters describe only the source they
-    were taken from)."""
+    the kernel's current definition (the counters describe only the code
+    they were taken from: the summary records the hash of the kernel's
+    definition text, so edits elsewhere in its file do not void it)."""
     import glob
-    import hashlib
     import re
     for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         for line in open(path, errors="replace"):
-            mt = re.match(r"traffic_bytes_per_launch: (\d+) kernel: (\S+) source: (\S+) sha256_16: ([0-9a-f]{16})"
+            mt = re.match(r"traffic_bytes_per_launch: (\d+) kernel: (\S+) source: (\S+) kernel_sha256_16: ([0-9a-f]{16})"
                           r"(?: workload: (\S+))?", line.strip())
             if not mt or mt.group(2) != kernel:
                 continue
             src = os.path.join(ROOT, mt.group(3))
             if not os.path.exists(src):
                 continue
-            if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] == mt.group(4):
+            if kernel_hash(src, kernel) == mt.group(4):
                 return int(mt.group(1)), os.path.relpath(path, ROOT), mt.group(5)
     return None, None, None
 
