@@ -269,7 +269,7 @@ def kernel_hash(path: str, kernel: str):
     return None if t is None else hashlib.sha256(t.encode()).hexdigest()[:16]
 
 
-def _profiled_traffic(kernel: str):
+def _profiled_traffic(kernel: str, workload=None):
     """DRAM bytes per launch of `kernel` and the summary's workload from a
     committed ncu summary under profiles/, or None when no summary matches
     the kernel's current definition (the counters describe only the code
@@ -282,6 +282,8 @@ def _profiled_traffic(kernel: str):
             mt = re.match(r"traffic_bytes_per_launch: (\d+) kernel: (\S+) source: (\S+) kernel_sha256_16: ([0-9a-f]{16})"
                           r"(?: workload: (\S+))?", line.strip())
             if not mt or mt.group(2) != kernel:
+                continue
+            if workload is not None and mt.group(5) not in (None, workload):
                 continue
             src = os.path.join(ROOT, mt.group(3))
             if not os.path.exists(src):
@@ -633,7 +635,7 @@ def run_gpu(args):
         dom = max(kern, key=lambda k: kern[k]["ms_total"])
         traffic, traffic_src, traffic_wl, traffic_kernel = None, None, None, None
         for kname in SLOT_KERNELS.get(dom, ()):
-            t, src, wl = _profiled_traffic(kname)
+            t, src, wl = _profiled_traffic(kname, args.workload)
             if t is not None and (wl is None or wl == args.workload):
                 traffic, traffic_src, traffic_wl, traffic_kernel = t, src, wl, kname
                 break
