@@ -55,3 +55,43 @@ def test_block_shapes_cover_the_grid():
     shapes = bench._block_shapes((20, 17), 8)
     assert sum(int(np.prod(s)) * c for s, c in shapes.items()) == 20 * 17
     assert shapes == {(8, 8): 4, (8, 1): 2, (4, 8): 2, (4, 1): 1}
+
+
+def test_kernel_text_isolates_the_definition(tmp_path):
+    """The traffic of a committed ncu summary is trusted only while the
+    captured kernel's own definition is unchanged: its text runs from the
+    name after `__global__` to the brace closing the body, launches and
+    other functions of the file are not part of it."""
+    src = tmp_path / "k.cu"
+    body = (
+        "template <int LD>\n__global__ void __launch_bounds__(256)\n"
+        "k_demo(const double* x, double* y) {\n    if (x) { y[0] = x[0]; }\n}\n"
+    )
+    other = "void launch_demo() { k_demo<8><<<1, 1>>>(nullptr, nullptr); }\n"
+    src.write_text("// header\n" + body + other)
+    t = bench.kernel_text(str(src), "k_demo")
+    assert t.startswith("k_demo(const double* x") and t.endswith("}") and "launch_demo" not in t
+    h0 = bench.kernel_hash(str(src), "k_demo")
+    src.write_text("// header changed\n" + body + other.replace("8", "16"))
+    assert bench.kernel_hash(str(src), "k_demo") == h0          # edits elsewhere: same hash
+    src.write_text("// header\n" + body.replace("y[0] = x[0]", "y[0] = 2 * x[0]") + other)
+    assert bench.kernel_hash(str(src), "k_demo") != h0          # the kernel changed: new hash
+    assert bench.kernel_text(str(src), "k_missing") is None
+
+
+def test_committed_traffic_summaries_name_existing_kernels():
+    """Every traffic line under profiles/ names a kernel that the named
+    source defines (a summary can lapse, but not point at nothing)."""
+    import glob
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    seen = 0
+    for path in glob.glob(os.path.join(root, "profiles", "*.md")):
+        for line in open(path):
+            m = re.match(r"traffic_bytes_per_launch: \d+ kernel: (\S+) source: (\S+) kernel_sha256_16: [0-9a-f]{16}",
+                         line.strip())
+            if m:
+                seen += 1
+                assert bench.kernel_text(os.path.join(root, m.group(2)), m.group(1)) is not None, line
+    assert seen > 0
