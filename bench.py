@@ -187,18 +187,22 @@ def slot_bytes(systems, nrhs, prec="mixed"):
     lnz = sum(local_factor_nnz(w) for w, _ in systems)
     cnz = sum(coarse_factor_nnz(w, m_i) for w, m_i in systems)
     fused = nrhs <= 4
+    # from 5 right-hand sides (stride 8) x += alpha p_old of the previous
+    # iteration rides on the direction update; below, the prolongation does it
+    xdir = nrhs > 4
     nv = n * nrhs
     return {
-        # z (apply precision), p_old, x in; p, q, x out (x += alpha p_old of the
-        # previous iteration rides on the direction update); A (values, columns, row pointers)
-        "spmv_direction": 12 * nnz + 4 * (n + len(systems)) + (40 + bF) * nv,
+        # z (apply precision), p_old in; p, q out; x in and out when xdir; A
+        # (values, columns, row pointers)
+        "spmv_direction": 12 * nnz + 4 * (n + len(systems)) + (24 + bF + (16 if xdir else 0)) * nv,
         # factor once; r, q in; z_f, r_c out; basis rows
         "local_solve_restrict": bF * lnz + 16 * nv + bF * nv + bP * psi + bF * nc * nrhs,
         # forward sweep (and the backward one when separate): factor, r_c in, y out
         "coarse_solve": (bF * cnz + 2 * bF * nc * nrhs) * (1 if fused else 2),
-        # (backward sweep when fused) e_c in, z_f, basis; r, q in; r out, z out (apply precision)
+        # (backward sweep when fused) e_c in, z_f, basis; r, q in; r out, z out
+        # (apply precision); p, x in and x out unless xdir
         "prolong_update": (bF * cnz + bF * nc * nrhs if fused else 0) + bF * nc * nrhs + bF * nv + bP * psi
-        + (24 + bF) * nv,
+        + (24 + bF + (0 if xdir else 24)) * nv,
         "_nnz_local_factor_nd": lnz, "_nnz_coarse_factor_nd": cnz,
     }
 
@@ -207,15 +211,17 @@ def slot_fp64_flops(systems, nrhs):
     """FP64 floating-point operations per launch of each slot (an FMA counts
     two): the SpMV and its fused dot and direction update, the residual
     update the local solves form, and the prolongation's CG update and
-    dots, with the x update on the direction update of the next iteration.
-    The preconditioner itself runs in FP32/TF32."""
+    dots, with the x update on the direction update of the next iteration
+    from 5 right-hand sides and on the prolongation below.  The
+    preconditioner itself runs in FP32/TF32."""
     n = sum(w.n for w, _ in systems)
     nnz = sum(w.nnz for w, _ in systems)
     nv = n * nrhs
-    return {"spmv_direction": 2 * nnz * nrhs + 6 * nv,   # q = A p, p = z + beta p_old, x += alpha p_old, p.q
-            "local_solve_restrict": 2 * nv,               # r' = r - alpha q
+    xdir = nrhs > 4
+    return {"spmv_direction": 2 * nnz * nrhs + (6 if xdir else 4) * nv,   # q = A p, p = z + beta p_old, p.q
+            "local_solve_restrict": 2 * nv,                                # r' = r - alpha q
             "coarse_solve": 0,
-            "prolong_update": 8 * nv}                     # r update; r.z, r.r, z.q
+            "prolong_update": (8 if xdir else 10) * nv}                    # r update; r.z, r.r, z.q; x
 
 
 # FP64 peak (no measured figure exists for it): the nominal GB300 rate

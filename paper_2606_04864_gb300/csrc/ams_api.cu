@@ -2029,8 +2029,10 @@ static double kernel_bytes(ams_handle h, int which, int ld) {
     const double n = (double)h->n_total, nl = n * ld;
     const double tf = (double)h->tf_bytes(), tp = (double)h->tp_bytes();
     switch (which) {
-        case AMS_KERNEL_SPMV:    // vals + cols, z (apply precision), p_old, x in, p, q, x out, slice pointers
-            return 12.0 * (double)h->nnz_total + (tf + 40.0) * nl + 8.0 * (double)h->n_pad / 32;
+        case AMS_KERNEL_SPMV:    // vals + cols, z (apply precision), p_old in, p, q out, slice pointers;
+                                 // x in and out where the direction update applies x += alpha p
+            return 12.0 * (double)h->nnz_total + (tf + (defer_x_update(ld) ? 40.0 : 24.0)) * nl +
+                   8.0 * (double)h->n_pad / 32;
         case AMS_KERNEL_LOCAL: {
             // factor once (tiles + pivots, or the packed factor), r and q in,
             // z_f out, basis rows, r_c out
@@ -2040,9 +2042,10 @@ static double kernel_bytes(ams_handle h, int which, int ld) {
         case AMS_KERNEL_COARSE:     // forward blocks, r_c in, y out (+ the backward pass when separate)
             return (double)h->R_elems * tf + 2.0 * (double)h->Nc * ld * tf +
                    (fused_backward(ld) ? 0.0 : (double)h->Q_elems * tf + 2.0 * (double)h->Nc * ld * tf);
-        case AMS_KERNEL_PROLONG:    // (backward blocks, y) or e_c; z_f, basis; r, q in; r out, z out (apply precision)
+        case AMS_KERNEL_PROLONG:    // (backward blocks, y) or e_c; z_f, basis; r, q in; r out, z out (apply
+                                    // precision); p, x in and x out where this kernel applies x += alpha p
             return (fused_backward(ld) ? (double)h->Q_elems * tf : 0.0) + (double)h->Nc * ld * tf + tf * nl +
-                   (double)h->psi_elems * tp + (24.0 + tf) * nl;
+                   (double)h->psi_elems * tp + (24.0 + tf + (defer_x_update(ld) ? 0.0 : 24.0)) * nl;
     }
     return 0.0;
 }

@@ -101,24 +101,33 @@ k_spmv_dot(const int64_t* __restrict__ sell_ptr, const int32_t* __restrict__ sel
 }
 
 // a7: p_new = z + beta p_old per (system, rhs); p_old and p_new are
-// different buffers (successive iterations alternate them)
-template <int LD, typename ZT>
+// different buffers (successive iterations alternate them).  XUPD: this
+// launch also applies the previous iteration's x += alpha p_old (from 8
+// right-hand sides, where the prolongation leaves it); without it the
+// kernel is the bare direction update.
+template <int LD, typename ZT, bool XUPD>
 __global__ void __launch_bounds__(kRedThreads)
 k_dir_update(const ZT* __restrict__ z, const double* __restrict__ p_old, double* __restrict__ p_new,
              double* __restrict__ x, RedLayout R, const CgScalars* sc, SolveState* st) {
     pdl_wait();
     if (st->done) return;
     pdl_trigger();
-    if (blockIdx.x == 0 && threadIdx.x == 0) st->xdone_it = st->it;
     const CgScalars& c = sc[R.blk_seg[blockIdx.x] * LD + threadIdx.x % LD];
-    const double beta = c.beta, alpha = c.alpha;
-    const bool xupd = x != nullptr && c.xpend != 0;   // x == NULL: the prolongation updates x
     const int64_t lo = R.blk_lo[blockIdx.x], hi = R.blk_lo[blockIdx.x + 1];
+    if constexpr (!XUPD) {
+        const double beta = c.beta;
 #pragma unroll 4
-    for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) {
-        const double po = p_old[e];
-        p_new[e] = fma(beta, po, widen(z[e]));
-        if (xupd) x[e] = fma(alpha, po, x[e]);   // the previous iteration's x += alpha p
+        for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) p_new[e] = fma(beta, p_old[e], widen(z[e]));
+    } else {
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->xdone_it = st->it;
+        const double beta = c.beta, alpha = c.alpha;
+        const bool xupd = c.xpend != 0;
+#pragma unroll 4
+        for (int64_t e = lo + threadIdx.x; e < hi; e += kRedThreads) {
+            const double po = p_old[e];
+            p_new[e] = fma(beta, po, widen(z[e]));
+            if (xupd) x[e] = fma(alpha, po, x[e]);   // the previous iteration's x += alpha p
+        }
     }
 }
 
@@ -756,12 +765,21 @@ void launch_spmv_dot(const LaunchCtx& L, const double* p, double* q, int with_do
 
 template <int LD>
 static void dir_ld(const LaunchCtx& L, int prec, const void* z, const double* p_old, double* p_new, double* x) {
-    if (prec == AMS_PREC_FP64)
-        launch_kernel(L.pdl, k_dir_update<LD, double>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream,
-                      (const double*)z, p_old, p_new, x, L.red, (const CgScalars*)L.sc, L.st);
-    else
-        launch_kernel(L.pdl, k_dir_update<LD, float>, dim3((unsigned)L.nblk), dim3(kRedThreads), 0, L.stream,
-                      (const float*)z, p_old, p_new, x, L.red, (const CgScalars*)L.sc, L.st);
+    const dim3 g((unsigned)L.nblk), b(kRedThreads);
+    const CgScalars* sc = (const CgScalars*)L.sc;
+    if (prec == AMS_PREC_FP64) {
+        const double* zd = (const double*)z;
+        if (x != nullptr)
+            launch_kernel(L.pdl, k_dir_update<LD, double, true>, g, b, 0, L.stream, zd, p_old, p_new, x, L.red, sc, L.st);
+        else
+            launch_kernel(L.pdl, k_dir_update<LD, double, false>, g, b, 0, L.stream, zd, p_old, p_new, x, L.red, sc, L.st);
+    } else {
+        const float* zf = (const float*)z;
+        if (x != nullptr)
+            launch_kernel(L.pdl, k_dir_update<LD, float, true>, g, b, 0, L.stream, zf, p_old, p_new, x, L.red, sc, L.st);
+        else
+            launch_kernel(L.pdl, k_dir_update<LD, float, false>, g, b, 0, L.stream, zf, p_old, p_new, x, L.red, sc, L.st);
+    }
 }
 void launch_dir_update(const LaunchCtx& L, int prec, const void* z, const double* p_old, double* p_new, double* x) {
     AMS_DISPATCH_LD(L.ld, dir_ld, L, prec, z, p_old, p_new, x);
