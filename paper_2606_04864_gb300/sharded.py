@@ -165,36 +165,62 @@ class RankOps(Protocol):
     def gather(self, x, idx): ...                         # x[idx]
 
 
+class RankFailure(RuntimeError):
+    """An exchange of the sharded iteration did not complete: a peer rank
+    left or died, or did not join within the process group's timeout.  The
+    solve on this rank stops at that exchange (its iterate is not returned);
+    the caller decides whether to rebuild the group and start again."""
+
+    def __init__(self, exchange: str, rank: int, cause: BaseException):
+        super().__init__(f"{exchange} on rank {rank} did not complete: {cause}")
+        self.exchange, self.rank = exchange, rank
+
+
 class TorchComm:
     """Collectives of the sharded iteration over the default process group
-    (gloo on CPU ranks, NCCL on GPUs): vectors travel as float64 tensors."""
+    (gloo on CPU ranks, NCCL on GPUs): vectors travel as float64 tensors.
+    ``group`` selects another process group spanning every rank (its
+    timeout then bounds each exchange).  A collective that fails (the
+    backend reports a closed connection or the group's timeout) is raised
+    as RankFailure naming the exchange."""
 
-    def __init__(self, plan: RankPlan, world: int):
+    def __init__(self, plan: RankPlan, world: int, group=None):
         import torch
         import torch.distributed as dist
         self.torch, self.dist = torch, dist
-        self.plan, self.world = plan, world
+        self.plan, self.world, self.group = plan, world, group
 
     def _t(self, x):
         return self.torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64))
 
+    def _run(self, exchange: str, fn):
+        try:
+            return fn()
+        except RuntimeError as e:   # torch's backend errors derive from RuntimeError
+            raise RankFailure(exchange, self.plan.rank, e) from e
+
     def allreduce(self, values) -> np.ndarray:
         t = self._t(values)
-        self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        self._run("all-reduce", lambda: self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM, group=self.group))
         return t.numpy()
 
     def halo(self, p_owned) -> np.ndarray:
         """Ghost entries of p from their owners (point-to-point)."""
         pl = self.plan
         out = np.zeros(len(pl.ghost))
-        reqs, bufs = [], {}
-        for q, rows in pl.send.items():
-            reqs.append(self.dist.isend(self._t(np.asarray(p_owned)[rows]), dst=q))
-        for q, pos in pl.recv.items():
-            bufs[q] = self.torch.empty(len(pos), dtype=self.torch.float64)
-            reqs.append(self.dist.irecv(bufs[q], src=q))
-        for rq in reqs:
-            rq.wait()
+        bufs = {}
+
+        def exchange():
+            reqs = []
+            for q, rows in pl.send.items():
+                reqs.append(self.dist.isend(self._t(np.asarray(p_owned)[rows]), dst=q, group=self.group))
+            for q, pos in pl.recv.items():
+                bufs[q] = self.torch.empty(len(pos), dtype=self.torch.float64)
+                reqs.append(self.dist.irecv(bufs[q], src=q, group=self.group))
+            for rq in reqs:
+                rq.wait()
+
+        self._run("halo exchange", exchange)
         for q, pos in pl.recv.items():
             out[pos] = bufs[q].numpy()
         return out
@@ -206,7 +232,7 @@ class TorchComm:
         mine = np.zeros(width)
         mine[:len(rc_owned)] = rc_owned
         parts = [self.torch.empty(width, dtype=self.torch.float64) for _ in range(self.world)]
-        self.dist.all_gather(parts, self._t(mine))
+        self._run("all-gather of r_c", lambda: self.dist.all_gather(parts, self._t(mine), group=self.group))
         return np.concatenate([parts[r].numpy()[:sizes[r]] for r in range(self.world)])
 
 

@@ -3,7 +3,9 @@ per rank, a halo exchange of p before each SpMV, all-reduces of the dots,
 an all-gather of r_c before the replicated coarse solve.  Its iterates
 equal the single-rank solve's (the oracle's PCG and flexible CG) to 1e-12
 at world sizes 2 and 4; the plan's ghost, send and receive lists are
-checked by brute force."""
+checked by brute force.  A lost peer (one that exits, never joins an
+exchange, or leaves between iterations) ends the other ranks' solve with
+RankFailure at the exchange that could not complete."""
 
 import os
 import sys
@@ -117,3 +119,71 @@ def test_sharded_iterates_equal_single_rank(case, world, flexible):
         # per iteration: one halo exchange, two all-reduces, one all-gather
         assert c["halo"] == ref.iters and c["allreduce"] == 2 + 2 * ref.iters
         assert c["allgather"] == 1 + ref.iters
+
+
+def _failure_worker(rank, world, port, mode, out):
+    """Rank 1 leaves the solve in one of three ways; rank 0 solves and
+    reports how its solve ended.  Every exchange runs in a group with a
+    3 s timeout (the default group keeps a long one for the rendezvous)."""
+    import datetime
+    import time
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=120))
+    group = dist.new_group(list(range(world)), timeout=datetime.timedelta(seconds=3))
+    from paper_2606_04864_gb300.sharded import RankFailure, TorchComm, sharded_pcg
+    from tests.sharded_oracle_ops import OracleRankOps
+    w = CASES["2d"]()
+    o, plan = _plan(w, world)
+    rp = plan.ranks[rank]
+    f_owned = w.rhs[0][plan.perm[rp.row_lo:rp.row_hi]]
+    comm = TorchComm(rp, world, group=group)
+    if rank == 1:
+        if mode == "exits":              # gone before the solve's first exchange
+            os._exit(0)
+        if mode == "never_joins":        # alive, but joins no exchange
+            time.sleep(40)
+            os._exit(0)
+        # "leaves_after_3": three full iterations, then gone between steps
+        sharded_pcg(plan, rank, OracleRankOps(o, plan, rank), comm, f_owned, rtol=1e-10, maxit=3)
+        os._exit(0)
+    t0 = time.monotonic()
+    try:
+        sharded_pcg(plan, rank, OracleRankOps(o, plan, rank), comm, f_owned, rtol=1e-10)
+        out[rank] = ("finished", time.monotonic() - t0, "")
+    except RankFailure as e:
+        out[rank] = ("RankFailure", time.monotonic() - t0, e.exchange)
+    os._exit(0)   # the group is broken: leave without a teardown that talks to the lost peer
+
+
+@pytest.mark.parametrize("mode, exchange", [("exits", "all-reduce"), ("never_joins", "all-reduce"),
+                                            ("leaves_after_3", "halo exchange")])
+def test_lost_rank_ends_the_solve_with_rank_failure(mode, exchange):
+    """Failure detection on the host: a peer that exits, one that never
+    joins, and one that leaves after three iterations each end the other
+    rank's solve with RankFailure at the exchange that could not complete,
+    within the group's timeout instead of hanging."""
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = 20000 + (os.getpid() * 11 + 17 * len(mode)) % 20000
+    procs = [ctx.Process(target=_failure_worker, args=(r, 2, port, mode, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        procs[0].join(120)
+        assert procs[0].exitcode == 0, "the surviving rank did not finish"
+    finally:
+        for p in procs:
+            p.join(0 if p is procs[1] and mode == "never_joins" else 60)
+            if p.is_alive():
+                p.kill()
+                p.join()
+    status, seconds, where = out[0]
+    assert status == "RankFailure", (status, seconds)
+    assert where == exchange
+    if mode == "never_joins":
+        assert 2.5 <= seconds < 30.0   # the group's 3 s timeout, not the idle peer's 40 s sleep
+    else:
+        assert seconds < 10.0          # a closed connection is reported at once
