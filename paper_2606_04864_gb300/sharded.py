@@ -151,17 +151,18 @@ def make_plan(rowptr, colind, vals, part, nparts: int, m_i, world: int) -> Shard
 # ---------------------------------------------------------------------------
 
 class RankOps(Protocol):
-    """Arithmetic of one rank on its owned block (vectors of n_owned rows,
-    internal order; coarse vectors in paper order)."""
+    """Arithmetic of one rank on its owned block: vectors of n_owned rows
+    (internal order), or blocks of n_owned rows by R right-hand sides;
+    coarse vectors in paper order, with the same columns."""
 
     def spmv(self, p_owned, p_ghost): ...                 # q = (A p) on the owned rows
     def local_restrict(self, r_owned): ...                # (z_f, r_c of the owned subdomains)
     def coarse_solve(self, rc_full): ...                  # e_c = A_0^{-1} r_c (replicated)
     def prolong(self, zf_owned, ec_full): ...             # z = z_f + R_0^T e_c on the owned rows
-    def dot(self, a, b) -> float: ...
-    def axpy(self, alpha: float, x, y): ...               # y + alpha x
+    def dot(self, a, b): ...                              # a.b: a float, or one per column
+    def axpy(self, alpha, x, y): ...                      # y + alpha x (alpha: float, or one per column)
     def copy(self, x): ...
-    def zeros(self, n: int): ...
+    def zeros_like(self, x): ...
     def gather(self, x, idx): ...                         # x[idx]
 
 
@@ -207,7 +208,8 @@ class TorchComm:
     def halo(self, p_owned) -> np.ndarray:
         """Ghost entries of p from their owners (point-to-point)."""
         pl = self.plan
-        out = np.zeros(len(pl.ghost))
+        cols = np.shape(p_owned)[1:]
+        out = np.zeros((len(pl.ghost),) + cols)
         bufs = {}
 
         def exchange():
@@ -215,7 +217,7 @@ class TorchComm:
             for q, rows in pl.send.items():
                 reqs.append(self.dist.isend(self._t(np.asarray(p_owned)[rows]), dst=q, group=self.group))
             for q, pos in pl.recv.items():
-                bufs[q] = self.torch.empty(len(pos), dtype=self.torch.float64)
+                bufs[q] = self.torch.empty((len(pos),) + cols, dtype=self.torch.float64)
                 reqs.append(self.dist.irecv(bufs[q], src=q, group=self.group))
             for rq in reqs:
                 rq.wait()
@@ -226,12 +228,14 @@ class TorchComm:
         return out
 
     def allgather_coarse(self, rc_owned, coarse_lo: List[int]) -> np.ndarray:
-        """The full coarse vector from every rank's contiguous block."""
+        """The full coarse vector (or block, one column per right-hand side)
+        from every rank's contiguous block of rows."""
         sizes = [coarse_lo[r + 1] - coarse_lo[r] for r in range(self.world)]
         width = max(max(sizes), 1)
-        mine = np.zeros(width)
-        mine[:len(rc_owned)] = rc_owned
-        parts = [self.torch.empty(width, dtype=self.torch.float64) for _ in range(self.world)]
+        rc = np.asarray(rc_owned, dtype=np.float64)
+        mine = np.zeros((width,) + rc.shape[1:])
+        mine[:len(rc)] = rc
+        parts = [self.torch.empty(mine.shape, dtype=self.torch.float64) for _ in range(self.world)]
         self._run("all-gather of r_c", lambda: self.dist.all_gather(parts, self._t(mine), group=self.group))
         return np.concatenate([parts[r].numpy()[:sizes[r]] for r in range(self.world)])
 
@@ -243,9 +247,9 @@ class TorchComm:
 @dataclass
 class ShardedResult:
     x: object                    # owned rows of the solution (internal order)
-    iters: int
-    relres: float
-    alphas: list
+    iters: object                # int, or one per column
+    relres: object               # recurrence residual / ||f||: float, or one per column
+    alphas: list                 # step lengths (one list per column with several)
     betas: list
     collectives: dict
 
@@ -256,10 +260,20 @@ def sharded_pcg(plan: ShardPlan, rank: int, ops: RankOps, comm, f_owned, rtol: f
     rank's block, with the exchanges of the module docstring; the recurrences
     and the stopping rule (first k with ||r_k|| <= rtol ||f||, recurrence
     residual) are those of the single-rank solve, and the step length and
-    beta use the globally reduced dots."""
+    beta use the globally reduced dots.
+
+    ``f_owned`` holds the rank's rows of one right-hand side, or of R of
+    them as columns.  Each column is its own CG (its own step lengths and
+    stop; a converged column keeps its x and r, with step length 0), and
+    every exchange carries all columns at once, so an iteration still has
+    one halo exchange, two all-reduces and one all-gather.  The scalars
+    (one per column) are formed here from the reduced dots."""
     rp = plan.ranks[rank]
     clo = [plan.ranks[r].coarse_lo for r in range(plan.world)] + [plan.ranks[-1].coarse_hi]
     coll = {"halo": 0, "allreduce": 0, "allgather": 0}
+    one = np.ndim(f_owned) == 1
+    R = 1 if one else int(np.shape(f_owned)[1])
+    coef = (lambda v: float(v[0])) if one else (lambda v: v)
 
     def precond(r):
         zf, rc = ops.local_restrict(r)
@@ -267,38 +281,54 @@ def sharded_pcg(plan: ShardPlan, rank: int, ops: RankOps, comm, f_owned, rtol: f
         rc_full = comm.allgather_coarse(rc, clo)
         return ops.prolong(zf, ops.coarse_solve(rc_full))
 
-    x = ops.zeros(rp.n_owned)
+    def reduce(*dots):
+        coll["allreduce"] += 1
+        v = comm.allreduce(np.concatenate([np.atleast_1d(np.asarray(d, dtype=np.float64)) for d in dots]))
+        return [np.asarray(v[i * R:(i + 1) * R], dtype=np.float64) for i in range(len(dots))]
+
+    def result(x, iters, rr, fn2, alphas, betas):
+        rel = np.sqrt(np.divide(rr, fn2, out=np.zeros(R), where=fn2 > 0))
+        if one:
+            return ShardedResult(x, int(iters[0]), float(rel[0]), alphas[0], betas[0], coll)
+        return ShardedResult(x, iters, rel, alphas, betas, coll)
+
     r = ops.copy(f_owned)
-    coll["allreduce"] += 1
-    fn2 = float(comm.allreduce([ops.dot(r, r)])[0])
-    alphas, betas = [], []
-    if fn2 == 0.0:
-        return ShardedResult(x, 0, 0.0, alphas, betas, coll)
+    x = ops.zeros_like(r)
+    (fn2,) = reduce(ops.dot(r, r))
+    alphas, betas = [[] for _ in range(R)], [[] for _ in range(R)]
+    iters = np.zeros(R, dtype=np.int64)
+    active = fn2 > 0.0
+    rr = fn2.copy()
+    if not active.any():
+        return result(x, iters, rr, fn2, alphas, betas)
     z = precond(r)
-    coll["allreduce"] += 1
-    rho = float(comm.allreduce([ops.dot(r, z)])[0])
+    (rho,) = reduce(ops.dot(r, z))
     p = ops.copy(z)
-    k, rr = 0, fn2
-    while k < maxit:
+    k = 0
+    while k < maxit and active.any():
         coll["halo"] += 1
         q = ops.spmv(p, comm.halo(p))
-        coll["allreduce"] += 1
-        pq = float(comm.allreduce([ops.dot(p, q)])[0])
-        if not pq > 0.0:
-            raise FloatingPointError("CG breakdown: p^T A p <= 0")
-        alpha = rho / pq
-        alphas.append(alpha)
-        x = ops.axpy(alpha, p, x)
-        r = ops.axpy(-alpha, q, r)
+        (pq,) = reduce(ops.dot(p, q))
+        bad = active & ~(pq > 0.0)
+        if bad.any():
+            raise FloatingPointError(f"CG breakdown: p^T A p <= 0 (column {int(np.flatnonzero(bad)[0])})")
+        alpha = np.divide(rho, pq, out=np.zeros(R), where=active)
+        for c in np.flatnonzero(active):
+            alphas[c].append(float(alpha[c]))
+        x = ops.axpy(coef(alpha), p, x)
+        r = ops.axpy(coef(-alpha), q, r)
         k += 1
         z = precond(r)
-        coll["allreduce"] += 1
-        rr, rz, zq = (float(v) for v in comm.allreduce([ops.dot(r, r), ops.dot(r, z), ops.dot(z, q)]))
-        if rr <= rtol * rtol * fn2:
-            break
+        rr_k, rz, zq = reduce(ops.dot(r, r), ops.dot(r, z), ops.dot(z, q))
+        rr = np.where(active, rr_k, rr)
+        done = active & (rr_k <= rtol * rtol * fn2)
+        iters[done] = k
+        active = active & ~done
         # flexible: z_{k+1}^T (r_{k+1} - r_k) = -alpha z_{k+1}^T q_k
-        beta = (-alpha * zq / rho) if flexible else (rz / rho)
-        betas.append(beta)
-        rho = rz
-        p = ops.axpy(beta, p, z)
-    return ShardedResult(x, k, float(np.sqrt(rr / fn2)), alphas, betas, coll)
+        beta = np.divide(-alpha * zq if flexible else rz, rho, out=np.zeros(R), where=active)
+        for c in np.flatnonzero(active):
+            betas[c].append(float(beta[c]))
+        rho = np.where(active, rz, rho)
+        p = ops.axpy(coef(beta), p, z)
+    iters[active] = k
+    return result(x, iters, rr, fn2, alphas, betas)

@@ -1,6 +1,7 @@
 """Per-rank operations of the sharded iteration built from the CPU oracle
 (test infrastructure): the rank's rows of A from the plan, and the oracle's
-local Cholesky factors, basis blocks and coarse factor for its subdomains."""
+local Cholesky factors, basis blocks and coarse factor for its subdomains.
+Vectors are 1-D, or blocks with one column per right-hand side."""
 
 import numpy as np
 import scipy.linalg as la
@@ -20,7 +21,7 @@ class OracleRankOps:
 
     def local_restrict(self, r):
         zf = np.zeros_like(r)
-        rc = np.zeros(self.rp.coarse_hi - self.rp.coarse_lo)
+        rc = np.zeros((self.rp.coarse_hi - self.rp.coarse_lo,) + r.shape[1:])
         for i, a, b, c0, c1 in self.subs:
             zf[a:b] = la.cho_solve(self.o.local_chol[i], r[a:b])
             rc[c0 - self.rp.coarse_lo:c1 - self.rp.coarse_lo] = self.o.Psis[i].T @ r[a:b]
@@ -36,7 +37,7 @@ class OracleRankOps:
         return z
 
     def dot(self, a, b):
-        return float(a @ b)
+        return float(a @ b) if a.ndim == 1 else np.einsum("ij,ij->j", a, b)
 
     def axpy(self, alpha, x, y):
         return y + alpha * x
@@ -44,8 +45,8 @@ class OracleRankOps:
     def copy(self, x):
         return np.array(x, dtype=np.float64, copy=True)
 
-    def zeros(self, n):
-        return np.zeros(n)
+    def zeros_like(self, x):
+        return np.zeros_like(x)
 
     def gather(self, x, idx):
         return np.asarray(x)[idx]

@@ -121,6 +121,74 @@ def test_sharded_iterates_equal_single_rank(case, world, flexible):
         assert c["allgather"] == 1 + ref.iters
 
 
+def _block_rhs(w):
+    """Four right-hand sides as columns: the workload's, a zero column, a
+    seeded N(0,1) one and the first scaled by 1e-3 (its own stop, the same
+    step lengths)."""
+    g = np.random.default_rng(5).standard_normal(w.n)
+    return np.column_stack([w.rhs[0], np.zeros(w.n), g, 1e-3 * w.rhs[0]])
+
+
+def _block_worker(rank, world, port, case, flexible, out):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2606_04864_gb300.sharded import TorchComm, sharded_pcg
+        from tests.sharded_oracle_ops import OracleRankOps
+        w = CASES[case]()
+        o, plan = _plan(w, world)
+        rp = plan.ranks[rank]
+        F = _block_rhs(w)[plan.perm[rp.row_lo:rp.row_hi]]
+        res = sharded_pcg(plan, rank, OracleRankOps(o, plan, rank), TorchComm(rp, world), F,
+                          rtol=1e-10, flexible=flexible)
+        out[rank] = (np.asarray(res.x), list(res.iters), res.alphas, res.betas, res.collectives)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("flexible", [False, True])
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_block_of_rhs_equals_single_rank_per_column(world, flexible):
+    """Several right-hand sides on shared exchanges: every column takes the
+    single-rank oracle solve's iteration count, step lengths and solution
+    (the zero column none), and an iteration still has one halo exchange,
+    two all-reduces and one all-gather, however many columns are active."""
+    from oracle import OracleAMS, csr_to_scipy, pcg
+    case = "3d"
+    w = CASES[case]()
+    A = csr_to_scipy(w.rowptr, w.colind, w.vals)
+    o = OracleAMS(A, w.part, w.nparts, w.m)
+    F = _block_rhs(w)
+    refs = [pcg(A, F[:, c], o.apply, rtol=1e-10, flexible=flexible) for c in range(F.shape[1])]
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = 20000 + (os.getpid() * 13 + world * 151 + (7 if flexible else 0)) % 20000
+    procs = [ctx.Process(target=_block_worker, args=(r, world, port, case, flexible, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    X = np.concatenate([out[r][0] for r in range(world)])
+    U = np.empty_like(X)
+    U[o.perm] = X
+    its = max(ref.iters for ref in refs)
+    assert refs[1].iters == 0 and refs[0].iters == refs[3].iters
+    for r in range(world):
+        assert out[r][1] == [ref.iters for ref in refs]
+        c = out[r][4]
+        assert c["halo"] == its and c["allreduce"] == 2 + 2 * its and c["allgather"] == 1 + its
+        for col, ref in enumerate(refs):
+            assert np.allclose(out[r][2][col], ref.alphas, rtol=1e-12, atol=0)
+            assert np.allclose(out[r][3][col], ref.betas, rtol=1e-10, atol=1e-14)
+    for col, ref in enumerate(refs):
+        assert np.linalg.norm(U[:, col] - ref.u) <= 1e-12 * max(np.linalg.norm(ref.u), 1e-300)
+    assert not U[:, 1].any()
+
+
 def _failure_worker(rank, world, port, mode, out):
     """Rank 1 leaves the solve in one of three ways; rank 0 solves and
     reports how its solve ended.  Every exchange runs in a group with a
