@@ -195,9 +195,11 @@ class TorchComm:
         return self.torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64))
 
     def _run(self, exchange: str, fn):
+        """Run the transfers of one exchange (fn holds nothing else: the
+        backends report a lost peer and a timeout as plain RuntimeError)."""
         try:
             return fn()
-        except RuntimeError as e:   # torch's backend errors derive from RuntimeError
+        except RuntimeError as e:
             raise RankFailure(exchange, self.plan.rank, e) from e
 
     def allreduce(self, values) -> np.ndarray:
@@ -210,15 +212,12 @@ class TorchComm:
         pl = self.plan
         cols = np.shape(p_owned)[1:]
         out = np.zeros((len(pl.ghost),) + cols)
-        bufs = {}
+        sends = {q: self._t(np.asarray(p_owned)[rows]) for q, rows in pl.send.items()}
+        bufs = {q: self.torch.empty((len(pos),) + cols, dtype=self.torch.float64) for q, pos in pl.recv.items()}
 
-        def exchange():
-            reqs = []
-            for q, rows in pl.send.items():
-                reqs.append(self.dist.isend(self._t(np.asarray(p_owned)[rows]), dst=q, group=self.group))
-            for q, pos in pl.recv.items():
-                bufs[q] = self.torch.empty((len(pos),) + cols, dtype=self.torch.float64)
-                reqs.append(self.dist.irecv(bufs[q], src=q, group=self.group))
+        def exchange():   # only the transfers: what fails here is the exchange
+            reqs = [self.dist.isend(s, dst=q, group=self.group) for q, s in sends.items()]
+            reqs += [self.dist.irecv(b, src=q, group=self.group) for q, b in bufs.items()]
             for rq in reqs:
                 rq.wait()
 
