@@ -248,3 +248,23 @@ def test_mutation_bf16_rounding(monkeypatch, kind):
     import oracle.ams_oracle as OA
     monkeypatch.setattr(OA, "round_basis", bad)
     _expect_some_pin_fails(_bf16_pins())
+
+
+@pytest.mark.parametrize("mistake", ["residual_sign", "stop_relative_to_r0"])
+def test_mutation_initial_guess(monkeypatch, mistake):
+    """CG from x_0 with r_0 = f + A x_0, or with the stop taken relative to
+    ||r_0|| instead of ||f||, must fail the initial-guess pin."""
+    orig = O.pcg
+
+    def bad(A, f, Minv, rtol=1e-8, maxit=10000, flexible=False, x0=None):
+        if x0 is None:
+            return orig(A, f, Minv, rtol, maxit, flexible)
+        f = np.asarray(f, dtype=np.float64)
+        nf = np.linalg.norm(f)
+        if mistake == "residual_sign":       # (f + 2 A x_0) - A x_0 = f + A x_0
+            return orig(A, f + 2.0 * (A @ x0), Minv, rtol, maxit, flexible, x0=x0)
+        r0 = np.linalg.norm(f - A @ x0)
+        return orig(A, f, Minv, rtol * r0 / nf if nf > 0 else rtol, maxit, flexible, x0=x0)
+
+    _patch(monkeypatch, "pcg", bad)
+    _expect_some_pin_fails([P.test_pcg_from_an_initial_guess])
