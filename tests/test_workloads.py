@@ -66,3 +66,23 @@ def test_channel_field_rectangles_are_axis_aligned_and_sized():
         assert 1 <= short <= 4 and long_ <= 512
         if ys.max() < 599 and xs.max() < 599:        # not clipped
             assert 2 <= short <= 4 and 64 <= long_ <= 512
+
+
+def test_batch_of_uneven_systems_recipe():
+    """The batch generator's draws, on small side ranges: 24 2-D and 24 3-D
+    systems, sides, log-std and m inside their ranges, 8 N(0,1) right-hand
+    sides each, 8^d blocks with partial blocks at the far edges."""
+    from workloads.darcy import make_batch48_uneven
+    ws = make_batch48_uneven(lo2=16, hi2=24, lo3=8, hi3=12)
+    assert len(ws) == 48
+    for i, w in enumerate(ws):
+        d = 3 if i >= 24 else 2
+        side = w.shape[0]
+        assert len(w.shape) == d and all(s == side for s in w.shape)
+        assert (8 <= side <= 12) if d == 3 else (16 <= side <= 24)
+        assert 2.0 - 1e-12 <= w.logk.std() <= 3.0 + 1e-12
+        assert 4 <= w.m <= 8 and w.nrhs == 8
+        assert w.nparts == ((side + 7) // 8) ** d
+        assert abs(w.rhs.mean()) < 0.2 and 0.8 < w.rhs.std() < 1.2
+    assert len({w.shape[0] for w in ws}) > 4          # uneven sizes
+    assert len({w.m for w in ws}) > 1
