@@ -187,8 +187,9 @@ ams_status ams_setup(int64_t n, const int64_t* rowptr, const int32_t* colind,
  * (Section 3.1; the paper's experiments use METIS, Section 5); this
  * built-in one is a multilevel recursive bisection of the pattern's graph
  * (heavy-edge matching, region growing on the coarsest graph,
- * Fiduccia-Mattheyses refinement on every level) for callers with no
- * partitioner of their own.  Host code only: no GPU, no CUDA context.
+ * Fiduccia-Mattheyses refinement on every level, the best of three
+ * bisections per split, a greedy k-way pass at the end) for callers with
+ * no partitioner of their own.  Host code only: no GPU, no CUDA context.
  *
  *  n, rowptr, colind  CSR pattern as for ams_setup (host memory); diagonal
  *                     entries are ignored and the pattern is symmetrised

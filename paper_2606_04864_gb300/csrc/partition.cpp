@@ -337,6 +337,21 @@ std::vector<uint8_t> initial_split(const Graph& g, const Balance& bal, Rng& rng)
     return best;
 }
 
+// Target and largest admissible weight of each side of a split of h into
+// fractions frac0 : 1-frac0, each side at most ub times its share.
+Balance split_bounds(const Graph& h, double frac0, double ub) {
+    Balance b;
+    const int64_t maxv = *std::max_element(h.vw.begin(), h.vw.end());
+    b.target[0] = frac0 * (double)h.total;
+    b.target[1] = (double)h.total - b.target[0];
+    for (int s = 0; s < 2; ++s) {
+        b.maxw[s] = std::max(ub * b.target[s], std::ceil(b.target[s]));
+        // coarse vertices are heavy: allow one of them above the bound
+        if (maxv > 1) b.maxw[s] = std::max(b.maxw[s], b.target[s] + (double)maxv);
+    }
+    return b;
+}
+
 // Multilevel bisection of g into sides of weight fractions frac0 : 1-frac0,
 // each side at most ub times its share (and never below the next integer).
 std::vector<uint8_t> bisect(const Graph& g, double frac0, double ub, Rng& rng) {
@@ -353,18 +368,7 @@ std::vector<uint8_t> bisect(const Graph& g, double frac0, double ub, Rng& rng) {
         levels.push_back(std::move(c));
         cur = levels.back().get();
     }
-    auto bounds = [&](const Graph& h) {
-        Balance b;
-        const int64_t maxv = *std::max_element(h.vw.begin(), h.vw.end());
-        b.target[0] = frac0 * (double)h.total;
-        b.target[1] = (double)h.total - b.target[0];
-        for (int s = 0; s < 2; ++s) {
-            b.maxw[s] = std::max(ub * b.target[s], std::ceil(b.target[s]));
-            // coarse vertices are heavy: allow one of them above the bound
-            if (maxv > 1) b.maxw[s] = std::max(b.maxw[s], b.target[s] + (double)maxv);
-        }
-        return b;
-    };
+    auto bounds = [&](const Graph& h) { return split_bounds(h, frac0, ub); };
     std::vector<uint8_t> side = initial_split(*cur, bounds(*cur), rng);
     for (int l = (int)levels.size() - 1; l >= 0; --l) {
         const Graph& fine = l == 0 ? g : *levels[l - 1];
@@ -440,6 +444,8 @@ struct RecurseCtx {
     std::atomic<bool> failed;   // a split on another thread threw
 };
 constexpr int32_t kParallelMin = 20000;
+constexpr int kBisectTries = 3;      // bisections tried per split ...
+constexpr int32_t kTryMin = 64;      // ... of graphs with at least this many vertices
 
 void recurse(const Graph& g, const std::vector<int32_t>& ids, int32_t k, int32_t part0, RecurseCtx& C) {
     if (k == 1) {
@@ -448,7 +454,28 @@ void recurse(const Graph& g, const std::vector<int32_t>& ids, int32_t k, int32_t
     }
     const int32_t k0 = k / 2, k1 = k - k0;
     Rng rng{C.seed ^ (0x9E3779B97F4A7C15ull * (uint64_t)(part0 + 1)) ^ ((uint64_t)k << 40)};
-    std::vector<uint8_t> side = bisect(g, (double)k0 / k, C.ub, rng);
+    // several multilevel bisections from the same generator, the best kept
+    // (balance first, then cut)
+    std::vector<uint8_t> side;
+    {
+        const double frac0 = (double)k0 / k;
+        const Balance bal = split_bounds(g, frac0, C.ub);
+        double best_exc = 0.0;
+        int64_t best_cut = 0;
+        const int tries = g.n >= kTryMin ? kBisectTries : 1;
+        for (int t = 0; t < tries; ++t) {
+            std::vector<uint8_t> s = bisect(g, frac0, C.ub, rng);
+            int64_t w[2] = {0, 0};
+            for (int32_t v = 0; v < g.n; ++v) w[s[v]] += g.vw[v];
+            const double exc = excess(w, bal);
+            const int64_t cut = cut_of(g, s);
+            if (t == 0 || exc < best_exc || (exc == best_exc && cut < best_cut)) {
+                side.swap(s);
+                best_exc = exc;
+                best_cut = cut;
+            }
+        }
+    }
     ensure_counts(g, side, k0, k1);
     std::vector<int32_t> ids0, ids1;
     Graph h0 = induced(g, side, 0, ids0);

@@ -67,7 +67,7 @@ def test_grid_2d_cut_balance_and_reported_cut(partition):
     part, cut = partition(rp, ci, 16)
     _check_valid(part, 64 * 64, 16)
     assert cut == _cut(rp, ci, part)
-    assert cut <= 1.25 * 384
+    assert cut <= 1.10 * 384
 
 
 def test_grid_3d_cut(partition):
@@ -77,7 +77,7 @@ def test_grid_3d_cut(partition):
     part, cut = partition(rp, ci, 8)
     _check_valid(part, 16 ** 3, 8)
     assert cut == _cut(rp, ci, part)
-    assert cut <= 1.3 * 768
+    assert cut <= 1.05 * 768
 
 
 @pytest.mark.parametrize("n,k,edges,best", [
