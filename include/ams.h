@@ -224,7 +224,10 @@ typedef struct {
 /*
  * ams_setup_batched — one handle over nsys independent systems of uneven
  * size, solved together (one launch sequence per iteration covers every
- * system and right-hand side; each system converges on its own).
+ * system and right-hand side; each system converges on its own).  Each
+ * system gets the preconditioner ams_setup builds (Sections 3.1-3.2) from
+ * its own matrix, partition and m; the paper has no batched solve.  Errors
+ * as for ams_setup, for the first system that fails.
  * Vectors passed to ams_solve on such a handle are the systems' n_s x nrhs
  * column-major blocks laid end to end in system order; iters/relres
  * have nsys*nrhs entries (system-major).
@@ -234,10 +237,14 @@ ams_status ams_setup_batched(int32_t nsys, const ams_system_desc* systems,
                              ams_handle* out);
 
 /*
- * ams_solve — preconditioned CG (flexible CG per the handle's options) from
- * u_0 = 0 (or from u with ams_options.warm_start) for nrhs right-hand sides
- * at once.  Each right-hand side stops at the first k >= 0 with
- * ||r_k||_2 <= rtol ||f||_2 on the recurrence residual.
+ * ams_solve — A u = f (Eq. matrix-form) by preconditioned CG (flexible CG
+ * per the handle's options) with the two-level preconditioner of Section
+ * 3.1 (or the cycle of Section 3.2), from u_0 = 0 (or from u with
+ * ams_options.warm_start) for nrhs right-hand sides at once.  The paper
+ * runs GMRES to 1e-6 (Section 5); CG is used here because A and the
+ * preconditioner are SPD.  Each right-hand side stops at the first k >= 0
+ * with ||r_k||_2 <= rtol ||f||_2 on the recurrence residual.  Pointers are
+ * host or device per ams_options.device_ptrs, owned by the caller.
  *
  *  f        n x nrhs right-hand sides (read only)
  *  nrhs     1 <= nrhs <= 32
@@ -256,9 +263,10 @@ ams_status ams_solve(ams_handle h, const double* f, int32_t nrhs, double rtol,
                      double* u, int32_t* iters, double* relres);
 
 /*
- * ams_solve_adjoint — backward pass of u = A^{-1} f for a loss L(u).
- * Solves A lambda = g with the same preconditioner (A is symmetric), then
- * forms the sampled outer product on A's pattern:
+ * ams_solve_adjoint — backward pass of u = A^{-1} f (Eq. matrix-form) for a
+ * loss L(u); the paper has no adjoint, this is the adjoint of a linear
+ * solve.  Solves A lambda = g with the same preconditioner (Section 3.1;
+ * A is symmetric), then forms the sampled outer product on A's pattern:
  *
  *   dvals[e] = - sum_k lambda_k[row_e] * u_k[col_e]     (dL/dA, CSR order)
  *   lambda   = dL/df
@@ -329,6 +337,8 @@ typedef struct {
                                     per multiply-add) */
 } ams_info;
 
+/* Sizes, timings and launch counts of a handle (host output; the paper's
+ * setup/solve split of Section 5 is setup_seconds against the solves). */
 ams_status ams_get_info(ams_handle h, ams_info* info);
 
 /*
@@ -400,12 +410,15 @@ ams_status ams_get_coarse_factor_inverse(ams_handle h, int64_t* nd_paper, double
 
 /*
  * One application z = M^{-1} r of the two-level preconditioner (n x nrhs,
- * caller's order), in the handle's precision.
+ * caller's order), in the handle's precision: M^{-1} = sum_i R_i^T A_i^{-1}
+ * R_i + R_0^T A_0^{-1} R_0 (Section 3.1), or with two_grid_omega the cycle
+ * of Section 3.2.  Pointers per ams_options.device_ptrs.
  */
 ams_status ams_apply_preconditioner(ams_handle h, const double* r,
                                     int32_t nrhs, double* z);
 
-/* y = A x with the handle's stored matrix (n x nrhs, caller's order). */
+/* y = A x with the handle's stored matrix A of Eq. matrix-form (n x nrhs,
+ * caller's order; pointers per ams_options.device_ptrs). */
 ams_status ams_spmv(ams_handle h, const double* x, int32_t nrhs, double* y);
 
 /*
