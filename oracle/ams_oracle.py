@@ -50,6 +50,13 @@ Readings where the paper is silent (each is listed in the design notes):
   smoother before and after the correction (so the cycle is symmetric),
   omega given by the caller (the cycle is SPD when
   0 < omega < 2 / lambda_max(sum_i R_i^T A_i^{-1} R_i A)).
+
+Pins: every function here is checked against something other than itself
+(closed forms, brute force on small inputs, library routines in the cases
+the method reduces to them, the paper's lemmas and theorems, hand-worked
+bfloat16 values) in tests/test_oracle_pins.py, and planted mistakes in
+tests/test_oracle_mutations.py must fail those pins; no function is parity
+unpinned.
 """
 
 from __future__ import annotations
