@@ -54,7 +54,7 @@ typedef enum {
     AMS_ERR_BREAKDOWN = 3,       /* p^T A p <= 0, r^T M^{-1} r <= 0 or a non-finite scalar in CG */
     AMS_ERR_NOT_CONVERGED = 4,   /* maxit reached; outputs hold the last iterate */
     AMS_ERR_DEVICE_TIMEOUT = 5,  /* a bounded device-side wait ran out */
-    AMS_ERR_CUDA = 6,            /* a CUDA runtime or cuSOLVER call failed */
+    AMS_ERR_CUDA = 6,            /* a CUDA runtime call failed, or a checking-build index check fired */
     AMS_ERR_OOM = 7              /* device allocation failed */
 } ams_status;
 
