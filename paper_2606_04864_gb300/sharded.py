@@ -54,6 +54,7 @@ class RankPlan:
     rowptr: Optional[np.ndarray] = None        # owned rows of A, internal order,
     colind: Optional[np.ndarray] = None        # columns: local owned index, then n_owned + ghost position
     vals: Optional[np.ndarray] = None
+    entry: Optional[np.ndarray] = None         # caller CSR entry of each of those entries
 
     @property
     def n_owned(self) -> int:
@@ -134,7 +135,7 @@ def make_plan(rowptr, colind, vals, part, nparts: int, m_i, world: int) -> Shard
         lrp[1:] = np.cumsum(cnt)
         rp = RankPlan(rank=r, sub_lo=int(slo[r]), sub_hi=int(slo[r + 1]), row_lo=a, row_hi=b,
                       coarse_lo=int(coarse_ptr[slo[r]]), coarse_hi=int(coarse_ptr[slo[r + 1]]),
-                      ghost=ghost, rowptr=lrp, colind=local, vals=vals[src])
+                      ghost=ghost, rowptr=lrp, colind=local, vals=vals[src], entry=src)
         gown = owner[ghost]
         for q in np.unique(gown):
             rp.recv[int(q)] = np.flatnonzero(gown == q)
@@ -159,6 +160,7 @@ class RankOps(Protocol):
     def local_restrict(self, r_owned): ...                # (z_f, r_c of the owned subdomains)
     def coarse_solve(self, rc_full): ...                  # e_c = A_0^{-1} r_c (replicated)
     def prolong(self, zf_owned, ec_full): ...             # z = z_f + R_0^T e_c on the owned rows
+    def sddmm(self, lam_owned, u_owned, u_ghost): ...     # -sum_k lam_k[row_e] u_k[col_e] per owned entry
     def dot(self, a, b): ...                              # a.b: a float, or one per column
     def axpy(self, alpha, x, y): ...                      # y + alpha x (alpha: float, or one per column)
     def copy(self, x): ...
@@ -331,3 +333,18 @@ def sharded_pcg(plan: ShardPlan, rank: int, ops: RankOps, comm, f_owned, rtol: f
         p = ops.axpy(coef(beta), p, z)
     iters[active] = k
     return result(x, iters, rr, fn2, alphas, betas)
+
+
+def sharded_adjoint(plan: ShardPlan, rank: int, ops: RankOps, comm, g_owned, u_owned, rtol: float = 1e-8,
+                    maxit: int = 10000):
+    """Adjoint of u = A^{-1} f for a loss L(u) with dL/du = g, on one rank's
+    block: lambda = A^{-1} g by the sharded PCG (A is symmetric, so the same
+    preconditioner serves), one more halo exchange (the ghost entries of u),
+    then dL/dA on the rank's own rows, dvals[e] = -sum_k lambda_k[row_e]
+    u_k[col_e], in the rank's entry order (``plan.ranks[rank].entry`` maps
+    each to the caller's CSR entry); dL/df = lambda.  Returns (lambda owned
+    rows, dvals, the PCG result)."""
+    res = sharded_pcg(plan, rank, ops, comm, g_owned, rtol=rtol, maxit=maxit)
+    res.collectives["halo"] += 1
+    u_ghost = comm.halo(u_owned)
+    return res.x, ops.sddmm(res.x, u_owned, u_ghost), res

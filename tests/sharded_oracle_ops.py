@@ -36,6 +36,12 @@ class OracleRankOps:
             z[a:b] += self.o.Psis[i] @ ec_full[c0:c1]
         return z
 
+    def sddmm(self, lam, u_owned, u_ghost):
+        uext = np.concatenate([u_owned, u_ghost])
+        rows = np.repeat(np.arange(self.rp.n_owned), np.diff(self.rp.rowptr))
+        prod = lam[rows] * uext[self.rp.colind]
+        return -(prod if prod.ndim == 1 else prod.sum(axis=1))
+
     def dot(self, a, b):
         return float(a @ b) if a.ndim == 1 else np.einsum("ij,ij->j", a, b)
 

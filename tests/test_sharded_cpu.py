@@ -5,7 +5,8 @@ equal the single-rank solve's (the oracle's PCG and flexible CG) to 1e-12
 at world sizes 2 and 4; the plan's ghost, send and receive lists are
 checked by brute force.  A lost peer (one that exits, never joins an
 exchange, or leaves between iterations) ends the other ranks' solve with
-RankFailure at the exchange that could not complete."""
+RankFailure at the exchange that could not complete.  The sharded adjoint
+(lambda on every rank, dL/dA on its entries) equals the oracle's."""
 
 import os
 import sys
@@ -63,6 +64,11 @@ def test_plan_ranges_ghosts_and_exchange_lists(case, world):
             src = plan.ranks[q]
             assert ((rp.ghost[pos] >= src.row_lo) & (rp.ghost[pos] < src.row_hi)).all()
             assert np.array_equal(src.send[rp.rank] + src.row_lo, rp.ghost[pos])
+    # every caller CSR entry sits on exactly one rank, with its value
+    ent = np.concatenate([rp.entry for rp in plan.ranks])
+    assert np.array_equal(np.sort(ent), np.arange(w.nnz))
+    for rp in plan.ranks:
+        assert np.array_equal(rp.vals, w.vals[rp.entry])
     # coarse blocks are contiguous and cover N_c in rank order
     assert plan.ranks[0].coarse_lo == 0 and plan.ranks[-1].coarse_hi == o.Nc
     for a, b in zip(plan.ranks[:-1], plan.ranks[1:]):
@@ -187,6 +193,81 @@ def test_sharded_block_of_rhs_equals_single_rank_per_column(world, flexible):
     for col, ref in enumerate(refs):
         assert np.linalg.norm(U[:, col] - ref.u) <= 1e-12 * max(np.linalg.norm(ref.u), 1e-300)
     assert not U[:, 1].any()
+
+
+def _adjoint_inputs(w, A, o, ncols):
+    """The forward solutions u (oracle CG to 1e-12) of the workload's
+    right-hand side and of a seeded N(0,1) one, and seeded loss gradients g,
+    as columns."""
+    from oracle import pcg
+    rng = np.random.default_rng(9)
+    F = np.column_stack([w.rhs[0], rng.standard_normal(w.n)])[:, :ncols]
+    U = np.column_stack([pcg(A, F[:, k], o.apply, rtol=1e-12).u for k in range(ncols)])
+    G = rng.standard_normal((w.n, ncols))
+    return U, G
+
+
+def _adjoint_worker(rank, world, port, ncols, out):
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import csr_to_scipy
+        from paper_2606_04864_gb300.sharded import TorchComm, sharded_adjoint
+        from tests.sharded_oracle_ops import OracleRankOps
+        w = CASES["2d"]()
+        o, plan = _plan(w, world)
+        U, G = _adjoint_inputs(w, csr_to_scipy(w.rowptr, w.colind, w.vals), o, ncols)
+        rp = plan.ranks[rank]
+        rows = plan.perm[rp.row_lo:rp.row_hi]
+        g, u = (G[rows, 0], U[rows, 0]) if ncols == 1 else (G[rows], U[rows])
+        lam, dvals, res = sharded_adjoint(plan, rank, OracleRankOps(o, plan, rank), TorchComm(rp, world), g, u,
+                                          rtol=1e-10)
+        out[rank] = (np.asarray(lam), np.asarray(dvals), res.iters, res.collectives)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("ncols", [1, 2])
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_adjoint_matches_oracle_gradient(world, ncols):
+    """The sharded adjoint: lambda on every rank's rows and dL/dA on its
+    entries, mapped back to the caller's CSR entries by the plan, equal the
+    oracle's adjoint (summed over the columns) to 1e-10; one halo exchange
+    more than the solve."""
+    from oracle import OracleAMS, adjoint_gradient, csr_to_scipy
+    w = CASES["2d"]()
+    A = csr_to_scipy(w.rowptr, w.colind, w.vals)
+    o = OracleAMS(A, w.part, w.nparts, w.m)
+    U, G = _adjoint_inputs(w, A, o, ncols)
+    refs = [adjoint_gradient(A, U[:, k], G[:, k], o.apply, rtol=1e-10) for k in range(ncols)]
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    port = 20000 + (os.getpid() * 17 + world * 173 + ncols * 29) % 20000
+    procs = [ctx.Process(target=_adjoint_worker, args=(r, world, port, ncols, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(300)
+        assert p.exitcode == 0
+    _, plan = _plan(w, world)
+    dv = np.full(w.nnz, np.nan)
+    for r in range(world):
+        rp = plan.ranks[r]
+        lam, dvals, iters, coll = out[r]
+        rows = plan.perm[rp.row_lo:rp.row_hi]
+        for k, ref in enumerate(refs):
+            lk = lam if ncols == 1 else lam[:, k]
+            assert np.linalg.norm(lk - ref[0][rows]) <= 1e-10 * np.linalg.norm(ref[0][rows])
+            assert (iters if ncols == 1 else iters[k]) == ref[2].iters
+        its = max(ref[2].iters for ref in refs)
+        assert coll["halo"] == its + 1
+        dv[rp.entry] = dvals
+    expect = sum(ref[1] for ref in refs)
+    assert not np.isnan(dv).any()          # every caller entry belongs to exactly one rank
+    assert np.linalg.norm(dv - expect) <= 1e-10 * np.linalg.norm(expect)
 
 
 def _failure_worker(rank, world, port, mode, out):
